@@ -1,0 +1,649 @@
+"""Plain FP64 CPU oracle: Projective Dynamics cloth time step with dry frictional
+(Signorini-Coulomb) contact, and its adjoint (DiffCloth, arXiv 2106.05306).
+
+TEST INFRASTRUCTURE.  Only tests/, ``__graft_entry__.smoke()`` and bench.py's
+CPU-baseline / reference arm import this package.  The CUDA library and its
+Python binding never import it, and it imports nothing from them: it shares only
+the seeded input generators in ``scenes``.
+
+It is deliberately slow and literal: numpy/scipy, float64, natural node order,
+a banded Cholesky of the PD matrix (a different algorithm from the CUDA path's
+nested-dissection factor), and a direct sparse LU of the full adjoint KKT
+system (the paper treats the direct solve as the ground-truth gradient, Sec. 5.3).
+
+Paper passages followed (section / equation labels of the paper):
+  * Sec. 3.1, Eq. implicit_x / implicit_v / implicit_energy: implicit Euler and
+    its energy form with y = x_n + h v_n + h^2 M^-1 f_ext.
+  * Sec. 3.1, Eq. pd_project / pd_energy / pd_global: PD energies
+    W_i = w_i/2 |A_i x - p_i|^2, local projections, and the global system
+    P x = M y + h^2 sum w_i A_i^T p_i with constant P = M + h^2 sum w_i A_i^T A_i.
+  * Sec. 3.2, Eq. contact_all / implicit_with_contact / pd_velocity /
+    pd_velocity_with_contact / ly_et_al_govrningEq: Signorini-Coulomb law and
+    the velocity-form global step with the contact impulse h J^T r.
+  * Sec. 4.1-4.2, Eq. adjoint / adjoint_pd / adjoint_vv / adjoint_v /
+    ppr_adjoint, and "Extensions" (curved obstacles): the adjoint.
+
+Readings of passages the paper leaves open (each also listed in the design doc):
+  R1 stretch: A_t maps a triangle to its deformation gradient F = X G (3x2),
+     w_t = k_stretch * rest area, projection onto matrices with orthonormal
+     columns (the polar factor of F).
+  R2 bending: A_b is the cotangent Laplacian row of vertex b divided by its
+     barycentric area, w_b = k_bend * area, projection onto the sphere of radius
+     s_b = |A_b x_rest| (p_b = 0 where the rest shape is flat, s_b = 0).
+  R3 lumped mass rho * (1/3 of incident rest area), f_ext = M g, pins are
+     Dirichlet (velocity 0, removed from the global system).
+  R4 contact set: free nodes whose predicted position x_n + h v_n lies within
+     delta of an obstacle (closest obstacle wins, lowest index on ties); normal
+     and signed distance are taken at x_n; the Signorini-Coulomb law is imposed
+     on the biased normal velocity u_N = n.v + phi(x_n)/h.
+  R5 contact iteration: every PD iteration runs local step, global step with
+     the previous contact impulse, then an exact per-node closed-form
+     Signorini-Coulomb solve with compliance c_j = h * (P^-1 1_I)_j (the row sum
+     of the contact block of h P^-1, a Gershgorin bound on the coupling).  The
+     printed M-splitting (Eq. ly_et_al_govrningEq) diverges for the stiffness
+     values used here; any positive compliance has the same fixed point.
+  R7 contact adjoint: the exact linearisation of the converged step, solved as
+     one KKT system; stick nodes constrain z_j = 0, slip nodes constrain
+     (n - mu t).z_j = 0 (oblique), and the slip friction direction adds
+     h mu f_N b b^T / |u_T| to the matrix (the paper's -Delta R).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+TAKEOFF, STICK, SLIP = 0, 1, 2
+
+# ----------------------------------------------------------------------------
+# Rest-shape operators (readings R1, R2, R3)
+# ----------------------------------------------------------------------------
+
+# Vertex-to-edge matrix: F = X @ E @ Dm^-1 with X the 3x3 matrix of vertex positions.
+_E = np.array([[-1.0, -1.0], [1.0, 0.0], [0.0, 1.0]])
+
+
+def triangle_rest(rest, tris):
+    """Per triangle: G = E Dm^-1 (3x2, so F = sum_a x_a G[a,:]) and rest area (R1)."""
+    X0, X1, X2 = rest[tris[:, 0]], rest[tris[:, 1]], rest[tris[:, 2]]
+    e1, e2 = X1 - X0, X2 - X0
+    cr = np.cross(e1, e2)
+    area = 0.5 * np.linalg.norm(cr, axis=1)
+    u = e1 / np.linalg.norm(e1, axis=1)[:, None]
+    nrm = cr / np.linalg.norm(cr, axis=1)[:, None]
+    w = np.cross(nrm, u)
+    Dm = np.zeros((len(tris), 2, 2))
+    Dm[:, 0, 0] = np.einsum("ij,ij->i", e1, u)
+    Dm[:, 0, 1] = np.einsum("ij,ij->i", e2, u)
+    Dm[:, 1, 0] = np.einsum("ij,ij->i", e1, w)
+    Dm[:, 1, 1] = np.einsum("ij,ij->i", e2, w)
+    G = np.einsum("ak,tkl->tal", _E, np.linalg.inv(Dm))
+    return G, area
+
+
+def cotan_laplacian(rest, tris, area):
+    """Bending operator rows l_b (R2): (A_b x) = sum_j l_bj x_j, as a sparse m x m matrix.
+
+    l_bj = c_bj / a_b for neighbours j, l_bb = -sum_j c_bj / a_b, where
+    c_bj = (cot alpha + cot beta)/2 over the triangles sharing edge bj and a_b is
+    one third of the rest area of the triangles around b.
+    """
+    m = rest.shape[0]
+    rows, cols, vals = [], [], []
+    for t in range(len(tris)):
+        for k in range(3):
+            o, i, j = tris[t, k], tris[t, (k + 1) % 3], tris[t, (k + 2) % 3]
+            a = rest[i] - rest[o]
+            b = rest[j] - rest[o]
+            cot = np.dot(a, b) / np.linalg.norm(np.cross(a, b))
+            rows += [i, j]
+            cols += [j, i]
+            vals += [0.5 * cot, 0.5 * cot]
+    Wc = sp.coo_matrix((vals, (rows, cols)), shape=(m, m)).tocsr()
+    abar = np.zeros(m)
+    np.add.at(abar, tris.reshape(-1), np.repeat(area / 3.0, 3))
+    deg = np.asarray(Wc.sum(axis=1)).ravel()
+    Lap = (Wc - sp.diags(deg)).tocsr()
+    Lb = sp.diags(1.0 / abar) @ Lap
+    return Lb.tocsr(), abar
+
+
+class Model:
+    """Rest data, parameters and the prefactorised PD matrix of one cloth."""
+
+    def __init__(self, rest_pos, tris, pins, obstacles, params):
+        self.rest = np.asarray(rest_pos, dtype=np.float64)
+        self.tris = np.asarray(tris, dtype=np.int64)
+        self.m = self.rest.shape[0]
+        self.pins = np.asarray(sorted(set(int(p) for p in pins)), dtype=np.int64)
+        is_pin = np.zeros(self.m, bool)
+        is_pin[self.pins] = True
+        self.is_pin = is_pin
+        self.free = np.nonzero(~is_pin)[0]
+        self.obstacles = list(obstacles)
+        self.params = params
+        self.h = float(params.h)
+        self.mu = float(params.mu)
+        self.k_s = float(params.k_stretch)
+        self.k_b = float(params.k_bend)
+        self.g = np.asarray(params.gravity, dtype=np.float64)
+        self.delta = float(params.contact_margin)
+
+        self.G, self.area = triangle_rest(self.rest, self.tris)
+        self.Lb, self.abar = cotan_laplacian(self.rest, self.tris, self.area)
+        # R3: lumped mass
+        self.mass = float(params.density) * self.abar
+        # R2: target curvature magnitudes; a flat rest shape gives s_b = 0.
+        q_rest = self.Lb @ self.rest
+        s = np.linalg.norm(q_rest, axis=1)
+        scale = (np.abs(self.Lb).sum(axis=1).A.ravel()
+                 * np.max(np.linalg.norm(self.rest - self.rest.mean(0), axis=1)))
+        s[s <= 1e-9 * scale] = 0.0
+        self.s_b = s
+        self.q_rest = q_rest
+        self.w_t = self.k_s * self.area
+        self.w_b = self.k_b * self.abar
+
+        # Eq. pd_global: P = M + h^2 sum_i w_i A_i^T A_i.  Every A_i is (K_i kron I3),
+        # so P = P_s kron I3 with a scalar m x m matrix P_s.
+        self.L = self._stiffness_scalar()
+        self.P = (sp.diags(self.mass) + self.h ** 2 * self.L).tocsr()
+        self.Pff = self.P[self.free][:, self.free].tocsr()
+        self._factor_banded()
+
+    # --- assembly of sum_i w_i A_i^T A_i (scalar) ---
+    def _stiffness_scalar(self):
+        m = self.m
+        T = len(self.tris)
+        GG = np.einsum("tak,tbk->tab", self.G, self.G) * self.w_t[:, None, None]
+        rows = np.repeat(self.tris, 3, axis=1).reshape(-1)
+        cols = np.tile(self.tris, (1, 3)).reshape(-1)
+        Ls = sp.coo_matrix((GG.reshape(-1), (rows, cols)), shape=(m, m)).tocsr()
+        Lb = self.Lb
+        Lbend = (Lb.T @ sp.diags(self.w_b) @ Lb).tocsr()
+        del T
+        return (Ls + Lbend).tocsr()
+
+    def _factor_banded(self):
+        """Banded Cholesky of P_ff in natural node order (upper band storage)."""
+        A = self.Pff.tocoo()
+        n = A.shape[0]
+        bw = int(np.max(np.abs(A.row - A.col))) if A.nnz else 0
+        ab = np.zeros((bw + 1, n))
+        up = A.col >= A.row
+        ab[bw + A.row[up] - A.col[up], A.col[up]] = A.data[up]
+        self.band = bw
+        self.chol = sla.cholesky_banded(ab, lower=False)
+
+    def solve_P(self, rhs_f):
+        """x = P_ff^-1 rhs on free nodes; rhs_f is (m_f,) or (m_f, k)."""
+        return sla.cho_solve_banded((self.chol, False), rhs_f)
+
+    # ------------------------------------------------------------------------
+    # Local step (Sec. 3.1): projections of A_i x onto M_i
+    # ------------------------------------------------------------------------
+    def deformation_gradients(self, x):
+        X = x[self.tris]                                 # (T, 3 vertices, 3 coords)
+        return np.einsum("tac,tak->tck", X, self.G)      # F[t] = sum_a x_a G[a,:]
+
+    def bending_vectors(self, x):
+        return self.Lb @ x                               # (m, 3): A_b x
+
+    def project(self, x):
+        """Local step: p_t = polar factor of F_t (R1); p_b = s_b q/|q| (R2)."""
+        F = self.deformation_gradients(x)
+        R, S = polar(F)
+        q = self.bending_vectors(x)
+        pb = project_bending(q, self.s_b, self.q_rest)
+        return R, pb, F, S, q
+
+    def AtWp(self, R, pb):
+        """sum_i w_i A_i^T p_i as an (m, 3) array."""
+        out = np.zeros((self.m, 3))
+        contrib = np.einsum("tck,tak->tac", R, self.G) * self.w_t[:, None, None]
+        np.add.at(out, self.tris.reshape(-1), contrib.reshape(-1, 3))
+        out += self.Lb.T @ (self.w_b[:, None] * pb)
+        return out
+
+    def energy_W(self, x):
+        """Sum of the PD surrogate energies at their projections (Eq. pd_energy)."""
+        R, pb, F, S, q = self.project(x)
+        return self.surrogate_W(x, R, pb)
+
+    def surrogate_W(self, x, R, pb):
+        F = self.deformation_gradients(x)
+        q = self.bending_vectors(x)
+        ws = 0.5 * np.sum(self.w_t * np.sum((F - R) ** 2, axis=(1, 2)))
+        wb = 0.5 * np.sum(self.w_b * np.sum((q - pb) ** 2, axis=1))
+        return ws + wb
+
+    def g_tilde(self, x, y, R, pb):
+        """Surrogate objective of the local/global solver (Sec. 3.1)."""
+        d = x - y
+        return 0.5 / self.h ** 2 * np.sum(self.mass[:, None] * d * d) + self.surrogate_W(x, R, pb)
+
+    # ------------------------------------------------------------------------
+    # Contact detection (R4)
+    # ------------------------------------------------------------------------
+    def detect(self, x_n, v_n):
+        """Contact list: (node, obstacle, normal n at x_n, beta = phi(x_n)/h)."""
+        xp = x_n + self.h * v_n
+        nodes, obs, normals, betas = [], [], [], []
+        for j in self.free:
+            best, best_o = np.inf, -1
+            for o, ob in enumerate(self.obstacles):
+                ph, _ = signed_distance(ob, xp[j])
+                if ph < best:
+                    best, best_o = ph, o
+            if best_o >= 0 and best <= self.delta:
+                ph0, n0 = signed_distance(self.obstacles[best_o], x_n[j])
+                nodes.append(j)
+                obs.append(best_o)
+                normals.append(n0)
+                betas.append(ph0 / self.h)
+        return Contacts(np.array(nodes, dtype=np.int64), np.array(obs, dtype=np.int64),
+                        np.array(normals).reshape(-1, 3), np.array(betas, dtype=np.float64))
+
+    def compliance(self, contacts):
+        """c_j = h (P^-1 1_I)_j for the current contact set (R5)."""
+        if len(contacts.nodes) == 0:
+            return np.zeros(0)
+        pos = np.searchsorted(self.free, contacts.nodes)
+        ind = np.zeros(len(self.free))
+        ind[pos] = 1.0
+        return self.h * self.solve_P(ind)[pos]
+
+
+class Contacts:
+    def __init__(self, nodes, obs, normals, betas):
+        self.nodes, self.obs, self.normals, self.betas = nodes, obs, normals, betas
+
+    def __len__(self):
+        return len(self.nodes)
+
+
+# ----------------------------------------------------------------------------
+# Projections
+# ----------------------------------------------------------------------------
+
+def polar(F):
+    """Polar factor R and stretch S of 3x2 matrices F = R S (R1).
+
+    S = sqrt(F^T F) in closed form for 2x2 SPD C: S = (C + sqrt(det C) I) /
+    sqrt(tr C + 2 sqrt(det C)), then R = F S^-1.
+    """
+    C = np.einsum("tck,tcl->tkl", F, F)
+    det = C[:, 0, 0] * C[:, 1, 1] - C[:, 0, 1] * C[:, 1, 0]
+    sd = np.sqrt(np.maximum(det, 0.0))
+    tr = C[:, 0, 0] + C[:, 1, 1]
+    t = np.sqrt(tr + 2.0 * sd)
+    S = (C + sd[:, None, None] * np.eye(2)) / t[:, None, None]
+    R = np.einsum("tck,tkl->tcl", F, np.linalg.inv(S))
+    return R, S
+
+
+def project_bending(q, s_b, q_rest):
+    """p_b = s_b q/|q| where s_b > 0, 0 where s_b = 0; q_rest if |q| collapses (R2)."""
+    nq = np.linalg.norm(q, axis=1)
+    pb = np.zeros_like(q)
+    on = s_b > 0
+    ok = on & (nq > 1e-14 * s_b)
+    pb[ok] = (s_b[ok] / nq[ok])[:, None] * q[ok]
+    tie = on & ~ok
+    pb[tie] = q_rest[tie]
+    return pb
+
+
+def polar_derivative(R, S, dF):
+    """dR for F = R S perturbed by dF (3x2): dR = R Om + (I - R R^T) dF S^-1 with
+    Om = w [[0,-1],[1,0]], w = ((R^T dF)_21 - (R^T dF)_12) / tr S."""
+    RtdF = R.T @ dF
+    w = (RtdF[1, 0] - RtdF[0, 1]) / np.trace(S)
+    Om = np.array([[0.0, -w], [w, 0.0]])
+    return R @ Om + (np.eye(3) - R @ R.T) @ dF @ np.linalg.inv(S)
+
+
+# ----------------------------------------------------------------------------
+# Obstacles (R4)
+# ----------------------------------------------------------------------------
+
+def signed_distance(ob, x):
+    """(phi, grad phi) of an analytic obstacle at point x."""
+    if ob.kind == "plane":
+        n = np.asarray(ob.normal, dtype=np.float64)
+        return float(np.dot(n, x) - ob.offset), n.copy()
+    if ob.kind == "sphere":
+        d = x - np.asarray(ob.center, dtype=np.float64)
+        r = np.linalg.norm(d)
+        return float(r - ob.radius), d / r
+    if ob.kind == "capsule":
+        a = np.asarray(ob.a, dtype=np.float64)
+        b = np.asarray(ob.b, dtype=np.float64)
+        ab = b - a
+        t = np.clip(np.dot(x - a, ab) / np.dot(ab, ab), 0.0, 1.0)
+        d = x - (a + t * ab)
+        r = np.linalg.norm(d)
+        return float(r - ob.radius), d / r
+    raise ValueError(ob.kind)
+
+
+def normal_jacobian(ob, x):
+    """d n / d x for the obstacle normal taken at x (3x3); zero for planes."""
+    if ob.kind == "plane":
+        return np.zeros((3, 3))
+    if ob.kind == "sphere":
+        d = x - np.asarray(ob.center, dtype=np.float64)
+        r = np.linalg.norm(d)
+        n = d / r
+        return (np.eye(3) - np.outer(n, n)) / r
+    if ob.kind == "capsule":
+        a = np.asarray(ob.a, dtype=np.float64)
+        b = np.asarray(ob.b, dtype=np.float64)
+        ab = b - a
+        t = np.dot(x - a, ab) / np.dot(ab, ab)
+        if t <= 0.0 or t >= 1.0:
+            c = a if t <= 0.0 else b
+            d = x - c
+            r = np.linalg.norm(d)
+            n = d / r
+            return (np.eye(3) - np.outer(n, n)) / r
+        e = ab / np.linalg.norm(ab)
+        d = x - (a + t * ab)
+        r = np.linalg.norm(d)
+        n = d / r
+        return (np.eye(3) - np.outer(n, n) - np.outer(e, e)) / r
+    raise ValueError(ob.kind)
+
+
+# ----------------------------------------------------------------------------
+# Per-node Signorini-Coulomb solve (Eq. contact_all), closed form (R5)
+# ----------------------------------------------------------------------------
+
+def signorini_coulomb(vt, n, beta, mu, c):
+    """Solve v = vt + c f with (f, u) satisfying Eq. contact_1-3 in world frame.
+
+    u_N = n.v + beta, u_T = v - (n.v) n.  Returns (f, v, case)."""
+    vn = float(np.dot(n, vt))
+    uN = vn + beta
+    if uN >= 0.0:                                     # take off: r = 0, u_N > 0
+        return np.zeros(3), vt.copy(), TAKEOFF
+    uT = vt - vn * n
+    nt = float(np.linalg.norm(uT))
+    if nt <= mu * (-uN):                              # stick: u = 0, |r_T| <= mu r_N
+        v = -beta * n
+        return (v - vt) / c, v, STICK
+    fN = -uN / c                                      # slip: u_N = 0, |r_T| = mu r_N
+    f = fN * n - (mu * fN / nt) * uT
+    return f, vt + c * f, SLIP
+
+
+# ----------------------------------------------------------------------------
+# One time step (Sec. 3.1-3.2)
+# ----------------------------------------------------------------------------
+
+class StepRecord:
+    """What the adjoint needs from a converged forward step."""
+
+    def __init__(self, x_n, v_n, x_np1, v_np1, contacts, forces, cases, c, iters):
+        self.x_n, self.v_n, self.x_np1, self.v_np1 = x_n, v_n, x_np1, v_np1
+        self.contacts, self.forces, self.cases, self.c, self.iters = contacts, forces, cases, c, iters
+
+
+def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace=None):
+    """One PD time step with dry frictional contact.
+
+    Fixed-iteration mode (n_iters): exactly that many local/global/contact
+    iterations (the method as run for timing and parity).  Tolerance mode
+    (tol): iterate until the max-norm change of v is below tol * max(|v|, 1e-3).
+    ``trace`` (a list) receives g~ after every local and every global step.
+    """
+    h = model.h
+    free = model.free
+    x_n = np.asarray(x_n, dtype=np.float64)
+    v_n = np.asarray(v_n, dtype=np.float64).copy()
+    v_n[model.pins] = 0.0
+    # Eq. implicit_energy: y = x_n + h v_n + h^2 M^-1 f_ext, f_ext = M g (R3)
+    y = x_n + h * v_n + h * h * model.g[None, :]
+    # b^(p) = (b(p) - P x_n)/h with b(p) = M y + h^2 sum w A^T p and P = M + h^2 sum w A^T A
+    # (Eq. pd_global, pd_velocity), expanded so that no O(h^2 |L x|) terms cancel:
+    #   b^(p) = M (y - x_n)/h + h sum_i w_i A_i^T (p_i - A_i x_n).
+    Mdy = model.mass[:, None] * (y - x_n) / h
+    F_n = model.deformation_gradients(x_n)
+    q_n = model.bending_vectors(x_n)
+    contacts = model.detect(x_n, v_n)                  # J_n from (x_n, v_n), Eq. implicit_with_contact
+    c = model.compliance(contacts)
+    nc = len(contacts)
+    f = np.zeros((nc, 3))
+    cases = np.zeros(nc, dtype=np.int64)
+    v = v_n.copy()
+    if n_iters is None and tol is None:
+        n_iters = model.params.n_pd_iters
+    limit = n_iters if n_iters is not None else max_iters
+    k = 0
+    while k < limit:
+        x = x_n + h * v
+        R, pb, _, _, _ = model.project(x)                          # local step
+        if trace is not None:
+            trace.append(model.g_tilde(x, y, R, pb))
+        bhat = Mdy + h * model.AtWp(R - F_n, pb - q_n)             # Eq. pd_global / pd_velocity
+        rhs = bhat.copy()
+        if nc:
+            rhs[contacts.nodes] += h * f                           # Eq. pd_velocity_with_contact
+        v_half = np.zeros_like(v)
+        v_half[free] = model.solve_P(rhs[free])                    # global step
+        if trace is not None:
+            trace.append(model.g_tilde(x_n + h * v_half, y, R, pb))
+        v_new = v_half
+        f_new = np.zeros_like(f)
+        for a in range(nc):                                        # per-node contact solve
+            j = contacts.nodes[a]
+            vt = v_half[j] - c[a] * f[a]
+            f_new[a], v_new[j], cases[a] = signorini_coulomb(
+                vt, contacts.normals[a], contacts.betas[a], model.mu, c[a])
+        dv = np.max(np.abs(v_new - v)) if v.size else 0.0
+        v, f = v_new, f_new
+        k += 1
+        if tol is not None and dv <= tol * max(np.max(np.abs(v)), 1e-3):
+            break
+    x_np1 = x_n + h * v
+    return x_np1, v, StepRecord(x_n, v_n, x_np1, v, contacts, f, cases, c, k)
+
+
+def rollout(model: Model, x0, v0, n_steps, n_iters=None, tol=None):
+    """Run n_steps; returns (xs, vs, records) with xs[0] = x0."""
+    xs, vs, recs = [np.asarray(x0, dtype=np.float64)], [np.asarray(v0, dtype=np.float64)], []
+    for _ in range(n_steps):
+        x1, v1, rec = step(model, xs[-1], vs[-1], n_iters=n_iters, tol=tol)
+        xs.append(x1)
+        vs.append(v1)
+        recs.append(rec)
+    return xs, vs, recs
+
+
+# ----------------------------------------------------------------------------
+# Adjoint (Sec. 4), reading R7
+# ----------------------------------------------------------------------------
+
+def _dof(nodes):
+    nodes = np.asarray(nodes)
+    return (3 * nodes[:, None] + np.arange(3)[None, :]).reshape(-1)
+
+
+def hessian_W(model: Model, x):
+    """grad^2 W(x) = sum_i w_i A_i^T (I - d p_i*/d(A_i x)) A_i as a 3m x 3m matrix (Sec. 4.1)."""
+    m = model.m
+    R, pb, F, S, q = model.project(x)
+    rows, cols, vals = [], [], []
+    T = len(model.tris)
+    # stretch: vec(F) index (c, k) -> 3*k + c; A_t[(c,k), (a,c')] = G[a,k] delta_cc'
+    for t in range(T):
+        A = np.zeros((6, 9))
+        for a in range(3):
+            for k in range(2):
+                for cc in range(3):
+                    A[3 * k + cc, 3 * a + cc] = model.G[t, a, k]
+        Jp = np.zeros((6, 6))
+        for e in range(6):
+            dF = np.zeros((3, 2))
+            dF[e % 3, e // 3] = 1.0
+            dR = polar_derivative(R[t], S[t], dF)
+            Jp[:, e] = dR.T.reshape(-1)          # column-major vec: index 3*k + c
+        Ht = model.w_t[t] * A.T @ (np.eye(6) - Jp) @ A
+        d = _dof(model.tris[t])
+        rows.append(np.repeat(d, 9))
+        cols.append(np.tile(d, 9))
+        vals.append(Ht.reshape(-1))
+    # bending: A_b = l_b kron I3
+    Lb = model.Lb.tocsr()
+    for b in range(m):
+        lo, hi = Lb.indptr[b], Lb.indptr[b + 1]
+        nb = Lb.indices[lo:hi]
+        lv = Lb.data[lo:hi]
+        if model.s_b[b] > 0:
+            nq = np.linalg.norm(q[b])
+            qh = q[b] / nq
+            Dp = model.s_b[b] * (np.eye(3) - np.outer(qh, qh)) / nq
+        else:
+            Dp = np.zeros((3, 3))
+        K = np.eye(3) - Dp
+        blk = model.w_b[b] * np.einsum("i,j,cd->icjd", lv, lv, K).reshape(3 * len(nb), 3 * len(nb))
+        d = _dof(nb)
+        rows.append(np.repeat(d, len(d)))
+        cols.append(np.tile(d, len(d)))
+        vals.append(blk.reshape(-1))
+    Hm = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(3 * m, 3 * m)).tocsr()
+    return Hm, (R, pb, F, S, q)
+
+
+def adjoint_step(model: Model, rec: StepRecord, gx, gv):
+    """Back-propagate (dL/dx_{n+1}, dL/dv_{n+1}) through one converged step.
+
+    Returns (dL/dx_n, dL/dv_n, dL/d[k_stretch, k_bend, mu], z, eta).
+
+    Unknowns of the linearised step: dv (free DOFs) and the contact multipliers
+    (stick: the 3D force; slip: the normal force; take-off: none).  Its
+    transpose gives the adjoint system
+        H z + B eta = g,   C^T z = 0,   g = dL/dv_{n+1} + h dL/dx_{n+1},
+    H = M + h^2 grad^2 W(x_{n+1}) + sum_slip h mu f_N b b^T / |u_T|
+    (Eq. adjoint_v with the contact term of Eq. ppr_adjoint), and
+    dL/dv_n = M z (Eq. adjoint_v), dL/dx_n = dL/dx_{n+1} - h grad^2 W z - contact terms.
+    """
+    h, mu = model.h, model.mu
+    m = model.m
+    free = model.free
+    x1, v1 = rec.x_np1, rec.v_np1
+    gx = np.asarray(gx, dtype=np.float64)
+    gv = np.asarray(gv, dtype=np.float64)
+    g = gv + h * gx
+    Hw, (R, pb, F, S, q) = hessian_W(model, x1)
+    Mfull = sp.diags(np.repeat(model.mass, 3))
+    fd = _dof(free)
+    H = (Mfull + h * h * Hw)[fd][:, fd].tolil()
+    pos_of = -np.ones(m, dtype=np.int64)
+    pos_of[free] = np.arange(len(free))
+    Bcols, Ccols = [], []
+    ctr = rec.contacts
+    tdirs = {}
+    for a in range(len(ctr)):
+        j = ctr.nodes[a]
+        nrm = ctr.normals[a]
+        base = 3 * pos_of[j]
+        if rec.cases[a] == STICK:
+            for e in range(3):
+                col = np.zeros(3)
+                col[e] = 1.0
+                Bcols.append((base, col))
+                Ccols.append((base, col))
+        elif rec.cases[a] == SLIP:
+            uT = v1[j] - np.dot(nrm, v1[j]) * nrm
+            nt = np.linalg.norm(uT)
+            th = uT / nt
+            bh = np.cross(nrm, th)
+            fN = float(np.dot(rec.forces[a], nrm))
+            blk = h * mu * fN / nt * np.outer(bh, bh)
+            for r_ in range(3):
+                for c_ in range(3):
+                    H[base + r_, base + c_] += blk[r_, c_]
+            Bcols.append((base, nrm.copy()))
+            Ccols.append((base, nrm - mu * th))
+            tdirs[a] = (th, nt, fN)
+    H = H.tocsr()
+    nf3 = 3 * len(free)
+    nk = len(Bcols)
+    Bm = sp.lil_matrix((nf3, nk))
+    Cm = sp.lil_matrix((nf3, nk))
+    for col, ((base, bv), (_, cv)) in enumerate(zip(Bcols, Ccols)):
+        for e in range(3):
+            Bm[base + e, col] = bv[e]
+            Cm[base + e, col] = cv[e]
+    K = sp.bmat([[H, Bm.tocsr()], [Cm.tocsr().T, None]], format="csc")
+    rhs = np.concatenate([g[free].reshape(-1), np.zeros(nk)])
+    sol = spla.spsolve(K, rhs) if nk or nf3 else rhs
+    sol = np.atleast_1d(sol)
+    z = np.zeros((m, 3))
+    z[free] = sol[:nf3].reshape(-1, 3)
+    eta = sol[nf3:]
+
+    # dL/dv_n = M z   (pinned velocities are fixed, their gradient is 0)
+    dv_n = model.mass[:, None] * z
+    dv_n[model.pins] = 0.0
+    # dL/dx_n = dL/dx_{n+1} - (dF/dx_n)^T z - (dG/dx_n)^T eta, dF/dx_n = h grad^2 W
+    dx_n = gx - h * (Hw @ z.reshape(-1)).reshape(m, 3)
+    # parameters: dF/dk_s = h sum_t area_t A_t^T (A_t x - p_t), similarly k_b;
+    # dF/dmu = h sum_slip f_N t (slip force f = f_N (n - mu t)).
+    Fz = model.deformation_gradients(z)
+    qz = model.bending_vectors(z)
+    dks = -h * np.sum(model.area * np.sum(Fz * (F - R), axis=(1, 2)))
+    dkb = -h * np.sum(model.abar * np.sum(qz * (q - pb), axis=1))
+    dmu = 0.0
+    col = 0
+    for a in range(len(ctr)):
+        j = ctr.nodes[a]
+        ob = model.obstacles[ctr.obs[a]]
+        nrm = ctr.normals[a]
+        Dn = normal_jacobian(ob, rec.x_n[j])
+        beta = ctr.betas[a]
+        if rec.cases[a] == STICK:
+            psi = eta[col:col + 3]
+            col += 3
+            # G_j = v_j + beta n:  dG/dx_n = beta Dn + n n^T / h
+            dx_n[j] -= beta * Dn.T @ psi + nrm * np.dot(nrm, psi) / h
+        elif rec.cases[a] == SLIP:
+            psi = eta[col]
+            col += 1
+            th, nt, fN = tdirs[a]
+            vj = v1[j]
+            dmu += -h * fN * np.dot(th, z[j])
+            # dt/dx_n through the normal: t = Pi v/|Pi v|, Pi = I - n n^T
+            dPiv = -(np.dot(nrm, vj) * np.eye(3) + np.outer(nrm, vj)) @ Dn
+            Dt = (np.eye(3) - np.outer(th, th)) @ dPiv / nt
+            # F_j contains -h f_N (n - mu t): contributes +h f_N (Dn - mu Dt)^T z_j
+            dx_n[j] += h * fN * (Dn - mu * Dt).T @ z[j]
+            # G_j = n.v_j + beta: dG/dx_n = Dn^T v_j + n / h
+            dx_n[j] -= (Dn.T @ vj + nrm / h) * psi
+    return dx_n, dv_n, np.array([dks, dkb, dmu]), z, eta
+
+
+def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dtraj_x=None):
+    """Reverse pass over a rollout: returns (dL/dx0, dL/dv0, dL/d[k_s, k_b, mu])."""
+    gx = np.asarray(dL_dx_final, dtype=np.float64).copy()
+    gv = np.zeros_like(gx) if dL_dv_final is None else np.asarray(dL_dv_final, dtype=np.float64).copy()
+    dth = np.zeros(3)
+    N = len(records)
+    for n in range(N - 1, -1, -1):
+        if dL_dtraj_x is not None:
+            gx = gx + dL_dtraj_x[n + 1]
+        gx, gv, d, _, _ = adjoint_step(model, records[n], gx, gv)
+        dth += d
+    if dL_dtraj_x is not None:
+        gx = gx + dL_dtraj_x[0]
+    return gx, gv, dth
+
+
+def model_from_scene(scene, **overrides):
+    """Convenience: build a Model from a scenes.Scene, optionally overriding parameters."""
+    import dataclasses
+    prm = dataclasses.replace(scene.params, **overrides) if overrides else scene.params
+    return Model(scene.rest_pos, scene.tris, scene.pins, scene.obstacles, prm)

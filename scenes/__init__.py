@@ -1,0 +1,212 @@
+"""Seeded synthetic cloth scenes: the inputs shared by the oracle, the tests and the benchmark.
+
+This module only builds inputs -- rest meshes, pins, obstacles, material and
+solver parameters, initial states and loss weights.  It holds none of the
+simulation arithmetic (no rest-shape operators, no masses, no system matrix,
+no projections): both the CPU oracle and the CUDA library derive those from
+the raw mesh on their own.
+
+Geometry conventions (the paper fixes none of them):
+  * y is up; gravity is (0, -9.8, 0) m/s^2.
+  * An n x n grid cloth of side ``side`` lies in the x-z plane at height
+    ``height``; node (i, j) has index j*n + i and rest position
+    (x0 + i*a, height, z0 + j*a) with a = side/(n-1).
+  * Each grid quad (i, j)-(i+1, j+1) is split along that diagonal into the
+    triangles (v00, v10, v11) and (v00, v11, v01).
+  * Obstacles are analytic: planes {x : n.x = d}, spheres and capsules.
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+GRAVITY = (0.0, -9.8, 0.0)
+
+
+@dataclasses.dataclass
+class Obstacle:
+    kind: str                      # "plane" | "sphere" | "capsule"
+    normal: tuple = (0.0, 1.0, 0.0)  # plane: unit normal
+    offset: float = 0.0            # plane: n.x = offset
+    center: tuple = (0.0, 0.0, 0.0)  # sphere centre
+    radius: float = 0.0            # sphere / capsule radius
+    a: tuple = (0.0, 0.0, 0.0)     # capsule segment end points
+    b: tuple = (0.0, 0.0, 0.0)
+
+
+@dataclasses.dataclass
+class Params:
+    k_stretch: float = 1e3
+    k_bend: float = 1e-3
+    density: float = 0.1           # kg / m^2
+    mu: float = 0.3
+    h: float = 1.0 / 120.0
+    gravity: tuple = GRAVITY
+    n_pd_iters: int = 20
+    contact_margin: float = 1e-6   # detection margin delta (m)
+
+
+@dataclasses.dataclass
+class Scene:
+    name: str
+    n: int                         # grid resolution (n x n nodes)
+    rest_pos: np.ndarray           # (m, 3) float64
+    tris: np.ndarray               # (T, 3) int32
+    pins: np.ndarray               # (p,) int32, sorted
+    obstacles: List[Obstacle]
+    params: Params
+    x0: np.ndarray                 # (m, 3) initial positions
+    v0: np.ndarray                 # (m, 3) initial velocities
+    n_steps: int
+    loss_w: Optional[np.ndarray] = None   # (m, 3) loss weights xi, L = sum(xi * x_N)
+    checkpoint_every: int = 0
+
+    @property
+    def m(self) -> int:
+        return self.rest_pos.shape[0]
+
+
+def grid_mesh(n: int, side: float = 1.0, height: float = 0.6,
+              x0: float = -0.5, z0: float = 0.0):
+    """Rest positions (n*n, 3) and triangles (2(n-1)^2, 3) of a flat n x n grid."""
+    a = side / (n - 1)
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="xy")
+    pos = np.zeros((n * n, 3))
+    pos[:, 0] = x0 + a * ii.reshape(-1)
+    pos[:, 1] = height
+    pos[:, 2] = z0 + a * jj.reshape(-1)
+    tris = []
+    for j in range(n - 1):
+        for i in range(n - 1):
+            v00 = j * n + i
+            v10 = v00 + 1
+            v01 = v00 + n
+            v11 = v01 + 1
+            tris.append((v00, v10, v11))
+            tris.append((v00, v11, v01))
+    return pos, np.asarray(tris, dtype=np.int32)
+
+
+def loss_weights(m: int, seed: int) -> np.ndarray:
+    """Standard-normal loss weights xi (m, 3); the loss is sum(xi * x_final)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x10557]))
+    return rng.standard_normal((m, 3))
+
+
+def _log_uniform(rng, lo, hi):
+    return float(np.exp(rng.uniform(np.log(lo), np.log(hi))))
+
+
+def hanging_cloth(n: int = 16, seed: int = 0, n_steps: int = 50) -> Scene:
+    """16x16 cloth pinned at two corners, falling onto a sphere and the ground.
+
+    Side 1 m, mu 0.3, h 1/120 s, 20 PD iterations, stretch 1e3, bend 1e-3,
+    density 0.1 kg/m^2; sphere of radius 0.3 m under the cloth centre.
+    """
+    pos, tris = grid_mesh(n, side=1.0, height=0.7)
+    pins = np.array([0, n - 1], dtype=np.int32)
+    obst = [Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.0),
+            Obstacle("sphere", center=(0.0, 0.35, 0.55), radius=0.3)]
+    prm = Params(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0)
+    return Scene("hanging_16", n, pos, tris, pins, obst, prm, pos.copy(),
+                 np.zeros_like(pos), n_steps, loss_weights(n * n, seed))
+
+
+def draped_cloth(n: int = 61, seed: int = 0, n_steps: int = 125,
+                 checkpoint_every: int = 25) -> Scene:
+    """Unpinned n x n cloth dropped over a sphere (r 0.3 m) and the ground.
+
+    mu ~ U[0.1, 0.6], k_stretch ~ logU[1e2, 1e4], k_bend ~ logU[1e-4, 1e-2]
+    drawn from the seed; h 1/120 s; 20 PD iterations.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xD7A9E]))
+    mu = float(rng.uniform(0.1, 0.6))
+    ks = _log_uniform(rng, 1e2, 1e4)
+    kb = _log_uniform(rng, 1e-4, 1e-2)
+    pos, tris = grid_mesh(n, side=1.0, height=0.8)
+    obst = [Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.0),
+            Obstacle("sphere", center=(0.0, 0.35, 0.5), radius=0.3)]
+    prm = Params(k_stretch=ks, k_bend=kb, density=0.1, mu=mu, h=1.0 / 120.0)
+    return Scene(f"draped_{n}", n, pos, tris, np.zeros(0, np.int32), obst, prm,
+                 pos.copy(), np.zeros_like(pos), n_steps, loss_weights(n * n, seed),
+                 checkpoint_every)
+
+
+def batch_instance(seed: int, n_lo: int = 16, n_hi: int = 64, n_steps: int = 50) -> Scene:
+    """One member of the batched workload: random grid size, material, sphere."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBA7C4]))
+    n = int(rng.integers(n_lo, n_hi + 1))
+    mu = float(rng.uniform(0.1, 0.6))
+    ks = _log_uniform(rng, 1e2, 1e4)
+    kb = _log_uniform(rng, 1e-4, 1e-2)
+    r = float(rng.uniform(0.2, 0.5))
+    cy = r + float(rng.uniform(0.0, 0.2))
+    pos, tris = grid_mesh(n, side=1.0, height=cy + r + 0.1)
+    obst = [Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.0),
+            Obstacle("sphere", center=(0.0, cy, 0.5), radius=r)]
+    prm = Params(k_stretch=ks, k_bend=kb, density=0.1, mu=mu, h=1.0 / 120.0)
+    return Scene(f"batch_{seed}_{n}", n, pos, tris, np.zeros(0, np.int32), obst, prm,
+                 pos.copy(), np.zeros_like(pos), n_steps, loss_weights(n * n, seed))
+
+
+def capsule_field(n: int = 200, seed: int = 0, n_steps: int = 100, n_capsules: int = 8) -> Scene:
+    """Large cloth dropped onto random capsules and the ground (mu 0.4, h 1/240)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xCA95]))
+    pos, tris = grid_mesh(n, side=1.0, height=0.5)
+    obst = [Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.0)]
+    for _ in range(n_capsules):
+        c = np.array([rng.uniform(-0.4, 0.4), rng.uniform(0.1, 0.35), rng.uniform(0.1, 0.9)])
+        th = rng.uniform(0, np.pi)
+        half = rng.uniform(0.05, 0.2)
+        d = np.array([np.cos(th), 0.0, np.sin(th)]) * half
+        obst.append(Obstacle("capsule", a=tuple(c - d), b=tuple(c + d),
+                             radius=float(rng.uniform(0.02, 0.1))))
+    prm = Params(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.4, h=1.0 / 240.0)
+    return Scene(f"capsules_{n}", n, pos, tris, np.zeros(0, np.int32), obst, prm,
+                 pos.copy(), np.zeros_like(pos), n_steps, loss_weights(n * n, seed), 10)
+
+
+def inclined_plane(theta: float, mu: float, n: int = 4, side: float = 0.3) -> Scene:
+    """A flat cloth resting on a plane tilted by theta about the z axis (no pins)."""
+    pos, tris = grid_mesh(n, side=side, height=0.0, x0=0.0, z0=0.0)
+    c, s = np.cos(theta), np.sin(theta)
+    rot = np.array([[c, -s, 0.0], [s, c, 0.0], [0.0, 0.0, 1.0]])
+    pos = pos @ rot.T
+    nrm = rot @ np.array([0.0, 1.0, 0.0])
+    obst = [Obstacle("plane", normal=tuple(nrm), offset=0.0)]
+    prm = Params(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=mu, h=1.0 / 100.0)
+    return Scene("slope", n, pos, tris, np.zeros(0, np.int32), obst, prm, pos.copy(),
+                 np.zeros_like(pos), 10)
+
+
+def small_scene(n: int = 4, seed: int = 0, contact: str = "sphere", pinned: bool = True,
+                n_steps: int = 3, drop: bool = False) -> Scene:
+    """Tiny seeded scenes for brute-force and finite-difference checks.
+
+    ``drop`` gives every node a downward velocity with little tangential noise
+    and a high friction coefficient, so that contacts stick.
+    """
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5A11]))
+    pos, tris = grid_mesh(n, side=0.3, height=0.2, x0=-0.15, z0=0.0)
+    x0 = pos + 0.01 * rng.standard_normal(pos.shape)
+    v0 = 0.2 * rng.standard_normal(pos.shape)
+    if drop:
+        v0 = 0.01 * rng.standard_normal(pos.shape) + np.array([0.0, -0.6, 0.0])
+    pins = np.array([0, n - 1], dtype=np.int32) if pinned else np.zeros(0, np.int32)
+    v0[pins] = 0.0
+    x0[pins] = pos[pins]
+    obst: List[Obstacle] = []
+    if contact in ("plane", "both"):
+        obst.append(Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.185))
+    if contact in ("sphere", "both"):
+        obst.append(Obstacle("sphere", center=(0.0, -0.1, 0.15), radius=0.3))
+    if contact == "capsule":
+        obst.append(Obstacle("capsule", a=(-0.3, -0.05, 0.15), b=(0.3, -0.02, 0.15), radius=0.25))
+    prm = Params(k_stretch=float(rng.uniform(50, 200)), k_bend=float(rng.uniform(1e-3, 1e-2)),
+                 density=0.1, mu=float(rng.uniform(0.1, 0.6)), h=1.0 / 60.0)
+    if drop:
+        prm.mu = float(rng.uniform(0.8, 1.5))
+    return Scene(f"small_{n}_{contact}", n, pos, tris, pins, obst, prm, x0, v0, n_steps,
+                 loss_weights(n * n, seed))
