@@ -1,0 +1,165 @@
+/*
+ * dc.h -- C ABI of the GB300 differentiable-cloth library (libdc.so).
+ *
+ * One Projective Dynamics (PD) cloth time step with dry frictional
+ * (Signorini-Coulomb) contact, and its adjoint, after "DiffCloth:
+ * Differentiable Cloth Simulation with Dry Frictional Contact"
+ * (arXiv 2106.05306), Sec. 3-4.
+ *
+ * Conventions for every entry point
+ *  - Functions return a dc_status (0 = DC_OK) and never throw.  dc_last_error()
+ *    gives a message for the last failing call on a context.
+ *  - Node arrays are FP64, node-major "[m][3]" (x0,y0,z0,x1,...), in the node
+ *    numbering of the mesh passed to dc_create_mesh.
+ *  - Array arguments may be host or device pointers (CUDA unified addressing
+ *    tells them apart).  Device pointers keep the call asynchronous on the
+ *    context's stream; if any argument is host memory the call synchronises the
+ *    stream before it returns.  The caller owns every argument array; the
+ *    library owns the factor, work buffers and checkpoints.
+ *  - All GPU work is enqueued on the CUDA stream given to dc_create_mesh.
+ *    Errors found on the device (non-finite values) are reported by the next
+ *    synchronising call (dc_sync, dc_get_stats, or any call with host buffers).
+ *  - A context is not thread-safe.
+ */
+#ifndef DC_H_
+#define DC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t dc_status;
+enum {
+    DC_OK = 0,
+    DC_ERR_INVALID = 1,      /* bad size, index, pointer or parameter (host check) */
+    DC_ERR_CUDA = 2,         /* a CUDA runtime call failed */
+    DC_ERR_NOT_SPD = 3,      /* the PD matrix factorisation met a pivot <= 0 */
+    DC_ERR_OOM = 4,          /* device allocation failed */
+    DC_ERR_NONFINITE = 5,    /* a NaN/Inf was produced on the device */
+    DC_ERR_NONCONVERGED = 6, /* the adjoint solve hit its iteration cap */
+    DC_ERR_STATE = 7         /* call out of order (e.g. dc_step before dc_set_params) */
+};
+
+enum { DC_PLANE = 0, DC_SPHERE = 1, DC_CAPSULE = 2 };
+#define DC_MAX_OBSTACLES 16
+
+/* Analytic obstacle (reading of Sec. 3.2 "Extensions": static, possibly curved).
+ *   DC_PLANE:   p[0..2] = unit normal n, p[3] = d        (surface n.x = d)
+ *   DC_SPHERE:  p[0..2] = centre, p[3] = radius
+ *   DC_CAPSULE: p[0..2] = a, p[3..5] = b, p[6] = radius  (segment a-b) */
+typedef struct dc_obstacle {
+    int32_t kind;
+    int32_t pad_;
+    double p[7];
+} dc_obstacle;
+
+typedef struct dc_params {
+    double k_stretch;        /* stretch stiffness; w_t = k_stretch * rest area     */
+    double k_bend;           /* bending stiffness; w_b = k_bend * vertex area      */
+    double density;          /* kg/m^2; lumped mass = density * vertex area        */
+    double mu;               /* Coulomb friction coefficient                       */
+    double h;                /* time step (s)                                       */
+    double gravity[3];       /* f_ext = M g                                         */
+    double contact_margin;   /* detection margin delta (m)                          */
+    double adj_tol;          /* adjoint: relative residual target (default 1e-10)   */
+    int32_t n_pd_iters;      /* local/global/contact iterations per step (K)       */
+    int32_t adj_max_iters;   /* adjoint: cap on preconditioned GMRES iterations     */
+    int32_t adj_restart;     /* adjoint: GMRES restart length (<= 256)              */
+    int32_t checkpoint_every;/* rollout: keep (x, v) every k steps (>= 1)           */
+    int32_t n_obstacles;
+    int32_t pad_;
+    dc_obstacle obstacles[DC_MAX_OBSTACLES];
+} dc_params;
+
+typedef struct dc_stats {
+    int64_t steps;             /* forward steps run since creation                    */
+    int64_t contacts_takeoff;  /* contact-node counts by final case, summed over steps */
+    int64_t contacts_stick;
+    int64_t contacts_slip;
+    int64_t adj_steps;         /* adjoint steps run                                   */
+    int64_t adj_iters;         /* preconditioned GMRES iterations, summed             */
+    int64_t adj_max_iters_seen;/* largest count in one adjoint step                   */
+    int64_t adj_nonconverged;  /* adjoint steps that hit the cap                      */
+    double adj_last_residual;  /* relative residual of the last adjoint step          */
+    int64_t factor_nnz;        /* nonzeros of the Cholesky factor L of P              */
+    int64_t solve_nnz;         /* nonzeros read by one P^-1 application (one column)  */
+    int32_t n_free;            /* free (unpinned) nodes                               */
+    int32_t nd_levels;         /* depth of the nested-dissection tree                 */
+} dc_stats;
+
+typedef struct dc_ctx dc_ctx;
+
+/* Create a cloth from its rest mesh.
+ *   rest_pos: [n_nodes][3] rest positions (host).  tris: [n_tris][3] node
+ *   indices (host).  pins: [n_pins] node indices held fixed (Dirichlet, velocity
+ *   0), may be NULL when n_pins = 0.  stream: a cudaStream_t (NULL = legacy
+ *   default stream).  Computes the rest-shape operators of the PD energies
+ *   (Sec. 3.1, Eq. pd_project: triangle stretch and vertex bending), the lumped
+ *   mass, and a nested-dissection ordering of the free nodes.  The new context
+ *   is returned in *out; it must be released with dc_destroy. */
+dc_status dc_create_mesh(dc_ctx** out, int32_t n_nodes, const double* rest_pos,
+                         int32_t n_tris, const int32_t* tris,
+                         int32_t n_pins, const int32_t* pins, void* stream);
+
+/* Set material, contact and solver parameters (host struct, copied).
+ * Assembles the constant PD matrix P = M + h^2 sum_i w_i A_i^T A_i (Sec. 3.1,
+ * Eq. pd_global), factorises it once (P = L L^T, host, nested-dissection
+ * order) and uploads the solve operators.  Synchronous.  DC_ERR_NOT_SPD if a
+ * pivot is not positive; DC_ERR_INVALID for non-finite or out-of-range values. */
+dc_status dc_set_params(dc_ctx* ctx, const dc_params* params);
+
+/* One time step (x_n, v_n) -> (x_{n+1}, v_{n+1}) (Sec. 3.2, Eq.
+ * implicit_with_contact solved by n_pd_iters PD local/global iterations with
+ * the per-node Signorini-Coulomb update, Eq. pd_velocity_with_contact).
+ * All four arrays are [m][3]; pinned nodes keep their position and get v = 0. */
+dc_status dc_step(dc_ctx* ctx, const double* x_n, const double* v_n,
+                  double* x_np1, double* v_np1);
+
+/* n_steps time steps from (x0, v0).  Keeps a checkpoint of (x, v) every
+ * checkpoint_every steps for dc_backward.  traj_x, if not NULL, receives all
+ * positions [(n_steps+1)][m][3] (traj_x[0] = x0). */
+dc_status dc_rollout(dc_ctx* ctx, int32_t n_steps, const double* x0, const double* v0,
+                     double* x_final, double* v_final, double* traj_x);
+
+/* Gradient of a loss L(x_N, v_N, x_0..x_N) through the last dc_rollout (Sec. 4,
+ * Eq. adjoint_v and ppr_adjoint, contact terms as the linearisation of the
+ * converged step).  Recomputes each checkpoint segment, then solves one adjoint
+ * system per step in reverse order.
+ *   dL_dx_final: [m][3] dL/dx_N.  dL_dv_final: [m][3] or NULL (zero).
+ *   dL_dtraj_x: [(n_steps+1)][m][3] per-step dL/dx_n or NULL.
+ * Outputs dL_dx0, dL_dv0: [m][3]; dL_dparams: [3] = dL/d(k_stretch, k_bend, mu).
+ * DC_ERR_NONCONVERGED is reported (after all outputs are written) when an
+ * adjoint step reached adj_max_iters above adj_tol. */
+dc_status dc_backward(dc_ctx* ctx, const double* dL_dx_final, const double* dL_dv_final,
+                      const double* dL_dtraj_x, double* dL_dx0, double* dL_dv0,
+                      double* dL_dparams);
+
+/* Apply P_ff^-1 (the prefactorised global-step matrix restricted to free
+ * nodes, Eq. pd_global) to three right-hand-side columns: out = P^-1 rhs.
+ * rhs, out: [m][3]; entries of pinned nodes are ignored on input and set to 0. */
+dc_status dc_global_solve(dc_ctx* ctx, const double* rhs, double* out);
+
+/* Counters and factor sizes (synchronises the stream). */
+dc_status dc_get_stats(dc_ctx* ctx, dc_stats* out);
+
+/* Wait for all work of the context; reports deferred device errors. */
+dc_status dc_sync(dc_ctx* ctx);
+
+/* Release the context and all its device memory (synchronises first). */
+void dc_destroy(dc_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing
+ * dc_create_mesh when ctx is NULL).  Valid until the next call. */
+const char* dc_last_error(dc_ctx* ctx);
+
+/* Fill *p with the library defaults (k_stretch 1e3, k_bend 1e-3, density 0.1,
+ * mu 0.3, h 1/120, g = (0,-9.8,0), delta 1e-6, K = 20, adjoint tol 1e-10,
+ * 2000 iterations, restart 200, checkpoint every step, no obstacles). */
+void dc_default_params(dc_params* p);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DC_H_ */

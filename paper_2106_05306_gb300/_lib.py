@@ -1,0 +1,86 @@
+"""ctypes declarations of the C ABI in include/dc.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "libdc.so")
+
+DC_OK = 0
+STATUS_NAMES = {0: "DC_OK", 1: "DC_ERR_INVALID", 2: "DC_ERR_CUDA", 3: "DC_ERR_NOT_SPD", 4: "DC_ERR_OOM",
+                5: "DC_ERR_NONFINITE", 6: "DC_ERR_NONCONVERGED", 7: "DC_ERR_STATE"}
+DC_PLANE, DC_SPHERE, DC_CAPSULE = 0, 1, 2
+DC_MAX_OBSTACLES = 16
+
+
+class dc_obstacle(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("pad_", ctypes.c_int32), ("p", ctypes.c_double * 7)]
+
+
+class dc_params(ctypes.Structure):
+    _fields_ = [("k_stretch", ctypes.c_double), ("k_bend", ctypes.c_double), ("density", ctypes.c_double),
+                ("mu", ctypes.c_double), ("h", ctypes.c_double), ("gravity", ctypes.c_double * 3),
+                ("contact_margin", ctypes.c_double), ("adj_tol", ctypes.c_double),
+                ("n_pd_iters", ctypes.c_int32), ("adj_max_iters", ctypes.c_int32),
+                ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
+                ("n_obstacles", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
+
+
+class dc_stats(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int64), ("contacts_takeoff", ctypes.c_int64),
+                ("contacts_stick", ctypes.c_int64), ("contacts_slip", ctypes.c_int64),
+                ("adj_steps", ctypes.c_int64), ("adj_iters", ctypes.c_int64),
+                ("adj_max_iters_seen", ctypes.c_int64), ("adj_nonconverged", ctypes.c_int64),
+                ("adj_last_residual", ctypes.c_double), ("factor_nnz", ctypes.c_int64),
+                ("solve_nnz", ctypes.c_int64), ("n_free", ctypes.c_int32), ("nd_levels", ctypes.c_int32)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+# name -> (restype, argtypes); every pointer argument is passed as a raw address
+SIGNATURES = {
+    "dc_create_mesh": (ctypes.c_int32, [ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                        ctypes.c_int32, _P, _P]),
+    "dc_set_params": (ctypes.c_int32, [_P, ctypes.POINTER(dc_params)]),
+    "dc_step": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
+    "dc_rollout": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
+    "dc_backward": (ctypes.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
+    "dc_global_solve": (ctypes.c_int32, [_P, _P, _P]),
+    "dc_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_stats)]),
+    "dc_sync": (ctypes.c_int32, [_P]),
+    "dc_destroy": (None, [_P]),
+    "dc_last_error": (ctypes.c_char_p, [_P]),
+    "dc_default_params": (None, [ctypes.POINTER(dc_params)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdc.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libdc.so not found at {path}; build it with paper_2106_05306_gb300.build.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class DCError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status, ctx=None):
+    if status != DC_OK:
+        msg = load().dc_last_error(ctx)
+        raise DCError(status, msg.decode() if msg else "")

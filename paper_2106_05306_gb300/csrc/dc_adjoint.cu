@@ -1,0 +1,705 @@
+// Adjoint kernels of libdc (FP64, sm_103a): the linearisation of one converged
+// time step, transposed (Sec. 4, Eq. adjoint_v and ppr_adjoint).
+//
+// The adjoint system of a step is
+//     H z + B eta = g,    C^T z = 0,     g = dL/dv_{n+1} + h dL/dx_{n+1},
+// with H = M + h^2 grad^2 W(x_{n+1}) - Delta R = P - Delta P - Delta R,
+// grad^2 W_i = w_i A_i^T (I - dp_i*/d(A_i x)) A_i, and per contact node:
+//   stick:    z_j = 0                      (B_j = C_j = I)
+//   slip:     (n - mu t).z_j = 0           (B_j = n, C_j = n - mu t; oblique)
+//             and Delta R_j = -h mu f_N b b^T / |u_T|, b = n x t
+//   take-off: no constraint.
+// It is solved with flexible GMRES on w -> Pi_B H K(w), where Pi_B removes the
+// B components and K is a two-level preconditioner: a per-node constrained
+// block inverse of H, the prefactorised P^-1 projected onto C^T z = 0, and the
+// block inverse again.  Every H application is matrix-free: a per-element pass
+// (the polar-factor derivative for stretch, the sphere-projection derivative
+// for bending) and a fixed-order per-node gather.
+#include "dc_internal.h"
+#include "dc_adjoint.h"
+
+namespace {
+
+__device__ __forceinline__ d4 ld(const d4* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = q[0], b = q[1];
+    d4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+__device__ __forceinline__ void st(d4* p, double x, double y, double z, double w = 0.0) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, w);
+}
+inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
+
+// ----------------------------------------------------------------- per-step setup
+
+// Per triangle at x_{n+1}: R (polar factor), S^-1, 1/tr S (reading R1).
+__global__ void k_adj_setup_tri(DevMesh dm, const d4* __restrict__ x1, d4* __restrict__ tr0,
+                                d4* __restrict__ tr1, d4* __restrict__ tr2) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= dm.T) return;
+    int4 tr = dm.tri[t];
+    d4 g = ld(dm.G + t);
+    d4 a = ld(x1 + tr.x), b = ld(x1 + tr.y), c = ld(x1 + tr.z);
+    double e1[3] = {b.x - a.x, b.y - a.y, b.z - a.z};
+    double e2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
+    double F[6];
+    for (int k = 0; k < 3; ++k) {
+        F[k] = e1[k] * g.x + e2[k] * g.z;
+        F[3 + k] = e1[k] * g.y + e2[k] * g.w;
+    }
+    double c00 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    double c01 = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
+    double c11 = F[3] * F[3] + F[4] * F[4] + F[5] * F[5];
+    double det = c00 * c11 - c01 * c01;
+    double is = rsqrt(det);
+    double s = det * is;
+    double it = rsqrt(c00 + c11 + 2.0 * s);
+    double k = is * it;
+    double s00 = (c11 + s) * k, s01 = -c01 * k, s11 = (c00 + s) * k;   // S^-1
+    double R[6];
+    for (int q = 0; q < 3; ++q) {
+        R[q] = s00 * F[q] + s01 * F[3 + q];
+        R[3 + q] = s01 * F[q] + s11 * F[3 + q];
+    }
+    st(tr0 + t, R[0], R[1], R[2], s00);
+    st(tr1 + t, R[3], R[4], R[5], s01);
+    st(tr2 + t, s11, it, 0.0, 0.0);   // tr S = t, so 1/tr S = it
+}
+
+// Per vertex at x_{n+1}: sphere-projection derivative data (q_hat, kappa = s/|q|)
+// (reading R2); kappa = 0 where the projection is constant.
+__global__ void k_adj_setup_bend(DevMesh dm, const d4* __restrict__ x1, d4* __restrict__ bq) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= dm.m) return;
+    double q[3] = {0, 0, 0};
+    for (int k = dm.bptr[b]; k < dm.bptr[b + 1]; ++k) {
+        d4 x = ld(x1 + dm.bidx[k]);
+        double l = dm.bval[k];
+        q[0] += l * x.x; q[1] += l * x.y; q[2] += l * x.z;
+    }
+    double s = dm.sb[b];
+    double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    if (s > 0.0 && nq > 1e-14 * s)
+        st(bq + b, q[0] / nq, q[1] / nq, q[2] / nq, s / nq);
+    else
+        st(bq + b, 0.0, 0.0, 0.0, 0.0);
+}
+
+__device__ __forceinline__ void sym_add(double H[6], double a, const double u[3]) {
+    // H += a u u^T, packed (00, 01, 02, 11, 12, 22)
+    H[0] += a * u[0] * u[0]; H[1] += a * u[0] * u[1]; H[2] += a * u[0] * u[2];
+    H[3] += a * u[1] * u[1]; H[4] += a * u[1] * u[2]; H[5] += a * u[2] * u[2];
+}
+
+__device__ void inv3(const double A[9], double X[9]) {
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    double id = 1.0 / det;
+    X[0] = c00 * id; X[1] = (A[2] * A[7] - A[1] * A[8]) * id; X[2] = (A[1] * A[5] - A[2] * A[4]) * id;
+    X[3] = c01 * id; X[4] = (A[0] * A[8] - A[2] * A[6]) * id; X[5] = (A[2] * A[3] - A[0] * A[5]) * id;
+    X[6] = c02 * id; X[7] = (A[1] * A[6] - A[0] * A[7]) * id; X[8] = (A[0] * A[4] - A[1] * A[3]) * id;
+}
+
+// Per free node: the node type, slip data and the constrained inverse
+// D+_j = Q (R^T H_jj Q)^-1 R^T of the diagonal block of H.
+__global__ void k_adj_setup_node(DevMesh dm, AdjDev ad, const d4* __restrict__ v1) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= dm.m_free) return;
+    const double h2 = ad.h * ad.h;
+    double H[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = dm.iptr[j]; k < dm.iptr[j + 1]; ++k) {
+        int e = dm.iidx[k];
+        int t = e / 3, a = e - 3 * t;
+        d4 g = ld(dm.G + t);
+        double ga0, ga1;
+        if (a == 1) { ga0 = g.x; ga1 = g.y; }
+        else if (a == 2) { ga0 = g.z; ga1 = g.w; }
+        else { ga0 = -(g.x + g.z); ga1 = -(g.y + g.w); }
+        d4 A0 = ld(ad.tr0 + t), A1 = ld(ad.tr1 + t), A2 = ld(ad.tr2 + t);
+        double R0[3] = {A0.x, A0.y, A0.z}, R1[3] = {A1.x, A1.y, A1.z};
+        double s00 = A0.w, s01 = A1.w, s11 = A2.x, itr = A2.y;
+        double w = h2 * dm.wt[t];
+        double gg = ga0 * ga0 + ga1 * ga1;
+        double gam = ga0 * ga0 * s00 + 2.0 * ga0 * ga1 * s01 + ga1 * ga1 * s11;
+        double av[3] = {(ga0 * R1[0] - ga1 * R0[0]) * itr, (ga0 * R1[1] - ga1 * R0[1]) * itr,
+                        (ga0 * R1[2] - ga1 * R0[2]) * itr};
+        // block = w (|g|^2 I - trS a a^T - gam (I - R0 R0^T - R1 R1^T))
+        double d = w * (gg - gam);
+        H[0] += d; H[3] += d; H[5] += d;
+        sym_add(H, -w / itr, av);
+        sym_add(H, w * gam, R0);
+        sym_add(H, w * gam, R1);
+    }
+    for (int k = dm.tbptr[j]; k < dm.tbptr[j + 1]; ++k) {
+        int b = dm.tbidx[k];
+        double l = dm.tbval[k];
+        d4 q = ld(ad.bq + b);
+        double w = h2 * dm.wb[b] * l * l;
+        double d = w * (1.0 - q.w);
+        H[0] += d; H[3] += d; H[5] += d;
+        double qh[3] = {q.x, q.y, q.z};
+        sym_add(H, w * q.w, qh);
+    }
+    double mj = dm.mass[j];
+    H[0] += mj; H[3] += mj; H[5] += mj;
+    int type = 0;
+    int cs = ad.contact[j] >= 0 ? ad.case_[j] : 0;
+    double Hf[9] = {H[0], H[1], H[2], H[1], H[3], H[4], H[2], H[4], H[5]};
+    double D[9];
+    if (cs == 1) {
+        type = 1;
+        for (int q = 0; q < 9; ++q) D[q] = 0.0;
+        st(ad.slip + j, 0, 0, 0, 0);
+    } else if (cs == 2) {
+        type = 2;
+        d4 nb = ld(ad.nb + j), f = ld(ad.f + j), v = ld(v1 + j);
+        double n[3] = {nb.x, nb.y, nb.z};
+        double vn = n[0] * v.x + n[1] * v.y + n[2] * v.z;
+        double uT[3] = {v.x - vn * n[0], v.y - vn * n[1], v.z - vn * n[2]};
+        double nt = sqrt(uT[0] * uT[0] + uT[1] * uT[1] + uT[2] * uT[2]);
+        double th[3] = {uT[0] / nt, uT[1] / nt, uT[2] / nt};
+        double bh[3] = {n[1] * th[2] - n[2] * th[1], n[2] * th[0] - n[0] * th[2], n[0] * th[1] - n[1] * th[0]};
+        double fN = f.x * n[0] + f.y * n[1] + f.z * n[2];
+        double ks = ad.h * ad.mu * fN / nt;
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) Hf[3 * r + c] += ks * bh[r] * bh[c];
+        st(ad.slip + j, th[0], th[1], th[2], ks);
+        // Q = [b, t + mu n] spans null(C^T); R = [t, b] spans null(B^T)
+        double Q[3][2], Rm[3][2];
+        for (int r = 0; r < 3; ++r) {
+            Q[r][0] = bh[r]; Q[r][1] = th[r] + ad.mu * n[r];
+            Rm[r][0] = th[r]; Rm[r][1] = bh[r];
+        }
+        double Rt_H_Q[2][2];
+        for (int p = 0; p < 2; ++p)
+            for (int q = 0; q < 2; ++q) {
+                double s = 0;
+                for (int r = 0; r < 3; ++r)
+                    for (int c = 0; c < 3; ++c) s += Rm[r][p] * Hf[3 * r + c] * Q[c][q];
+                Rt_H_Q[p][q] = s;
+            }
+        double det = Rt_H_Q[0][0] * Rt_H_Q[1][1] - Rt_H_Q[0][1] * Rt_H_Q[1][0];
+        double iv[2][2] = {{Rt_H_Q[1][1] / det, -Rt_H_Q[0][1] / det}, {-Rt_H_Q[1][0] / det, Rt_H_Q[0][0] / det}};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0;
+                for (int p = 0; p < 2; ++p)
+                    for (int q = 0; q < 2; ++q) s += Q[r][p] * iv[p][q] * Rm[c][q];
+                D[3 * r + c] = s;
+            }
+    } else {
+        inv3(Hf, D);
+        st(ad.slip + j, 0, 0, 0, 0);
+    }
+    ad.type[j] = type;
+    st(ad.dinv + 3 * j, D[0], D[1], D[2]);
+    st(ad.dinv + 3 * j + 1, D[3], D[4], D[5]);
+    st(ad.dinv + 3 * j + 2, D[6], D[7], D[8]);
+}
+
+// ----------------------------------------------------------------- H application
+
+// Element pass: per triangle E = h^2 w (dF - Dp[dF]) with dF = A_t z, stored as the
+// vertex-1 and vertex-2 columns E g_a^T; per vertex u = h^2 w_b (dq - Dp_b[dq]).
+__global__ void k_adj_elem(DevMesh dm, AdjDev ad, const d4* __restrict__ z, d4* __restrict__ c1,
+                           d4* __restrict__ c2, d4* __restrict__ bu) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const double h2 = ad.h * ad.h;
+    if (id < dm.T) {
+        int4 tr = dm.tri[id];
+        d4 g = ld(dm.G + id);
+        d4 z0 = ld(z + tr.x), z1 = ld(z + tr.y), z2 = ld(z + tr.z);
+        double e1[3] = {z1.x - z0.x, z1.y - z0.y, z1.z - z0.z};
+        double e2[3] = {z2.x - z0.x, z2.y - z0.y, z2.z - z0.z};
+        double dF0[3], dF1[3];
+        for (int k = 0; k < 3; ++k) {
+            dF0[k] = e1[k] * g.x + e2[k] * g.z;
+            dF1[k] = e1[k] * g.y + e2[k] * g.w;
+        }
+        d4 A0 = ld(ad.tr0 + id), A1 = ld(ad.tr1 + id), A2 = ld(ad.tr2 + id);
+        double R0[3] = {A0.x, A0.y, A0.z}, R1[3] = {A1.x, A1.y, A1.z};
+        double s00 = A0.w, s01 = A1.w, s11 = A2.x, itr = A2.y;
+        double r00 = R0[0] * dF0[0] + R0[1] * dF0[1] + R0[2] * dF0[2];
+        double r01 = R0[0] * dF1[0] + R0[1] * dF1[1] + R0[2] * dF1[2];
+        double r10 = R1[0] * dF0[0] + R1[1] * dF0[1] + R1[2] * dF0[2];
+        double r11 = R1[0] * dF1[0] + R1[1] * dF1[1] + R1[2] * dF1[2];
+        double om = (r10 - r01) * itr;
+        double w = h2 * dm.wt[id];
+        double E0[3], E1[3];
+        for (int k = 0; k < 3; ++k) {
+            double p0 = dF0[k] - R0[k] * r00 - R1[k] * r10;   // (I - R R^T) dF, column 0
+            double p1 = dF1[k] - R0[k] * r01 - R1[k] * r11;   // column 1
+            double dR0 = om * R1[k] + p0 * s00 + p1 * s01;    // R Om + (..) S^-1, column 0
+            double dR1 = -om * R0[k] + p0 * s01 + p1 * s11;   // column 1
+            E0[k] = w * (dF0[k] - dR0);
+            E1[k] = w * (dF1[k] - dR1);
+        }
+        st(c1 + id, E0[0] * g.x + E1[0] * g.y, E0[1] * g.x + E1[1] * g.y, E0[2] * g.x + E1[2] * g.y);
+        st(c2 + id, E0[0] * g.z + E1[0] * g.w, E0[1] * g.z + E1[1] * g.w, E0[2] * g.z + E1[2] * g.w);
+        return;
+    }
+    int b = id - dm.T;
+    if (b >= dm.m) return;
+    double dq[3] = {0, 0, 0};
+    for (int k = dm.bptr[b]; k < dm.bptr[b + 1]; ++k) {
+        d4 zz = ld(z + dm.bidx[k]);
+        double l = dm.bval[k];
+        dq[0] += l * zz.x; dq[1] += l * zz.y; dq[2] += l * zz.z;
+    }
+    d4 q = ld(ad.bq + b);
+    double qd = q.x * dq[0] + q.y * dq[1] + q.z * dq[2];
+    double w = h2 * dm.wb[b];
+    double k1 = 1.0 - q.w;
+    st(bu + b, w * (k1 * dq[0] + q.w * qd * q.x), w * (k1 * dq[1] + q.w * qd * q.y),
+       w * (k1 * dq[2] + q.w * qd * q.z));
+}
+
+// Gather of the element pass.  mode 0: out = Pi_B (H z)  (free nodes)
+//                               mode 1: out = w - Pi_B (H z)
+//                               mode 2: out = w - H z (no projection; free nodes)
+//                               mode 3: out = element part only (all m nodes)
+__global__ void k_adj_gather(DevMesh dm, AdjDev ad, int mode, const d4* __restrict__ z,
+                             const d4* __restrict__ c1, const d4* __restrict__ c2,
+                             const d4* __restrict__ bu, const d4* __restrict__ w, d4* __restrict__ out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int n = (mode == 3) ? dm.m : dm.m_free;
+    if (i >= n) return;
+    double r0 = 0, r1 = 0, r2 = 0;
+    for (int k = dm.iptr[i]; k < dm.iptr[i + 1]; ++k) {
+        int e = dm.iidx[k];
+        int t = e / 3, a = e - 3 * t;
+        if (a == 1) {
+            d4 c = ld(c1 + t);
+            r0 += c.x; r1 += c.y; r2 += c.z;
+        } else if (a == 2) {
+            d4 c = ld(c2 + t);
+            r0 += c.x; r1 += c.y; r2 += c.z;
+        } else {
+            d4 ca = ld(c1 + t), cb = ld(c2 + t);
+            r0 -= ca.x + cb.x; r1 -= ca.y + cb.y; r2 -= ca.z + cb.z;
+        }
+    }
+    for (int k = dm.tbptr[i]; k < dm.tbptr[i + 1]; ++k) {
+        double l = dm.tbval[k];
+        d4 u = ld(bu + dm.tbidx[k]);
+        r0 += l * u.x; r1 += l * u.y; r2 += l * u.z;
+    }
+    if (mode == 3) {
+        st(out + i, r0, r1, r2);
+        return;
+    }
+    d4 zi = ld(z + i);
+    double mi = dm.mass[i];
+    r0 += mi * zi.x; r1 += mi * zi.y; r2 += mi * zi.z;
+    int type = ad.type[i];
+    if (type == 2) {
+        d4 sl = ld(ad.slip + i);
+        d4 nb = ld(ad.nb + i);
+        double th[3] = {sl.x, sl.y, sl.z};
+        double n[3] = {nb.x, nb.y, nb.z};
+        double bh[3] = {n[1] * th[2] - n[2] * th[1], n[2] * th[0] - n[0] * th[2], n[0] * th[1] - n[1] * th[0]};
+        double bz = sl.w * (bh[0] * zi.x + bh[1] * zi.y + bh[2] * zi.z);
+        r0 += bz * bh[0]; r1 += bz * bh[1]; r2 += bz * bh[2];
+        if (mode != 2) {
+            double nr = n[0] * r0 + n[1] * r1 + n[2] * r2;
+            r0 -= nr * n[0]; r1 -= nr * n[1]; r2 -= nr * n[2];
+        }
+    } else if (type == 1 && mode != 2) {
+        r0 = r1 = r2 = 0.0;
+    }
+    if (mode >= 1) {
+        d4 wi = ld(w + i);
+        r0 = wi.x - r0; r1 = wi.y - r1; r2 = wi.z - r2;
+        if (type == 1 && mode == 1) r0 = r1 = r2 = 0.0;
+    }
+    st(out + i, r0, r1, r2);
+}
+
+// out = base + D+ w  (base may be null)
+__global__ void k_adj_dplus(int n, const d4* __restrict__ dinv, const d4* __restrict__ base,
+                            const d4* __restrict__ w, d4* __restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    d4 a = ld(dinv + 3 * j), b = ld(dinv + 3 * j + 1), c = ld(dinv + 3 * j + 2), x = ld(w + j);
+    double o0 = a.x * x.x + a.y * x.y + a.z * x.z;
+    double o1 = b.x * x.x + b.y * x.y + b.z * x.z;
+    double o2 = c.x * x.x + c.y * x.y + c.z * x.z;
+    if (base) {
+        d4 bb = ld(base + j);
+        o0 += bb.x; o1 += bb.y; o2 += bb.z;
+    }
+    st(out + j, o0, o1, o2);
+}
+
+// out = base + S_C (L^-T y): backward substitution followed by the projection onto C^T z = 0.
+__global__ void k_adj_solve_bwd(DevMesh dm, AdjDev ad, const d4* __restrict__ y, const d4* __restrict__ base,
+                                d4* __restrict__ out) {
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= dm.m_free) return;
+    int lane = threadIdx.x & 31;
+    double s0 = 0, s1 = 0, s2 = 0;
+    for (int k = dm.kptr[row] + lane; k < dm.kptr[row + 1]; k += 32) {
+        double a = dm.kval[k];
+        d4 u = ld(y + dm.kidx[k]);
+        s0 += a * u.x; s1 += a * u.y; s2 += a * u.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane != 0) return;
+    int type = ad.type[row];
+    if (type == 1) {
+        s0 = s1 = s2 = 0.0;
+    } else if (type == 2) {
+        d4 sl = ld(ad.slip + row), nb = ld(ad.nb + row);
+        double cz = (nb.x - ad.mu * sl.x) * s0 + (nb.y - ad.mu * sl.y) * s1 + (nb.z - ad.mu * sl.z) * s2;
+        s0 -= cz * nb.x; s1 -= cz * nb.y; s2 -= cz * nb.z;
+    }
+    d4 bb = ld(base + row);
+    st(out + row, bb.x + s0, bb.y + s1, bb.z + s2);
+}
+
+// ----------------------------------------------------------------- Krylov helpers
+
+constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
+constexpr int RED_THREADS = 256;
+
+// partial[j * RED_BLOCKS + blk] = sum over this block's chunk of V_j . w
+__global__ void k_mdot(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ w, long n,
+                       double* __restrict__ partial) {
+    __shared__ double sh[RED_THREADS / 32];
+    long chunk = (n + gridDim.x - 1) / gridDim.x;
+    long lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
+    for (int j = 0; j < nvec; ++j) {
+        const double* v = V + j * ldv;
+        double s = 0.0;
+        for (long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += v[i] * w[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < RED_THREADS / 32; ++q) t += sh[q];
+            partial[j * gridDim.x + blockIdx.x] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[j] = sum_b partial[j * nb + b] in a fixed tree order (one block per j)
+__global__ void k_reduce(const double* __restrict__ partial, int nb, double* __restrict__ out) {
+    __shared__ double sh[RED_THREADS];
+    int j = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[j * nb + b];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[j] = sh[0];
+}
+
+// w[i] -= sum_j V_j[i] c[j]   (c on device)
+__global__ void k_vupdate(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ c,
+                          double* __restrict__ w, long n, double sign) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int j = 0; j < nvec; ++j) s += V[j * ldv + i] * c[j];
+    w[i] += sign * s;
+}
+
+__global__ void k_scale(const double* __restrict__ a, double s, double* __restrict__ out, long n) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[i] * s;
+}
+
+__global__ void k_axpby(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
+                        double* __restrict__ out, long n) {
+    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * x[i] + b * y[i];
+}
+
+// ----------------------------------------------------------------- gradient outputs
+
+__device__ void normal_jacobian(const DevParams& P, int o, const double x[3], double Dn[9]) {
+    for (int q = 0; q < 9; ++q) Dn[q] = 0.0;
+    int kind = P.kind[o];
+    if (kind == DC_PLANE) return;
+    const double* p = P.op[o];
+    double c[3];
+    double e[3] = {0, 0, 0};
+    bool axis = false;
+    if (kind == DC_SPHERE) {
+        c[0] = p[0]; c[1] = p[1]; c[2] = p[2];
+    } else {
+        double ab[3] = {p[3] - p[0], p[4] - p[1], p[5] - p[2]};
+        double L2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+        double t = ((x[0] - p[0]) * ab[0] + (x[1] - p[1]) * ab[1] + (x[2] - p[2]) * ab[2]) / L2;
+        if (t <= 0.0) {
+            c[0] = p[0]; c[1] = p[1]; c[2] = p[2];
+        } else if (t >= 1.0) {
+            c[0] = p[3]; c[1] = p[4]; c[2] = p[5];
+        } else {
+            for (int k = 0; k < 3; ++k) c[k] = p[k] + t * ab[k];
+            double L = sqrt(L2);
+            for (int k = 0; k < 3; ++k) e[k] = ab[k] / L;
+            axis = true;
+        }
+    }
+    double d[3] = {x[0] - c[0], x[1] - c[1], x[2] - c[2]};
+    double r = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    double n[3] = {d[0] / r, d[1] / r, d[2] / r};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double v = (a == b ? 1.0 : 0.0) - n[a] * n[b];
+            if (axis) v -= e[a] * e[b];
+            Dn[3 * a + b] = v / r;
+        }
+}
+
+// dL/dx_n = gx - E/h - contact terms (all m nodes); dL/dv_n = M z (free nodes).
+// E = h^2 grad^2 W z, resid = g - H z (free nodes; gives the multipliers eta).
+__global__ void k_adj_outputs(DevMesh dm, AdjDev ad, DevParams P, const d4* __restrict__ z,
+                              const d4* __restrict__ E, const d4* __restrict__ resid, const d4* __restrict__ x_n,
+                              const d4* __restrict__ v1, const d4* __restrict__ gx, d4* __restrict__ gx_out,
+                              d4* __restrict__ gv_out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= dm.m) return;
+    const double h = ad.h;
+    d4 g = ld(gx + j), e = ld(E + j);
+    double o[3] = {g.x - e.x / h, g.y - e.y / h, g.z - e.z / h};
+    if (j >= dm.m_free) {
+        st(gx_out + j, o[0], o[1], o[2]);
+        st(gv_out + j, 0.0, 0.0, 0.0);
+        return;
+    }
+    d4 zj = ld(z + j);
+    double mj = dm.mass[j];
+    st(gv_out + j, mj * zj.x, mj * zj.y, mj * zj.z);
+    int type = ad.type[j];
+    if (type != 0) {
+        int ob = ad.contact[j];
+        d4 xn = ld(x_n + j), nb = ld(ad.nb + j), r = ld(resid + j);
+        double x[3] = {xn.x, xn.y, xn.z}, n[3] = {nb.x, nb.y, nb.z};
+        double beta = nb.w;
+        double Dn[9];
+        normal_jacobian(P, ob, x, Dn);   // symmetric
+        if (type == 1) {
+            // G_j = v_j + beta n: dG/dx_n = beta Dn + n n^T / h; eta_j = r_j
+            double psi[3] = {r.x, r.y, r.z};
+            double npsi = n[0] * psi[0] + n[1] * psi[1] + n[2] * psi[2];
+            for (int a = 0; a < 3; ++a) {
+                double s = 0;
+                for (int b = 0; b < 3; ++b) s += Dn[3 * b + a] * psi[b];
+                o[a] -= beta * s + n[a] * npsi / h;
+            }
+        } else {
+            // slip: eta_j = n . r_j; G_j = n.v_j + beta; F_j has -h f_N (n - mu t)
+            double psi = n[0] * r.x + n[1] * r.y + n[2] * r.z;
+            d4 sl = ld(ad.slip + j), vv = ld(v1 + j), ff = ld(ad.f + j);
+            double th[3] = {sl.x, sl.y, sl.z};
+            double v[3] = {vv.x, vv.y, vv.z};
+            double fN = ff.x * n[0] + ff.y * n[1] + ff.z * n[2];
+            double vn = n[0] * v[0] + n[1] * v[1] + n[2] * v[2];
+            double uT[3] = {v[0] - vn * n[0], v[1] - vn * n[1], v[2] - vn * n[2]};
+            double nt = sqrt(uT[0] * uT[0] + uT[1] * uT[1] + uT[2] * uT[2]);
+            // dPiv = -((n.v) I + n v^T) Dn ; Dt = (I - t t^T) dPiv / |u_T|
+            double M1[9], Dt[9];
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0;
+                    for (int c = 0; c < 3; ++c) s += ((a == c ? vn : 0.0) + n[a] * v[c]) * Dn[3 * c + b];
+                    M1[3 * a + b] = -s;
+                }
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) {
+                    double s = 0;
+                    for (int c = 0; c < 3; ++c) s += ((a == c ? 1.0 : 0.0) - th[a] * th[c]) * M1[3 * c + b];
+                    Dt[3 * a + b] = s / nt;
+                }
+            double zz[3] = {zj.x, zj.y, zj.z};
+            for (int a = 0; a < 3; ++a) {
+                double s = 0, s2 = 0;
+                for (int b = 0; b < 3; ++b) {
+                    s += (Dn[3 * b + a] - P.mu * Dt[3 * b + a]) * zz[b];
+                    s2 += Dn[3 * b + a] * v[b];
+                }
+                o[a] += h * fN * s;
+                o[a] -= (s2 + n[a] / h) * psi;
+            }
+        }
+    }
+    st(gx_out + j, o[0], o[1], o[2]);
+}
+
+// Per-element parameter-gradient terms, reduced per block:
+// part[0][blk] = -h sum_t area_t <A_t z, A_t x - R_t>, part[1][blk] = -h sum_b a_b <l_b z, q_b - p_b>,
+// part[2][blk] = -h sum_slip f_N (t . z_j).
+__global__ void k_adj_param_terms(DevMesh dm, AdjDev ad, const d4* __restrict__ z, const d4* __restrict__ x1,
+                                  double* __restrict__ part) {
+    __shared__ double sh[3][RED_THREADS / 32];
+    const double h = ad.h;
+    double s_ks = 0.0, s_kb = 0.0, s_mu = 0.0;
+    long total = (long)dm.T + dm.m + dm.m_free;
+    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
+        if (id < dm.T) {
+            int t = (int)id;
+            int4 tr = dm.tri[t];
+            d4 g = ld(dm.G + t);
+            d4 a = ld(x1 + tr.x), b = ld(x1 + tr.y), c = ld(x1 + tr.z);
+            d4 za = ld(z + tr.x), zb = ld(z + tr.y), zc = ld(z + tr.z);
+            d4 A0 = ld(ad.tr0 + t), A1 = ld(ad.tr1 + t);
+            double acc = 0;
+            double xe1[3] = {b.x - a.x, b.y - a.y, b.z - a.z}, xe2[3] = {c.x - a.x, c.y - a.y, c.z - a.z};
+            double ze1[3] = {zb.x - za.x, zb.y - za.y, zb.z - za.z}, ze2[3] = {zc.x - za.x, zc.y - za.y, zc.z - za.z};
+            double R0[3] = {A0.x, A0.y, A0.z}, R1[3] = {A1.x, A1.y, A1.z};
+            for (int k = 0; k < 3; ++k) {
+                double F0 = xe1[k] * g.x + xe2[k] * g.z, F1 = xe1[k] * g.y + xe2[k] * g.w;
+                double Z0 = ze1[k] * g.x + ze2[k] * g.z, Z1 = ze1[k] * g.y + ze2[k] * g.w;
+                acc += Z0 * (F0 - R0[k]) + Z1 * (F1 - R1[k]);
+            }
+            s_ks -= h * dm.area[t] * acc;
+        } else if (id < (long)dm.T + dm.m) {
+            int b = (int)(id - dm.T);
+            double q[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
+            for (int k = dm.bptr[b]; k < dm.bptr[b + 1]; ++k) {
+                d4 x = ld(x1 + dm.bidx[k]), zz = ld(z + dm.bidx[k]);
+                double l = dm.bval[k];
+                q[0] += l * x.x; q[1] += l * x.y; q[2] += l * x.z;
+                dq[0] += l * zz.x; dq[1] += l * zz.y; dq[2] += l * zz.z;
+            }
+            double s = dm.sb[b], p[3] = {0, 0, 0};
+            if (s > 0.0) {
+                double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+                if (nq > 1e-14 * s) {
+                    for (int k = 0; k < 3; ++k) p[k] = s * q[k] / nq;
+                } else {
+                    d4 qr = ld(dm.qrest + b);
+                    p[0] = qr.x; p[1] = qr.y; p[2] = qr.z;
+                }
+            }
+            s_kb -= h * dm.abar[b] * (dq[0] * (q[0] - p[0]) + dq[1] * (q[1] - p[1]) + dq[2] * (q[2] - p[2]));
+        } else {
+            int j = (int)(id - dm.T - dm.m);
+            if (ad.type[j] == 2) {
+                d4 sl = ld(ad.slip + j), nb = ld(ad.nb + j), ff = ld(ad.f + j), zj = ld(z + j);
+                double fN = ff.x * nb.x + ff.y * nb.y + ff.z * nb.z;
+                s_mu -= h * fN * (sl.x * zj.x + sl.y * zj.y + sl.z * zj.z);
+            }
+        }
+    }
+    double v[3] = {s_ks, s_kb, s_mu};
+    for (int q = 0; q < 3; ++q) {
+        double s = v[q];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        double t = 0.0;
+        for (int k = 0; k < RED_THREADS / 32; ++k) t += sh[threadIdx.x][k];
+        part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+    }
+}
+
+// acc[q] += sum_b part[q * nb + b] (fixed order, one thread per parameter)
+__global__ void k_param_accumulate(const double* __restrict__ part, int nb, double* __restrict__ acc) {
+    int q = threadIdx.x;
+    if (q >= 3) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += part[q * nb + b];
+    acc[q] += s;
+}
+
+__global__ void k_add_ext(d4* __restrict__ g, const double* __restrict__ ext, const int* __restrict__ int2ext,
+                          int m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int e = int2ext[i];
+    d4 a = ld(g + i);
+    st(g + i, a.x + ext[3 * e], a.y + ext[3 * e + 1], a.z + ext[3 * e + 2]);
+}
+
+// rhs = Pi_B (gv + h gx) on free nodes
+__global__ void k_adj_rhs(DevMesh dm, AdjDev ad, const d4* __restrict__ gx, const d4* __restrict__ gv,
+                          d4* __restrict__ g, d4* __restrict__ rhs) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= dm.m_free) return;
+    d4 a = ld(gx + j), b = ld(gv + j);
+    double r[3] = {b.x + ad.h * a.x, b.y + ad.h * a.y, b.z + ad.h * a.z};
+    st(g + j, r[0], r[1], r[2]);
+    int type = ad.type[j];
+    if (type == 1) {
+        r[0] = r[1] = r[2] = 0.0;
+    } else if (type == 2) {
+        d4 nb = ld(ad.nb + j);
+        double nr = nb.x * r[0] + nb.y * r[1] + nb.z * r[2];
+        r[0] -= nr * nb.x; r[1] -= nr * nb.y; r[2] -= nr * nb.z;
+    }
+    st(rhs + j, r[0], r[1], r[2]);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers
+
+void adj_setup(const DevMesh& dm, const AdjDev& ad, const d4* x1, const d4* v1, cudaStream_t s) {
+    k_adj_setup_tri<<<nblk(dm.T, 128), 128, 0, s>>>(dm, x1, ad.tr0, ad.tr1, ad.tr2);
+    k_adj_setup_bend<<<nblk(dm.m, 128), 128, 0, s>>>(dm, x1, ad.bq);
+    k_adj_setup_node<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, ad, v1);
+}
+void adj_rhs(const DevMesh& dm, const AdjDev& ad, const d4* gx, const d4* gv, d4* g, d4* rhs, cudaStream_t s) {
+    k_adj_rhs<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, ad, gx, gv, g, rhs);
+}
+void adj_apply_H(const DevMesh& dm, const AdjDev& ad, int mode, const d4* z, const d4* w, d4* out, cudaStream_t s) {
+    k_adj_elem<<<nblk((long)dm.T + dm.m, 128), 128, 0, s>>>(dm, ad, z, ad.c1, ad.c2, ad.bu);
+    int n = (mode == 3) ? dm.m : dm.m_free;
+    k_adj_gather<<<nblk(n, 128), 128, 0, s>>>(dm, ad, mode, z, ad.c1, ad.c2, ad.bu, w, out);
+}
+void adj_dplus(const DevMesh& dm, const AdjDev& ad, const d4* base, const d4* w, d4* out, cudaStream_t s) {
+    k_adj_dplus<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm.m_free, ad.dinv, base, w, out);
+}
+void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytmp, const d4* base, d4* out,
+                       cudaStream_t s) {
+    launch_solve_fwd(dm, r, ytmp, s);
+    k_adj_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, ad, ytmp, base, out);
+}
+void adj_mdot(const double* V, long ldv, int nvec, const double* w, long n, double* partial, double* out,
+              cudaStream_t s) {
+    k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ldv, nvec, w, n, partial);
+    k_reduce<<<nvec, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, out);
+}
+void adj_vupdate(const double* V, long ldv, int nvec, const double* c, double* w, long n, double sign,
+                 cudaStream_t s) {
+    k_vupdate<<<nblk(n, 256), 256, 0, s>>>(V, ldv, nvec, c, w, n, sign);
+}
+void adj_scale(const double* a, double sc, double* out, long n, cudaStream_t s) {
+    k_scale<<<nblk(n, 256), 256, 0, s>>>(a, sc, out, n);
+}
+void adj_axpby(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s) {
+    k_axpby<<<nblk(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
+}
+void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
+                 const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
+                 cudaStream_t s) {
+    k_adj_outputs<<<nblk(dm.m, 128), 128, 0, s>>>(dm, ad, P, z, E, resid, x_n, v1, gx, gx_out, gv_out);
+}
+void adj_params(const DevMesh& dm, const AdjDev& ad, const d4* z, const d4* x1, double* part, double* acc,
+                cudaStream_t s) {
+    k_adj_param_terms<<<RED_BLOCKS, RED_THREADS, 0, s>>>(dm, ad, z, x1, part);
+    k_param_accumulate<<<1, 32, 0, s>>>(part, RED_BLOCKS, acc);
+}
+void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s) {
+    k_add_ext<<<nblk(m, 256), 256, 0, s>>>(g, ext, int2ext, m);
+}
+int adj_red_blocks() { return RED_BLOCKS; }

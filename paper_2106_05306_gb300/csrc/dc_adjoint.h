@@ -1,0 +1,43 @@
+// Device view and launchers of the adjoint step (see dc_adjoint.cu).
+#pragma once
+
+#include "dc_internal.h"
+
+struct AdjDev {
+    double h, mu;
+    d4* tr0;              // [T] (R col 0, S^-1_00)
+    d4* tr1;              // [T] (R col 1, S^-1_01)
+    d4* tr2;              // [T] (S^-1_11, 1/tr S, -, -)
+    d4* bq;               // [m] (q_hat, s/|q|)
+    d4* dinv;             // [3 m_free] rows of the constrained block inverse D+
+    d4* slip;             // [m_free] (t_hat, h mu f_N / |u_T|) for slip nodes
+    int* type;            // [m_free] 0 free / take-off, 1 stick, 2 slip
+    const int* contact;   // step record: obstacle index or -1
+    const int* case_;     // step record: 0 take-off, 1 stick, 2 slip
+    const d4* nb;         // step record: (normal, beta)
+    const d4* f;          // step record: contact force
+    d4* c1;               // element-pass scratch [T]
+    d4* c2;               // [T]
+    d4* bu;               // [m]
+};
+
+void adj_setup(const DevMesh& dm, const AdjDev& ad, const d4* x1, const d4* v1, cudaStream_t s);
+void adj_rhs(const DevMesh& dm, const AdjDev& ad, const d4* gx, const d4* gv, d4* g, d4* rhs, cudaStream_t s);
+// mode 0: out = Pi_B H z; 1: out = w - Pi_B H z; 2: out = w - H z; 3: out = h^2 grad^2 W z on all nodes
+void adj_apply_H(const DevMesh& dm, const AdjDev& ad, int mode, const d4* z, const d4* w, d4* out, cudaStream_t s);
+void adj_dplus(const DevMesh& dm, const AdjDev& ad, const d4* base, const d4* w, d4* out, cudaStream_t s);
+void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytmp, const d4* base, d4* out,
+                       cudaStream_t s);
+void adj_mdot(const double* V, long ldv, int nvec, const double* w, long n, double* partial, double* out,
+              cudaStream_t s);
+void adj_vupdate(const double* V, long ldv, int nvec, const double* c, double* w, long n, double sign,
+                 cudaStream_t s);
+void adj_scale(const double* a, double sc, double* out, long n, cudaStream_t s);
+void adj_axpby(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s);
+void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
+                 const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
+                 cudaStream_t s);
+void adj_params(const DevMesh& dm, const AdjDev& ad, const d4* z, const d4* x1, double* part, double* acc,
+                cudaStream_t s);
+void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s);
+int adj_red_blocks();

@@ -1,0 +1,131 @@
+// Internal declarations shared by the host setup, the kernels and the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/dc.h"
+
+// A node vector record: (x, y, z, pad).  Node vectors are read by index (by
+// triangles, bending stencils and the solve), so one 32-byte record is a single
+// sector per gather.
+struct __align__(32) d4 {
+    double x, y, z, w;
+};
+
+// ---------------------------------------------------------------- host setup
+
+struct HostMesh {
+    int m = 0, T = 0, m_free = 0;
+    // node numbering: internal index = position in (ND order of free nodes, then pins)
+    std::vector<int> ext2int, int2ext;
+    std::vector<double> rest;          // [m][3], internal order
+    // triangles (internal node indices)
+    std::vector<int> tri;              // [T][3]
+    std::vector<double> G;             // [T][4]: rows 1 and 2 of G = E Dm^-1 (row 0 = -(row1+row2))
+    std::vector<double> area;          // [T]
+    // bending stencil rows l_b (CSR over vertices, internal indices, self included)
+    std::vector<int> bptr, bidx;
+    std::vector<double> bval;
+    std::vector<double> abar, sb;      // [m]
+    std::vector<double> qrest;         // [m][3]
+    // ND tree levels per free node (depth of its separator / leaf)
+    std::vector<int> nd_level;
+    int nd_depth = 0;
+};
+
+// Builds rest operators and the nested-dissection ordering.  Returns "" or an error.
+std::string dc_build_mesh(HostMesh& hm, int n_nodes, const double* rest_pos, int n_tris,
+                          const int32_t* tris, int n_pins, const int32_t* pins);
+
+// Sparse lower-triangular factor in CSC (row indices ascending, diagonal first).
+struct HostFactor {
+    int n = 0;
+    std::vector<int> colptr, rowidx;
+    std::vector<double> val;
+    std::vector<int> parent;           // elimination tree
+    // L^-1 as CSR by rows (forward solve) and L^-T as CSR by rows (backward solve)
+    std::vector<int> fptr, fidx;
+    std::vector<double> fval;
+    std::vector<int> bptr, bidx;
+    std::vector<double> bval;
+};
+
+// Assembles P_ff (free nodes, internal order) and factorises it.  Returns
+// DC_OK, DC_ERR_NOT_SPD or DC_ERR_INVALID with a message in err.
+dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vector<double>& mass,
+                          HostFactor& hf, std::string& err);
+
+// ---------------------------------------------------------------- device views
+
+struct DevMesh {
+    int m, m_free, T;
+    const int4* tri;                   // [T] (i0, i1, i2, 0)
+    const d4* G;                       // [T] (g1x, g1y, g2x, g2y)
+    const double* wt;                  // [T] k_stretch * area
+    const double* area;                // [T]
+    const int* bptr;                   // bending stencil rows (CSR over m vertices)
+    const int* bidx;
+    const double* bval;
+    const double* wb;                  // [m] k_bend * abar
+    const double* abar;                // [m]
+    const double* sb;                  // [m]
+    const d4* qrest;                   // [m]
+    const double* mass;                // [m]
+    const int* iptr;                   // node -> triangle incidences (t*3 + a)
+    const int* iidx;
+    const int* tbptr;                  // node j -> bending rows b containing j, with l_bj
+    const int* tbidx;
+    const double* tbval;
+    const int* fptr;                   // L^-1 rows (CSR), rows 0..m_free-1
+    const int* fidx;
+    const double* fval;
+    const int* kptr;                   // L^-T rows (CSR)
+    const int* kidx;
+    const double* kval;
+};
+
+// Per-step record kept for the adjoint: the contact state of the step.
+// contact[j]: -1 = none, else obstacle index; case_[j] in {0,1,2}.
+struct DevParams {
+    double k_stretch, k_bend, mu, h;
+    double g[3];
+    double delta;
+    int n_obst;
+    int kind[DC_MAX_OBSTACLES];
+    double op[DC_MAX_OBSTACLES][7];
+};
+
+// ---------------------------------------------------------------- kernel launchers
+// (all asynchronous on the given stream)
+
+void launch_permute_in(const double* ext, d4* out, const int* ext2int, int m, cudaStream_t s);
+void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, cudaStream_t s);
+void launch_zero_pins(d4* v, int m_free, int m, cudaStream_t s);
+
+// contact detection + per-step constants (Sec. 3.2, reading R4)
+void launch_detect(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v_n,
+                   int* contact, d4* normal_beta, d4* f, d4* ind, cudaStream_t s);
+// local step over triangles and bending vertices (Sec. 3.1)
+void launch_local(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v,
+                  d4* tri_c1, d4* tri_c2, d4* bend_u, cudaStream_t s);
+// right-hand side gather: b = M (v_n + h g) + sum contributions + h f
+void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, const d4* tri_c1,
+                       const d4* tri_c2, const d4* bend_u, const d4* f, d4* b, cudaStream_t s);
+// forward solve y = L^-1 b
+void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s);
+// backward solve out = L^-T y; mode 0: plain output; mode 1: output then per-node
+// Signorini-Coulomb update (writes v, f, case); mode 2: compliance c_j = h * out_j.x
+void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode,
+                      const int* contact, const d4* normal_beta, const double* c, d4* f,
+                      int* case_, double* c_out, cudaStream_t s);
+void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v,
+                     d4* x_np1, cudaStream_t s);
+void launch_count_cases(const int* contact, const int* case_, int m_free,
+                        unsigned long long* counters, cudaStream_t s);
+
+// ---------------------------------------------------------------- adjoint
+struct AdjStep;   // defined in dc_adjoint.cu

@@ -1,0 +1,350 @@
+// Forward-step kernels of libdc (FP64, sm_103a).
+//
+// One PD iteration (Sec. 3.1-3.2) is four launches:
+//   local   -- per triangle: polar projection of F (stretch) and its right-hand
+//              side contribution; per vertex: bending projection;
+//   gather  -- per free node: b = M (v_n + h g) + h sum_i w_i A_i^T (p_i - A_i x_n)
+//              + h f   (Eq. pd_velocity / pd_velocity_with_contact, expanded so
+//              that the O(h^2 |L x|) terms never cancel);
+//   solve_fwd / solve_bwd -- v_half = L^-T L^-1 b with the explicit inverse
+//              factor, and the per-node Signorini-Coulomb update fused into the
+//              backward sweep (Eq. contact_all).
+// Every reduction is a fixed-order gather (no atomics), so a launch is bitwise
+// repeatable and independent of what else runs on the GPU.
+#include "dc_internal.h"
+
+namespace {
+
+__device__ __forceinline__ d4 ld(const d4* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = q[0], b = q[1];
+    d4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+__device__ __forceinline__ void st(d4* p, double x, double y, double z, double w = 0.0) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, w);
+}
+
+// Signed distance and its gradient for one analytic obstacle (reading R4).
+__device__ double sdf(const DevParams& P, int o, double x, double y, double z, double* n) {
+    const double* q = P.op[o];
+    if (P.kind[o] == DC_PLANE) {
+        if (n) { n[0] = q[0]; n[1] = q[1]; n[2] = q[2]; }
+        return q[0] * x + q[1] * y + q[2] * z - q[3];
+    }
+    double cx, cy, cz, r;
+    if (P.kind[o] == DC_SPHERE) {
+        cx = q[0]; cy = q[1]; cz = q[2]; r = q[3];
+    } else {
+        double abx = q[3] - q[0], aby = q[4] - q[1], abz = q[5] - q[2];
+        double t = ((x - q[0]) * abx + (y - q[1]) * aby + (z - q[2]) * abz) /
+                   (abx * abx + aby * aby + abz * abz);
+        t = fmin(fmax(t, 0.0), 1.0);
+        cx = q[0] + t * abx; cy = q[1] + t * aby; cz = q[2] + t * abz; r = q[6];
+    }
+    double dx = x - cx, dy = y - cy, dz = z - cz;
+    double d = sqrt(dx * dx + dy * dy + dz * dz);
+    if (n) { n[0] = dx / d; n[1] = dy / d; n[2] = dz / d; }
+    return d - r;
+}
+
+__global__ void k_permute_in(const double* __restrict__ ext, d4* __restrict__ out,
+                             const int* __restrict__ int2ext, int m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int e = int2ext[i];
+    st(out + i, ext[3 * e], ext[3 * e + 1], ext[3 * e + 2]);
+}
+
+__global__ void k_permute_out(const d4* __restrict__ in, double* __restrict__ ext,
+                              const int* __restrict__ int2ext, int m) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    int e = int2ext[i];
+    d4 a = ld(in + i);
+    ext[3 * e] = a.x; ext[3 * e + 1] = a.y; ext[3 * e + 2] = a.z;
+}
+
+__global__ void k_zero_range(d4* v, int lo, int hi) {
+    int i = lo + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < hi) st(v + i, 0.0, 0.0, 0.0);
+}
+
+// Contact set, normal and bias for the step (reading R4); resets the impulse.
+__global__ void k_detect(DevMesh dm, DevParams P, const d4* __restrict__ x_n, const d4* __restrict__ v_n,
+                         int* __restrict__ contact, d4* __restrict__ nb, d4* __restrict__ f,
+                         d4* __restrict__ ind) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dm.m_free) return;
+    d4 x = ld(x_n + i), v = ld(v_n + i);
+    double px = x.x + P.h * v.x, py = x.y + P.h * v.y, pz = x.z + P.h * v.z;
+    double best = 1e300;
+    int bo = -1;
+    for (int o = 0; o < P.n_obst; ++o) {
+        double ph = sdf(P, o, px, py, pz, nullptr);
+        if (ph < best) { best = ph; bo = o; }
+    }
+    st(f + i, 0.0, 0.0, 0.0);
+    if (bo >= 0 && best <= P.delta) {
+        double n[3];
+        double ph0 = sdf(P, bo, x.x, x.y, x.z, n);
+        contact[i] = bo;
+        st(nb + i, n[0], n[1], n[2], ph0 / P.h);
+        st(ind + i, 1.0, 1.0, 1.0);
+    } else {
+        contact[i] = -1;
+        st(ind + i, 0.0, 0.0, 0.0);
+    }
+}
+
+// Closed-form polar factor R of a 3x2 F (reading R1):
+// S = (C + s I)/t, C = F^T F, s = sqrt(det C), t = sqrt(tr C + 2 s), R = F S^-1
+// = F adj(C + s I) / (s t).
+__device__ __forceinline__ void polar3x2(const double F[6], double R[6]) {
+    double c00 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+    double c01 = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
+    double c11 = F[3] * F[3] + F[4] * F[4] + F[5] * F[5];
+    double det = c00 * c11 - c01 * c01;
+    double is = rsqrt(det);
+    double s = det * is;
+    double it = rsqrt(c00 + c11 + 2.0 * s);
+    double k = is * it;
+    double a = (c11 + s) * k, b = -c01 * k, d = (c00 + s) * k;
+    // R[:,0] = a F0 + b F1 ; R[:,1] = b F0 + d F1
+    R[0] = a * F[0] + b * F[3]; R[1] = a * F[1] + b * F[4]; R[2] = a * F[2] + b * F[5];
+    R[3] = b * F[0] + d * F[3]; R[4] = b * F[1] + d * F[4]; R[5] = b * F[2] + d * F[5];
+}
+
+// Local step.  Threads [0, T): triangles; [T, T + m): bending vertices.
+__global__ void k_local(DevMesh dm, DevParams P, const d4* __restrict__ x_n, const d4* __restrict__ v,
+                        d4* __restrict__ c1, d4* __restrict__ c2, d4* __restrict__ bu) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    const double h = P.h;
+    if (id < dm.T) {
+        int4 tr = dm.tri[id];
+        d4 g = ld(dm.G + id);
+        double w = dm.wt[id] * h;
+        d4 x0 = ld(x_n + tr.x), x1 = ld(x_n + tr.y), x2 = ld(x_n + tr.z);
+        d4 v0 = ld(v + tr.x), v1 = ld(v + tr.y), v2 = ld(v + tr.z);
+        double e1[3] = {x1.x - x0.x, x1.y - x0.y, x1.z - x0.z};
+        double e2[3] = {x2.x - x0.x, x2.y - x0.y, x2.z - x0.z};
+        double f1[3] = {v1.x - v0.x, v1.y - v0.y, v1.z - v0.z};
+        double f2[3] = {v2.x - v0.x, v2.y - v0.y, v2.z - v0.z};
+        double Fn[6], F[6], R[6];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            Fn[c] = e1[c] * g.x + e2[c] * g.z;          // column 0
+            Fn[3 + c] = e1[c] * g.y + e2[c] * g.w;      // column 1
+            F[c] = Fn[c] + h * (f1[c] * g.x + f2[c] * g.z);
+            F[3 + c] = Fn[3 + c] + h * (f1[c] * g.y + f2[c] * g.w);
+        }
+        polar3x2(F, R);
+        double D[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) D[k] = w * (R[k] - Fn[k]);
+        st(c1 + id, D[0] * g.x + D[3] * g.y, D[1] * g.x + D[4] * g.y, D[2] * g.x + D[5] * g.y);
+        st(c2 + id, D[0] * g.z + D[3] * g.w, D[1] * g.z + D[4] * g.w, D[2] * g.z + D[5] * g.w);
+        return;
+    }
+    int b = id - dm.T;
+    if (b >= dm.m) return;
+    double qn[3] = {0, 0, 0}, qv[3] = {0, 0, 0};
+    for (int k = dm.bptr[b]; k < dm.bptr[b + 1]; ++k) {
+        int j = dm.bidx[k];
+        double l = dm.bval[k];
+        d4 xj = ld(x_n + j), vj = ld(v + j);
+        qn[0] += l * xj.x; qn[1] += l * xj.y; qn[2] += l * xj.z;
+        qv[0] += l * vj.x; qv[1] += l * vj.y; qv[2] += l * vj.z;
+    }
+    double q[3] = {qn[0] + h * qv[0], qn[1] + h * qv[1], qn[2] + h * qv[2]};
+    double s = dm.sb[b];
+    double p[3] = {0, 0, 0};
+    if (s > 0.0) {
+        double nq = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+        if (nq > 1e-14 * s) {
+            double k = s / nq;
+            p[0] = k * q[0]; p[1] = k * q[1]; p[2] = k * q[2];
+        } else {
+            d4 qr = ld(dm.qrest + b);
+            p[0] = qr.x; p[1] = qr.y; p[2] = qr.z;
+        }
+    }
+    double w = dm.wb[b] * h;
+    st(bu + b, w * (p[0] - qn[0]), w * (p[1] - qn[1]), w * (p[2] - qn[2]));
+}
+
+__global__ void k_gather_rhs(DevMesh dm, DevParams P, const d4* __restrict__ v_n, const d4* __restrict__ c1,
+                             const d4* __restrict__ c2, const d4* __restrict__ bu, const d4* __restrict__ f,
+                             d4* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dm.m_free) return;
+    d4 vn = ld(v_n + i);
+    double mi = dm.mass[i];
+    double r0 = mi * (vn.x + P.h * P.g[0]);
+    double r1 = mi * (vn.y + P.h * P.g[1]);
+    double r2 = mi * (vn.z + P.h * P.g[2]);
+    for (int k = dm.iptr[i]; k < dm.iptr[i + 1]; ++k) {
+        int e = dm.iidx[k];
+        int t = e / 3, a = e - 3 * t;
+        if (a == 1) {
+            d4 c = ld(c1 + t);
+            r0 += c.x; r1 += c.y; r2 += c.z;
+        } else if (a == 2) {
+            d4 c = ld(c2 + t);
+            r0 += c.x; r1 += c.y; r2 += c.z;
+        } else {
+            d4 ca = ld(c1 + t), cb = ld(c2 + t);
+            r0 -= ca.x + cb.x; r1 -= ca.y + cb.y; r2 -= ca.z + cb.z;
+        }
+    }
+    for (int k = dm.tbptr[i]; k < dm.tbptr[i + 1]; ++k) {
+        double l = dm.tbval[k];
+        d4 u = ld(bu + dm.tbidx[k]);
+        r0 += l * u.x; r1 += l * u.y; r2 += l * u.z;
+    }
+    d4 fi = ld(f + i);
+    st(b + i, r0 + P.h * fi.x, r1 + P.h * fi.y, r2 + P.h * fi.z);
+}
+
+// y_i = sum_k Linv(i,k) b_k, one warp per row, fixed lane order.
+__device__ __forceinline__ void warp_row(const int* __restrict__ ptr, const int* __restrict__ idx,
+                                         const double* __restrict__ val, const d4* __restrict__ in, int row,
+                                         double& s0, double& s1, double& s2) {
+    int lane = threadIdx.x & 31;
+    s0 = s1 = s2 = 0.0;
+    for (int k = ptr[row] + lane; k < ptr[row + 1]; k += 32) {
+        double a = val[k];
+        d4 u = ld(in + idx[k]);
+        s0 += a * u.x; s1 += a * u.y; s2 += a * u.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+}
+
+__global__ void k_solve_fwd(DevMesh dm, const d4* __restrict__ b, d4* __restrict__ y) {
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= dm.m_free) return;
+    double s0, s1, s2;
+    warp_row(dm.fptr, dm.fidx, dm.fval, b, row, s0, s1, s2);
+    if ((threadIdx.x & 31) == 0) st(y + row, s0, s1, s2);
+}
+
+// Per-node Signorini-Coulomb solve (Eq. contact_1-3, reading R5) in world
+// frame: v = vt + c f, u_N = n.v + beta, u_T = v - (n.v) n.
+__device__ __forceinline__ int coulomb(double mu, double c, const double n[3], double beta,
+                                       const double vt[3], double v[3], double f[3]) {
+    double vn = n[0] * vt[0] + n[1] * vt[1] + n[2] * vt[2];
+    double uN = vn + beta;
+    if (uN >= 0.0) {                                        // take off
+        v[0] = vt[0]; v[1] = vt[1]; v[2] = vt[2];
+        f[0] = f[1] = f[2] = 0.0;
+        return 0;
+    }
+    double uT[3] = {vt[0] - vn * n[0], vt[1] - vn * n[1], vt[2] - vn * n[2]};
+    double nt = sqrt(uT[0] * uT[0] + uT[1] * uT[1] + uT[2] * uT[2]);
+    if (nt <= mu * (-uN)) {                                 // stick
+        for (int k = 0; k < 3; ++k) {
+            v[k] = -beta * n[k];
+            f[k] = (v[k] - vt[k]) / c;
+        }
+        return 1;
+    }
+    double fN = -uN / c;                                    // slip
+    double ft = mu * fN / nt;
+    for (int k = 0; k < 3; ++k) {
+        f[k] = fN * n[k] - ft * uT[k];
+        v[k] = vt[k] + c * f[k];
+    }
+    return 2;
+}
+
+__global__ void k_solve_bwd(DevMesh dm, DevParams P, const d4* __restrict__ y, d4* __restrict__ out, int mode,
+                            const int* __restrict__ contact, const d4* __restrict__ nb,
+                            const double* __restrict__ cc, d4* __restrict__ f, int* __restrict__ case_,
+                            double* __restrict__ c_out) {
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= dm.m_free) return;
+    double s0, s1, s2;
+    warp_row(dm.kptr, dm.kidx, dm.kval, y, row, s0, s1, s2);
+    if ((threadIdx.x & 31) != 0) return;
+    if (mode == 2) {
+        c_out[row] = P.h * s0;
+        return;
+    }
+    if (mode == 1 && contact[row] >= 0) {
+        d4 q = ld(nb + row), fo = ld(f + row);
+        double c = cc[row];
+        double n[3] = {q.x, q.y, q.z};
+        double vt[3] = {s0 - c * fo.x, s1 - c * fo.y, s2 - c * fo.z};
+        double v[3], fn[3];
+        case_[row] = coulomb(P.mu, c, n, q.w, vt, v, fn);
+        st(f + row, fn[0], fn[1], fn[2]);
+        st(out + row, v[0], v[1], v[2]);
+        return;
+    }
+    st(out + row, s0, s1, s2);
+}
+
+__global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4* __restrict__ v,
+                           d4* __restrict__ x1) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m) return;
+    d4 a = ld(x_n + i), b = ld(v + i);
+    st(x1 + i, a.x + h * b.x, a.y + h * b.y, a.z + h * b.z);
+}
+
+__global__ void k_count_cases(const int* __restrict__ contact, const int* __restrict__ case_, int n,
+                              unsigned long long* counters) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || contact[i] < 0) return;
+    atomicAdd(counters + case_[i], 1ull);
+}
+
+inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
+
+}  // namespace
+
+void launch_permute_in(const double* ext, d4* out, const int* int2ext, int m, cudaStream_t s) {
+    k_permute_in<<<nblk(m, 256), 256, 0, s>>>(ext, out, int2ext, m);
+}
+void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, cudaStream_t s) {
+    k_permute_out<<<nblk(m, 256), 256, 0, s>>>(in, ext, int2ext, m);
+}
+void launch_zero_pins(d4* v, int m_free, int m, cudaStream_t s) {
+    if (m > m_free) k_zero_range<<<nblk(m - m_free, 256), 256, 0, s>>>(v, m_free, m);
+}
+void launch_detect(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v_n, int* contact,
+                   d4* nb, d4* f, d4* ind, cudaStream_t s) {
+    k_detect<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, P, x_n, v_n, contact, nb, f, ind);
+}
+void launch_local(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* c1, d4* c2,
+                  d4* bu, cudaStream_t s) {
+    k_local<<<nblk((long)dm.T + dm.m, 128), 128, 0, s>>>(dm, P, x_n, v, c1, c2, bu);
+}
+void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, const d4* c1, const d4* c2,
+                       const d4* bu, const d4* f, d4* b, cudaStream_t s) {
+    k_gather_rhs<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, P, v_n, c1, c2, bu, f, b);
+}
+void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
+    k_solve_fwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, b, y);
+}
+void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode, const int* contact,
+                      const d4* nb, const double* c, d4* f, int* case_, double* c_out, cudaStream_t s) {
+    k_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, P, y, out, mode, contact, nb, c, f, case_,
+                                                                c_out);
+}
+void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* x_np1,
+                     cudaStream_t s) {
+    k_finalize<<<nblk(dm.m, 256), 256, 0, s>>>(dm.m, P.h, x_n, v, x_np1);
+}
+void launch_count_cases(const int* contact, const int* case_, int m_free, unsigned long long* counters,
+                        cudaStream_t s) {
+    k_count_cases<<<nblk(m_free, 256), 256, 0, s>>>(contact, case_, m_free, counters);
+}
