@@ -69,7 +69,9 @@ typedef struct dc_params {
     int32_t adj_restart;     /* adjoint: GMRES restart length (<= 256)              */
     int32_t checkpoint_every;/* rollout: keep (x, v) every k steps (>= 1)           */
     int32_t n_obstacles;
-    int32_t pad_;
+    int32_t adj_precond;     /* adjoint preconditioner: 0 = per-step single-precision
+                                multifrontal LDL^T of the constrained matrix (default);
+                                1 = node-block inverse + projected P^-1 (no factorisation) */
     dc_obstacle obstacles[DC_MAX_OBSTACLES];
 } dc_params;
 

@@ -24,7 +24,7 @@ class dc_params(ctypes.Structure):
                 ("contact_margin", ctypes.c_double), ("adj_tol", ctypes.c_double),
                 ("n_pd_iters", ctypes.c_int32), ("adj_max_iters", ctypes.c_int32),
                 ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
-                ("n_obstacles", ctypes.c_int32), ("pad_", ctypes.c_int32),
+                ("n_obstacles", ctypes.c_int32), ("adj_precond", ctypes.c_int32),
                 ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
 
 

@@ -41,3 +41,12 @@ void adj_params(const DevMesh& dm, const AdjDev& ad, const d4* z, const d4* x1, 
                 cudaStream_t s);
 void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s);
 int adj_red_blocks();
+
+// Per-step multifrontal LDL^T preconditioner (dc_frontal.cu).
+size_t frontal_factor_smem(int max_f);
+size_t frontal_solve_smem(int max_f);
+cudaError_t frontal_configure(int max_f);
+void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
+                       int max_f, cudaStream_t s);
+void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, int max_f, int n_free,
+                     const d4* w, d4* out, cudaStream_t s);

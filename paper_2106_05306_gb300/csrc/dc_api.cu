@@ -35,7 +35,10 @@ struct dc_ctx {
     dc_params prm{};
     DevParams dp{};
     DevMesh dm{};
-    std::vector<void*> mesh_allocs, factor_allocs, work_allocs, ck_allocs, seg_allocs, adj_allocs;
+    std::vector<void*> mesh_allocs, factor_allocs, work_allocs, ck_allocs, seg_allocs, adj_allocs, front_allocs;
+    HostFronts fr;
+    FrontDev fdv{};
+    int nlev = 0;
     int* d_int2ext = nullptr;
     // forward work
     d4 *xa = nullptr, *va = nullptr, *xb = nullptr, *vb = nullptr, *v = nullptr, *b = nullptr, *y = nullptr;
@@ -238,6 +241,10 @@ void precond(dc_ctx* c, const d4* w, d4* out) {
     cudaStream_t s = c->stream;
     const DevMesh& dm = c->dm;
     const AdjDev& ad = c->ad;
+    if (c->prm.adj_precond == 0) {
+        frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, dm.m_free, w, out, s);
+        return;
+    }
     adj_dplus(dm, ad, nullptr, w, c->x1, s);
     adj_apply_H(dm, ad, 1, c->x1, w, c->r1, s);
     adj_solve_project(dm, ad, c->r1, c->ytmp, c->x1, c->x2, s);
@@ -373,6 +380,8 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, con
     ad.nb = r.nb;
     ad.f = r.f;
     adj_setup(c->dm, ad, x1, v1, s);
+    if (c->prm.adj_precond == 0)
+        frontal_factorize(c->dm, ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s);
     adj_rhs(c->dm, ad, c->gx, c->gv, c->g, c->rhs, s);
     int it = 0;
     double rel = 0.0;
@@ -534,7 +543,8 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
     if (!c || !p) return DC_ERR_INVALID;
     if (!finite_params(*p) || !(p->h > 0) || p->k_stretch < 0 || p->k_bend < 0 || !(p->density > 0) ||
         p->mu < 0 || p->n_pd_iters < 0 || p->n_obstacles < 0 || p->n_obstacles > DC_MAX_OBSTACLES ||
-        p->checkpoint_every < 1 || p->adj_max_iters < 1 || p->adj_restart < 1 || !(p->adj_tol > 0)) {
+        p->checkpoint_every < 1 || p->adj_max_iters < 1 || p->adj_restart < 1 || !(p->adj_tol > 0) ||
+        p->adj_precond < 0 || p->adj_precond > 1) {
         c->err = "dc_set_params: invalid or non-finite parameter";
         return DC_ERR_INVALID;
     }
@@ -614,6 +624,68 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
     c->dm.kptr = d_kptr;
     c->dm.kidx = d_kidx;
     c->dm.kval = d_kval;
+    // multifrontal structure for the adjoint preconditioner
+    HostFronts fr;
+    std::string fe = dc_build_fronts(hm, hf, fr);
+    if (!fe.empty()) {
+        c->err = "dc_set_params: " + fe;
+        return DC_ERR_INVALID;
+    }
+    int dev = 0, smem_optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (frontal_factor_smem(fr.max_f) > (size_t)smem_optin) {
+        c->err = "dc_set_params: the largest front (" + std::to_string(fr.max_f) +
+                 " unknowns) exceeds the shared memory of one CTA";
+        return DC_ERR_INVALID;
+    }
+    CK(frontal_configure(fr.max_f));
+    free_pool(c->front_allocs);
+    {
+        auto& F = c->front_allocs;
+        FrontDev fd{};
+        fd.S = fr.S;
+        fd.NP = (int)fr.pr_i.size();
+        fd.tau = (float)(1e-7 * hf.max_diag);
+        fd.pool_size = fr.pool_size;
+        int *d_begin, *d_f, *d_p, *d_uptr, *d_unode, *d_cptr, *d_child, *d_cmap, *d_lvl, *d_pi, *d_pj, *d_pld, *d_pcp,
+            *d_pcode;
+        long long *d_off, *d_acc_off, *d_pdst;
+        double* d_pcoef;
+        if ((s = upload(c, F, &d_begin, fr.begin)) || (s = upload(c, F, &d_f, fr.f)) || (s = upload(c, F, &d_p, fr.p)) ||
+            (s = upload(c, F, &d_off, fr.off)) || (s = upload(c, F, &d_acc_off, fr.acc_off)) ||
+            (s = upload(c, F, &d_uptr, fr.uptr)) || (s = upload(c, F, &d_unode, fr.unode)) ||
+            (s = upload(c, F, &d_cptr, fr.cptr)) || (s = upload(c, F, &d_child, fr.child)) ||
+            (s = upload(c, F, &d_cmap, fr.cmap)) || (s = upload(c, F, &d_lvl, fr.lvl_sn)) ||
+            (s = upload(c, F, &d_pi, fr.pr_i)) || (s = upload(c, F, &d_pj, fr.pr_j)) ||
+            (s = upload(c, F, &d_pdst, fr.pr_dst)) || (s = upload(c, F, &d_pld, fr.pr_ld)) ||
+            (s = upload(c, F, &d_pcp, fr.pr_cptr)) || (s = upload(c, F, &d_pcode, fr.pr_code)) ||
+            (s = upload(c, F, &d_pcoef, fr.pr_coef)) || (s = dalloc(c, F, &fd.pool, (size_t)fr.pool_size)) ||
+            (s = dalloc(c, F, &fd.acc, (size_t)fr.acc_size)) || (s = dalloc(c, F, &fd.rvec, 3 * (size_t)hm.m_free)) ||
+            (s = dalloc(c, F, &fd.zvec, 3 * (size_t)hm.m_free)) || (s = dalloc(c, F, &fd.xvec, 3 * (size_t)hm.m_free)))
+            return s;
+        fd.begin = d_begin;
+        fd.f = d_f;
+        fd.p = d_p;
+        fd.off = d_off;
+        fd.acc_off = d_acc_off;
+        fd.uptr = d_uptr;
+        fd.unode = d_unode;
+        fd.cptr = d_cptr;
+        fd.child = d_child;
+        fd.cmap = d_cmap;
+        fd.lvl_sn = d_lvl;
+        fd.pr_i = d_pi;
+        fd.pr_j = d_pj;
+        fd.pr_dst = d_pdst;
+        fd.pr_ld = d_pld;
+        fd.pr_cptr = d_pcp;
+        fd.pr_code = d_pcode;
+        fd.pr_coef = d_pcoef;
+        c->fdv = fd;
+    }
+    c->nlev = (int)fr.lvl_ptr.size() - 1;
+    c->fr = std::move(fr);
     c->hf = std::move(hf);
     c->prm = q;
     c->dp = dp;
@@ -836,6 +908,7 @@ void dc_destroy(dc_ctx* c) {
     free_pool(c->ck_allocs);
     free_pool(c->work_allocs);
     free_pool(c->factor_allocs);
+    free_pool(c->front_allocs);
     free_pool(c->mesh_allocs);
     if (c->hpin) cudaFreeHost(c->hpin);
     delete c;

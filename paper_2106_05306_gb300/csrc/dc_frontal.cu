@@ -1,0 +1,398 @@
+// Per-step single-precision multifrontal LDL^T of the constrained adjoint
+// matrix, used as the preconditioner of the FP64 adjoint Krylov solve.
+//
+// The matrix factorised is H^ = T H T + (I - T T) with H = P - Delta P - Delta R
+// (Sec. 4, Eq. ppr_adjoint) and a per-node T: the identity for free nodes, 0 for
+// stick nodes, the tangent-plane projector I - n n^T for slip nodes.  It differs
+// from the exact constrained operator only by the obliqueness of the slip
+// constraint and by single-precision rounding; the outer FP64 GMRES removes both.
+// No pivoting beyond the supernode order; a pivot below tau is replaced by
+// +-tau (the preconditioner stays usable, GMRES corrects).
+//
+// Fronts are dense column-major f x f blocks (DOF granularity, 3 per node) in
+// one pool; only their lower triangles are used.  One CTA handles one front.
+#include "dc_adjoint.h"
+#include "dc_internal.h"
+
+namespace {
+
+constexpr int PB = 32;        // panel width of the blocked factorisation
+constexpr int LDS = PB + 1;   // shared-memory row stride (no bank conflicts)
+constexpr int FT = 256;       // threads per front CTA
+
+__device__ __forceinline__ d4 ld(const d4* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = q[0], b = q[1];
+    d4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+__device__ __forceinline__ void st(d4* p, double x, double y, double z, double w = 0.0) {
+    double2* q = reinterpret_cast<double2*>(p);
+    q[0] = make_double2(x, y);
+    q[1] = make_double2(z, w);
+}
+inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
+
+// Node transform of the constraint: 0 free, 1 stick, 2 slip (normal n).
+__device__ __forceinline__ void node_T(int type, const double n[3], double T[9]) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double v = (r == c) ? 1.0 : 0.0;
+            if (type == 1) v = 0.0;
+            else if (type == 2) v -= n[r] * n[c];
+            T[3 * r + c] = v;
+        }
+}
+
+// One 3x3 block H^_ij of the constrained matrix, written into its front.
+__global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= fd.NP) return;
+    const int i = fd.pr_i[id], j = fd.pr_j[id];
+    const double h2 = ad.h * ad.h;
+    double H[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int k = fd.pr_cptr[id]; k < fd.pr_cptr[id + 1]; ++k) {
+        int code = fd.pr_code[k];
+        if (code >= 0) {
+            int t = code / 9, a = (code / 3) % 3, b = code % 3;
+            d4 g = ld(dm.G + t);
+            double ga0, ga1, gb0, gb1;
+            if (a == 1) { ga0 = g.x; ga1 = g.y; } else if (a == 2) { ga0 = g.z; ga1 = g.w; }
+            else { ga0 = -(g.x + g.z); ga1 = -(g.y + g.w); }
+            if (b == 1) { gb0 = g.x; gb1 = g.y; } else if (b == 2) { gb0 = g.z; gb1 = g.w; }
+            else { gb0 = -(g.x + g.z); gb1 = -(g.y + g.w); }
+            d4 A0 = ld(ad.tr0 + t), A1 = ld(ad.tr1 + t), A2 = ld(ad.tr2 + t);
+            double R0[3] = {A0.x, A0.y, A0.z}, R1[3] = {A1.x, A1.y, A1.z};
+            double s00 = A0.w, s01 = A1.w, s11 = A2.x, itr = A2.y;
+            double w = h2 * dm.wt[t];
+            double gg = ga0 * gb0 + ga1 * gb1;
+            double gam = ga0 * gb0 * s00 + (ga0 * gb1 + ga1 * gb0) * s01 + ga1 * gb1 * s11;
+            double aa[3], ab[3];
+            for (int q = 0; q < 3; ++q) {
+                aa[q] = (ga0 * R1[q] - ga1 * R0[q]) * itr;
+                ab[q] = (gb0 * R1[q] - gb1 * R0[q]) * itr;
+            }
+            double trS = 1.0 / itr;
+            // block = w ((g_a.g_b) I - trS a_a a_b^T - gam (I - R0 R0^T - R1 R1^T))
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) {
+                    double dl = (r == c) ? 1.0 : 0.0;
+                    H[3 * r + c] += w * (gg * dl - trS * aa[r] * ab[c] -
+                                         gam * (dl - R0[r] * R0[c] - R1[r] * R1[c]));
+                }
+        } else {
+            int b = -code - 1;
+            d4 q = ld(ad.bq + b);
+            double w = h2 * dm.wb[b] * fd.pr_coef[k];
+            double qh[3] = {q.x, q.y, q.z};
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c)
+                    H[3 * r + c] += w * (((r == c) ? (1.0 - q.w) : 0.0) + q.w * qh[r] * qh[c]);
+        }
+    }
+    int ti = ad.type[i], tj = ad.type[j];
+    if (i == j) {
+        double mi = dm.mass[i];
+        H[0] += mi; H[4] += mi; H[8] += mi;
+        if (ti == 2) {
+            d4 sl = ld(ad.slip + i), nb = ld(ad.nb + i);
+            double th[3] = {sl.x, sl.y, sl.z}, n[3] = {nb.x, nb.y, nb.z};
+            double bh[3] = {n[1] * th[2] - n[2] * th[1], n[2] * th[0] - n[0] * th[2], n[0] * th[1] - n[1] * th[0]};
+            for (int r = 0; r < 3; ++r)
+                for (int c = 0; c < 3; ++c) H[3 * r + c] += sl.w * bh[r] * bh[c];
+        }
+    }
+    double Hc[9];
+    if (ti == 0 && tj == 0) {
+        for (int q = 0; q < 9; ++q) Hc[q] = H[q];
+    } else {
+        double ni[3] = {0, 0, 0}, nj[3] = {0, 0, 0};
+        if (ti == 2) { d4 nb = ld(ad.nb + i); ni[0] = nb.x; ni[1] = nb.y; ni[2] = nb.z; }
+        if (tj == 2) { d4 nb = ld(ad.nb + j); nj[0] = nb.x; nj[1] = nb.y; nj[2] = nb.z; }
+        double Ti[9], Tj[9], M1[9];
+        node_T(ti, ni, Ti);
+        node_T(tj, nj, Tj);
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0;
+                for (int q = 0; q < 3; ++q) s += H[3 * r + q] * Tj[3 * q + c];
+                M1[3 * r + c] = s;
+            }
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) {
+                double s = 0;
+                for (int q = 0; q < 3; ++q) s += Ti[3 * r + q] * M1[3 * q + c];
+                Hc[3 * r + c] = s;
+            }
+        if (i == j)   // + (I - T): identity on the constrained directions
+            for (int q = 0; q < 9; ++q) Hc[q] += ((q % 4) == 0 ? 1.0 : 0.0) - Ti[q];
+    }
+    float* F = fd.pool + fd.pr_dst[id];
+    const long ldf = fd.pr_ld[id];
+    for (int c = 0; c < 3; ++c)
+        for (int r = 0; r < 3; ++r) F[c * ldf + r] = (float)Hc[3 * r + c];
+}
+
+// Extend-add of the children's update blocks, then the partial LDL^T of the
+// front's pivot columns; the trailing lower triangle becomes the update block.
+__global__ void __launch_bounds__(FT) k_front_level(FrontDev fd, int lvl_begin) {
+    extern __shared__ float Ls[];
+    const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    float* F = fd.pool + fd.off[s];
+    const int f = fd.f[s], p = fd.p[s];
+    for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
+        const int c = fd.child[q];
+        const float* Fc = fd.pool + fd.off[c];
+        const int fc = fd.f[c], pc = fd.p[c], nu = fc - pc;
+        const int* map = fd.cmap + fd.uptr[c];
+        for (long idx = tid; idx < (long)nu * nu; idx += nt) {
+            int a = (int)(idx % nu), b = (int)(idx / nu);
+            if (a < b) continue;
+            int pa = 3 * map[a / 3] + a % 3, pb = 3 * map[b / 3] + b % 3;
+            F[(long)pb * f + pa] += Fc[(long)(pc + b) * fc + pc + a];
+        }
+        __syncthreads();
+    }
+    const float tau = fd.tau;
+    for (int k0 = 0; k0 < p; k0 += PB) {
+        const int kb = min(PB, p - k0);
+        const int nr = f - k0;
+        for (long idx = tid; idx < (long)nr * kb; idx += nt) {
+            int c = (int)(idx / nr), r = (int)(idx % nr);
+            Ls[r * LDS + c] = F[(long)(k0 + c) * f + k0 + r];
+        }
+        __syncthreads();
+        for (int c = 0; c < kb; ++c) {
+            float d = Ls[c * LDS + c];
+            if (fabsf(d) < tau) d = (d < 0.0f) ? -tau : tau;
+            const float id = 1.0f / d;
+            const int w = kb - c - 1;
+            if (w > 0) {
+                for (long idx = tid; idx < (long)(nr - c - 1) * w; idx += nt) {
+                    int r = c + 1 + (int)(idx / w), j = c + 1 + (int)(idx % w);
+                    if (j <= r) Ls[r * LDS + j] -= Ls[r * LDS + c] * id * Ls[j * LDS + c];
+                }
+            }
+            __syncthreads();
+            for (int r = c + 1 + tid; r < nr; r += nt) Ls[r * LDS + c] *= id;
+            if (tid == 0) Ls[c * LDS + c] = d;
+            __syncthreads();
+        }
+        for (long idx = tid; idx < (long)nr * kb; idx += nt) {
+            int c = (int)(idx / nr), r = (int)(idx % nr);
+            if (r >= c) F[(long)(k0 + c) * f + k0 + r] = Ls[r * LDS + c];
+        }
+        // trailing update of rows/cols >= k0 + kb (lower triangle), 4x4 micro-tiles
+        const int n2 = nr - kb;
+        const int nT = (n2 + 3) / 4;
+        const long ntiles = (long)nT * (nT + 1) / 2;
+        for (long t = tid; t < ntiles; t += nt) {
+            int ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+            while ((long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
+            while ((long)ti * (ti + 1) / 2 > t) --ti;
+            int tj = (int)(t - (long)ti * (ti + 1) / 2);
+            float acc[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
+            const int r0 = kb + 4 * ti, c0 = kb + 4 * tj;
+            for (int c = 0; c < kb; ++c) {
+                const float dc = Ls[c * LDS + c];
+                float a[4], bv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    a[u] = (r0 + u < nr) ? Ls[(r0 + u) * LDS + c] : 0.0f;
+                    bv[u] = (c0 + u < nr) ? Ls[(c0 + u) * LDS + c] * dc : 0.0f;
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * bv[v];
+            }
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int col = c0 + v;
+                if (col >= nr) continue;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int row = r0 + u;
+                    if (row < nr && row >= col) F[(long)(k0 + col) * f + k0 + row] -= acc[u][v];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Forward substitution L y = r over one level (CTA per front), then z = D^-1 y.
+// The rows below the pivot block accumulate -L_Us y into the front's update
+// vector, which the parent adds in.
+__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
+    extern __shared__ float w[];
+    const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float* F = fd.pool + fd.off[s];
+    const int f = fd.f[s], p = fd.p[s];
+    const int base = 3 * fd.begin[s];
+    for (int t = tid; t < f; t += nt) w[t] = 0.0f;
+    __syncthreads();
+    for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
+        const int c = fd.child[q];
+        const int nu = fd.f[c] - fd.p[c];
+        const int* map = fd.cmap + fd.uptr[c];
+        const float* acc = fd.acc + fd.acc_off[c];
+        for (int k = tid; k < nu; k += nt) w[3 * map[k / 3] + k % 3] += acc[k];
+        __syncthreads();
+    }
+    for (int t = tid; t < p; t += nt) w[t] += fd.rvec[base + t];
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int k0 = 0; k0 < p; k0 += PB) {
+        const int kb = min(PB, p - k0);
+        if (warp == 0) {
+            for (int c = 0; c < kb; ++c) {
+                float yc = w[k0 + c];
+                __syncwarp();
+                if (lane > c && lane < kb) w[k0 + lane] -= F[(long)(k0 + c) * f + k0 + lane] * yc;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+        for (int i = k0 + kb + tid; i < f; i += nt) {
+            float sum = 0.0f;
+            for (int c = 0; c < kb; ++c) sum += F[(long)(k0 + c) * f + i] * w[k0 + c];
+            w[i] -= sum;
+        }
+        __syncthreads();
+    }
+    float* acc = fd.acc + fd.acc_off[s];
+    for (int t = p + tid; t < f; t += nt) acc[t - p] = w[t];
+    for (int t = tid; t < p; t += nt) fd.zvec[base + t] = w[t] / F[(long)t * f + t];
+}
+
+// Backward substitution L^T x = z over one level (CTA per front), top-down.
+__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
+    extern __shared__ float sm[];
+    const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const float* F = fd.pool + fd.off[s];
+    const int f = fd.f[s], p = fd.p[s], nu = f - p;
+    const int base = 3 * fd.begin[s];
+    float* w = sm;
+    float* xu = sm + p;
+    const int* un = fd.unode + fd.uptr[s];
+    for (int t = tid; t < p; t += nt) w[t] = fd.zvec[base + t];
+    for (int k = tid; k < nu; k += nt) xu[k] = fd.xvec[3 * un[k / 3] + k % 3];
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    // w_t -= sum_k L[p + k][t] xu_k  (column t of the off-diagonal block)
+    for (int t = warp; t < p; t += nw) {
+        float sum = 0.0f;
+        for (int k = lane; k < nu; k += 32) sum += F[(long)t * f + p + k] * xu[k];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) w[t] -= sum;
+    }
+    __syncthreads();
+    const int nblocks = (p + PB - 1) / PB;
+    for (int bi = nblocks - 1; bi >= 0; --bi) {
+        const int k0 = bi * PB, kb = min(PB, p - k0), kend = k0 + kb;
+        // subtract the rows already solved below this block
+        for (int c = warp; c < kb; c += nw) {
+            float sum = 0.0f;
+            for (int i = kend + lane; i < p; i += 32) sum += F[(long)(k0 + c) * f + i] * w[i];
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane == 0) w[k0 + c] -= sum;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            for (int c = kb - 1; c >= 0; --c) {
+                float xc = w[k0 + c];
+                __syncwarp();
+                if (lane < c) w[k0 + lane] -= F[(long)(k0 + lane) * f + k0 + c] * xc;
+                __syncwarp();
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < p; t += nt) fd.xvec[base + t] = w[t];
+}
+
+// r = Pi_B w in single precision (DOF order 3*node + c).
+__global__ void k_pre_in(int n, const int* __restrict__ type, const d4* __restrict__ nb, const d4* __restrict__ w,
+                         float* __restrict__ r) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    d4 a = ld(w + j);
+    double v[3] = {a.x, a.y, a.z};
+    int ty = type[j];
+    if (ty == 1) {
+        v[0] = v[1] = v[2] = 0.0;
+    } else if (ty == 2) {
+        d4 q = ld(nb + j);
+        double s = q.x * v[0] + q.y * v[1] + q.z * v[2];
+        v[0] -= s * q.x; v[1] -= s * q.y; v[2] -= s * q.z;
+    }
+    r[3 * j] = (float)v[0];
+    r[3 * j + 1] = (float)v[1];
+    r[3 * j + 2] = (float)v[2];
+}
+
+// out = S_C x in double precision: stick -> 0, slip -> x - n ((n - mu t).x).
+__global__ void k_pre_out(int n, double mu, const int* __restrict__ type, const d4* __restrict__ nb,
+                          const d4* __restrict__ slip, const float* __restrict__ x, d4* __restrict__ out) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double v[3] = {(double)x[3 * j], (double)x[3 * j + 1], (double)x[3 * j + 2]};
+    int ty = type[j];
+    if (ty == 1) {
+        v[0] = v[1] = v[2] = 0.0;
+    } else if (ty == 2) {
+        d4 q = ld(nb + j), sl = ld(slip + j);
+        double cz = (q.x - mu * sl.x) * v[0] + (q.y - mu * sl.y) * v[1] + (q.z - mu * sl.z) * v[2];
+        v[0] -= cz * q.x; v[1] -= cz * q.y; v[2] -= cz * q.z;
+    }
+    st(out + j, v[0], v[1], v[2]);
+}
+
+}  // namespace
+
+size_t frontal_factor_smem(int max_f) { return (size_t)max_f * LDS * sizeof(float) + 64; }
+size_t frontal_solve_smem(int max_f) { return (size_t)max_f * sizeof(float) + 64; }
+
+cudaError_t frontal_configure(int max_f) {
+    cudaError_t e = cudaFuncSetAttribute(k_front_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)frontal_factor_smem(max_f));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_msolve_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)frontal_solve_smem(max_f));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_msolve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)frontal_solve_smem(max_f));
+}
+
+void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
+                       int max_f, cudaStream_t s) {
+    cudaMemsetAsync(fd.pool, 0, sizeof(float) * fd.pool_size, s);
+    k_pairs<<<nblk(fd.NP, 128), 128, 0, s>>>(dm, ad, fd);
+    for (int l = 0; l < nlev; ++l) {
+        int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
+        if (cnt > 0) k_front_level<<<cnt, FT, frontal_factor_smem(max_f), s>>>(fd, lvl_ptr[l]);
+    }
+}
+
+void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, int max_f, int n_free,
+                     const d4* w, d4* out, cudaStream_t s) {
+    k_pre_in<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.type, ad.nb, w, fd.rvec);
+    for (int l = 0; l < nlev; ++l) {
+        int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
+        if (cnt > 0) k_msolve_fwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+    }
+    for (int l = nlev - 1; l >= 0; --l) {
+        int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
+        if (cnt > 0) k_msolve_bwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+    }
+    k_pre_out<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.mu, ad.type, ad.nb, ad.slip, fd.xvec, out);
+}

@@ -1,0 +1,184 @@
+// Host-side symbolic structure of the per-step multifrontal LDL^T that the
+// adjoint uses as its preconditioner (the matrix H of Sec. 4, Eq. ppr_adjoint,
+// with the contact constraints applied per node).
+//
+// H has the node-level sparsity of P (every element couples the same nodes), so
+// the elimination tree and column structures of P's Cholesky factor apply.
+// Supernodes are maximal runs of consecutive columns j, j+1 with
+// parent(j) = j+1 inside one nested-dissection block; the front of supernode s
+// holds its own nodes followed by U_s = struct(last column of s).  Fronts are
+// processed level by level (leaves first); each child's update block is added
+// into its parent's front through a node-position map.
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "dc_internal.h"
+
+std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts& fr) {
+    const int n = hf.n;
+    fr = HostFronts();
+    // ---- supernodes
+    std::vector<int> sn_of(n, -1);
+    for (int j = 0; j < n; ++j) {
+        bool cont = j > 0 && hm.nd_block[j] == hm.nd_block[j - 1] && hf.parent[j - 1] == j;
+        if (!cont) {
+            fr.begin.push_back(j);
+            fr.end.push_back(j + 1);
+        } else {
+            fr.end.back() = j + 1;
+        }
+        sn_of[j] = (int)fr.begin.size() - 1;
+    }
+    const int S = (int)fr.begin.size();
+    fr.S = S;
+    fr.parent.assign(S, -1);
+    fr.uptr.assign(1, 0);
+    for (int s = 0; s < S; ++s) {
+        int last = fr.end[s] - 1;
+        for (int q = hf.colptr[last] + 1; q < hf.colptr[last + 1]; ++q) fr.unode.push_back(hf.rowidx[q]);
+        fr.uptr.push_back((int)fr.unode.size());
+        int par = hf.parent[last];
+        fr.parent[s] = par >= 0 ? sn_of[par] : -1;
+        if (fr.parent[s] >= 0 && fr.parent[s] <= s) return "supernode tree is not in post-order";
+    }
+    // children lists
+    std::vector<std::vector<int>> ch(S);
+    for (int s = 0; s < S; ++s)
+        if (fr.parent[s] >= 0) ch[fr.parent[s]].push_back(s);
+    fr.cptr.assign(1, 0);
+    for (int s = 0; s < S; ++s) {
+        for (int c : ch[s]) fr.child.push_back(c);
+        fr.cptr.push_back((int)fr.child.size());
+    }
+    // sizes, offsets, levels
+    fr.f.resize(S);
+    fr.p.resize(S);
+    fr.off.resize(S);
+    fr.acc_off.resize(S);
+    fr.level.assign(S, 0);
+    long long off = 0, acc = 0;
+    fr.max_f = 0;
+    for (int s = 0; s < S; ++s) {
+        int ns = fr.end[s] - fr.begin[s];
+        int nu = fr.uptr[s + 1] - fr.uptr[s];
+        fr.p[s] = 3 * ns;
+        fr.f[s] = 3 * (ns + nu);
+        fr.max_f = std::max(fr.max_f, fr.f[s]);
+        fr.off[s] = off;
+        off += ((long long)fr.f[s] * fr.f[s] + 31) / 32 * 32;
+        fr.acc_off[s] = acc;
+        acc += (3LL * nu + 31) / 32 * 32;
+        for (int c : ch[s]) fr.level[s] = std::max(fr.level[s], fr.level[c] + 1);
+    }
+    fr.pool_size = off;
+    fr.acc_size = acc;
+    int nlev = 0;
+    for (int s = 0; s < S; ++s) nlev = std::max(nlev, fr.level[s] + 1);
+    fr.lvl_ptr.assign(nlev + 1, 0);
+    for (int s = 0; s < S; ++s) fr.lvl_ptr[fr.level[s] + 1]++;
+    for (int l = 0; l < nlev; ++l) fr.lvl_ptr[l + 1] += fr.lvl_ptr[l];
+    fr.lvl_sn.assign(S, 0);
+    {
+        std::vector<int> fill(fr.lvl_ptr.begin(), fr.lvl_ptr.end() - 1);
+        for (int s = 0; s < S; ++s) fr.lvl_sn[fill[fr.level[s]]++] = s;
+    }
+    // child -> parent position maps: position of U_c[k] in the parent's node list
+    fr.cmap.assign(fr.unode.size(), -1);
+    for (int c = 0; c < S; ++c) {
+        int par = fr.parent[c];
+        if (par < 0) {
+            if (fr.uptr[c + 1] != fr.uptr[c]) return "root supernode with a non-empty update";
+            continue;
+        }
+        const int* pu = fr.unode.data() + fr.uptr[par];
+        int npu = fr.uptr[par + 1] - fr.uptr[par];
+        for (int k = fr.uptr[c]; k < fr.uptr[c + 1]; ++k) {
+            int node = fr.unode[k];
+            int pos;
+            if (node >= fr.begin[par] && node < fr.end[par]) {
+                pos = node - fr.begin[par];
+            } else {
+                const int* it = std::lower_bound(pu, pu + npu, node);
+                if (it == pu + npu || *it != node) return "update row missing from the parent front";
+                pos = (fr.end[par] - fr.begin[par]) + (int)(it - pu);
+            }
+            fr.cmap[k] = pos;
+        }
+    }
+    // ---- node pairs (i >= j, both free) of H's lower pattern and their contributions
+    std::vector<std::vector<int>> rows(n);
+    auto add_pair = [&](int i, int j) {
+        if (i < j) std::swap(i, j);
+        if (i < n && j < n) rows[j].push_back(i);
+    };
+    for (int j = 0; j < n; ++j) add_pair(j, j);
+    for (int t = 0; t < hm.T; ++t)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) add_pair(hm.tri[3 * t + a], hm.tri[3 * t + b]);
+    for (int b = 0; b < hm.m; ++b)
+        for (int u = hm.bptr[b]; u < hm.bptr[b + 1]; ++u)
+            for (int v = hm.bptr[b]; v < hm.bptr[b + 1]; ++v) add_pair(hm.bidx[u], hm.bidx[v]);
+    std::vector<int> colstart(n + 1, 0);
+    for (int j = 0; j < n; ++j) {
+        std::sort(rows[j].begin(), rows[j].end());
+        rows[j].erase(std::unique(rows[j].begin(), rows[j].end()), rows[j].end());
+        colstart[j + 1] = colstart[j] + (int)rows[j].size();
+    }
+    const int NP = colstart[n];
+    fr.pr_i.resize(NP);
+    fr.pr_j.resize(NP);
+    fr.pr_dst.resize(NP);
+    fr.pr_ld.resize(NP);
+    for (int j = 0; j < n; ++j) {
+        int s = sn_of[j];
+        const int* pu = fr.unode.data() + fr.uptr[s];
+        int npu = fr.uptr[s + 1] - fr.uptr[s];
+        int ns = fr.end[s] - fr.begin[s];
+        int pj = j - fr.begin[s];
+        for (int q = 0; q < (int)rows[j].size(); ++q) {
+            int i = rows[j][q];
+            int pi;
+            if (i < fr.end[s]) {
+                pi = i - fr.begin[s];
+            } else {
+                const int* it = std::lower_bound(pu, pu + npu, i);
+                if (it == pu + npu || *it != i) return "matrix entry outside its front";
+                pi = ns + (int)(it - pu);
+            }
+            int id = colstart[j] + q;
+            fr.pr_i[id] = i;
+            fr.pr_j[id] = j;
+            fr.pr_ld[id] = fr.f[s];
+            fr.pr_dst[id] = fr.off[s] + (long long)(3 * pj) * fr.f[s] + 3 * pi;
+        }
+    }
+    auto pair_id = [&](int i, int j) {
+        const std::vector<int>& r = rows[j];
+        return colstart[j] + (int)(std::lower_bound(r.begin(), r.end(), i) - r.begin());
+    };
+    std::vector<std::vector<std::pair<int, double>>> contrib(NP);
+    for (int t = 0; t < hm.T; ++t)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) {
+                int i = hm.tri[3 * t + a], j = hm.tri[3 * t + b];
+                if (i < j || i >= n || j >= n) continue;
+                contrib[pair_id(i, j)].push_back({t * 9 + a * 3 + b, 0.0});
+            }
+    for (int b = 0; b < hm.m; ++b)
+        for (int u = hm.bptr[b]; u < hm.bptr[b + 1]; ++u)
+            for (int v = hm.bptr[b]; v < hm.bptr[b + 1]; ++v) {
+                int i = hm.bidx[u], j = hm.bidx[v];
+                if (i < j || i >= n || j >= n) continue;
+                contrib[pair_id(i, j)].push_back({-(b + 1), hm.bval[u] * hm.bval[v]});
+            }
+    fr.pr_cptr.assign(1, 0);
+    for (int id = 0; id < NP; ++id) {
+        for (auto& e : contrib[id]) {
+            fr.pr_code.push_back(e.first);
+            fr.pr_coef.push_back(e.second);
+        }
+        fr.pr_cptr.push_back((int)fr.pr_code.size());
+    }
+    return "";
+}

@@ -32,8 +32,8 @@ struct HostMesh {
     std::vector<double> bval;
     std::vector<double> abar, sb;      // [m]
     std::vector<double> qrest;         // [m][3]
-    // ND tree levels per free node (depth of its separator / leaf)
-    std::vector<int> nd_level;
+    // ND tree levels per free node (depth of its separator / leaf) and block id
+    std::vector<int> nd_level, nd_block;
     int nd_depth = 0;
 };
 
@@ -52,12 +52,26 @@ struct HostFactor {
     std::vector<double> fval;
     std::vector<int> bptr, bidx;
     std::vector<double> bval;
+    double max_diag = 0.0;             // largest diagonal entry of P_ff
 };
 
 // Assembles P_ff (free nodes, internal order) and factorises it.  Returns
 // DC_OK, DC_ERR_NOT_SPD or DC_ERR_INVALID with a message in err.
 dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vector<double>& mass,
                           HostFactor& hf, std::string& err);
+
+// Symbolic structure of the per-step multifrontal LDL^T (dc_frontal_setup.cpp).
+struct HostFronts {
+    int S = 0, max_f = 0;
+    std::vector<int> begin, end, parent, level, f, p;
+    std::vector<long long> off, acc_off;
+    long long pool_size = 0, acc_size = 0;
+    std::vector<int> uptr, unode, cptr, child, cmap, lvl_ptr, lvl_sn;
+    std::vector<int> pr_i, pr_j, pr_ld, pr_cptr, pr_code;
+    std::vector<long long> pr_dst;
+    std::vector<double> pr_coef;
+};
+std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts& fr);
 
 // ---------------------------------------------------------------- device views
 
@@ -127,5 +141,32 @@ void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const
 void launch_count_cases(const int* contact, const int* case_, int m_free,
                         unsigned long long* counters, cudaStream_t s);
 
-// ---------------------------------------------------------------- adjoint
-struct AdjStep;   // defined in dc_adjoint.cu
+// Device view of the multifrontal structure and its per-step numeric storage.
+struct FrontDev {
+    int S, NP;
+    float tau;                         // pivots below tau are replaced by +-tau
+    long long pool_size;
+    const int* begin;
+    const int* f;
+    const int* p;
+    const long long* off;
+    const long long* acc_off;
+    const int* uptr;
+    const int* unode;
+    const int* cptr;
+    const int* child;
+    const int* cmap;
+    const int* lvl_sn;
+    const int* pr_i;
+    const int* pr_j;
+    const long long* pr_dst;
+    const int* pr_ld;
+    const int* pr_cptr;
+    const int* pr_code;
+    const double* pr_coef;
+    float* pool;                       // fronts (lower triangles used)
+    float* acc;                        // per-front update vectors of the forward solve
+    float* rvec;                       // [3 m_free] right-hand side
+    float* zvec;                       // [3 m_free] D^-1 L^-1 r
+    float* xvec;                       // [3 m_free] solution
+};

@@ -34,13 +34,16 @@ inline V3 scale(V3 a, double s) { return {a.x * s, a.y * s, a.z * s}; }
 // (sub-domains first, separator last) and records each node's tree depth.
 void nd_recurse(const std::vector<std::vector<int>>& adj, const std::vector<double>& xyz,
                 std::vector<int> nodes, std::vector<int>& order, std::vector<int>& level,
-                std::vector<int>& side, int depth, int& maxdepth, size_t leaf) {
+                std::vector<int>& side, int depth, int& maxdepth, size_t leaf, std::vector<int>& block,
+                int& nblock) {
     maxdepth = std::max(maxdepth, depth);
     if (nodes.size() <= leaf) {
         std::sort(nodes.begin(), nodes.end());
+        int id = nblock++;
         for (int u : nodes) {
             order.push_back(u);
             level[u] = depth;
+            block[u] = id;
         }
         return;
     }
@@ -78,18 +81,22 @@ void nd_recurse(const std::vector<std::vector<int>>& adj, const std::vector<doub
     for (size_t i = nl; i < nodes.size(); ++i) R.push_back(nodes[i]);
     for (int u : nodes) side[u] = 0;
     if (L.empty() && R.empty()) {
+        int id = nblock++;
         for (int u : S) {
             order.push_back(u);
             level[u] = depth;
+            block[u] = id;
         }
         return;
     }
-    nd_recurse(adj, xyz, L, order, level, side, depth + 1, maxdepth, leaf);
-    nd_recurse(adj, xyz, R, order, level, side, depth + 1, maxdepth, leaf);
+    if (!L.empty()) nd_recurse(adj, xyz, L, order, level, side, depth + 1, maxdepth, leaf, block, nblock);
+    if (!R.empty()) nd_recurse(adj, xyz, R, order, level, side, depth + 1, maxdepth, leaf, block, nblock);
     std::sort(S.begin(), S.end());
+    int id = nblock++;
     for (int u : S) {
         order.push_back(u);
         level[u] = depth;
+        block[u] = id;
     }
 }
 
@@ -179,9 +186,9 @@ std::string dc_build_mesh(HostMesh& hm, int m, const double* rest_pos, int T, co
         for (int v : adjx[u])
             if (!is_pin[v]) adjf[u].push_back(v);
     std::vector<double> xyz(rest_pos, rest_pos + 3 * (size_t)m);
-    std::vector<int> order, lvl(m, 0), side(m, 0);
-    int maxdepth = 0;
-    nd_recurse(adjf, xyz, freen, order, lvl, side, 0, maxdepth, 24);
+    std::vector<int> order, lvl(m, 0), side(m, 0), blk(m, -1);
+    int maxdepth = 0, nblock = 0;
+    nd_recurse(adjf, xyz, freen, order, lvl, side, 0, maxdepth, 24, blk, nblock);
     hm.m_free = (int)order.size();
     for (int i = 0; i < m; ++i)
         if (is_pin[i]) order.push_back(i);
@@ -190,7 +197,11 @@ std::string dc_build_mesh(HostMesh& hm, int m, const double* rest_pos, int T, co
     for (int i = 0; i < m; ++i) hm.ext2int[order[i]] = i;
     hm.nd_depth = maxdepth;
     hm.nd_level.resize(hm.m_free);
-    for (int i = 0; i < hm.m_free; ++i) hm.nd_level[i] = lvl[order[i]];
+    hm.nd_block.resize(hm.m_free);
+    for (int i = 0; i < hm.m_free; ++i) {
+        hm.nd_level[i] = lvl[order[i]];
+        hm.nd_block[i] = blk[order[i]];
+    }
 
     // ---- store everything in internal numbering
     hm.rest.resize(3 * (size_t)m);
@@ -264,6 +275,7 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
         col[j][i] += v;
     };
     for (int i = 0; i < n; ++i) add(i, i, mass[i]);
+    hf.max_diag = 0.0;
     for (int t = 0; t < hm.T; ++t) {
         const double* g = &hm.G[4 * t];
         double gr[3][2] = {{-(g[0] + g[2]), -(g[1] + g[3])}, {g[0], g[1]}, {g[2], g[3]}};
@@ -290,6 +302,7 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
                     add(iu, iv, val);
             }
     }
+    for (int j = 0; j < n; ++j) hf.max_diag = std::max(hf.max_diag, col[j][j]);
     // ---- elimination tree (Liu's algorithm with path compression)
     std::vector<std::vector<int>> lower_rows(n);   // rows i > j of column j
     std::vector<std::vector<int>> upper_cols(n);   // for row i: columns j < i

@@ -40,11 +40,15 @@ def test_backward_parity_small(contact, drop, pinned):
     _grad_parity(sc, 3)
 
 
-def test_backward_parity_hanging_cloth_16x16():
+@pytest.mark.parametrize("precond", [0, 1])
+def test_backward_parity_hanging_cloth_16x16(precond):
+    """precond 0: per-step multifrontal LDL^T; 1: node-block inverse + projected P^-1."""
     sc = scenes.hanging_cloth()
-    got, want, st, recs = _grad_parity(sc, sc.n_steps, ck=10)
+    got, want, st, recs = _grad_parity(sc, sc.n_steps, ck=10, adj_precond=precond)
     assert sum(len(r.contacts) for r in recs) > 0
     assert st["adj_steps"] == sc.n_steps
+    if precond == 0:
+        assert st["adj_max_iters_seen"] <= 40
 
 
 def test_backward_with_per_step_loss_and_checkpoint_invariance():
