@@ -89,7 +89,26 @@ typedef struct dc_stats {
     int64_t solve_nnz;         /* nonzeros read by one P^-1 application (one column)  */
     int32_t n_free;            /* free (unpinned) nodes                               */
     int32_t nd_levels;         /* depth of the nested-dissection tree                 */
+    int64_t kernel_launches;   /* kernels launched by the library (process-wide)      */
+    double timer_ms;           /* dc_set_kernel_timer: accumulated device time (ms)   */
+    int64_t timer_launches;    /* dc_set_kernel_timer: launches timed                 */
+    int64_t fwd_solve_nnz;     /* nonzeros of L^-1 read by one forward substitution   */
+    int64_t bwd_solve_nnz;     /* nonzeros of L^-T read by one backward substitution  */
+    double front_flops;        /* FP32 flops of one multifrontal factorisation        */
+    int32_t front_levels;      /* levels (launches) of one multifrontal factorisation */
+    int32_t n_supernodes;      /* supernodes (fronts)                                 */
 } dc_stats;
+
+/* Kernel classes for dc_set_kernel_timer. */
+enum {
+    DC_KT_NONE = 0,
+    DC_KT_SOLVE_FWD = 1,   /* forward substitution of the PD global step (L^-1 rows)   */
+    DC_KT_SOLVE_BWD = 2,   /* backward substitution + per-node contact solve           */
+    DC_KT_LOCAL = 3,       /* local step (projections)                                 */
+    DC_KT_GATHER = 4,      /* right-hand-side gather                                   */
+    DC_KT_FRONT = 5,       /* one level of the adjoint multifrontal factorisation      */
+    DC_KT_MSOLVE = 6       /* one level of the multifrontal forward or backward solve  */
+};
 
 typedef struct dc_ctx dc_ctx;
 
@@ -142,6 +161,12 @@ dc_status dc_backward(dc_ctx* ctx, const double* dL_dx_final, const double* dL_d
  * nodes, Eq. pd_global) to three right-hand-side columns: out = P^-1 rhs.
  * rhs, out: [m][3]; entries of pinned nodes are ignored on input and set to 0. */
 dc_status dc_global_solve(dc_ctx* ctx, const double* rhs, double* out);
+
+/* Time every launch of one kernel class (DC_KT_*) with CUDA events recorded on
+ * the context's stream; DC_KT_NONE switches timing off.  Resets the
+ * accumulated time and count, which dc_get_stats reports.  No counterpart in
+ * the paper: measurement support for the roofline report. */
+dc_status dc_set_kernel_timer(dc_ctx* ctx, int32_t kernel_class);
 
 /* Counters and factor sizes (synchronises the stream). */
 dc_status dc_get_stats(dc_ctx* ctx, dc_stats* out);

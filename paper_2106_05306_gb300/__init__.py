@@ -181,6 +181,11 @@ class Cloth:
         check(self._lib.dc_get_stats(self._ctx, ctypes.byref(s)), self._ctx)
         return {k: getattr(s, k) for k, _ in s._fields_}
 
+    def set_kernel_timer(self, kernel_class):
+        """Time every launch of one kernel class (name from _lib.KT_CLASSES) on the context's stream."""
+        from ._lib import KT_CLASSES
+        check(self._lib.dc_set_kernel_timer(self._ctx, KT_CLASSES[kernel_class]), self._ctx)
+
     def sync(self):
         check(self._lib.dc_sync(self._ctx), self._ctx)
 

@@ -34,7 +34,13 @@ class dc_stats(ctypes.Structure):
                 ("adj_steps", ctypes.c_int64), ("adj_iters", ctypes.c_int64),
                 ("adj_max_iters_seen", ctypes.c_int64), ("adj_nonconverged", ctypes.c_int64),
                 ("adj_last_residual", ctypes.c_double), ("factor_nnz", ctypes.c_int64),
-                ("solve_nnz", ctypes.c_int64), ("n_free", ctypes.c_int32), ("nd_levels", ctypes.c_int32)]
+                ("solve_nnz", ctypes.c_int64), ("n_free", ctypes.c_int32), ("nd_levels", ctypes.c_int32),
+                ("kernel_launches", ctypes.c_int64), ("timer_ms", ctypes.c_double),
+                ("timer_launches", ctypes.c_int64), ("fwd_solve_nnz", ctypes.c_int64),
+                ("bwd_solve_nnz", ctypes.c_int64), ("front_flops", ctypes.c_double),
+                ("front_levels", ctypes.c_int32), ("n_supernodes", ctypes.c_int32)]
+
+KT_CLASSES = {"none": 0, "solve_fwd": 1, "solve_bwd": 2, "local": 3, "gather": 4, "front": 5, "msolve": 6}
 
 
 _P = ctypes.c_void_p
@@ -49,6 +55,7 @@ SIGNATURES = {
     "dc_backward": (ctypes.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
     "dc_global_solve": (ctypes.c_int32, [_P, _P, _P]),
     "dc_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_stats)]),
+    "dc_set_kernel_timer": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_sync": (ctypes.c_int32, [_P]),
     "dc_destroy": (None, [_P]),
     "dc_last_error": (ctypes.c_char_p, [_P]),

@@ -654,52 +654,69 @@ __global__ void k_adj_rhs(DevMesh dm, AdjDev ad, const d4* __restrict__ gx, cons
 // ----------------------------------------------------------------- launchers
 
 void adj_setup(const DevMesh& dm, const AdjDev& ad, const d4* x1, const d4* v1, cudaStream_t s) {
+    dc_note_launch();
     k_adj_setup_tri<<<nblk(dm.T, 128), 128, 0, s>>>(dm, x1, ad.tr0, ad.tr1, ad.tr2);
+    dc_note_launch();
     k_adj_setup_bend<<<nblk(dm.m, 128), 128, 0, s>>>(dm, x1, ad.bq);
+    dc_note_launch();
     k_adj_setup_node<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, ad, v1);
 }
 void adj_rhs(const DevMesh& dm, const AdjDev& ad, const d4* gx, const d4* gv, d4* g, d4* rhs, cudaStream_t s) {
+    dc_note_launch();
     k_adj_rhs<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, ad, gx, gv, g, rhs);
 }
 void adj_apply_H(const DevMesh& dm, const AdjDev& ad, int mode, const d4* z, const d4* w, d4* out, cudaStream_t s) {
+    dc_note_launch();
     k_adj_elem<<<nblk((long)dm.T + dm.m, 128), 128, 0, s>>>(dm, ad, z, ad.c1, ad.c2, ad.bu);
     int n = (mode == 3) ? dm.m : dm.m_free;
+    dc_note_launch();
     k_adj_gather<<<nblk(n, 128), 128, 0, s>>>(dm, ad, mode, z, ad.c1, ad.c2, ad.bu, w, out);
 }
 void adj_dplus(const DevMesh& dm, const AdjDev& ad, const d4* base, const d4* w, d4* out, cudaStream_t s) {
+    dc_note_launch();
     k_adj_dplus<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm.m_free, ad.dinv, base, w, out);
 }
 void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytmp, const d4* base, d4* out,
                        cudaStream_t s) {
     launch_solve_fwd(dm, r, ytmp, s);
+    dc_note_launch();
     k_adj_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, ad, ytmp, base, out);
 }
 void adj_mdot(const double* V, long ldv, int nvec, const double* w, long n, double* partial, double* out,
               cudaStream_t s) {
+    dc_note_launch();
     k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ldv, nvec, w, n, partial);
+    dc_note_launch();
     k_reduce<<<nvec, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, out);
 }
 void adj_vupdate(const double* V, long ldv, int nvec, const double* c, double* w, long n, double sign,
                  cudaStream_t s) {
+    dc_note_launch();
     k_vupdate<<<nblk(n, 256), 256, 0, s>>>(V, ldv, nvec, c, w, n, sign);
 }
 void adj_scale(const double* a, double sc, double* out, long n, cudaStream_t s) {
+    dc_note_launch();
     k_scale<<<nblk(n, 256), 256, 0, s>>>(a, sc, out, n);
 }
 void adj_axpby(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s) {
+    dc_note_launch();
     k_axpby<<<nblk(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
 }
 void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
                  const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
                  cudaStream_t s) {
+    dc_note_launch();
     k_adj_outputs<<<nblk(dm.m, 128), 128, 0, s>>>(dm, ad, P, z, E, resid, x_n, v1, gx, gx_out, gv_out);
 }
 void adj_params(const DevMesh& dm, const AdjDev& ad, const d4* z, const d4* x1, double* part, double* acc,
                 cudaStream_t s) {
+    dc_note_launch();
     k_adj_param_terms<<<RED_BLOCKS, RED_THREADS, 0, s>>>(dm, ad, z, x1, part);
+    dc_note_launch();
     k_param_accumulate<<<1, 32, 0, s>>>(part, RED_BLOCKS, acc);
 }
 void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s) {
+    dc_note_launch();
     k_add_ext<<<nblk(m, 256), 256, 0, s>>>(g, ext, int2ext, m);
 }
 int adj_red_blocks() { return RED_BLOCKS; }

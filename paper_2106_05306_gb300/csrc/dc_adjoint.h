@@ -47,6 +47,6 @@ size_t frontal_factor_smem(int max_f);
 size_t frontal_solve_smem(int max_f);
 cudaError_t frontal_configure(int max_f);
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
-                       int max_f, cudaStream_t s);
+                       int max_f, cudaStream_t s, KTimer* kt = nullptr);
 void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, int max_f, int n_free,
-                     const d4* w, d4* out, cudaStream_t s);
+                     const d4* w, d4* out, cudaStream_t s, KTimer* kt = nullptr);

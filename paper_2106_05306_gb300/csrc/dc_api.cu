@@ -26,9 +26,44 @@ struct StepRec {
 
 }  // namespace
 
+void KTimer::begin(int c) {
+    if (c != cls || cls == 0) return;
+    if (ev.empty()) {
+        ev.resize(2 * 4096);
+        for (auto& e : ev) cudaEventCreate(&e);
+    }
+    if (used + 2 > (int)ev.size()) flush();
+    cudaEventRecord(ev[used], stream);
+}
+
+void KTimer::end(int c) {
+    if (c != cls || cls == 0) return;
+    cudaEventRecord(ev[used + 1], stream);
+    used += 2;
+    ++launches;
+}
+
+void KTimer::flush() {
+    if (used == 0) return;
+    cudaEventSynchronize(ev[used - 1]);
+    for (int i = 0; i < used; i += 2) {
+        float t = 0.0f;
+        if (cudaEventElapsedTime(&t, ev[i], ev[i + 1]) == cudaSuccess) ms += t;
+    }
+    used = 0;
+}
+
+void KTimer::release() {
+    for (auto& e : ev) cudaEventDestroy(e);
+    ev.clear();
+    used = 0;
+}
+
 struct dc_ctx {
     cudaStream_t stream = nullptr;
     std::string err;
+    KTimer kt;
+    double front_flops = 0.0;
     HostMesh hm;
     HostFactor hf;
     bool have_params = false;
@@ -170,11 +205,20 @@ void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepR
     launch_solve_fwd(dm, c->ind, c->y, s);
     launch_solve_bwd(dm, P, c->y, nullptr, 2, nullptr, nullptr, nullptr, nullptr, nullptr, c->cc, s);
     cudaMemcpyAsync(c->v, vin, sizeof(d4) * dm.m, cudaMemcpyDeviceToDevice, s);
+    KTimer& kt = c->kt;
     for (int k = 0; k < c->prm.n_pd_iters; ++k) {
+        kt.begin(DC_KT_LOCAL);
         launch_local(dm, P, xin, c->v, c->c1, c->c2, c->bu, s);
+        kt.end(DC_KT_LOCAL);
+        kt.begin(DC_KT_GATHER);
         launch_gather_rhs(dm, P, vin, c->c1, c->c2, c->bu, r.f, c->b, s);
+        kt.end(DC_KT_GATHER);
+        kt.begin(DC_KT_SOLVE_FWD);
         launch_solve_fwd(dm, c->b, c->y, s);
+        kt.end(DC_KT_SOLVE_FWD);
+        kt.begin(DC_KT_SOLVE_BWD);
         launch_solve_bwd(dm, P, c->y, c->v, 1, r.contact, r.nb, c->cc, r.f, r.case_, nullptr, s);
+        kt.end(DC_KT_SOLVE_BWD);
     }
     launch_finalize(dm, P, xin, c->v, xout, s);
     if (vout != c->v) cudaMemcpyAsync(vout, c->v, sizeof(d4) * dm.m, cudaMemcpyDeviceToDevice, s);
@@ -242,7 +286,7 @@ void precond(dc_ctx* c, const d4* w, d4* out) {
     const DevMesh& dm = c->dm;
     const AdjDev& ad = c->ad;
     if (c->prm.adj_precond == 0) {
-        frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, dm.m_free, w, out, s);
+        frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, dm.m_free, w, out, s, &c->kt);
         return;
     }
     adj_dplus(dm, ad, nullptr, w, c->x1, s);
@@ -381,7 +425,7 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, con
     ad.f = r.f;
     adj_setup(c->dm, ad, x1, v1, s);
     if (c->prm.adj_precond == 0)
-        frontal_factorize(c->dm, ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s);
+        frontal_factorize(c->dm, ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s, &c->kt);
     adj_rhs(c->dm, ad, c->gx, c->gv, c->g, c->rhs, s);
     int it = 0;
     double rel = 0.0;
@@ -441,6 +485,7 @@ dc_status dc_create_mesh(dc_ctx** out, int32_t n_nodes, const double* rest_pos, 
     *out = nullptr;
     dc_ctx* c = new dc_ctx();
     c->stream = reinterpret_cast<cudaStream_t>(stream);
+    c->kt.stream = c->stream;
     std::string e = dc_build_mesh(c->hm, n_nodes, rest_pos, n_tris, tris, n_pins, pins);
     if (!e.empty()) {
         g_create_err = "dc_create_mesh: " + e;
@@ -685,6 +730,12 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
         c->fdv = fd;
     }
     c->nlev = (int)fr.lvl_ptr.size() - 1;
+    c->front_flops = 0.0;
+    for (int q = 0; q < fr.S; ++q)
+        for (int k = 0; k < fr.p[q]; ++k) {
+            double r = fr.f[q] - k - 1;
+            c->front_flops += r + r * (r + 1.0);
+        }
     c->fr = std::move(fr);
     c->hf = std::move(hf);
     c->prm = q;
@@ -890,6 +941,28 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->solve_nnz = (int64_t)c->hf.fval.size() + (int64_t)c->hf.bval.size();
     o->n_free = c->hm.m_free;
     o->nd_levels = c->hm.nd_depth + 1;
+    c->kt.flush();
+    o->kernel_launches = dc_launch_count();
+    o->timer_ms = c->kt.ms;
+    o->timer_launches = c->kt.launches;
+    o->fwd_solve_nnz = (int64_t)c->hf.fval.size();
+    o->bwd_solve_nnz = (int64_t)c->hf.bval.size();
+    o->front_flops = c->front_flops;
+    o->front_levels = c->nlev;
+    o->n_supernodes = c->fr.S;
+    return DC_OK;
+}
+
+dc_status dc_set_kernel_timer(dc_ctx* c, int32_t kernel_class) {
+    if (!c) return DC_ERR_INVALID;
+    if (kernel_class < DC_KT_NONE || kernel_class > DC_KT_MSOLVE) {
+        c->err = "dc_set_kernel_timer: unknown kernel class";
+        return DC_ERR_INVALID;
+    }
+    c->kt.flush();
+    c->kt.cls = kernel_class;
+    c->kt.ms = 0.0;
+    c->kt.launches = 0;
     return DC_OK;
 }
 
@@ -903,6 +976,7 @@ dc_status dc_sync(dc_ctx* c) {
 void dc_destroy(dc_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    c->kt.release();
     free_pool(c->adj_allocs);
     free_pool(c->seg_allocs);
     free_pool(c->ck_allocs);

@@ -374,25 +374,43 @@ cudaError_t frontal_configure(int max_f) {
 }
 
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
-                       int max_f, cudaStream_t s) {
+                       int max_f, cudaStream_t s, KTimer* kt) {
     cudaMemsetAsync(fd.pool, 0, sizeof(float) * fd.pool_size, s);
+    dc_note_launch();
     k_pairs<<<nblk(fd.NP, 128), 128, 0, s>>>(dm, ad, fd);
     for (int l = 0; l < nlev; ++l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
-        if (cnt > 0) k_front_level<<<cnt, FT, frontal_factor_smem(max_f), s>>>(fd, lvl_ptr[l]);
+        if (cnt > 0) {
+            dc_note_launch();
+            if (kt) kt->begin(DC_KT_FRONT);
+            k_front_level<<<cnt, FT, frontal_factor_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            if (kt) kt->end(DC_KT_FRONT);
+        }
     }
 }
 
 void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, int max_f, int n_free,
-                     const d4* w, d4* out, cudaStream_t s) {
+                     const d4* w, d4* out, cudaStream_t s, KTimer* kt) {
+    dc_note_launch();
     k_pre_in<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.type, ad.nb, w, fd.rvec);
     for (int l = 0; l < nlev; ++l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
-        if (cnt > 0) k_msolve_fwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+        if (cnt > 0) {
+            dc_note_launch();
+            if (kt) kt->begin(DC_KT_MSOLVE);
+            k_msolve_fwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            if (kt) kt->end(DC_KT_MSOLVE);
+        }
     }
     for (int l = nlev - 1; l >= 0; --l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
-        if (cnt > 0) k_msolve_bwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+        if (cnt > 0) {
+            dc_note_launch();
+            if (kt) kt->begin(DC_KT_MSOLVE);
+            k_msolve_bwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            if (kt) kt->end(DC_KT_MSOLVE);
+        }
     }
+    dc_note_launch();
     k_pre_out<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.mu, ad.type, ad.nb, ad.slip, fd.xvec, out);
 }

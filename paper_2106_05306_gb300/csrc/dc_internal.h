@@ -16,6 +16,24 @@ struct __align__(32) d4 {
     double x, y, z, w;
 };
 
+// Host-side count of kernel launches made by the library (all contexts).
+void dc_note_launch();
+long long dc_launch_count();
+
+// CUDA-event timing of one kernel class on a context's stream (classes: DC_KT_*).
+struct KTimer {
+    int cls = 0;
+    cudaStream_t stream = nullptr;
+    std::vector<cudaEvent_t> ev;
+    int used = 0;
+    double ms = 0.0;
+    long long launches = 0;
+    void begin(int c);
+    void end(int c);
+    void flush();
+    void release();
+};
+
 // ---------------------------------------------------------------- host setup
 
 struct HostMesh {

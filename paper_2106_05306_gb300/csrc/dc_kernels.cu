@@ -11,7 +11,16 @@
 //              backward sweep (Eq. contact_all).
 // Every reduction is a fixed-order gather (no atomics), so a launch is bitwise
 // repeatable and independent of what else runs on the GPU.
+#include <atomic>
+
 #include "dc_internal.h"
+
+namespace {
+std::atomic<long long> g_launches{0};
+}  // namespace
+
+void dc_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long dc_launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -312,39 +321,51 @@ inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 }  // namespace
 
 void launch_permute_in(const double* ext, d4* out, const int* int2ext, int m, cudaStream_t s) {
+    dc_note_launch();
     k_permute_in<<<nblk(m, 256), 256, 0, s>>>(ext, out, int2ext, m);
 }
 void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, cudaStream_t s) {
+    dc_note_launch();
     k_permute_out<<<nblk(m, 256), 256, 0, s>>>(in, ext, int2ext, m);
 }
 void launch_zero_pins(d4* v, int m_free, int m, cudaStream_t s) {
-    if (m > m_free) k_zero_range<<<nblk(m - m_free, 256), 256, 0, s>>>(v, m_free, m);
+    if (m > m_free) {
+        dc_note_launch();
+        k_zero_range<<<nblk(m - m_free, 256), 256, 0, s>>>(v, m_free, m);
+    }
 }
 void launch_detect(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v_n, int* contact,
                    d4* nb, d4* f, d4* ind, cudaStream_t s) {
+    dc_note_launch();
     k_detect<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, P, x_n, v_n, contact, nb, f, ind);
 }
 void launch_local(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* c1, d4* c2,
                   d4* bu, cudaStream_t s) {
+    dc_note_launch();
     k_local<<<nblk((long)dm.T + dm.m, 128), 128, 0, s>>>(dm, P, x_n, v, c1, c2, bu);
 }
 void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, const d4* c1, const d4* c2,
                        const d4* bu, const d4* f, d4* b, cudaStream_t s) {
+    dc_note_launch();
     k_gather_rhs<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, P, v_n, c1, c2, bu, f, b);
 }
 void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
+    dc_note_launch();
     k_solve_fwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, b, y);
 }
 void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode, const int* contact,
                       const d4* nb, const double* c, d4* f, int* case_, double* c_out, cudaStream_t s) {
+    dc_note_launch();
     k_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, P, y, out, mode, contact, nb, c, f, case_,
                                                                 c_out);
 }
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* x_np1,
                      cudaStream_t s) {
+    dc_note_launch();
     k_finalize<<<nblk(dm.m, 256), 256, 0, s>>>(dm.m, P.h, x_n, v, x_np1);
 }
 void launch_count_cases(const int* contact, const int* case_, int m_free, unsigned long long* counters,
                         cudaStream_t s) {
+    dc_note_launch();
     k_count_cases<<<nblk(m_free, 256), 256, 0, s>>>(contact, case_, m_free, counters);
 }
