@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--roofline-kernel", default="front")
+    ap.add_argument("--rollout-steps", type=int, default=N_STEPS,
+                    help="cloth steps per rollout (125 for the workload; ncu launch lists use a shorter rollout)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -216,11 +218,12 @@ def run_ours(args):
     xi = torch.tensor(sc.loss_w, device=dev)
     theta = torch.tensor([p.k_stretch, p.k_bend, p.mu], dtype=torch.float64, requires_grad=True)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    n_cloth = args.rollout_steps
 
     def one_step():
         a = x0.detach().requires_grad_(True)
         b = v0.detach().requires_grad_(True)
-        xN, vN = dc.rollout_fn(cloth, a, b, theta, N_STEPS)
+        xN, vN = dc.rollout_fn(cloth, a, b, theta, n_cloth)
         L = (xN * xi).sum()
         L.backward()
         return a.grad, b.grad
@@ -249,7 +252,7 @@ def run_ours(args):
     st1 = cloth.stats()
     cloth.set_kernel_timer("none")
     max_ms = aggregate(total_ms, world)
-    value = world * args.steps * N_STEPS / (max_ms / 1e3)
+    value = world * args.steps * n_cloth / (max_ms / 1e3)
 
     # end to end through the C ABI with pinned host buffers (copies inside the timed region)
     x0h = x0.cpu().pin_memory()
@@ -260,13 +263,13 @@ def run_ours(args):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        xN, vN = cloth.rollout(x0h, v0h, N_STEPS)
+        xN, vN = cloth.rollout(x0h, v0h, n_cloth)
         dx0, dv0, dth = cloth.backward(xih)
         _ = float(dth[0])
         e2e_s += time.perf_counter() - t0
     e2e_max = aggregate(e2e_s * 1e3, world) / 1e3
     m = sc.m
-    e2e = {"value": world * args.steps * N_STEPS / e2e_max, "unit": UNIT,
+    e2e = {"value": world * args.steps * n_cloth / e2e_max, "unit": UNIT,
            "h2d_bytes_per_step": 3 * m * 3 * 8, "d2h_bytes_per_step": 4 * m * 3 * 8 + 3 * 8}
 
     # roofline of the dominant kernel (live CUDA-event timing over the timed region)
@@ -297,7 +300,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cloth_steps_per_bench_step": N_STEPS, "nodes": m,
+        "config": {"workload": WORKLOAD if n_cloth == N_STEPS else WORKLOAD.replace("125 steps", f"{n_cloth} steps"),
+                   "cloth_steps_per_bench_step": n_cloth, "nodes": m,
                    "triangles": int(sc.tris.shape[0]), "pd_iters": p.n_pd_iters,
                    "checkpoint_every": CHECKPOINT_EVERY, "parallelism": f"replicas x{world}",
                    "l2": "flushed (512 MB write) before every timed step"},

@@ -654,12 +654,20 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
     free_pool(c->factor_allocs);
     auto& P = c->factor_allocs;
     double *d_mass, *d_wt, *d_wb, *d_fval, *d_kval;
-    int *d_fptr, *d_fidx, *d_kptr, *d_kidx;
+    int *d_fptr, *d_fidx, *d_kptr, *d_kidx, *d_long, *d_short;
+    std::vector<int> long_rows, short_rows;
+    for (int i = 0; i < hm.m_free; ++i)
+        (hf.fptr[i + 1] - hf.fptr[i] > 1024 ? long_rows : short_rows).push_back(i);
     if ((s = upload(c, P, &d_mass, mass)) || (s = upload(c, P, &d_wt, wt)) || (s = upload(c, P, &d_wb, wb)) ||
         (s = upload(c, P, &d_fptr, hf.fptr)) || (s = upload(c, P, &d_fidx, hf.fidx)) ||
         (s = upload(c, P, &d_fval, hf.fval)) || (s = upload(c, P, &d_kptr, hf.bptr)) ||
-        (s = upload(c, P, &d_kidx, hf.bidx)) || (s = upload(c, P, &d_kval, hf.bval)))
+        (s = upload(c, P, &d_kidx, hf.bidx)) || (s = upload(c, P, &d_kval, hf.bval)) ||
+        (s = upload(c, P, &d_long, long_rows)) || (s = upload(c, P, &d_short, short_rows)))
         return s;
+    c->dm.n_long = (int)long_rows.size();
+    c->dm.n_short = (int)short_rows.size();
+    c->dm.long_rows = d_long;
+    c->dm.short_rows = d_short;
     c->dm.mass = d_mass;
     c->dm.wt = d_wt;
     c->dm.wb = d_wb;
@@ -692,13 +700,15 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
         fd.S = fr.S;
         fd.NP = (int)fr.pr_i.size();
         fd.tau = (float)(1e-7 * hf.max_diag);
+        fd.max_f = fr.max_f;
         fd.pool_size = fr.pool_size;
         int *d_begin, *d_f, *d_p, *d_uptr, *d_unode, *d_cptr, *d_child, *d_cmap, *d_lvl, *d_pi, *d_pj, *d_pld, *d_pcp,
             *d_pcode;
-        long long *d_off, *d_acc_off, *d_pdst;
+        long long *d_off, *d_acc_off, *d_pdst, *d_binv_off;
         double* d_pcoef;
         if ((s = upload(c, F, &d_begin, fr.begin)) || (s = upload(c, F, &d_f, fr.f)) || (s = upload(c, F, &d_p, fr.p)) ||
             (s = upload(c, F, &d_off, fr.off)) || (s = upload(c, F, &d_acc_off, fr.acc_off)) ||
+            (s = upload(c, F, &d_binv_off, fr.binv_off)) || (s = dalloc(c, F, &fd.binv, (size_t)fr.binv_size)) ||
             (s = upload(c, F, &d_uptr, fr.uptr)) || (s = upload(c, F, &d_unode, fr.unode)) ||
             (s = upload(c, F, &d_cptr, fr.cptr)) || (s = upload(c, F, &d_child, fr.child)) ||
             (s = upload(c, F, &d_cmap, fr.cmap)) || (s = upload(c, F, &d_lvl, fr.lvl_sn)) ||
@@ -714,6 +724,7 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
         fd.p = d_p;
         fd.off = d_off;
         fd.acc_off = d_acc_off;
+        fd.binv_off = d_binv_off;
         fd.uptr = d_uptr;
         fd.unode = d_unode;
         fd.cptr = d_cptr;

@@ -18,7 +18,9 @@ namespace {
 
 constexpr int PB = 32;        // panel width of the blocked factorisation
 constexpr int LDS = PB + 1;   // shared-memory row stride (no bank conflicts)
-constexpr int FT = 256;       // threads per front CTA
+constexpr int FT = 256;       // threads per solve CTA
+constexpr int FT2 = 512;      // threads per factorisation CTA
+constexpr int TM = 8;         // register tile of the trailing update
 
 __device__ __forceinline__ d4 ld(const d4* p) {
     const double2* q = reinterpret_cast<const double2*>(p);
@@ -136,90 +138,108 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
 
 // Extend-add of the children's update blocks, then the partial LDL^T of the
 // front's pivot columns; the trailing lower triangle becomes the update block.
-__global__ void __launch_bounds__(FT) k_front_level(FrontDev fd, int lvl_begin) {
-    extern __shared__ float Ls[];
+// Panels of PB pivot columns are factorised in shared memory (each thread owns
+// rows), the inverse of each unit-lower PB x PB diagonal block is stored for the
+// solves, and the trailing matrix is updated with TM x TM register tiles.
+__global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin) {
+    extern __shared__ float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     float* F = fd.pool + fd.off[s];
     const int f = fd.f[s], p = fd.p[s];
+    float* Ls = sm;                                  // [f][LDS]
+    float* Xs = sm + (long)fd.max_f * LDS;           // [PB][LDS] scratch for the block inverse
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
         const int c = fd.child[q];
         const float* Fc = fd.pool + fd.off[c];
         const int fc = fd.f[c], pc = fd.p[c], nu = fc - pc;
         const int* map = fd.cmap + fd.uptr[c];
-        for (long idx = tid; idx < (long)nu * nu; idx += nt) {
-            int a = (int)(idx % nu), b = (int)(idx / nu);
-            if (a < b) continue;
-            int pa = 3 * map[a / 3] + a % 3, pb = 3 * map[b / 3] + b % 3;
-            F[(long)pb * f + pa] += Fc[(long)(pc + b) * fc + pc + a];
+        for (int b = warp; b < nu; b += nw) {
+            const int pb = 3 * map[b / 3] + b % 3;
+            const float* src = Fc + (long)(pc + b) * fc + pc;
+            float* dst = F + (long)pb * f;
+            for (int a = b + lane; a < nu; a += 32) dst[3 * map[a / 3] + a % 3] += src[a];
         }
         __syncthreads();
     }
     const float tau = fd.tau;
+    float* binv = fd.binv + fd.binv_off[s];
     for (int k0 = 0; k0 < p; k0 += PB) {
         const int kb = min(PB, p - k0);
         const int nr = f - k0;
-        for (long idx = tid; idx < (long)nr * kb; idx += nt) {
-            int c = (int)(idx / nr), r = (int)(idx % nr);
-            Ls[r * LDS + c] = F[(long)(k0 + c) * f + k0 + r];
+        for (int c = warp; c < kb; c += nw) {
+            const float* src = F + (long)(k0 + c) * f + k0;
+            for (int r = lane; r < nr; r += 32) Ls[r * LDS + c] = src[r];
         }
         __syncthreads();
         for (int c = 0; c < kb; ++c) {
             float d = Ls[c * LDS + c];
             if (fabsf(d) < tau) d = (d < 0.0f) ? -tau : tau;
             const float id = 1.0f / d;
-            const int w = kb - c - 1;
-            if (w > 0) {
-                for (long idx = tid; idx < (long)(nr - c - 1) * w; idx += nt) {
-                    int r = c + 1 + (int)(idx / w), j = c + 1 + (int)(idx % w);
-                    if (j <= r) Ls[r * LDS + j] -= Ls[r * LDS + c] * id * Ls[j * LDS + c];
-                }
+            for (int r = c + 1 + tid; r < nr; r += nt) {
+                const float l = Ls[r * LDS + c] * id;
+                const int jmax = min(kb - 1, r);
+                for (int j = c + 1; j <= jmax; ++j) Ls[r * LDS + j] -= l * Ls[j * LDS + c];
             }
             __syncthreads();
             for (int r = c + 1 + tid; r < nr; r += nt) Ls[r * LDS + c] *= id;
             if (tid == 0) Ls[c * LDS + c] = d;
             __syncthreads();
         }
-        for (long idx = tid; idx < (long)nr * kb; idx += nt) {
-            int c = (int)(idx / nr), r = (int)(idx % nr);
-            if (r >= c) F[(long)(k0 + c) * f + k0 + r] = Ls[r * LDS + c];
+        for (int c = warp; c < kb; c += nw) {
+            float* dst = F + (long)(k0 + c) * f + k0;
+            for (int r = c + lane; r < nr; r += 32) dst[r] = Ls[r * LDS + c];
         }
-        // trailing update of rows/cols >= k0 + kb (lower triangle), 4x4 micro-tiles
+        if (warp == 0) {
+            // column `lane` of the inverse of the unit lower diagonal block
+            const int c = lane;
+            for (int i = 0; i < PB; ++i) Xs[i * LDS + c] = (i == c) ? 1.0f : 0.0f;
+            if (c < kb)
+                for (int i = c + 1; i < kb; ++i) {
+                    float acc = 0.0f;
+                    for (int k = c; k < i; ++k) acc += Ls[i * LDS + k] * Xs[k * LDS + c];
+                    Xs[i * LDS + c] = -acc;
+                }
+            __syncwarp();
+            float* Bi = binv + (long)(k0 / PB) * PB * PB;   // column-major PB x PB
+            for (int cc = 0; cc < PB; ++cc) Bi[cc * PB + lane] = Xs[lane * LDS + cc];
+        }
         const int n2 = nr - kb;
-        const int nT = (n2 + 3) / 4;
+        const int nT = (n2 + TM - 1) / TM;
         const long ntiles = (long)nT * (nT + 1) / 2;
         for (long t = tid; t < ntiles; t += nt) {
             int ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
             while ((long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
             while ((long)ti * (ti + 1) / 2 > t) --ti;
-            int tj = (int)(t - (long)ti * (ti + 1) / 2);
-            float acc[4][4];
+            const int tj = (int)(t - (long)ti * (ti + 1) / 2);
+            const int r0 = kb + TM * ti, c0 = kb + TM * tj;
+            float acc[TM][TM];
 #pragma unroll
-            for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < TM; ++u)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) acc[u][v] = 0.0f;
-            const int r0 = kb + 4 * ti, c0 = kb + 4 * tj;
+                for (int v = 0; v < TM; ++v) acc[u][v] = 0.0f;
             for (int c = 0; c < kb; ++c) {
                 const float dc = Ls[c * LDS + c];
-                float a[4], bv[4];
+                float a[TM], bv[TM];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < TM; ++u) {
                     a[u] = (r0 + u < nr) ? Ls[(r0 + u) * LDS + c] : 0.0f;
                     bv[u] = (c0 + u < nr) ? Ls[(c0 + u) * LDS + c] * dc : 0.0f;
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int u = 0; u < TM; ++u)
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * bv[v];
+                    for (int v = 0; v < TM; ++v) acc[u][v] += a[u] * bv[v];
             }
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
+            for (int v = 0; v < TM; ++v) {
                 const int col = c0 + v;
                 if (col >= nr) continue;
+                float* dst = F + (long)(k0 + col) * f + k0;
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < TM; ++u) {
                     const int row = r0 + u;
-                    if (row < nr && row >= col) F[(long)(k0 + col) * f + k0 + row] -= acc[u][v];
+                    if (row < nr && row >= col) dst[row] -= acc[u][v];
                 }
             }
         }
@@ -228,13 +248,14 @@ __global__ void __launch_bounds__(FT) k_front_level(FrontDev fd, int lvl_begin) 
 }
 
 // Forward substitution L y = r over one level (CTA per front), then z = D^-1 y.
-// The rows below the pivot block accumulate -L_Us y into the front's update
-// vector, which the parent adds in.
+// Each PB block applies the stored inverse of its diagonal block; the rows below
+// accumulate -L y into the front's update vector, which the parent adds in.
 __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
     extern __shared__ float w[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
     const float* F = fd.pool + fd.off[s];
+    const float* binv = fd.binv + fd.binv_off[s];
     const int f = fd.f[s], p = fd.p[s];
     const int base = 3 * fd.begin[s];
     for (int t = tid; t < f; t += nt) w[t] = 0.0f;
@@ -249,16 +270,15 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
     }
     for (int t = tid; t < p; t += nt) w[t] += fd.rvec[base + t];
     __syncthreads();
-    const int lane = tid & 31, warp = tid >> 5;
     for (int k0 = 0; k0 < p; k0 += PB) {
         const int kb = min(PB, p - k0);
         if (warp == 0) {
-            for (int c = 0; c < kb; ++c) {
-                float yc = w[k0 + c];
-                __syncwarp();
-                if (lane > c && lane < kb) w[k0 + lane] -= F[(long)(k0 + c) * f + k0 + lane] * yc;
-                __syncwarp();
-            }
+            const float* Bi = binv + (long)(k0 / PB) * PB * PB;
+            float y = 0.0f;
+            if (lane < kb)
+                for (int c = 0; c <= lane; ++c) y += Bi[c * PB + lane] * w[k0 + c];
+            __syncwarp();
+            if (lane < kb) w[k0 + lane] = y;
         }
         __syncthreads();
         for (int i = k0 + kb + tid; i < f; i += nt) {
@@ -279,6 +299,7 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
+    const float* binv = fd.binv + fd.binv_off[s];
     const int f = fd.f[s], p = fd.p[s], nu = f - p;
     const int base = 3 * fd.begin[s];
     float* w = sm;
@@ -299,7 +320,6 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
     const int nblocks = (p + PB - 1) / PB;
     for (int bi = nblocks - 1; bi >= 0; --bi) {
         const int k0 = bi * PB, kb = min(PB, p - k0), kend = k0 + kb;
-        // subtract the rows already solved below this block
         for (int c = warp; c < kb; c += nw) {
             float sum = 0.0f;
             for (int i = kend + lane; i < p; i += 32) sum += F[(long)(k0 + c) * f + i] * w[i];
@@ -308,12 +328,12 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
         }
         __syncthreads();
         if (warp == 0) {
-            for (int c = kb - 1; c >= 0; --c) {
-                float xc = w[k0 + c];
-                __syncwarp();
-                if (lane < c) w[k0 + lane] -= F[(long)(k0 + lane) * f + k0 + c] * xc;
-                __syncwarp();
-            }
+            const float* Bi = binv + (long)bi * PB * PB;
+            float x = 0.0f;
+            if (lane < kb)
+                for (int c = lane; c < kb; ++c) x += Bi[lane * PB + c] * w[k0 + c];
+            __syncwarp();
+            if (lane < kb) w[k0 + lane] = x;
         }
         __syncthreads();
     }
@@ -359,7 +379,7 @@ __global__ void k_pre_out(int n, double mu, const int* __restrict__ type, const 
 
 }  // namespace
 
-size_t frontal_factor_smem(int max_f) { return (size_t)max_f * LDS * sizeof(float) + 64; }
+size_t frontal_factor_smem(int max_f) { return ((size_t)max_f + PB) * LDS * sizeof(float) + 64; }
 size_t frontal_solve_smem(int max_f) { return (size_t)max_f * sizeof(float) + 64; }
 
 cudaError_t frontal_configure(int max_f) {
@@ -383,7 +403,7 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
         if (cnt > 0) {
             dc_note_launch();
             if (kt) kt->begin(DC_KT_FRONT);
-            k_front_level<<<cnt, FT, frontal_factor_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            k_front_level<<<cnt, FT2, frontal_factor_smem(max_f), s>>>(fd, lvl_ptr[l]);
             if (kt) kt->end(DC_KT_FRONT);
         }
     }

@@ -56,8 +56,9 @@ std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts
     fr.p.resize(S);
     fr.off.resize(S);
     fr.acc_off.resize(S);
+    fr.binv_off.resize(S);
     fr.level.assign(S, 0);
-    long long off = 0, acc = 0;
+    long long off = 0, acc = 0, binv = 0;
     fr.max_f = 0;
     for (int s = 0; s < S; ++s) {
         int ns = fr.end[s] - fr.begin[s];
@@ -69,10 +70,13 @@ std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts
         off += ((long long)fr.f[s] * fr.f[s] + 31) / 32 * 32;
         fr.acc_off[s] = acc;
         acc += (3LL * nu + 31) / 32 * 32;
+        fr.binv_off[s] = binv;
+        binv += (long long)((fr.p[s] + 31) / 32) * 32 * 32;
         for (int c : ch[s]) fr.level[s] = std::max(fr.level[s], fr.level[c] + 1);
     }
     fr.pool_size = off;
     fr.acc_size = acc;
+    fr.binv_size = binv;
     int nlev = 0;
     for (int s = 0; s < S; ++s) nlev = std::max(nlev, fr.level[s] + 1);
     fr.lvl_ptr.assign(nlev + 1, 0);

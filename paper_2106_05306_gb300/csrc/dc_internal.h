@@ -82,8 +82,8 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
 struct HostFronts {
     int S = 0, max_f = 0;
     std::vector<int> begin, end, parent, level, f, p;
-    std::vector<long long> off, acc_off;
-    long long pool_size = 0, acc_size = 0;
+    std::vector<long long> off, acc_off, binv_off;
+    long long pool_size = 0, acc_size = 0, binv_size = 0;
     std::vector<int> uptr, unode, cptr, child, cmap, lvl_ptr, lvl_sn;
     std::vector<int> pr_i, pr_j, pr_ld, pr_cptr, pr_code;
     std::vector<long long> pr_dst;
@@ -115,6 +115,9 @@ struct DevMesh {
     const int* fptr;                   // L^-1 rows (CSR), rows 0..m_free-1
     const int* fidx;
     const double* fval;
+    int n_long, n_short;               // L^-1 rows split by length (CTA / warp per row)
+    const int* long_rows;
+    const int* short_rows;
     const int* kptr;                   // L^-T rows (CSR)
     const int* kidx;
     const double* kval;
@@ -161,7 +164,7 @@ void launch_count_cases(const int* contact, const int* case_, int m_free,
 
 // Device view of the multifrontal structure and its per-step numeric storage.
 struct FrontDev {
-    int S, NP;
+    int S, NP, max_f;
     float tau;                         // pivots below tau are replaced by +-tau
     long long pool_size;
     const int* begin;
@@ -169,6 +172,7 @@ struct FrontDev {
     const int* p;
     const long long* off;
     const long long* acc_off;
+    const long long* binv_off;         // per front: offset of its diagonal-block inverses
     const int* uptr;
     const int* unode;
     const int* cptr;
@@ -184,6 +188,7 @@ struct FrontDev {
     const double* pr_coef;
     float* pool;                       // fronts (lower triangles used)
     float* acc;                        // per-front update vectors of the forward solve
+    float* binv;                       // inverses of the 32x32 unit-lower diagonal blocks
     float* rvec;                       // [3 m_free] right-hand side
     float* zvec;                       // [3 m_free] D^-1 L^-1 r
     float* xvec;                       // [3 m_free] solution

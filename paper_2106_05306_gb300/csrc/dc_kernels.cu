@@ -237,12 +237,66 @@ __device__ __forceinline__ void warp_row(const int* __restrict__ ptr, const int*
     }
 }
 
-__global__ void k_solve_fwd(DevMesh dm, const d4* __restrict__ b, d4* __restrict__ y) {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= dm.m_free) return;
-    double s0, s1, s2;
-    warp_row(dm.fptr, dm.fidx, dm.fval, b, row, s0, s1, s2);
-    if ((threadIdx.x & 31) == 0) st(y + row, s0, s1, s2);
+// Forward substitution with the explicit inverse factor, y = L^-1 b.  Rows with
+// more than LONG_ROW nonzeros (separator rows near the top of the elimination
+// tree) get a whole CTA each; the other rows one warp each.  Both reductions
+// run in a fixed order, so the result is bitwise repeatable.
+__global__ void __launch_bounds__(256) k_solve_fwd(DevMesh dm, const d4* __restrict__ b, d4* __restrict__ y) {
+    __shared__ double red[3][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if ((int)blockIdx.x < dm.n_long) {
+        const int row = dm.long_rows[blockIdx.x];
+        double s0 = 0, s1 = 0, s2 = 0;
+        const int lo = dm.fptr[row], hi = dm.fptr[row + 1];
+        int k = lo + threadIdx.x;
+        for (; k + 256 < hi; k += 512) {
+            const double a0 = dm.fval[k], a1 = dm.fval[k + 256];
+            const d4 u0 = ld(b + dm.fidx[k]), u1 = ld(b + dm.fidx[k + 256]);
+            s0 += a0 * u0.x + a1 * u1.x; s1 += a0 * u0.y + a1 * u1.y; s2 += a0 * u0.z + a1 * u1.z;
+        }
+        if (k < hi) {
+            const double a = dm.fval[k];
+            const d4 u = ld(b + dm.fidx[k]);
+            s0 += a * u.x; s1 += a * u.y; s2 += a * u.z;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) { red[0][warp] = s0; red[1][warp] = s1; red[2][warp] = s2; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t0 = 0, t1 = 0, t2 = 0;
+            for (int w = 0; w < 8; ++w) { t0 += red[0][w]; t1 += red[1][w]; t2 += red[2][w]; }
+            st(y + row, t0, t1, t2);
+        }
+        return;
+    }
+    const int q = ((int)blockIdx.x - dm.n_long) * 8 + warp;
+    if (q >= dm.n_short) return;
+    const int row = dm.short_rows[q];
+    double s0 = 0, s1 = 0, s2 = 0;
+    const int lo = dm.fptr[row], hi = dm.fptr[row + 1];
+    int k = lo + lane;
+    for (; k + 32 < hi; k += 64) {
+        const double a0 = dm.fval[k], a1 = dm.fval[k + 32];
+        const d4 u0 = ld(b + dm.fidx[k]), u1 = ld(b + dm.fidx[k + 32]);
+        s0 += a0 * u0.x + a1 * u1.x; s1 += a0 * u0.y + a1 * u1.y; s2 += a0 * u0.z + a1 * u1.z;
+    }
+    if (k < hi) {
+        const double a = dm.fval[k];
+        const d4 u = ld(b + dm.fidx[k]);
+        s0 += a * u.x; s1 += a * u.y; s2 += a * u.z;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+        s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+    }
+    if (lane == 0) st(y + row, s0, s1, s2);
 }
 
 // Per-node Signorini-Coulomb solve (Eq. contact_1-3, reading R5) in world
@@ -351,7 +405,7 @@ void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, con
 }
 void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
     dc_note_launch();
-    k_solve_fwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, b, y);
+    k_solve_fwd<<<dm.n_long + nblk(dm.n_short, 8), 256, 0, s>>>(dm, b, y);
 }
 void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode, const int* contact,
                       const d4* nb, const double* c, d4* f, int* case_, double* c_out, cudaStream_t s) {
