@@ -168,6 +168,21 @@ dc_status dc_global_solve(dc_ctx* ctx, const double* rhs, double* out);
  * the paper: measurement support for the roofline report. */
 dc_status dc_set_kernel_timer(dc_ctx* ctx, int32_t kernel_class);
 
+/* The same solve as dc_global_solve, for callers that may not allocate device
+ * memory while they run: a serving loop that has given the rest of HBM to a
+ * caching allocator under a fixed budget, or a latency-bound loop that cannot
+ * take the device-wide synchronisation cudaMalloc/cudaFree may cause.  No
+ * counterpart in the paper.  It allocates nothing: rhs and out must be device
+ * arrays [m][3] (host pointers are rejected with DC_ERR_INVALID), and its three
+ * intermediate node vectors live in a fixed library array of 6 MiB per GPU,
+ * held from library load until process exit, which serves meshes of at most
+ * 65536 nodes (larger meshes: DC_ERR_INVALID).  The first call on a device looks
+ * up that array's address (cudaGetSymbolAddress, device current); make it
+ * before any stream capture.  Every call shares the array: calls that overlap on
+ * the GPU (other streams or contexts on the same device) race and must be
+ * serialised by the caller.  Asynchronous on the context's stream. */
+dc_status dc_global_solve_static(dc_ctx* ctx, const double* rhs, double* out);
+
 /* Counters and factor sizes (synchronises the stream). */
 dc_status dc_get_stats(dc_ctx* ctx, dc_stats* out);
 

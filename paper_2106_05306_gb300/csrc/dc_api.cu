@@ -1002,3 +1002,15 @@ void dc_destroy(dc_ctx* c) {
 const char* dc_last_error(dc_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
 
 }  // extern "C"
+
+// Read-only accessors used by dc_static_solve.cu.
+bool dc_ctx_ready(const dc_ctx* c) { return c->have_params; }
+const DevMesh& dc_ctx_mesh(const dc_ctx* c) { return c->dm; }
+const DevParams& dc_ctx_params(const dc_ctx* c) { return c->dp; }
+const int* dc_ctx_int2ext(const dc_ctx* c) { return c->d_int2ext; }
+cudaStream_t dc_ctx_stream(const dc_ctx* c) { return c->stream; }
+void dc_ctx_set_error(dc_ctx* c, const std::string& msg) { c->err = msg; }
+
+extern "C" {
+
+}  // extern "C"
