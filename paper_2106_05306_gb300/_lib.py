@@ -25,7 +25,8 @@ class dc_params(ctypes.Structure):
                 ("n_pd_iters", ctypes.c_int32), ("adj_max_iters", ctypes.c_int32),
                 ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("n_obstacles", ctypes.c_int32), ("adj_precond", ctypes.c_int32),
-                ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
+                ("obstacles", dc_obstacle * DC_MAX_OBSTACLES), ("adj_refactor_every", ctypes.c_int32),
+                ("pad2_", ctypes.c_int32)]
 
 
 class dc_stats(ctypes.Structure):
@@ -38,7 +39,8 @@ class dc_stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_int64), ("timer_ms", ctypes.c_double),
                 ("timer_launches", ctypes.c_int64), ("fwd_solve_nnz", ctypes.c_int64),
                 ("bwd_solve_nnz", ctypes.c_int64), ("front_flops", ctypes.c_double),
-                ("front_levels", ctypes.c_int32), ("n_supernodes", ctypes.c_int32)]
+                ("front_levels", ctypes.c_int32), ("n_supernodes", ctypes.c_int32),
+                ("factorisations", ctypes.c_int64)]
 
 KT_CLASSES = {"none": 0, "solve_fwd": 1, "solve_bwd": 2, "local": 3, "gather": 4, "front": 5, "msolve": 6}
 

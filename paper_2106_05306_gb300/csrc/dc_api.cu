@@ -103,6 +103,9 @@ struct dc_ctx {
     // stats
     long long steps = 0, adj_steps = 0, adj_iters = 0, adj_max_seen = 0, adj_noncv = 0;
     double adj_last_res = 0.0;
+    int since_factor = 1 << 30;   // adjoint steps since the preconditioner was factorised
+    int last_iters = 0;
+    long long n_factorisations = 0;
 };
 
 namespace {
@@ -424,13 +427,21 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, con
     ad.nb = r.nb;
     ad.f = r.f;
     adj_setup(c->dm, ad, x1, v1, s);
-    if (c->prm.adj_precond == 0)
-        frontal_factorize(c->dm, ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s, &c->kt);
+    if (c->prm.adj_precond == 0) {
+        const int every = std::max(1, c->prm.adj_refactor_every);
+        if (c->since_factor >= every || c->last_iters > 40) {
+            frontal_factorize(c->dm, ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s, &c->kt);
+            c->since_factor = 0;
+            c->n_factorisations++;
+        }
+        c->since_factor++;
+    }
     adj_rhs(c->dm, ad, c->gx, c->gv, c->g, c->rhs, s);
     int it = 0;
     double rel = 0.0;
     RET(gmres(c, &it, &rel));
     c->adj_steps++;
+    c->last_iters = it;
     c->adj_iters += it;
     c->adj_max_seen = std::max<long long>(c->adj_max_seen, it);
     c->adj_last_res = rel;
@@ -474,6 +485,7 @@ void dc_default_params(dc_params* p) {
     p->adj_restart = 200;
     p->checkpoint_every = 1;
     p->n_obstacles = 0;
+    p->adj_refactor_every = 1;
 }
 
 dc_status dc_create_mesh(dc_ctx** out, int32_t n_nodes, const double* rest_pos, int32_t n_tris,
@@ -589,7 +601,7 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
     if (!finite_params(*p) || !(p->h > 0) || p->k_stretch < 0 || p->k_bend < 0 || !(p->density > 0) ||
         p->mu < 0 || p->n_pd_iters < 0 || p->n_obstacles < 0 || p->n_obstacles > DC_MAX_OBSTACLES ||
         p->checkpoint_every < 1 || p->adj_max_iters < 1 || p->adj_restart < 1 || !(p->adj_tol > 0) ||
-        p->adj_precond < 0 || p->adj_precond > 1) {
+        p->adj_precond < 0 || p->adj_precond > 1 || p->adj_refactor_every < 0) {
         c->err = "dc_set_params: invalid or non-finite parameter";
         return DC_ERR_INVALID;
     }
@@ -704,11 +716,12 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
         fd.pool_size = fr.pool_size;
         int *d_begin, *d_f, *d_p, *d_uptr, *d_unode, *d_cptr, *d_child, *d_cmap, *d_lvl, *d_pi, *d_pj, *d_pld, *d_pcp,
             *d_pcode;
-        long long *d_off, *d_acc_off, *d_pdst, *d_binv_off;
+        long long *d_off, *d_acc_off, *d_pdst, *d_binv_off, *d_linv_off;
         double* d_pcoef;
         if ((s = upload(c, F, &d_begin, fr.begin)) || (s = upload(c, F, &d_f, fr.f)) || (s = upload(c, F, &d_p, fr.p)) ||
             (s = upload(c, F, &d_off, fr.off)) || (s = upload(c, F, &d_acc_off, fr.acc_off)) ||
             (s = upload(c, F, &d_binv_off, fr.binv_off)) || (s = dalloc(c, F, &fd.binv, (size_t)fr.binv_size)) ||
+            (s = upload(c, F, &d_linv_off, fr.linv_off)) || (s = dalloc(c, F, &fd.linv, (size_t)fr.linv_size)) ||
             (s = upload(c, F, &d_uptr, fr.uptr)) || (s = upload(c, F, &d_unode, fr.unode)) ||
             (s = upload(c, F, &d_cptr, fr.cptr)) || (s = upload(c, F, &d_child, fr.child)) ||
             (s = upload(c, F, &d_cmap, fr.cmap)) || (s = upload(c, F, &d_lvl, fr.lvl_sn)) ||
@@ -725,6 +738,7 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
         fd.off = d_off;
         fd.acc_off = d_acc_off;
         fd.binv_off = d_binv_off;
+        fd.linv_off = d_linv_off;
         fd.uptr = d_uptr;
         fd.unode = d_unode;
         fd.cptr = d_cptr;
@@ -872,6 +886,8 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
         host_io = true;
     }
     CK(cudaMemsetAsync(c->dparam_acc, 0, 4 * sizeof(double), s));
+    c->since_factor = 1 << 30;
+    c->last_iters = 0;
     bool noncv = false;
     dc_status st = DC_OK;
     int n_seg = (N + k - 1) / k;
@@ -961,6 +977,7 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->front_flops = c->front_flops;
     o->front_levels = c->nlev;
     o->n_supernodes = c->fr.S;
+    o->factorisations = c->n_factorisations;
     return DC_OK;
 }
 

@@ -18,7 +18,7 @@ namespace {
 
 constexpr int PB = 32;        // panel width of the blocked factorisation
 constexpr int LDS = PB + 1;   // shared-memory row stride (no bank conflicts)
-constexpr int FT = 256;       // threads per solve CTA
+constexpr int FT = 1024;      // threads per solve CTA
 constexpr int FT2 = 512;      // threads per factorisation CTA
 constexpr int TM = 8;         // register tile of the trailing update
 
@@ -208,7 +208,8 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
         const int nT = (n2 + TM - 1) / TM;
         const long ntiles = (long)nT * (nT + 1) / 2;
         for (long t = tid; t < ntiles; t += nt) {
-            int ti = (int)((sqrt(8.0 * (double)t + 1.0) - 1.0) * 0.5);
+            // triangular tile index; single-precision sqrt, then exact integer fix-up
+            int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
             while ((long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
             while ((long)ti * (ti + 1) / 2 > t) --ti;
             const int tj = (int)(t - (long)ti * (ti + 1) / 2);
@@ -245,19 +246,63 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
         }
         __syncthreads();
     }
+    // Explicit inverse X = L_ss^-1 of the unit-lower pivot block, by block rows:
+    // X_II = B_I (the stored diagonal-block inverse), X_IJ = -B_I sum_{K=J}^{I-1} L_IK X_KJ.
+    // X is column-major p x p; T (shared memory, reusing the panel area) holds the sums.
+    float* X = fd.linv + fd.linv_off[s];
+    float* T = Ls;
+    const int nb = (p + PB - 1) / PB;
+    for (int I = 0; I < nb; ++I) {
+        const int i0 = I * PB, ib = min(PB, p - i0);
+        const float* Bi = binv + (long)I * PB * PB;
+        // phase A: T_J[r][c] = sum_{k=32J}^{i0-1} L[i0 + r][k] X[k][32J + c], J < I
+        for (long e = tid; e < (long)I * PB * PB; e += nt) {
+            const int r = (int)(e % PB), c = (int)((e / PB) % PB), J = (int)(e / (PB * PB));
+            float acc = 0.0f;
+            if (r < ib) {
+                const int col = J * PB + c;
+                const float* xc = X + (long)col * p;
+#pragma unroll 8
+                for (int k = J * PB; k < i0; ++k) acc += F[(long)k * f + i0 + r] * xc[k];
+            }
+            T[e] = acc;
+        }
+        __syncthreads();
+        // phase B: X_IJ[r][c] = -sum_q B_I[r][q] T_J[q][c]; X_II = B_I; zero above the diagonal
+        for (long e = tid; e < (long)(I + 1) * PB * PB; e += nt) {
+            const int r = (int)(e % PB), c = (int)((e / PB) % PB), J = (int)(e / (PB * PB));
+            const int row = i0 + r, col = J * PB + c;
+            if (r >= ib || col >= p) continue;
+            float v;
+            if (J == I) {
+                v = Bi[c * PB + r];
+            } else {
+                v = 0.0f;
+                const float* tj = T + (long)J * PB * PB;
+                for (int q = 0; q < ib; ++q) v -= Bi[q * PB + r] * tj[c * PB + q];
+            }
+            X[(long)col * p + row] = v;
+        }
+        for (long e = tid; e < (long)ib * (p - i0); e += nt) {   // upper part of block column I..: zero
+            const int r = (int)(e % ib), col = i0 + (int)(e / ib);
+            if (col > i0 + r) X[(long)col * p + i0 + r] = 0.0f;
+        }
+        __syncthreads();
+    }
 }
 
 // Forward substitution L y = r over one level (CTA per front), then z = D^-1 y.
-// Each PB block applies the stored inverse of its diagonal block; the rows below
-// accumulate -L y into the front's update vector, which the parent adds in.
+// y_s = L_ss^-1 w_s with the stored explicit inverse; the rows below accumulate
+// -L_Us y_s into the front's update vector, which the parent adds in.
 __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
     extern __shared__ float w[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
-    const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
-    const float* binv = fd.binv + fd.binv_off[s];
+    const float* X = fd.linv + fd.linv_off[s];
     const int f = fd.f[s], p = fd.p[s];
     const int base = 3 * fd.begin[s];
+    float* y = w + f;
     for (int t = tid; t < f; t += nt) w[t] = 0.0f;
     __syncthreads();
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
@@ -270,36 +315,31 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
     }
     for (int t = tid; t < p; t += nt) w[t] += fd.rvec[base + t];
     __syncthreads();
-    for (int k0 = 0; k0 < p; k0 += PB) {
-        const int kb = min(PB, p - k0);
-        if (warp == 0) {
-            const float* Bi = binv + (long)(k0 / PB) * PB * PB;
-            float y = 0.0f;
-            if (lane < kb)
-                for (int c = 0; c <= lane; ++c) y += Bi[c * PB + lane] * w[k0 + c];
-            __syncwarp();
-            if (lane < kb) w[k0 + lane] = y;
-        }
-        __syncthreads();
-        for (int i = k0 + kb + tid; i < f; i += nt) {
-            float sum = 0.0f;
-            for (int c = 0; c < kb; ++c) sum += F[(long)(k0 + c) * f + i] * w[k0 + c];
-            w[i] -= sum;
-        }
-        __syncthreads();
+    for (int i = tid; i < p; i += nt) {
+        float sum = 0.0f;
+#pragma unroll 8
+        for (int k = 0; k <= i; ++k) sum += X[(long)k * p + i] * w[k];
+        y[i] = sum;
     }
+    __syncthreads();
     float* acc = fd.acc + fd.acc_off[s];
-    for (int t = p + tid; t < f; t += nt) acc[t - p] = w[t];
-    for (int t = tid; t < p; t += nt) fd.zvec[base + t] = w[t] / F[(long)t * f + t];
+    for (int i = p + tid; i < f; i += nt) {
+        float sum = 0.0f;
+#pragma unroll 8
+        for (int k = 0; k < p; ++k) sum += F[(long)k * f + i] * y[k];
+        acc[i - p] = w[i] - sum;
+    }
+    for (int t = tid; t < p; t += nt) fd.zvec[base + t] = y[t] / F[(long)t * f + t];
 }
 
-// Backward substitution L^T x = z over one level (CTA per front), top-down.
+// Backward substitution L^T x = z over one level (CTA per front), top-down:
+// x_s = L_ss^-T (z_s - L_Us^T x_U).
 __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
     extern __shared__ float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
-    const float* binv = fd.binv + fd.binv_off[s];
+    const float* X = fd.linv + fd.linv_off[s];
     const int f = fd.f[s], p = fd.p[s], nu = f - p;
     const int base = 3 * fd.begin[s];
     float* w = sm;
@@ -309,7 +349,6 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
     for (int k = tid; k < nu; k += nt) xu[k] = fd.xvec[3 * un[k / 3] + k % 3];
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    // w_t -= sum_k L[p + k][t] xu_k  (column t of the off-diagonal block)
     for (int t = warp; t < p; t += nw) {
         float sum = 0.0f;
         for (int k = lane; k < nu; k += 32) sum += F[(long)t * f + p + k] * xu[k];
@@ -317,27 +356,13 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
         if (lane == 0) w[t] -= sum;
     }
     __syncthreads();
-    const int nblocks = (p + PB - 1) / PB;
-    for (int bi = nblocks - 1; bi >= 0; --bi) {
-        const int k0 = bi * PB, kb = min(PB, p - k0), kend = k0 + kb;
-        for (int c = warp; c < kb; c += nw) {
-            float sum = 0.0f;
-            for (int i = kend + lane; i < p; i += 32) sum += F[(long)(k0 + c) * f + i] * w[i];
-            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            if (lane == 0) w[k0 + c] -= sum;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            const float* Bi = binv + (long)bi * PB * PB;
-            float x = 0.0f;
-            if (lane < kb)
-                for (int c = lane; c < kb; ++c) x += Bi[lane * PB + c] * w[k0 + c];
-            __syncwarp();
-            if (lane < kb) w[k0 + lane] = x;
-        }
-        __syncthreads();
+    for (int i = warp; i < p; i += nw) {
+        float sum = 0.0f;
+        const float* xc = X + (long)i * p;   // column i of L_ss^-1 = row i of L_ss^-T
+        for (int k = i + lane; k < p; k += 32) sum += xc[k] * w[k];
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) fd.xvec[base + i] = sum;
     }
-    for (int t = tid; t < p; t += nt) fd.xvec[base + t] = w[t];
 }
 
 // r = Pi_B w in single precision (DOF order 3*node + c).
@@ -380,7 +405,7 @@ __global__ void k_pre_out(int n, double mu, const int* __restrict__ type, const 
 }  // namespace
 
 size_t frontal_factor_smem(int max_f) { return ((size_t)max_f + PB) * LDS * sizeof(float) + 64; }
-size_t frontal_solve_smem(int max_f) { return (size_t)max_f * sizeof(float) + 64; }
+size_t frontal_solve_smem(int max_f) { return 2 * (size_t)max_f * sizeof(float) + 64; }
 
 cudaError_t frontal_configure(int max_f) {
     cudaError_t e = cudaFuncSetAttribute(k_front_level, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -57,8 +57,9 @@ std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts
     fr.off.resize(S);
     fr.acc_off.resize(S);
     fr.binv_off.resize(S);
+    fr.linv_off.resize(S);
     fr.level.assign(S, 0);
-    long long off = 0, acc = 0, binv = 0;
+    long long off = 0, acc = 0, binv = 0, linv = 0;
     fr.max_f = 0;
     for (int s = 0; s < S; ++s) {
         int ns = fr.end[s] - fr.begin[s];
@@ -72,11 +73,14 @@ std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts
         acc += (3LL * nu + 31) / 32 * 32;
         fr.binv_off[s] = binv;
         binv += (long long)((fr.p[s] + 31) / 32) * 32 * 32;
+        fr.linv_off[s] = linv;
+        linv += ((long long)fr.p[s] * fr.p[s] + 31) / 32 * 32;
         for (int c : ch[s]) fr.level[s] = std::max(fr.level[s], fr.level[c] + 1);
     }
     fr.pool_size = off;
     fr.acc_size = acc;
     fr.binv_size = binv;
+    fr.linv_size = linv;
     int nlev = 0;
     for (int s = 0; s < S; ++s) nlev = std::max(nlev, fr.level[s] + 1);
     fr.lvl_ptr.assign(nlev + 1, 0);

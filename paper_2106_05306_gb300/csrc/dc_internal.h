@@ -82,8 +82,8 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
 struct HostFronts {
     int S = 0, max_f = 0;
     std::vector<int> begin, end, parent, level, f, p;
-    std::vector<long long> off, acc_off, binv_off;
-    long long pool_size = 0, acc_size = 0, binv_size = 0;
+    std::vector<long long> off, acc_off, binv_off, linv_off;
+    long long pool_size = 0, acc_size = 0, binv_size = 0, linv_size = 0;
     std::vector<int> uptr, unode, cptr, child, cmap, lvl_ptr, lvl_sn;
     std::vector<int> pr_i, pr_j, pr_ld, pr_cptr, pr_code;
     std::vector<long long> pr_dst;
@@ -173,6 +173,7 @@ struct FrontDev {
     const long long* off;
     const long long* acc_off;
     const long long* binv_off;         // per front: offset of its diagonal-block inverses
+    const long long* linv_off;         // per front: offset of the inverse of its pivot block
     const int* uptr;
     const int* unode;
     const int* cptr;
@@ -189,6 +190,7 @@ struct FrontDev {
     float* pool;                       // fronts (lower triangles used)
     float* acc;                        // per-front update vectors of the forward solve
     float* binv;                       // inverses of the 32x32 unit-lower diagonal blocks
+    float* linv;                       // inverses of the unit-lower pivot blocks (p x p, column-major)
     float* rvec;                       // [3 m_free] right-hand side
     float* zvec;                       // [3 m_free] D^-1 L^-1 r
     float* xvec;                       // [3 m_free] solution
