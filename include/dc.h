@@ -73,10 +73,6 @@ typedef struct dc_params {
                                 multifrontal LDL^T of the constrained matrix (default);
                                 1 = node-block inverse + projected P^-1 (no factorisation) */
     dc_obstacle obstacles[DC_MAX_OBSTACLES];
-    int32_t adj_refactor_every; /* adjoint: refactorise the preconditioner every k adjoint
-                                   steps (1 = every step); a step that needed more than 40
-                                   iterations forces a refactorisation for the next one */
-    int32_t pad2_;
 } dc_params;
 
 typedef struct dc_stats {
@@ -204,7 +200,7 @@ const char* dc_last_error(dc_ctx* ctx);
 /* Fill *p with the library defaults (k_stretch 1e3, k_bend 1e-3, density 0.1,
  * mu 0.3, h 1/120, g = (0,-9.8,0), delta 1e-6, K = 20, adjoint tol 1e-10,
  * 2000 iterations, restart 200, checkpoint every step, no obstacles,
- * per-step multifrontal preconditioner refactorised every step). */
+ * multifrontal preconditioner). */
 void dc_default_params(dc_params* p);
 
 #ifdef __cplusplus

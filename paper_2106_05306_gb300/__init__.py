@@ -81,8 +81,7 @@ class Cloth:
     # ------------------------------------------------------------------ params
     def set_params(self, k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0,
                    gravity=(0.0, -9.8, 0.0), contact_margin=1e-6, n_pd_iters=20, obstacles=(),
-                   adj_tol=1e-10, adj_max_iters=2000, adj_restart=200, checkpoint_every=1, adj_precond=0,
-                   adj_refactor_every=1):
+                   adj_tol=1e-10, adj_max_iters=2000, adj_restart=200, checkpoint_every=1, adj_precond=0):
         p = dc_params()
         self._lib.dc_default_params(ctypes.byref(p))
         p.k_stretch, p.k_bend, p.density, p.mu, p.h = k_stretch, k_bend, density, mu, h
@@ -95,7 +94,6 @@ class Cloth:
         p.adj_restart = int(adj_restart)
         p.checkpoint_every = int(checkpoint_every)
         p.adj_precond = int(adj_precond)
-        p.adj_refactor_every = int(adj_refactor_every)
         obstacles = list(obstacles)
         if len(obstacles) > DC_MAX_OBSTACLES:
             raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
@@ -106,8 +104,7 @@ class Cloth:
         self.params = dict(k_stretch=k_stretch, k_bend=k_bend, density=density, mu=mu, h=h, gravity=tuple(gravity),
                            contact_margin=contact_margin, n_pd_iters=n_pd_iters, obstacles=obstacles,
                            adj_tol=adj_tol, adj_max_iters=adj_max_iters, adj_restart=adj_restart,
-                           checkpoint_every=checkpoint_every, adj_precond=adj_precond,
-                           adj_refactor_every=adj_refactor_every)
+                           checkpoint_every=checkpoint_every, adj_precond=adj_precond)
         self._theta = (float(k_stretch), float(k_bend), float(mu))
         return self
 

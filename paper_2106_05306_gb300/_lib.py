@@ -25,8 +25,7 @@ class dc_params(ctypes.Structure):
                 ("n_pd_iters", ctypes.c_int32), ("adj_max_iters", ctypes.c_int32),
                 ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("n_obstacles", ctypes.c_int32), ("adj_precond", ctypes.c_int32),
-                ("obstacles", dc_obstacle * DC_MAX_OBSTACLES), ("adj_refactor_every", ctypes.c_int32),
-                ("pad2_", ctypes.c_int32)]
+                ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
 
 
 class dc_stats(ctypes.Structure):

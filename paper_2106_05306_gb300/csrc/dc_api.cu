@@ -93,7 +93,12 @@ struct dc_ctx {
     std::vector<StepRec> seg_rec;
     // adjoint buffers
     int adj_restart_cap = 0;
-    AdjDev ad{};
+    AdjDev ad{};                  // the slot in use by the GMRES of the current adjoint step
+    AdjDev ads[2]{};              // per-step adjoint data, two slots (even / odd steps)
+    FrontDev fds[2]{};            // numeric fronts, two slots
+    cudaStream_t stream2 = nullptr;   // assembles and factorises the next step's fronts
+    cudaEvent_t ev_fact[2]{}, ev_free[2]{}, ev_seg = nullptr;
+    KTimer kt2;
     d4 *gx = nullptr, *gv = nullptr, *gx2 = nullptr, *gv2 = nullptr, *g = nullptr, *rhs = nullptr, *z = nullptr;
     d4 *x1 = nullptr, *r1 = nullptr, *x2 = nullptr, *r2 = nullptr, *ytmp = nullptr, *wv = nullptr, *E = nullptr;
     d4 *resid = nullptr;
@@ -103,8 +108,6 @@ struct dc_ctx {
     // stats
     long long steps = 0, adj_steps = 0, adj_iters = 0, adj_max_seen = 0, adj_noncv = 0;
     double adj_last_res = 0.0;
-    int since_factor = 1 << 30;   // adjoint steps since the preconditioner was factorised
-    int last_iters = 0;
     long long n_factorisations = 0;
 };
 
@@ -256,16 +259,34 @@ dc_status ensure_adjoint(dc_ctx* c) {
     free_pool(c->adj_allocs);
     const int m = c->hm.m, mf = c->hm.m_free, T = c->hm.T;
     auto& P = c->adj_allocs;
-    RET(dalloc(c, P, &c->ad.tr0, T));
-    RET(dalloc(c, P, &c->ad.tr1, T));
-    RET(dalloc(c, P, &c->ad.tr2, T));
-    RET(dalloc(c, P, &c->ad.bq, m));
-    RET(dalloc(c, P, &c->ad.dinv, 3 * (size_t)mf));
-    RET(dalloc(c, P, &c->ad.slip, mf));
-    RET(dalloc(c, P, &c->ad.type, mf));
-    RET(dalloc(c, P, &c->ad.c1, T));
-    RET(dalloc(c, P, &c->ad.c2, T));
-    RET(dalloc(c, P, &c->ad.bu, m));
+    d4 *c1, *c2, *bu;
+    RET(dalloc(c, P, &c1, T));
+    RET(dalloc(c, P, &c2, T));
+    RET(dalloc(c, P, &bu, m));
+    for (int k = 0; k < 2; ++k) {
+        AdjDev& a = c->ads[k];
+        RET(dalloc(c, P, &a.tr0, T));
+        RET(dalloc(c, P, &a.tr1, T));
+        RET(dalloc(c, P, &a.tr2, T));
+        RET(dalloc(c, P, &a.bq, m));
+        RET(dalloc(c, P, &a.dinv, 3 * (size_t)mf));
+        RET(dalloc(c, P, &a.slip, mf));
+        RET(dalloc(c, P, &a.type, mf));
+        a.c1 = c1;
+        a.c2 = c2;
+        a.bu = bu;
+    }
+    c->ad = c->ads[0];
+    if (!c->stream2) {
+        CK(cudaStreamCreateWithFlags(&c->stream2, cudaStreamNonBlocking));
+        for (int k = 0; k < 2; ++k) {
+            CK(cudaEventCreateWithFlags(&c->ev_fact[k], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&c->ev_free[k], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&c->ev_seg, cudaEventDisableTiming));
+        c->kt2.stream = c->stream2;
+        c->kt2.cls = c->kt.cls;
+    }
     d4** vecs[] = {&c->gx, &c->gv, &c->gx2, &c->gv2, &c->g, &c->rhs, &c->z, &c->x1,
                    &c->r1, &c->x2, &c->r2, &c->ytmp, &c->wv, &c->E, &c->resid};
     for (d4** p : vecs) RET(dalloc(c, P, p, m));
@@ -416,32 +437,39 @@ dc_status gmres(dc_ctx* c, int* iters, double* rel) {
     return DC_OK;
 }
 
-// One adjoint step: (gx, gv) at n+1 -> (gx2, gv2) at n, parameter terms into dparam_acc.
-dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, const StepRec& r, bool& noncv) {
-    cudaStream_t s = c->stream;
-    AdjDev& ad = c->ad;
+// Per-step adjoint data of step q into slot k: the element linearisation, node
+// types and (with the multifrontal preconditioner) the factorised fronts.  Runs on
+// stream2 so that it overlaps the GMRES of the step after q.
+void prepare_step(dc_ctx* c, int q, int k, cudaStream_t s) {
+    AdjDev& ad = c->ads[k];
+    const StepRec& r = c->seg_rec[q];
+    const int m = c->hm.m;
     ad.h = c->prm.h;
     ad.mu = c->prm.mu;
     ad.contact = r.contact;
     ad.case_ = r.case_;
     ad.nb = r.nb;
     ad.f = r.f;
-    adj_setup(c->dm, ad, x1, v1, s);
+    adj_setup(c->dm, ad, c->segX + (size_t)(q + 1) * m, c->segV + (size_t)(q + 1) * m, s);
     if (c->prm.adj_precond == 0) {
-        const int every = std::max(1, c->prm.adj_refactor_every);
-        if (c->since_factor >= every || c->last_iters > 40) {
-            frontal_factorize(c->dm, ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s, &c->kt);
-            c->since_factor = 0;
-            c->n_factorisations++;
-        }
-        c->since_factor++;
+        frontal_factorize(c->dm, ad, c->fds[k], c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s,
+                          s == c->stream ? &c->kt : &c->kt2);
+        c->n_factorisations++;
     }
+}
+
+// One adjoint step from slot k: (gx, gv) at n+1 -> (gx2, gv2) at n, parameter
+// terms into dparam_acc.
+dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv) {
+    cudaStream_t s = c->stream;
+    c->ad = c->ads[k];
+    c->fdv = c->fds[k];
+    AdjDev& ad = c->ad;
     adj_rhs(c->dm, ad, c->gx, c->gv, c->g, c->rhs, s);
     int it = 0;
     double rel = 0.0;
     RET(gmres(c, &it, &rel));
     c->adj_steps++;
-    c->last_iters = it;
     c->adj_iters += it;
     c->adj_max_seen = std::max<long long>(c->adj_max_seen, it);
     c->adj_last_res = rel;
@@ -453,6 +481,7 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, con
     adj_apply_H(c->dm, ad, 2, c->z, c->g, c->resid, s);
     adj_outputs(c->dm, ad, c->dp, c->z, c->E, c->resid, x_n, v1, c->gx, c->gx2, c->gv2, s);
     adj_params(c->dm, ad, c->z, x1, c->dparam_part, c->dparam_acc, s);
+    CK(cudaEventRecord(c->ev_free[k], s));
     std::swap(c->gx, c->gx2);
     std::swap(c->gv, c->gv2);
     return DC_OK;
@@ -485,7 +514,6 @@ void dc_default_params(dc_params* p) {
     p->adj_restart = 200;
     p->checkpoint_every = 1;
     p->n_obstacles = 0;
-    p->adj_refactor_every = 1;
 }
 
 dc_status dc_create_mesh(dc_ctx** out, int32_t n_nodes, const double* rest_pos, int32_t n_tris,
@@ -601,7 +629,7 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
     if (!finite_params(*p) || !(p->h > 0) || p->k_stretch < 0 || p->k_bend < 0 || !(p->density > 0) ||
         p->mu < 0 || p->n_pd_iters < 0 || p->n_obstacles < 0 || p->n_obstacles > DC_MAX_OBSTACLES ||
         p->checkpoint_every < 1 || p->adj_max_iters < 1 || p->adj_restart < 1 || !(p->adj_tol > 0) ||
-        p->adj_precond < 0 || p->adj_precond > 1 || p->adj_refactor_every < 0) {
+        p->adj_precond < 0 || p->adj_precond > 1) {
         c->err = "dc_set_params: invalid or non-finite parameter";
         return DC_ERR_INVALID;
     }
@@ -753,6 +781,12 @@ dc_status dc_set_params(dc_ctx* c, const dc_params* p) {
         fd.pr_code = d_pcode;
         fd.pr_coef = d_pcoef;
         c->fdv = fd;
+        c->fds[0] = fd;
+        c->fds[1] = fd;   // second slot: its own numeric storage, shared structure
+        if ((s = dalloc(c, F, &c->fds[1].pool, (size_t)fr.pool_size)) ||
+            (s = dalloc(c, F, &c->fds[1].binv, (size_t)fr.binv_size)) ||
+            (s = dalloc(c, F, &c->fds[1].linv, (size_t)fr.linv_size)))
+            return s;
     }
     c->nlev = (int)fr.lvl_ptr.size() - 1;
     c->front_flops = 0.0;
@@ -886,8 +920,6 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
         host_io = true;
     }
     CK(cudaMemsetAsync(c->dparam_acc, 0, 4 * sizeof(double), s));
-    c->since_factor = 1 << 30;
-    c->last_iters = 0;
     bool noncv = false;
     dc_status st = DC_OK;
     int n_seg = (N + k - 1) / k;
@@ -899,10 +931,28 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
         for (int q = 0; q < s1 - s0; ++q)
             run_step(c, c->segX + (size_t)q * m, c->segV + (size_t)q * m, c->segX + (size_t)(q + 1) * m,
                      c->segV + (size_t)(q + 1) * m, c->seg_rec[q], false);
+        // step q's data is prepared on stream2 while the GMRES of step q+1 runs on
+        // the main stream; slot (s0 + q) % 2 alternates between consecutive steps
+        CK(cudaEventRecord(c->ev_seg, s));
+        CK(cudaStreamWaitEvent(c->stream2, c->ev_seg, 0));
+        {
+            const int q = s1 - s0 - 1, k2 = (s0 + q) % 2;
+            CK(cudaStreamWaitEvent(c->stream2, c->ev_free[k2], 0));
+            prepare_step(c, q, k2, c->stream2);
+            CK(cudaEventRecord(c->ev_fact[k2], c->stream2));
+        }
         for (int q = s1 - s0 - 1; q >= 0; --q) {
+            const int k2 = (s0 + q) % 2;
+            if (q > 0) {
+                const int kn = (s0 + q - 1) % 2;
+                CK(cudaStreamWaitEvent(c->stream2, c->ev_free[kn], 0));
+                prepare_step(c, q - 1, kn, c->stream2);
+                CK(cudaEventRecord(c->ev_fact[kn], c->stream2));
+            }
+            CK(cudaStreamWaitEvent(s, c->ev_fact[k2], 0));
             if (traj) adj_add_ext(c->gx, traj + (size_t)(s0 + q + 1) * 3 * m, c->d_int2ext, m, s);
             st = adjoint_step(c, c->segX + (size_t)q * m, c->segX + (size_t)(q + 1) * m,
-                              c->segV + (size_t)(q + 1) * m, c->seg_rec[q], noncv);
+                              c->segV + (size_t)(q + 1) * m, k2, noncv);
             if (st) break;
         }
     }
@@ -918,6 +968,7 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
         }
     }
     CK(cudaStreamSynchronize(s));
+    if (c->stream2) CK(cudaStreamSynchronize(c->stream2));
     free_pool(tmp);
     CK(cudaGetLastError());
     if (st) return st;
@@ -969,9 +1020,10 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->n_free = c->hm.m_free;
     o->nd_levels = c->hm.nd_depth + 1;
     c->kt.flush();
+    c->kt2.flush();
     o->kernel_launches = dc_launch_count();
-    o->timer_ms = c->kt.ms;
-    o->timer_launches = c->kt.launches;
+    o->timer_ms = c->kt.ms + c->kt2.ms;
+    o->timer_launches = c->kt.launches + c->kt2.launches;
     o->fwd_solve_nnz = (int64_t)c->hf.fval.size();
     o->bwd_solve_nnz = (int64_t)c->hf.bval.size();
     o->front_flops = c->front_flops;
@@ -988,9 +1040,10 @@ dc_status dc_set_kernel_timer(dc_ctx* c, int32_t kernel_class) {
         return DC_ERR_INVALID;
     }
     c->kt.flush();
-    c->kt.cls = kernel_class;
-    c->kt.ms = 0.0;
-    c->kt.launches = 0;
+    c->kt2.flush();
+    c->kt.cls = c->kt2.cls = kernel_class;
+    c->kt.ms = c->kt2.ms = 0.0;
+    c->kt.launches = c->kt2.launches = 0;
     return DC_OK;
 }
 
@@ -1004,7 +1057,15 @@ dc_status dc_sync(dc_ctx* c) {
 void dc_destroy(dc_ctx* c) {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->stream2) cudaStreamSynchronize(c->stream2);
     c->kt.release();
+    c->kt2.release();
+    for (int k = 0; k < 2; ++k) {
+        if (c->ev_fact[k]) cudaEventDestroy(c->ev_fact[k]);
+        if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
+    }
+    if (c->ev_seg) cudaEventDestroy(c->ev_seg);
+    if (c->stream2) cudaStreamDestroy(c->stream2);
     free_pool(c->adj_allocs);
     free_pool(c->seg_allocs);
     free_pool(c->ck_allocs);

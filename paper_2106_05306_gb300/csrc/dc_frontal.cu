@@ -138,17 +138,22 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
 
 // Extend-add of the children's update blocks, then the partial LDL^T of the
 // front's pivot columns; the trailing lower triangle becomes the update block.
-// Panels of PB pivot columns are factorised in shared memory (each thread owns
-// rows), the inverse of each unit-lower PB x PB diagonal block is stored for the
-// solves, and the trailing matrix is updated with TM x TM register tiles.
+// Per panel of PB pivot columns: warp 0 factorises the PB x PB diagonal block in
+// registers (shuffles only) and inverts it; every thread then solves its rows
+// below the block against that inverse; the trailing matrix is updated with
+// TM x TM register tiles whose operands come from a transposed, zero-padded
+// copy of the panel (128-bit shared-memory loads).
 __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin) {
-    extern __shared__ float sm[];
+    extern __shared__ __align__(16) float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     float* F = fd.pool + fd.off[s];
     const int f = fd.f[s], p = fd.p[s];
-    float* Ls = sm;                                  // [f][LDS]
-    float* Xs = sm + (long)fd.max_f * LDS;           // [PB][LDS] scratch for the block inverse
+    const int ldt = (fd.max_f + 7) / 8 * 8;          // row stride of the transposed panel
+    float* Ls = sm;                                  // [f][LDS] panel, row-major
+    float* Xs = sm + (long)fd.max_f * LDS;           // [PB][LDS] diagonal-block inverse
+    float* Dd = Xs + PB * LDS;                       // [PB] pivots of the panel
+    float* Lt = sm + ((long)fd.max_f * LDS + PB * LDS + PB + 3) / 4 * 4;   // [PB][ldt], 16-byte aligned
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
         const int c = fd.child[q];
         const float* Fc = fd.pool + fd.off[c];
@@ -158,7 +163,22 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
             const int pb = 3 * map[b / 3] + b % 3;
             const float* src = Fc + (long)(pc + b) * fc + pc;
             float* dst = F + (long)pb * f;
-            for (int a = b + lane; a < nu; a += 32) dst[3 * map[a / 3] + a % 3] += src[a];
+            // four rows per lane per round: loads first, then stores
+            for (int a0 = b + lane; a0 < nu; a0 += 128) {
+                float val[4], old[4];
+                int di[4];
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2) {
+                    const int a = a0 + 32 * q2;
+                    di[q2] = (a < nu) ? 3 * map[a / 3] + a % 3 : -1;
+                    val[q2] = (a < nu) ? src[a] : 0.0f;
+                }
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2) old[q2] = (di[q2] >= 0) ? dst[di[q2]] : 0.0f;
+#pragma unroll
+                for (int q2 = 0; q2 < 4; ++q2)
+                    if (di[q2] >= 0) dst[di[q2]] = old[q2] + val[q2];
+            }
         }
         __syncthreads();
     }
@@ -172,75 +192,129 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
             for (int r = lane; r < nr; r += 32) Ls[r * LDS + c] = src[r];
         }
         __syncthreads();
-        for (int c = 0; c < kb; ++c) {
-            float d = Ls[c * LDS + c];
-            if (fabsf(d) < tau) d = (d < 0.0f) ? -tau : tau;
-            const float id = 1.0f / d;
-            for (int r = c + 1 + tid; r < nr; r += nt) {
-                const float l = Ls[r * LDS + c] * id;
-                const int jmax = min(kb - 1, r);
-                for (int j = c + 1; j <= jmax; ++j) Ls[r * LDS + j] -= l * Ls[j * LDS + c];
+        if (warp == 0) {
+            // lane r holds row r of the diagonal block
+            float row[PB];
+#pragma unroll
+            for (int j = 0; j < PB; ++j) row[j] = (lane < kb && j < kb) ? Ls[lane * LDS + j] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < PB; ++c) {
+                if (c < kb) {
+                    float d = __shfl_sync(0xffffffffu, row[c], c);
+                    if (fabsf(d) < tau) d = (d < 0.0f) ? -tau : tau;
+                    const float id = 1.0f / d;
+                    const float a_rc = row[c];                  // = l_r d for lanes below c
+#pragma unroll
+                    for (int j = c + 1; j < PB; ++j) {
+                        const float lj = __shfl_sync(0xffffffffu, row[c], j) * id;
+                        if (lane > c && j <= lane) row[j] -= a_rc * lj;
+                    }
+                    if (lane > c) row[c] = a_rc * id;
+                    if (lane == c) row[c] = d;
+                }
             }
-            __syncthreads();
-            for (int r = c + 1 + tid; r < nr; r += nt) Ls[r * LDS + c] *= id;
-            if (tid == 0) Ls[c * LDS + c] = d;
-            __syncthreads();
+            // column `lane` of X = L_dd^-1: X[i][c] = -sum_{k=c}^{i-1} L[i][k] X[k][c]
+            float xc[PB];
+#pragma unroll
+            for (int i = 0; i < PB; ++i) xc[i] = (i == lane) ? 1.0f : 0.0f;
+#pragma unroll
+            for (int i = 1; i < PB; ++i) {
+                float acc = 0.0f;
+#pragma unroll
+                for (int k = 0; k < i; ++k) acc += __shfl_sync(0xffffffffu, row[k], i) * xc[k];
+                if (i > lane) xc[i] = -acc;
+            }
+            if (lane < kb) {
+                float dl = 0.0f;
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    if (j <= lane && j < kb) Ls[lane * LDS + j] = row[j];
+                    if (j == lane) dl = row[j];
+                }
+                Dd[lane] = dl;
+            }
+#pragma unroll
+            for (int i = 0; i < PB; ++i) Xs[i * LDS + lane] = (lane < kb && i < kb) ? xc[i] : (i == lane ? 1.0f : 0.0f);
+            float* Bi = binv + (long)(k0 / PB) * PB * PB;   // column-major PB x PB
+#pragma unroll
+            for (int i = 0; i < PB; ++i) Bi[lane * PB + i] = (lane < kb && i < kb) ? xc[i] : (i == lane ? 1.0f : 0.0f);
         }
+        __syncthreads();
+        // rows below the diagonal block: l_r = D^-1 L_dd^-1 a_r (one row per thread)
+        for (int r = kb + tid; r < nr; r += nt) {
+            float a[PB];
+#pragma unroll
+            for (int j = 0; j < PB; ++j) a[j] = (j < kb) ? Ls[r * LDS + j] : 0.0f;
+#pragma unroll
+            for (int c = 0; c < PB; ++c) {
+                if (c < kb) {
+                    float sum = 0.0f;
+#pragma unroll
+                    for (int j = 0; j <= c; ++j) sum += Xs[c * LDS + j] * a[j];
+                    Ls[r * LDS + c] = sum / Dd[c];
+                }
+            }
+        }
+        __syncthreads();
+        const int n2 = nr - kb;
+        const int n2p = (n2 + TM - 1) / TM * TM;
         for (int c = warp; c < kb; c += nw) {
             float* dst = F + (long)(k0 + c) * f + k0;
             for (int r = c + lane; r < nr; r += 32) dst[r] = Ls[r * LDS + c];
         }
-        if (warp == 0) {
-            // column `lane` of the inverse of the unit lower diagonal block
-            const int c = lane;
-            for (int i = 0; i < PB; ++i) Xs[i * LDS + c] = (i == c) ? 1.0f : 0.0f;
-            if (c < kb)
-                for (int i = c + 1; i < kb; ++i) {
-                    float acc = 0.0f;
-                    for (int k = c; k < i; ++k) acc += Ls[i * LDS + k] * Xs[k * LDS + c];
-                    Xs[i * LDS + c] = -acc;
-                }
-            __syncwarp();
-            float* Bi = binv + (long)(k0 / PB) * PB * PB;   // column-major PB x PB
-            for (int cc = 0; cc < PB; ++cc) Bi[cc * PB + lane] = Xs[lane * LDS + cc];
+        // transposed, zero-padded copy of the trailing rows of the panel
+        for (long e = tid; e < (long)PB * n2p; e += nt) {
+            const int c = (int)(e / n2p), r = (int)(e % n2p);
+            Lt[c * ldt + r] = (c < kb && r < n2) ? Ls[(kb + r) * LDS + c] : 0.0f;
         }
-        const int n2 = nr - kb;
-        const int nT = (n2 + TM - 1) / TM;
-        const long ntiles = (long)nT * (nT + 1) / 2;
-        for (long t = tid; t < ntiles; t += nt) {
+        __syncthreads();
+        // trailing update in TM x 4 half-tiles of the TM x TM tiles of the lower
+        // triangle; each thread prefetches its tile's current values before the FMA
+        // loop so that the memory latency overlaps the arithmetic
+        const int nT = n2p / TM;
+        const long nunits = (long)nT * (nT + 1);               // two halves per tile
+        for (long t2 = tid; t2 < nunits; t2 += nt) {
+            const long t = t2 >> 1;
+            const int half = (int)(t2 & 1);
             // triangular tile index; single-precision sqrt, then exact integer fix-up
             int ti = (int)((sqrtf(8.0f * (float)t + 1.0f) - 1.0f) * 0.5f);
             while ((long)(ti + 1) * (ti + 2) / 2 <= t) ++ti;
             while ((long)ti * (ti + 1) / 2 > t) --ti;
             const int tj = (int)(t - (long)ti * (ti + 1) / 2);
-            const int r0 = kb + TM * ti, c0 = kb + TM * tj;
-            float acc[TM][TM];
+            const int r0 = TM * ti, c0 = TM * tj + 4 * half;   // relative to the trailing start
+            float old[TM][4], acc[TM][4];
 #pragma unroll
-            for (int u = 0; u < TM; ++u)
-#pragma unroll
-                for (int v = 0; v < TM; ++v) acc[u][v] = 0.0f;
-            for (int c = 0; c < kb; ++c) {
-                const float dc = Ls[c * LDS + c];
-                float a[TM], bv[TM];
+            for (int v = 0; v < 4; ++v) {
+                const int col = kb + c0 + v;
+                const float* dst = F + (long)(k0 + min(col, nr - 1)) * f + k0 + kb;
 #pragma unroll
                 for (int u = 0; u < TM; ++u) {
-                    a[u] = (r0 + u < nr) ? Ls[(r0 + u) * LDS + c] : 0.0f;
-                    bv[u] = (c0 + u < nr) ? Ls[(c0 + u) * LDS + c] * dc : 0.0f;
+                    const int row = kb + r0 + u;
+                    old[u][v] = (col < nr && row < nr && row >= col) ? dst[r0 + u] : 0.0f;
+                    acc[u][v] = 0.0f;
                 }
+            }
+            for (int c = 0; c < kb; ++c) {
+                const float dc = Dd[c];
+                const float4* la = reinterpret_cast<const float4*>(Lt + c * ldt + r0);
+                const float4 a0 = la[0], a1 = la[1];
+                const float4 b0 = *reinterpret_cast<const float4*>(Lt + c * ldt + c0);
+                const float a[TM] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+                const float bv[4] = {b0.x * dc, b0.y * dc, b0.z * dc, b0.w * dc};
 #pragma unroll
                 for (int u = 0; u < TM; ++u)
 #pragma unroll
-                    for (int v = 0; v < TM; ++v) acc[u][v] += a[u] * bv[v];
+                    for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * bv[v];
             }
 #pragma unroll
-            for (int v = 0; v < TM; ++v) {
-                const int col = c0 + v;
+            for (int v = 0; v < 4; ++v) {
+                const int col = kb + c0 + v;
                 if (col >= nr) continue;
-                float* dst = F + (long)(k0 + col) * f + k0;
+                float* dst = F + (long)(k0 + col) * f + k0 + kb;
 #pragma unroll
                 for (int u = 0; u < TM; ++u) {
-                    const int row = r0 + u;
-                    if (row < nr && row >= col) dst[row] -= acc[u][v];
+                    const int row = kb + r0 + u;
+                    if (row < nr && row >= col) dst[r0 + u] = old[u][v] - acc[u][v];
                 }
             }
         }
@@ -248,42 +322,60 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
     }
     // Explicit inverse X = L_ss^-1 of the unit-lower pivot block, by block rows:
     // X_II = B_I (the stored diagonal-block inverse), X_IJ = -B_I sum_{K=J}^{I-1} L_IK X_KJ.
-    // X is column-major p x p; T (shared memory, reusing the panel area) holds the sums.
+    // X is column-major p x p.  Per block row I the rows L[i0.., 0..i0) are staged in
+    // shared memory, and per block column J the needed part of X as well.
     float* X = fd.linv + fd.linv_off[s];
-    float* T = Ls;
     const int nb = (p + PB - 1) / PB;
     for (int I = 0; I < nb; ++I) {
         const int i0 = I * PB, ib = min(PB, p - i0);
         const float* Bi = binv + (long)I * PB * PB;
-        // phase A: T_J[r][c] = sum_{k=32J}^{i0-1} L[i0 + r][k] X[k][32J + c], J < I
-        for (long e = tid; e < (long)I * PB * PB; e += nt) {
-            const int r = (int)(e % PB), c = (int)((e / PB) % PB), J = (int)(e / (PB * PB));
-            float acc = 0.0f;
-            if (r < ib) {
-                const int col = J * PB + c;
-                const float* xc = X + (long)col * p;
+        const int lr = i0 + 1;                         // odd row stride: no bank conflicts
+        float* Lrow = sm;                              // [PB][lr]: L[i0 + r][k], k < i0
+        float* Xc = Lrow + (long)PB * lr;              // [PB][lr]: X[k][32J + c], k < i0
+        float* T = Xc + (long)PB * lr;                 // [PB][PB] partial sums of one J
+        for (long e = tid; e < (long)ib * i0; e += nt) {
+            const int r = (int)(e % ib), k = (int)(e / ib);
+            Lrow[r * lr + k] = F[(long)k * f + i0 + r];
+        }
+        for (int J = 0; J <= I; ++J) {
+            const int k1 = J * PB;
+            if (J < I) {
+                for (long e = tid; e < (long)PB * (i0 - k1); e += nt) {
+                    const int k = k1 + (int)(e % (i0 - k1)), c = (int)(e / (i0 - k1));
+                    Xc[c * lr + k] = X[(long)(k1 + c) * p + k];
+                }
+                __syncthreads();
+                // T[r][c] = sum_{k=32J}^{i0-1} L[i0 + r][k] X[k][32J + c]
+                for (int e = tid; e < PB * PB; e += nt) {
+                    const int r = e % PB, c = e / PB;
+                    float acc = 0.0f;
+                    if (r < ib) {
+                        const float* lrow = Lrow + r * lr;
+                        const float* xcol = Xc + c * lr;
 #pragma unroll 8
-                for (int k = J * PB; k < i0; ++k) acc += F[(long)k * f + i0 + r] * xc[k];
+                        for (int k = k1; k < i0; ++k) acc += lrow[k] * xcol[k];
+                    }
+                    T[c * PB + r] = acc;
+                }
+                __syncthreads();
             }
-            T[e] = acc;
-        }
-        __syncthreads();
-        // phase B: X_IJ[r][c] = -sum_q B_I[r][q] T_J[q][c]; X_II = B_I; zero above the diagonal
-        for (long e = tid; e < (long)(I + 1) * PB * PB; e += nt) {
-            const int r = (int)(e % PB), c = (int)((e / PB) % PB), J = (int)(e / (PB * PB));
-            const int row = i0 + r, col = J * PB + c;
-            if (r >= ib || col >= p) continue;
-            float v;
-            if (J == I) {
-                v = Bi[c * PB + r];
-            } else {
-                v = 0.0f;
-                const float* tj = T + (long)J * PB * PB;
-                for (int q = 0; q < ib; ++q) v -= Bi[q * PB + r] * tj[c * PB + q];
+            // X_IJ[r][c] = -sum_q B_I[r][q] T[q][c]; X_II = B_I
+            for (int e = tid; e < PB * PB; e += nt) {
+                const int r = e % PB, c = e / PB;
+                const int row = i0 + r, col = k1 + c;
+                if (r >= ib || col >= p) continue;
+                float v;
+                if (J == I) {
+                    v = Bi[c * PB + r];
+                } else {
+                    v = 0.0f;
+                    for (int q = 0; q < ib; ++q) v -= Bi[q * PB + r] * T[c * PB + q];
+                }
+                X[(long)col * p + row] = v;
             }
-            X[(long)col * p + row] = v;
+            __syncthreads();
         }
-        for (long e = tid; e < (long)ib * (p - i0); e += nt) {   // upper part of block column I..: zero
+        for (long e = tid; e < (long)ib * (p - i0); e += nt) {   // upper part of block row I: zero
             const int r = (int)(e % ib), col = i0 + (int)(e / ib);
             if (col > i0 + r) X[(long)col * p + i0 + r] = 0.0f;
         }
@@ -404,7 +496,13 @@ __global__ void k_pre_out(int n, double mu, const int* __restrict__ type, const 
 
 }  // namespace
 
-size_t frontal_factor_smem(int max_f) { return ((size_t)max_f + PB) * LDS * sizeof(float) + 64; }
+size_t frontal_factor_smem(int max_f) {
+    const size_t ldt = ((size_t)max_f + 7) / 8 * 8;
+    size_t panel = ((size_t)max_f * LDS + PB * LDS + PB + 3) / 4 * 4 + PB * ldt;
+    size_t inverse = 2 * (size_t)PB * (max_f + 1) + (size_t)PB * PB;
+    return (panel > inverse ? panel : inverse) * sizeof(float) + 64;
+}
+
 size_t frontal_solve_smem(int max_f) { return 2 * (size_t)max_f * sizeof(float) + 64; }
 
 cudaError_t frontal_configure(int max_f) {
