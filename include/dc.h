@@ -20,6 +20,13 @@
  *    Errors found on the device (non-finite values) are reported by the next
  *    synchronising call (dc_sync, dc_get_stats, or any call with host buffers).
  *  - A context is not thread-safe.
+ *  - Batches.  dc_create_batch packs several cloths (instances) of any sizes
+ *    into one context; every call below then works on all of them at once,
+ *    with one kernel launch per phase covering every instance.  Node arrays
+ *    are the concatenation of the instances' [m_i][3] arrays in instance order
+ *    (dc_get_layout gives the offsets) and dL_dparams holds 3 values per
+ *    instance.  An instance's results do not depend on the other instances of
+ *    its batch: they are bitwise those of a one-instance context of that cloth.
  */
 #ifndef DC_H_
 #define DC_H_
@@ -98,6 +105,14 @@ typedef struct dc_stats {
     int32_t front_levels;      /* levels (launches) of one multifrontal factorisation */
     int32_t n_supernodes;      /* supernodes (fronts)                                 */
     int64_t factorisations;    /* multifrontal factorisations run                     */
+    int32_t n_instances;       /* cloths packed in the context                        */
+    int32_t graphs;            /* 1 if rollouts replay captured CUDA graphs           */
+    int64_t graph_replays;     /* CUDA graph launches made                            */
+    int32_t block_local;       /* threads per block chosen for the local-step kernel  */
+    int32_t block_gather;      /* ... for the right-hand-side and adjoint gathers     */
+    int32_t block_node;        /* ... for the per-node kernels                        */
+    int32_t block_elem;        /* ... for the adjoint per-element kernel              */
+    int64_t adj_batch_iters;   /* GMRES iterations run by a context, all instances in lockstep */
 } dc_stats;
 
 /* Kernel classes for dc_set_kernel_timer. */
@@ -108,7 +123,10 @@ enum {
     DC_KT_LOCAL = 3,       /* local step (projections)                                 */
     DC_KT_GATHER = 4,      /* right-hand-side gather                                   */
     DC_KT_FRONT = 5,       /* one level of the adjoint multifrontal factorisation      */
-    DC_KT_MSOLVE = 6       /* one level of the multifrontal forward or backward solve  */
+    DC_KT_MSOLVE = 6,      /* one level of the multifrontal forward or backward solve  */
+    DC_KT_KRYLOV = 7,      /* GMRES vector kernels (dot products, updates, scaling)    */
+    DC_KT_APPLYH = 8,      /* adjoint operator application (element pass + gather)    */
+    DC_KT_ASSEMBLE = 9     /* per-step adjoint setup and front assembly               */
 };
 
 typedef struct dc_ctx dc_ctx;
@@ -125,12 +143,54 @@ dc_status dc_create_mesh(dc_ctx** out, int32_t n_nodes, const double* rest_pos,
                          int32_t n_tris, const int32_t* tris,
                          int32_t n_pins, const int32_t* pins, void* stream);
 
+/* One cloth of a batch (host arrays, as for dc_create_mesh). */
+typedef struct dc_instance {
+    int32_t n_nodes;
+    int32_t n_tris;
+    int32_t n_pins;
+    int32_t pad_;
+    const double* rest_pos;   /* [n_nodes][3] */
+    const int32_t* tris;      /* [n_tris][3]  */
+    const int32_t* pins;      /* [n_pins], may be NULL when n_pins = 0 */
+} dc_instance;
+
+/* Create one context holding n_instances cloths (n_instances >= 1; DC_ERR_INVALID
+ * for an invalid mesh, naming the instance).  The per-instance rest operators
+ * and orderings are built on several host threads.  Node numbering: instance i
+ * occupies nodes [off_i, off_i + n_nodes_i) of every node array, off_0 = 0. */
+dc_status dc_create_batch(dc_ctx** out, int32_t n_instances, const dc_instance* instances,
+                          void* stream);
+
+/* Number of instances and, if node_offsets is not NULL, the n_instances + 1
+ * node offsets of the concatenated node arrays (host array). */
+dc_status dc_get_layout(dc_ctx* ctx, int32_t* n_instances, int64_t* node_offsets);
+
 /* Set material, contact and solver parameters (host struct, copied).
  * Assembles the constant PD matrix P = M + h^2 sum_i w_i A_i^T A_i (Sec. 3.1,
  * Eq. pd_global), factorises it once (P = L L^T, host, nested-dissection
  * order) and uploads the solve operators.  Synchronous.  DC_ERR_NOT_SPD if a
  * pivot is not positive; DC_ERR_INVALID for non-finite or out-of-range values. */
 dc_status dc_set_params(dc_ctx* ctx, const dc_params* params);
+
+/* Per-instance parameters of a batch: params[i] for instance i (n_instances
+ * entries).  k_stretch, k_bend, density, mu and the obstacles may differ between
+ * instances; every other field must be equal in all entries (DC_ERR_INVALID
+ * otherwise).  dc_set_params on a batch gives every instance the same values.
+ * Each instance's P is assembled and factorised on its own (host threads). */
+dc_status dc_set_params_batch(dc_ctx* ctx, int32_t n_instances, const dc_params* params);
+
+/* Replay the forward steps of dc_rollout and of dc_backward's checkpoint
+ * recomputation as captured CUDA graphs (enable = 1) or launch them one by one
+ * (0, the default).  A graph is captured on first use for a given step count and
+ * replayed afterwards; the results are identical either way.  Graphs are not
+ * used while a kernel timer is set, for a trajectory output, or on the legacy
+ * default stream (which cannot be captured).  No counterpart in the paper. */
+dc_status dc_set_graphs(dc_ctx* ctx, int32_t enable);
+
+/* Time the element and node kernels of the forward step at several block sizes
+ * on this context's mesh and keep the fastest (synchronous; reported in
+ * dc_stats).  No block size changes any result.  No counterpart in the paper. */
+dc_status dc_autotune(dc_ctx* ctx);
 
 /* One time step (x_n, v_n) -> (x_{n+1}, v_{n+1}) (Sec. 3.2, Eq.
  * implicit_with_contact solved by n_pd_iters PD local/global iterations with
@@ -151,7 +211,8 @@ dc_status dc_rollout(dc_ctx* ctx, int32_t n_steps, const double* x0, const doubl
  * system per step in reverse order.
  *   dL_dx_final: [m][3] dL/dx_N.  dL_dv_final: [m][3] or NULL (zero).
  *   dL_dtraj_x: [(n_steps+1)][m][3] per-step dL/dx_n or NULL.
- * Outputs dL_dx0, dL_dv0: [m][3]; dL_dparams: [3] = dL/d(k_stretch, k_bend, mu).
+ * Outputs dL_dx0, dL_dv0: [m][3]; dL_dparams: [n_instances][3] =
+ * dL/d(k_stretch, k_bend, mu) of each instance.
  * DC_ERR_NONCONVERGED is reported (after all outputs are written) when an
  * adjoint step reached adj_max_iters above adj_tol. */
 dc_status dc_backward(dc_ctx* ctx, const double* dL_dx_final, const double* dL_dv_final,
@@ -196,6 +257,76 @@ void dc_destroy(dc_ctx* ctx);
 /* Message of the last failing call on ctx (or of the last failing
  * dc_create_mesh when ctx is NULL).  Valid until the next call. */
 const char* dc_last_error(dc_ctx* ctx);
+
+/* ------------------------------------------------------------------ serving
+ * A request server: many independent forward + adjoint rollouts (each its own
+ * cloth, size, step count and parameters) submitted at any time and run
+ * concurrently on one GPU.  No counterpart in the paper.
+ *  - Each request is prepared on a host thread (ordering, factorisation,
+ *    fronts) as soon as it is submitted, which also gives its exact device
+ *    footprint.  It is admitted, in submission order, when one of n_slots
+ *    slots is free and its footprint fits in what the HBM budget has left.  A
+ *    request larger than the whole budget fails with DC_ERR_OOM.
+ *  - An admitted request keeps its factorisation, fronts and checkpoints
+ *    resident until it finishes; slots run on their own CUDA streams and host
+ *    threads, so requests overlap on the device, and device memory comes from
+ *    the stream-ordered pool (no device-wide synchronisation when a request
+ *    starts or ends).
+ *  - A request's results are bitwise those of the same rollout and backward
+ *    run alone through dc_create_mesh / dc_rollout / dc_backward. */
+typedef struct dc_server dc_server;
+
+typedef struct dc_server_config {
+    int32_t n_slots;           /* requests on the device at once (>= 1)              */
+    int32_t n_prep_threads;    /* host threads preparing requests (>= 1)             */
+    int64_t hbm_budget_bytes;  /* device bytes the admitted requests may hold        */
+    int32_t max_prepared;      /* prepared requests waiting for a slot, at most      */
+    int32_t device;            /* CUDA device ordinal                                */
+} dc_server_config;
+
+typedef struct dc_request {
+    int32_t n_nodes, n_tris, n_pins, n_steps;
+    const double* rest_pos;      /* [n_nodes][3] host, copied at submission             */
+    const int32_t* tris;         /* [n_tris][3]                                         */
+    const int32_t* pins;         /* [n_pins] or NULL                                    */
+    const double* x0;            /* [n_nodes][3] initial positions                      */
+    const double* v0;            /* [n_nodes][3] initial velocities                     */
+    const double* dL_dx_final;   /* [n_nodes][3] loss gradient at the last step          */
+    const double* dL_dv_final;   /* [n_nodes][3] or NULL                                */
+    dc_params params;
+} dc_request;
+
+typedef struct dc_result {
+    dc_status status;
+    int32_t slot;                /* slot that ran the request (-1 if never admitted)    */
+    double* x_final;             /* caller-owned [n_nodes][3] host arrays, or NULL:     */
+    double* v_final;             /*   filled by dc_server_wait                          */
+    double* dL_dx0;
+    double* dL_dv0;
+    double dL_dparams[3];        /* dL/d(k_stretch, k_bend, mu)                          */
+    double t_submit, t_admit, t_done;   /* seconds on the server's clock                */
+    int64_t device_bytes;        /* footprint reserved at admission                     */
+    int64_t device_bytes_peak;   /* most device memory the request actually held        */
+    int64_t adj_iters;           /* GMRES iterations of its adjoint                     */
+    char message[256];           /* error message when status != DC_OK                  */
+} dc_result;
+
+typedef struct dc_server_stats {
+    int64_t submitted, completed, failed;
+    int64_t in_flight, peak_in_flight;
+    int64_t bytes_reserved, peak_bytes_reserved;
+    int64_t cloth_steps;         /* forward steps of the completed requests             */
+} dc_server_stats;
+
+/* Start a server (threads and streams) on cfg->device. */
+dc_status dc_server_create(dc_server** out, const dc_server_config* cfg);
+/* Queue a request (its arrays are copied before the call returns). */
+dc_status dc_server_submit(dc_server* srv, const dc_request* req, int64_t* ticket);
+/* Wait for a request to finish and collect its results (once per ticket). */
+dc_status dc_server_wait(dc_server* srv, int64_t ticket, dc_result* out);
+dc_status dc_server_get_stats(dc_server* srv, dc_server_stats* out);
+/* Finish every queued request, then stop the threads and free the server. */
+void dc_server_destroy(dc_server* srv);
 
 /* Fill *p with the library defaults (k_stretch 1e3, k_bend 1e-3, density 0.1,
  * mu 0.3, h 1/120, g = (0,-9.8,0), delta 1e-6, K = 20, adjoint tol 1e-10,

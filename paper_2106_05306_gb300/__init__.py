@@ -10,6 +10,11 @@ built library every call raises.
     xN, vN = cloth.rollout(x0, v0, n_steps)            # torch float64 (m, 3) tensors
     dx0, dv0, dtheta = cloth.backward(dL_dxN)          # dtheta = dL/d(k_stretch, k_bend, mu)
 
+    batch = ClothBatch([(rest_0, tris_0, pins_0), (rest_1, tris_1, pins_1), ...])
+    batch.set_params([dict(k_stretch=..., mu=..., obstacles=[...]), ...])
+    xN, vN = batch.rollout(x0, v0, n_steps)            # concatenated (sum m_i, 3) tensors
+    dx0, dv0, dtheta = batch.backward(dL_dxN)          # dtheta: (n_instances, 3)
+
 ``rollout_fn`` wraps rollout/backward as a torch.autograd.Function.
 """
 from __future__ import annotations
@@ -18,12 +23,16 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (DC_CAPSULE, DC_MAX_OBSTACLES, DC_PLANE, DC_SPHERE, DCError, check, dc_params, dc_stats,
-                   load)
+from ._lib import (DC_CAPSULE, DC_MAX_OBSTACLES, DC_PLANE, DC_SPHERE, STATUS_NAMES, DCError, check, dc_instance,
+                   dc_params, dc_request, dc_result, dc_server_config, dc_server_stats, dc_stats, load)
 
-__all__ = ["Cloth", "rollout_fn", "DCError", "load"]
+__all__ = ["Cloth", "ClothBatch", "Server", "rollout_fn", "DCError", "load"]
 
 _KIND = {"plane": DC_PLANE, "sphere": DC_SPHERE, "capsule": DC_CAPSULE}
+
+_PARAM_DEFAULTS = dict(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0, gravity=(0.0, -9.8, 0.0),
+                       contact_margin=1e-6, n_pd_iters=20, obstacles=(), adj_tol=1e-10, adj_max_iters=2000,
+                       adj_restart=200, checkpoint_every=1, adj_precond=0)
 
 
 def _torch():
@@ -54,67 +63,56 @@ def _obstacle_struct(ob, out):
         out.p[i] = float(p[i])
 
 
-class Cloth:
-    """One cloth mesh on the GPU (a libdc context)."""
+def _make_params(lib, kw) -> dc_params:
+    unknown = set(kw) - set(_PARAM_DEFAULTS)
+    if unknown:
+        raise TypeError(f"unknown parameter(s): {sorted(unknown)}")
+    q = dict(_PARAM_DEFAULTS)
+    q.update(kw)
+    p = dc_params()
+    lib.dc_default_params(ctypes.byref(p))
+    p.k_stretch, p.k_bend, p.density, p.mu, p.h = q["k_stretch"], q["k_bend"], q["density"], q["mu"], q["h"]
+    for i in range(3):
+        p.gravity[i] = float(q["gravity"][i])
+    p.contact_margin = q["contact_margin"]
+    p.n_pd_iters = int(q["n_pd_iters"])
+    p.adj_tol = q["adj_tol"]
+    p.adj_max_iters = int(q["adj_max_iters"])
+    p.adj_restart = int(q["adj_restart"])
+    p.checkpoint_every = int(q["checkpoint_every"])
+    p.adj_precond = int(q["adj_precond"])
+    obstacles = list(q["obstacles"])
+    if len(obstacles) > DC_MAX_OBSTACLES:
+        raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
+    p.n_obstacles = len(obstacles)
+    for i, ob in enumerate(obstacles):
+        _obstacle_struct(ob, p.obstacles[i])
+    q["obstacles"] = obstacles
+    q["gravity"] = tuple(q["gravity"])
+    return p, q
 
-    def __init__(self, rest_pos, tris, pins=(), device="cuda", stream=None):
-        torch = _torch()
-        lib = load()
-        self._lib = lib
-        self.device = torch.device(device)
-        rest = np.ascontiguousarray(np.asarray(rest_pos, dtype=np.float64).reshape(-1, 3))
-        tri = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
-        pin = np.ascontiguousarray(np.asarray(pins, dtype=np.int32).reshape(-1))
-        self.m = rest.shape[0]
-        self.n_tris = tri.shape[0]
-        if stream is None:
-            stream = torch.cuda.current_stream(self.device).cuda_stream
-        self.stream = stream
-        ctx = ctypes.c_void_p()
-        st = lib.dc_create_mesh(ctypes.byref(ctx), self.m, rest.ctypes.data, self.n_tris, tri.ctypes.data,
-                                len(pin), pin.ctypes.data if len(pin) else None, ctypes.c_void_p(stream))
-        check(st, None)
+
+def _mesh_arrays(rest_pos, tris, pins):
+    rest = np.ascontiguousarray(np.asarray(rest_pos, dtype=np.float64).reshape(-1, 3))
+    tri = np.ascontiguousarray(np.asarray(tris, dtype=np.int32).reshape(-1, 3))
+    pin = np.ascontiguousarray(np.asarray(pins, dtype=np.int32).reshape(-1))
+    return rest, tri, pin
+
+
+class _Context:
+    """Common marshalling of a libdc context (one cloth or a batch)."""
+
+    def _init_common(self, ctx, device):
         self._ctx = ctx
+        self.device = device
+        n = ctypes.c_int32()
+        check(self._lib.dc_get_layout(self._ctx, ctypes.byref(n), None), self._ctx)
+        offs = np.zeros(n.value + 1, dtype=np.int64)
+        check(self._lib.dc_get_layout(self._ctx, ctypes.byref(n), offs.ctypes.data), self._ctx)
+        self.n_instances = int(n.value)
+        self.node_offsets = offs
+        self.m = int(offs[-1])
         self.params = None
-        self._theta = None
-
-    # ------------------------------------------------------------------ params
-    def set_params(self, k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0,
-                   gravity=(0.0, -9.8, 0.0), contact_margin=1e-6, n_pd_iters=20, obstacles=(),
-                   adj_tol=1e-10, adj_max_iters=2000, adj_restart=200, checkpoint_every=1, adj_precond=0):
-        p = dc_params()
-        self._lib.dc_default_params(ctypes.byref(p))
-        p.k_stretch, p.k_bend, p.density, p.mu, p.h = k_stretch, k_bend, density, mu, h
-        for i in range(3):
-            p.gravity[i] = float(gravity[i])
-        p.contact_margin = contact_margin
-        p.n_pd_iters = int(n_pd_iters)
-        p.adj_tol = adj_tol
-        p.adj_max_iters = int(adj_max_iters)
-        p.adj_restart = int(adj_restart)
-        p.checkpoint_every = int(checkpoint_every)
-        p.adj_precond = int(adj_precond)
-        obstacles = list(obstacles)
-        if len(obstacles) > DC_MAX_OBSTACLES:
-            raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
-        p.n_obstacles = len(obstacles)
-        for i, ob in enumerate(obstacles):
-            _obstacle_struct(ob, p.obstacles[i])
-        check(self._lib.dc_set_params(self._ctx, ctypes.byref(p)), self._ctx)
-        self.params = dict(k_stretch=k_stretch, k_bend=k_bend, density=density, mu=mu, h=h, gravity=tuple(gravity),
-                           contact_margin=contact_margin, n_pd_iters=n_pd_iters, obstacles=obstacles,
-                           adj_tol=adj_tol, adj_max_iters=adj_max_iters, adj_restart=adj_restart,
-                           checkpoint_every=checkpoint_every, adj_precond=adj_precond)
-        self._theta = (float(k_stretch), float(k_bend), float(mu))
-        return self
-
-    def set_theta(self, k_stretch, k_bend, mu):
-        """Change the differentiable parameters (refactorises P when they change)."""
-        th = (float(k_stretch), float(k_bend), float(mu))
-        if th != self._theta:
-            kw = dict(self.params)
-            kw.update(k_stretch=th[0], k_bend=th[1], mu=th[2])
-            self.set_params(**kw)
 
     # ------------------------------------------------------------------ helpers
     def _arr(self, a, name):
@@ -135,6 +133,11 @@ class Cloth:
         return torch.empty(shape, dtype=torch.float64, device=a.device,
                            pin_memory=(a.device.type == "cpu" and a.is_pinned()))
 
+    def split(self, a):
+        """Split a concatenated (m, 3) node array into the per-instance (m_i, 3) views."""
+        o = self.node_offsets
+        return [a[int(o[i]):int(o[i + 1])] for i in range(self.n_instances)]
+
     # ------------------------------------------------------------------ API
     def step(self, x, v):
         x = self._arr(x, "x")
@@ -153,7 +156,7 @@ class Cloth:
         self.n_steps = int(n_steps)
         return (xN, vN, tr) if traj else (xN, vN)
 
-    def backward(self, dL_dx, dL_dv=None, dL_dtraj=None, allow_nonconverged=False):
+    def _backward(self, dL_dx, dL_dv, dL_dtraj, allow_nonconverged, dth_shape):
         torch = _torch()
         gx = self._arr(dL_dx, "dL_dx")
         gv = self._arr(dL_dv, "dL_dv") if dL_dv is not None else None
@@ -162,7 +165,8 @@ class Cloth:
             gt = dL_dtraj if isinstance(dL_dtraj, torch.Tensor) else torch.from_numpy(np.asarray(dL_dtraj))
             gt = gt.to(torch.float64).contiguous()
         dx0, dv0 = self._like(gx), self._like(gx)
-        dth = torch.empty(3, dtype=torch.float64, device=gx.device)
+        dth = torch.empty(dth_shape, dtype=torch.float64, device=gx.device,
+                          pin_memory=(gx.device.type == "cpu" and gx.is_pinned()))
         st = self._lib.dc_backward(self._ctx, gx.data_ptr(), gv.data_ptr() if gv is not None else None,
                                    gt.data_ptr() if gt is not None else None, dx0.data_ptr(), dv0.data_ptr(),
                                    dth.data_ptr())
@@ -175,6 +179,16 @@ class Cloth:
         out = self._like(rhs)
         check(self._lib.dc_global_solve(self._ctx, rhs.data_ptr(), out.data_ptr()), self._ctx)
         return out
+
+    def set_graphs(self, enable=True):
+        """Replay the forward steps of rollouts as captured CUDA graphs (results unchanged)."""
+        check(self._lib.dc_set_graphs(self._ctx, 1 if enable else 0), self._ctx)
+        return self
+
+    def autotune(self):
+        """Pick the block sizes of the element and node kernels by timing them (results unchanged)."""
+        check(self._lib.dc_autotune(self._ctx), self._ctx)
+        return self
 
     def stats(self):
         s = dc_stats()
@@ -193,6 +207,160 @@ class Cloth:
         if getattr(self, "_ctx", None):
             self._lib.dc_destroy(self._ctx)
             self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Cloth(_Context):
+    """One cloth mesh on the GPU (a libdc context)."""
+
+    def __init__(self, rest_pos, tris, pins=(), device="cuda", stream=None):
+        torch = _torch()
+        self._lib = load()
+        device = torch.device(device)
+        rest, tri, pin = _mesh_arrays(rest_pos, tris, pins)
+        self.n_tris = tri.shape[0]
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        st = self._lib.dc_create_mesh(ctypes.byref(ctx), rest.shape[0], rest.ctypes.data, self.n_tris,
+                                      tri.ctypes.data, len(pin), pin.ctypes.data if len(pin) else None,
+                                      ctypes.c_void_p(stream))
+        check(st, None)
+        self._init_common(ctx, device)
+        self._theta = None
+
+    def set_params(self, **kw):
+        p, q = _make_params(self._lib, kw)
+        check(self._lib.dc_set_params(self._ctx, ctypes.byref(p)), self._ctx)
+        self.params = q
+        self._theta = (float(q["k_stretch"]), float(q["k_bend"]), float(q["mu"]))
+        return self
+
+    def set_theta(self, k_stretch, k_bend, mu):
+        """Change the differentiable parameters (refactorises P when they change)."""
+        th = (float(k_stretch), float(k_bend), float(mu))
+        if th != self._theta:
+            kw = dict(self.params)
+            kw.update(k_stretch=th[0], k_bend=th[1], mu=th[2])
+            self.set_params(**kw)
+
+    def backward(self, dL_dx, dL_dv=None, dL_dtraj=None, allow_nonconverged=False):
+        return self._backward(dL_dx, dL_dv, dL_dtraj, allow_nonconverged, (3,))
+
+
+class ClothBatch(_Context):
+    """Several cloth meshes of any sizes packed into one libdc context: every phase of
+    the step and of the adjoint is one launch over all of them.  Node arrays are the
+    concatenation of the instances' (m_i, 3) arrays (``node_offsets``)."""
+
+    def __init__(self, meshes, device="cuda", stream=None):
+        torch = _torch()
+        self._lib = load()
+        device = torch.device(device)
+        arrays = [_mesh_arrays(*mesh) for mesh in meshes]
+        if not arrays:
+            raise ValueError("ClothBatch needs at least one mesh")
+        inst = (dc_instance * len(arrays))()
+        for i, (rest, tri, pin) in enumerate(arrays):
+            inst[i].n_nodes = rest.shape[0]
+            inst[i].n_tris = tri.shape[0]
+            inst[i].n_pins = len(pin)
+            inst[i].rest_pos = rest.ctypes.data
+            inst[i].tris = tri.ctypes.data
+            inst[i].pins = pin.ctypes.data if len(pin) else None
+        if stream is None:
+            stream = torch.cuda.current_stream(device).cuda_stream
+        self.stream = stream
+        ctx = ctypes.c_void_p()
+        check(self._lib.dc_create_batch(ctypes.byref(ctx), len(arrays), ctypes.addressof(inst),
+                                        ctypes.c_void_p(stream)), None)
+        self._init_common(ctx, device)
+
+    def set_params(self, params):
+        """params: one dict for every instance, or a list of n_instances dicts.  Only
+        k_stretch, k_bend, density, mu and obstacles may differ between instances."""
+        if isinstance(params, dict):
+            params = [params] * self.n_instances
+        params = list(params)
+        built = [_make_params(self._lib, kw) for kw in params]
+        arr = (dc_params * len(built))(*[b[0] for b in built])
+        check(self._lib.dc_set_params_batch(self._ctx, len(built), ctypes.addressof(arr)), self._ctx)
+        self.params = [b[1] for b in built]
+        return self
+
+    def backward(self, dL_dx, dL_dv=None, dL_dtraj=None, allow_nonconverged=False):
+        return self._backward(dL_dx, dL_dv, dL_dtraj, allow_nonconverged, (self.n_instances, 3))
+
+
+class Server:
+    """Request server (dc_server_*): forward + adjoint rollouts submitted at any time,
+    admitted by free slot and HBM budget, run concurrently on one GPU.
+
+    ``submit`` copies its arguments and returns a ticket; ``wait(ticket)`` blocks
+    until that request is done and returns its results (numpy arrays) and timings."""
+
+    def __init__(self, n_slots=4, n_prep_threads=4, hbm_budget_bytes=None, max_prepared=None, device=0):
+        self._lib = load()
+        if hbm_budget_bytes is None:
+            torch = _torch()
+            free, _ = torch.cuda.mem_get_info(device)
+            hbm_budget_bytes = int(0.8 * free)
+        cfg = dc_server_config(n_slots=int(n_slots), n_prep_threads=int(n_prep_threads),
+                               hbm_budget_bytes=int(hbm_budget_bytes),
+                               max_prepared=int(max_prepared if max_prepared is not None else 2 * n_slots + 2),
+                               device=int(device))
+        srv = ctypes.c_void_p()
+        check(self._lib.dc_server_create(ctypes.byref(srv), ctypes.byref(cfg)), None)
+        self._srv = srv
+        self._sizes = {}
+        self.hbm_budget_bytes = int(hbm_budget_bytes)
+
+    def submit(self, rest_pos, tris, pins, x0, v0, dL_dx, n_steps, params=None, dL_dv=None):
+        rest, tri, pin = _mesh_arrays(rest_pos, tris, pins)
+        f64 = [np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(-1, 3)) for a in (x0, v0, dL_dx)]
+        gv = np.ascontiguousarray(np.asarray(dL_dv, dtype=np.float64).reshape(-1, 3)) if dL_dv is not None else None
+        m = rest.shape[0]
+        for a in f64 + ([gv] if gv is not None else []):
+            if a.shape[0] != m:
+                raise ValueError(f"expected {m} x 3 values, got {a.shape}")
+        p, _ = _make_params(self._lib, dict(params or {}))
+        req = dc_request(n_nodes=m, n_tris=tri.shape[0], n_pins=len(pin), n_steps=int(n_steps),
+                         rest_pos=rest.ctypes.data, tris=tri.ctypes.data,
+                         pins=pin.ctypes.data if len(pin) else None, x0=f64[0].ctypes.data, v0=f64[1].ctypes.data,
+                         dL_dx_final=f64[2].ctypes.data, dL_dv_final=gv.ctypes.data if gv is not None else None,
+                         params=p)
+        t = ctypes.c_int64()
+        check(self._lib.dc_server_submit(self._srv, ctypes.byref(req), ctypes.byref(t)), None)
+        self._sizes[t.value] = m
+        return t.value
+
+    def wait(self, ticket):
+        m = self._sizes.pop(ticket)
+        out = {k: np.empty((m, 3)) for k in ("x_final", "v_final", "dL_dx0", "dL_dv0")}
+        r = dc_result(x_final=out["x_final"].ctypes.data, v_final=out["v_final"].ctypes.data,
+                      dL_dx0=out["dL_dx0"].ctypes.data, dL_dv0=out["dL_dv0"].ctypes.data)
+        check(self._lib.dc_server_wait(self._srv, int(ticket), ctypes.byref(r)), None)
+        out.update(status=STATUS_NAMES.get(r.status, r.status), dL_dparams=np.array(list(r.dL_dparams)),
+                   slot=r.slot, t_submit=r.t_submit, t_admit=r.t_admit, t_done=r.t_done,
+                   device_bytes=r.device_bytes, device_bytes_peak=r.device_bytes_peak, adj_iters=r.adj_iters,
+                   message=r.message.decode())
+        return out
+
+    def stats(self):
+        s = dc_server_stats()
+        check(self._lib.dc_server_get_stats(self._srv, ctypes.byref(s)), None)
+        return {k: getattr(s, k) for k, _ in s._fields_}
+
+    def close(self):
+        if getattr(self, "_srv", None):
+            self._lib.dc_server_destroy(self._srv)
+            self._srv = None
 
     def __del__(self):
         try:

@@ -39,9 +39,45 @@ class dc_stats(ctypes.Structure):
                 ("timer_launches", ctypes.c_int64), ("fwd_solve_nnz", ctypes.c_int64),
                 ("bwd_solve_nnz", ctypes.c_int64), ("front_flops", ctypes.c_double),
                 ("front_levels", ctypes.c_int32), ("n_supernodes", ctypes.c_int32),
-                ("factorisations", ctypes.c_int64)]
+                ("factorisations", ctypes.c_int64), ("n_instances", ctypes.c_int32), ("graphs", ctypes.c_int32),
+                ("graph_replays", ctypes.c_int64), ("block_local", ctypes.c_int32), ("block_gather", ctypes.c_int32),
+                ("block_node", ctypes.c_int32), ("block_elem", ctypes.c_int32), ("adj_batch_iters", ctypes.c_int64)]
 
-KT_CLASSES = {"none": 0, "solve_fwd": 1, "solve_bwd": 2, "local": 3, "gather": 4, "front": 5, "msolve": 6}
+
+class dc_instance(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_tris", ctypes.c_int32), ("n_pins", ctypes.c_int32),
+                ("pad_", ctypes.c_int32), ("rest_pos", ctypes.c_void_p), ("tris", ctypes.c_void_p),
+                ("pins", ctypes.c_void_p)]
+
+class dc_server_config(ctypes.Structure):
+    _fields_ = [("n_slots", ctypes.c_int32), ("n_prep_threads", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
+                ("max_prepared", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+class dc_request(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int32), ("n_tris", ctypes.c_int32), ("n_pins", ctypes.c_int32),
+                ("n_steps", ctypes.c_int32), ("rest_pos", ctypes.c_void_p), ("tris", ctypes.c_void_p),
+                ("pins", ctypes.c_void_p), ("x0", ctypes.c_void_p), ("v0", ctypes.c_void_p),
+                ("dL_dx_final", ctypes.c_void_p), ("dL_dv_final", ctypes.c_void_p), ("params", dc_params)]
+
+
+class dc_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("slot", ctypes.c_int32), ("x_final", ctypes.c_void_p),
+                ("v_final", ctypes.c_void_p), ("dL_dx0", ctypes.c_void_p), ("dL_dv0", ctypes.c_void_p),
+                ("dL_dparams", ctypes.c_double * 3), ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("device_bytes", ctypes.c_int64), ("device_bytes_peak", ctypes.c_int64),
+                ("adj_iters", ctypes.c_int64), ("message", ctypes.c_char * 256)]
+
+
+class dc_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
+                ("in_flight", ctypes.c_int64), ("peak_in_flight", ctypes.c_int64),
+                ("bytes_reserved", ctypes.c_int64), ("peak_bytes_reserved", ctypes.c_int64),
+                ("cloth_steps", ctypes.c_int64)]
+
+
+KT_CLASSES = {"none": 0, "solve_fwd": 1, "solve_bwd": 2, "local": 3, "gather": 4, "front": 5, "msolve": 6,
+              "krylov": 7, "apply_h": 8, "assemble": 9}
 
 
 _P = ctypes.c_void_p
@@ -50,7 +86,12 @@ _D = ctypes.POINTER(ctypes.c_double)
 SIGNATURES = {
     "dc_create_mesh": (ctypes.c_int32, [ctypes.POINTER(_P), ctypes.c_int32, _P, ctypes.c_int32, _P,
                                         ctypes.c_int32, _P, _P]),
+    "dc_create_batch": (ctypes.c_int32, [ctypes.POINTER(_P), ctypes.c_int32, _P, _P]),
+    "dc_get_layout": (ctypes.c_int32, [_P, ctypes.POINTER(ctypes.c_int32), _P]),
     "dc_set_params": (ctypes.c_int32, [_P, ctypes.POINTER(dc_params)]),
+    "dc_set_params_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
+    "dc_set_graphs": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_autotune": (ctypes.c_int32, [_P]),
     "dc_step": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
     "dc_rollout": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
     "dc_backward": (ctypes.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
@@ -62,6 +103,11 @@ SIGNATURES = {
     "dc_destroy": (None, [_P]),
     "dc_last_error": (ctypes.c_char_p, [_P]),
     "dc_default_params": (None, [ctypes.POINTER(dc_params)]),
+    "dc_server_create": (ctypes.c_int32, [ctypes.POINTER(_P), ctypes.POINTER(dc_server_config)]),
+    "dc_server_submit": (ctypes.c_int32, [_P, ctypes.POINTER(dc_request), ctypes.POINTER(ctypes.c_int64)]),
+    "dc_server_wait": (ctypes.c_int32, [_P, ctypes.c_int64, ctypes.POINTER(dc_result)]),
+    "dc_server_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_server_stats)]),
+    "dc_server_destroy": (None, [_P]),
 }
 
 _lib = None

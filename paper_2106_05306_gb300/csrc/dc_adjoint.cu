@@ -164,14 +164,14 @@ __global__ void k_adj_setup_node(DevMesh dm, AdjDev ad, const d4* __restrict__ v
         double th[3] = {uT[0] / nt, uT[1] / nt, uT[2] / nt};
         double bh[3] = {n[1] * th[2] - n[2] * th[1], n[2] * th[0] - n[0] * th[2], n[0] * th[1] - n[1] * th[0]};
         double fN = f.x * n[0] + f.y * n[1] + f.z * n[2];
-        double ks = ad.h * ad.mu * fN / nt;
+        double ks = ad.h * ad.mu[j] * fN / nt;
         for (int r = 0; r < 3; ++r)
             for (int c = 0; c < 3; ++c) Hf[3 * r + c] += ks * bh[r] * bh[c];
         st(ad.slip + j, th[0], th[1], th[2], ks);
         // Q = [b, t + mu n] spans null(C^T); R = [t, b] spans null(B^T)
         double Q[3][2], Rm[3][2];
         for (int r = 0; r < 3; ++r) {
-            Q[r][0] = bh[r]; Q[r][1] = th[r] + ad.mu * n[r];
+            Q[r][0] = bh[r]; Q[r][1] = th[r] + ad.mu[j] * n[r];
             Rm[r][0] = th[r]; Rm[r][1] = bh[r];
         }
         double Rt_H_Q[2][2];
@@ -359,7 +359,8 @@ __global__ void k_adj_solve_bwd(DevMesh dm, AdjDev ad, const d4* __restrict__ y,
         s0 = s1 = s2 = 0.0;
     } else if (type == 2) {
         d4 sl = ld(ad.slip + row), nb = ld(ad.nb + row);
-        double cz = (nb.x - ad.mu * sl.x) * s0 + (nb.y - ad.mu * sl.y) * s1 + (nb.z - ad.mu * sl.z) * s2;
+        const double mu = ad.mu[row];
+        double cz = (nb.x - mu * sl.x) * s0 + (nb.y - mu * sl.y) * s1 + (nb.z - mu * sl.z) * s2;
         s0 -= cz * nb.x; s1 -= cz * nb.y; s2 -= cz * nb.z;
     }
     d4 bb = ld(base + row);
@@ -367,75 +368,75 @@ __global__ void k_adj_solve_bwd(DevMesh dm, AdjDev ad, const d4* __restrict__ y,
 }
 
 // ----------------------------------------------------------------- Krylov helpers
+//
+// Every vector of the Krylov solve holds the free nodes of all instances (4
+// doubles per node).  Reductions are per instance: each instance's segment is
+// cut into chunks counted from the instance's own first node, every chunk is
+// reduced in a fixed order, and the chunk sums of an instance are added in
+// chunk order.  An instance therefore gets bitwise the same dot products alone
+// and in any batch.
 
-constexpr int RED_BLOCKS = 304;   // 2 x 152 SMs
 constexpr int RED_THREADS = 256;
+constexpr int DOT_THREADS = 128;
 
-// partial[j * RED_BLOCKS + blk] = sum over this block's chunk of V_j . w
-__global__ void k_mdot(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ w, long n,
-                       double* __restrict__ partial) {
-    __shared__ double sh[RED_THREADS / 32];
-    long chunk = (n + gridDim.x - 1) / gridDim.x;
-    long lo = blockIdx.x * chunk, hi = min(n, lo + chunk);
-    for (int j = 0; j < nvec; ++j) {
-        const double* v = V + j * ldv;
-        double s = 0.0;
-        for (long i = lo + threadIdx.x; i < hi; i += blockDim.x) s += v[i] * w[i];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int q = 0; q < RED_THREADS / 32; ++q) t += sh[q];
-            partial[j * gridDim.x + blockIdx.x] = t;
-        }
-        __syncthreads();
-    }
-}
-
-// out[j] = sum_b partial[j * nb + b] in a fixed tree order (one block per j)
-__global__ void k_reduce(const double* __restrict__ partial, int nb, double* __restrict__ out) {
-    __shared__ double sh[RED_THREADS];
-    int j = blockIdx.x;
+// partial[j * nchunk + c] = sum over chunk c of V_j . w   (grid: chunks x vectors)
+__global__ void __launch_bounds__(DOT_THREADS) k_bmdot(const double* __restrict__ V, long ldv,
+                                                       const double* __restrict__ w, const int4* __restrict__ chunk,
+                                                       int nchunk, double* __restrict__ partial) {
+    __shared__ double sh[DOT_THREADS / 32];
+    const int c = blockIdx.x, j = blockIdx.y;
+    const int4 ch = chunk[c];
+    const double* v = V + j * ldv;
     double s = 0.0;
-    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += partial[j * nb + b];
-    sh[threadIdx.x] = s;
+    for (int i = ch.y + threadIdx.x; i < ch.z; i += DOT_THREADS) s += v[i] * w[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < DOT_THREADS / 32; ++q) t += sh[q];
+        partial[(long)j * nchunk + c] = t;
     }
-    if (threadIdx.x == 0) out[j] = sh[0];
 }
 
-// w[i] -= sum_j V_j[i] c[j]   (c on device)
-__global__ void k_vupdate(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ c,
-                          double* __restrict__ w, long n, double sign) {
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// out[j * B + i] = sum of instance i's chunk partials of vector j, in chunk order
+__global__ void k_breduce(const double* __restrict__ partial, int nchunk, const int* __restrict__ cptr, int B,
+                          int nvec, double* __restrict__ out) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= B * nvec) return;
+    int j = id / B, i = id - j * B;
+    const double* p = partial + (long)j * nchunk;
     double s = 0.0;
-    for (int j = 0; j < nvec; ++j) s += V[j * ldv + i] * c[j];
-    w[i] += sign * s;
+    for (int c = cptr[i]; c < cptr[i + 1]; ++c) s += p[c];
+    out[id] = s;
 }
 
-__global__ void k_scale(const double* __restrict__ a, double s, double* __restrict__ out, long n) {
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = a[i] * s;
+// w += sign * sum_j V_j coef[j * B + inst]   (one block per chunk)
+__global__ void k_bvupdate(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ coef, int B,
+                           const int4* __restrict__ chunk, double* __restrict__ w, double sign) {
+    const int4 ch = chunk[blockIdx.x];
+    for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = 0; j < nvec; ++j) s += V[j * ldv + i] * coef[j * B + ch.x];
+        w[i] += sign * s;
+    }
 }
 
-__global__ void k_axpby(double a, const double* __restrict__ x, double b, const double* __restrict__ y,
-                        double* __restrict__ out, long n) {
-    long i = blockIdx.x * (long)blockDim.x + threadIdx.x;
-    if (i < n) out[i] = a * x[i] + b * y[i];
+// out = a * sc[inst]   (one block per chunk)
+__global__ void k_bscale(const double* __restrict__ a, const double* __restrict__ sc,
+                         const int4* __restrict__ chunk, double* __restrict__ out) {
+    const int4 ch = chunk[blockIdx.x];
+    const double f = sc[ch.x];
+    for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) out[i] = a[i] * f;
 }
 
 // ----------------------------------------------------------------- gradient outputs
 
 __device__ void normal_jacobian(const DevParams& P, int o, const double x[3], double Dn[9]) {
     for (int q = 0; q < 9; ++q) Dn[q] = 0.0;
-    int kind = P.kind[o];
+    int kind = P.okind[o];
     if (kind == DC_PLANE) return;
-    const double* p = P.op[o];
+    const double* p = P.oprm + 8 * o;
     double c[3];
     double e[3] = {0, 0, 0};
     bool axis = false;
@@ -531,7 +532,7 @@ __global__ void k_adj_outputs(DevMesh dm, AdjDev ad, DevParams P, const d4* __re
             for (int a = 0; a < 3; ++a) {
                 double s = 0, s2 = 0;
                 for (int b = 0; b < 3; ++b) {
-                    s += (Dn[3 * b + a] - P.mu * Dt[3 * b + a]) * zz[b];
+                    s += (Dn[3 * b + a] - P.node_mu[j] * Dt[3 * b + a]) * zz[b];
                     s2 += Dn[3 * b + a] * v[b];
                 }
                 o[a] += h * fN * s;
@@ -542,18 +543,19 @@ __global__ void k_adj_outputs(DevMesh dm, AdjDev ad, DevParams P, const d4* __re
     st(gx_out + j, o[0], o[1], o[2]);
 }
 
-// Per-element parameter-gradient terms, reduced per block:
-// part[0][blk] = -h sum_t area_t <A_t z, A_t x - R_t>, part[1][blk] = -h sum_b a_b <l_b z, q_b - p_b>,
-// part[2][blk] = -h sum_slip f_N (t . z_j).
+// Per-element parameter-gradient terms of one chunk (inst, kind, lo, hi):
+// kind 0: -h area_t <A_t z, A_t x - R_t> over triangles t in [lo, hi);
+// kind 1: -h a_b <l_b z, q_b - p_b> over bending vertices b in [lo, hi);
+// kind 2: -h f_N (t . z_j) over slip nodes j in [lo, hi).   part[c] = chunk sum.
 __global__ void k_adj_param_terms(DevMesh dm, AdjDev ad, const d4* __restrict__ z, const d4* __restrict__ x1,
-                                  double* __restrict__ part) {
-    __shared__ double sh[3][RED_THREADS / 32];
+                                  const int4* __restrict__ chunk, double* __restrict__ part) {
+    __shared__ double sh[RED_THREADS / 32];
     const double h = ad.h;
-    double s_ks = 0.0, s_kb = 0.0, s_mu = 0.0;
-    long total = (long)dm.T + dm.m + dm.m_free;
-    for (long id = blockIdx.x * (long)blockDim.x + threadIdx.x; id < total; id += (long)gridDim.x * blockDim.x) {
-        if (id < dm.T) {
-            int t = (int)id;
+    const int4 ch = chunk[blockIdx.x];
+    double acc_s = 0.0;
+    for (int id = ch.z + threadIdx.x; id < ch.w; id += blockDim.x) {
+        if (ch.y == 0) {
+            int t = id;
             int4 tr = dm.tri[t];
             d4 g = ld(dm.G + t);
             d4 a = ld(x1 + tr.x), b = ld(x1 + tr.y), c = ld(x1 + tr.z);
@@ -568,9 +570,9 @@ __global__ void k_adj_param_terms(DevMesh dm, AdjDev ad, const d4* __restrict__ 
                 double Z0 = ze1[k] * g.x + ze2[k] * g.z, Z1 = ze1[k] * g.y + ze2[k] * g.w;
                 acc += Z0 * (F0 - R0[k]) + Z1 * (F1 - R1[k]);
             }
-            s_ks -= h * dm.area[t] * acc;
-        } else if (id < (long)dm.T + dm.m) {
-            int b = (int)(id - dm.T);
+            acc_s -= h * dm.area[t] * acc;
+        } else if (ch.y == 1) {
+            int b = id;
             double q[3] = {0, 0, 0}, dq[3] = {0, 0, 0};
             for (int k = dm.bptr[b]; k < dm.bptr[b + 1]; ++k) {
                 d4 x = ld(x1 + dm.bidx[k]), zz = ld(z + dm.bidx[k]);
@@ -588,37 +590,36 @@ __global__ void k_adj_param_terms(DevMesh dm, AdjDev ad, const d4* __restrict__ 
                     p[0] = qr.x; p[1] = qr.y; p[2] = qr.z;
                 }
             }
-            s_kb -= h * dm.abar[b] * (dq[0] * (q[0] - p[0]) + dq[1] * (q[1] - p[1]) + dq[2] * (q[2] - p[2]));
+            acc_s -= h * dm.abar[b] * (dq[0] * (q[0] - p[0]) + dq[1] * (q[1] - p[1]) + dq[2] * (q[2] - p[2]));
         } else {
-            int j = (int)(id - dm.T - dm.m);
+            int j = id;
             if (ad.type[j] == 2) {
                 d4 sl = ld(ad.slip + j), nb = ld(ad.nb + j), ff = ld(ad.f + j), zj = ld(z + j);
                 double fN = ff.x * nb.x + ff.y * nb.y + ff.z * nb.z;
-                s_mu -= h * fN * (sl.x * zj.x + sl.y * zj.y + sl.z * zj.z);
+                acc_s -= h * fN * (sl.x * zj.x + sl.y * zj.y + sl.z * zj.z);
             }
         }
     }
-    double v[3] = {s_ks, s_kb, s_mu};
-    for (int q = 0; q < 3; ++q) {
-        double s = v[q];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if ((threadIdx.x & 31) == 0) sh[q][threadIdx.x >> 5] = s;
-    }
+    double s = acc_s;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
     __syncthreads();
-    if (threadIdx.x < 3) {
+    if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int k = 0; k < RED_THREADS / 32; ++k) t += sh[threadIdx.x][k];
-        part[threadIdx.x * gridDim.x + blockIdx.x] = t;
+        for (int k = 0; k < RED_THREADS / 32; ++k) t += sh[k];
+        part[blockIdx.x] = t;
     }
 }
 
-// acc[q] += sum_b part[q * nb + b] (fixed order, one thread per parameter)
-__global__ void k_param_accumulate(const double* __restrict__ part, int nb, double* __restrict__ acc) {
-    int q = threadIdx.x;
-    if (q >= 3) return;
+// acc[4 i + q] += sum of part over the chunks of (instance i, kind q), in order
+__global__ void k_param_accumulate(const double* __restrict__ part, const int* __restrict__ pcptr, int B,
+                                   double* __restrict__ acc) {
+    int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= 3 * B) return;
+    int i = id / 3, q = id - 3 * i;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += part[q * nb + b];
-    acc[q] += s;
+    for (int c = pcptr[id]; c < pcptr[id + 1]; ++c) s += part[c];
+    acc[4 * i + q] += s;
 }
 
 __global__ void k_add_ext(d4* __restrict__ g, const double* __restrict__ ext, const int* __restrict__ int2ext,
@@ -667,10 +668,10 @@ void adj_rhs(const DevMesh& dm, const AdjDev& ad, const d4* gx, const d4* gv, d4
 }
 void adj_apply_H(const DevMesh& dm, const AdjDev& ad, int mode, const d4* z, const d4* w, d4* out, cudaStream_t s) {
     dc_note_launch();
-    k_adj_elem<<<nblk((long)dm.T + dm.m, 128), 128, 0, s>>>(dm, ad, z, ad.c1, ad.c2, ad.bu);
+    k_adj_elem<<<nblk((long)dm.T + dm.m, dm.bs_elem), dm.bs_elem, 0, s>>>(dm, ad, z, ad.c1, ad.c2, ad.bu);
     int n = (mode == 3) ? dm.m : dm.m_free;
     dc_note_launch();
-    k_adj_gather<<<nblk(n, 128), 128, 0, s>>>(dm, ad, mode, z, ad.c1, ad.c2, ad.bu, w, out);
+    k_adj_gather<<<nblk(n, dm.bs_gather), dm.bs_gather, 0, s>>>(dm, ad, mode, z, ad.c1, ad.c2, ad.bu, w, out);
 }
 void adj_dplus(const DevMesh& dm, const AdjDev& ad, const d4* base, const d4* w, d4* out, cudaStream_t s) {
     dc_note_launch();
@@ -682,25 +683,21 @@ void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytm
     dc_note_launch();
     k_adj_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, ad, ytmp, base, out);
 }
-void adj_mdot(const double* V, long ldv, int nvec, const double* w, long n, double* partial, double* out,
+void adj_bdot(const Segs& sg, const double* V, long ldv, int nvec, const double* w, double* partial, double* out,
               cudaStream_t s) {
     dc_note_launch();
-    k_mdot<<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ldv, nvec, w, n, partial);
+    k_bmdot<<<dim3(sg.nchunk, nvec), DOT_THREADS, 0, s>>>(V, ldv, w, sg.chunk, sg.nchunk, partial);
     dc_note_launch();
-    k_reduce<<<nvec, RED_THREADS, 0, s>>>(partial, RED_BLOCKS, out);
+    k_breduce<<<nblk((long)sg.B * nvec, 128), 128, 0, s>>>(partial, sg.nchunk, sg.cptr, sg.B, nvec, out);
 }
-void adj_vupdate(const double* V, long ldv, int nvec, const double* c, double* w, long n, double sign,
-                 cudaStream_t s) {
+void adj_bvupdate(const Segs& sg, const double* V, long ldv, int nvec, const double* coef, double* w, double sign,
+                  cudaStream_t s) {
     dc_note_launch();
-    k_vupdate<<<nblk(n, 256), 256, 0, s>>>(V, ldv, nvec, c, w, n, sign);
+    k_bvupdate<<<sg.nchunk, 128, 0, s>>>(V, ldv, nvec, coef, sg.B, sg.chunk, w, sign);
 }
-void adj_scale(const double* a, double sc, double* out, long n, cudaStream_t s) {
+void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s) {
     dc_note_launch();
-    k_scale<<<nblk(n, 256), 256, 0, s>>>(a, sc, out, n);
-}
-void adj_axpby(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s) {
-    dc_note_launch();
-    k_axpby<<<nblk(n, 256), 256, 0, s>>>(a, x, b, y, out, n);
+    k_bscale<<<sg.nchunk, 128, 0, s>>>(a, sc, sg.chunk, out);
 }
 void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
                  const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
@@ -708,15 +705,14 @@ void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const 
     dc_note_launch();
     k_adj_outputs<<<nblk(dm.m, 128), 128, 0, s>>>(dm, ad, P, z, E, resid, x_n, v1, gx, gx_out, gv_out);
 }
-void adj_params(const DevMesh& dm, const AdjDev& ad, const d4* z, const d4* x1, double* part, double* acc,
-                cudaStream_t s) {
+void adj_params(const DevMesh& dm, const AdjDev& ad, const Segs& sg, const d4* z, const d4* x1, double* part,
+                double* acc, cudaStream_t s) {
     dc_note_launch();
-    k_adj_param_terms<<<RED_BLOCKS, RED_THREADS, 0, s>>>(dm, ad, z, x1, part);
+    k_adj_param_terms<<<sg.npchunk, RED_THREADS, 0, s>>>(dm, ad, z, x1, sg.pchunk, part);
     dc_note_launch();
-    k_param_accumulate<<<1, 32, 0, s>>>(part, RED_BLOCKS, acc);
+    k_param_accumulate<<<nblk(3L * sg.B, 128), 128, 0, s>>>(part, sg.pcptr, sg.B, acc);
 }
 void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s) {
     dc_note_launch();
     k_add_ext<<<nblk(m, 256), 256, 0, s>>>(g, ext, int2ext, m);
 }
-int adj_red_blocks() { return RED_BLOCKS; }

@@ -4,7 +4,8 @@
 #include "dc_internal.h"
 
 struct AdjDev {
-    double h, mu;
+    double h;
+    const double* mu;     // [m] friction coefficient of each node's instance
     d4* tr0;              // [T] (R col 0, S^-1_00)
     d4* tr1;              // [T] (R col 1, S^-1_01)
     d4* tr2;              // [T] (S^-1_11, 1/tr S, -, -)
@@ -28,19 +29,29 @@ void adj_apply_H(const DevMesh& dm, const AdjDev& ad, int mode, const d4* z, con
 void adj_dplus(const DevMesh& dm, const AdjDev& ad, const d4* base, const d4* w, d4* out, cudaStream_t s);
 void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytmp, const d4* base, d4* out,
                        cudaStream_t s);
-void adj_mdot(const double* V, long ldv, int nvec, const double* w, long n, double* partial, double* out,
+// Per-instance reduction layout of a context (see the Krylov helpers).
+struct Segs {
+    int B = 0, nchunk = 0, npchunk = 0;
+    const int4* chunk = nullptr;     // [nchunk] (inst, lo, hi, -) in doubles of the free-node vectors
+    const int* cptr = nullptr;       // [B + 1] chunks of instance i
+    const int4* pchunk = nullptr;    // [npchunk] (inst, kind, lo, hi) element ranges of the parameter terms
+    const int* pcptr = nullptr;      // [3 B + 1] chunks of (instance i, kind q) at 3 i + q
+};
+// out[j * B + i] = V_j . w over instance i's free nodes, j < nvec
+void adj_bdot(const Segs& sg, const double* V, long ldv, int nvec, const double* w, double* partial, double* out,
               cudaStream_t s);
-void adj_vupdate(const double* V, long ldv, int nvec, const double* c, double* w, long n, double sign,
-                 cudaStream_t s);
-void adj_scale(const double* a, double sc, double* out, long n, cudaStream_t s);
-void adj_axpby(double a, const double* x, double b, const double* y, double* out, long n, cudaStream_t s);
+// w += sign * sum_j V_j coef[j * B + i] on instance i's free nodes
+void adj_bvupdate(const Segs& sg, const double* V, long ldv, int nvec, const double* coef, double* w, double sign,
+                  cudaStream_t s);
+// out = a * sc[i] on instance i's free nodes
+void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s);
 void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
                  const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
                  cudaStream_t s);
-void adj_params(const DevMesh& dm, const AdjDev& ad, const d4* z, const d4* x1, double* part, double* acc,
-                cudaStream_t s);
+// acc[4 i + q] += dL/d(k_stretch, k_bend, mu)_q of instance i for this step
+void adj_params(const DevMesh& dm, const AdjDev& ad, const Segs& sg, const d4* z, const d4* x1, double* part,
+                double* acc, cudaStream_t s);
 void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s);
-int adj_red_blocks();
 
 // Per-step multifrontal LDL^T preconditioner (dc_frontal.cu).
 size_t frontal_factor_smem(int max_f);

@@ -11,6 +11,8 @@
 //
 // Fronts are dense column-major f x f blocks (DOF granularity, 3 per node) in
 // one pool; only their lower triangles are used.  One CTA handles one front.
+#include <mutex>
+
 #include "dc_adjoint.h"
 #include "dc_internal.h"
 
@@ -182,7 +184,7 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
         }
         __syncthreads();
     }
-    const float tau = fd.tau;
+    const float tau = fd.tau[s];
     float* binv = fd.binv + fd.binv_off[s];
     for (int k0 = 0; k0 < p; k0 += PB) {
         const int kb = min(PB, p - k0);
@@ -478,7 +480,7 @@ __global__ void k_pre_in(int n, const int* __restrict__ type, const d4* __restri
 }
 
 // out = S_C x in double precision: stick -> 0, slip -> x - n ((n - mu t).x).
-__global__ void k_pre_out(int n, double mu, const int* __restrict__ type, const d4* __restrict__ nb,
+__global__ void k_pre_out(int n, const double* __restrict__ mu, const int* __restrict__ type, const d4* __restrict__ nb,
                           const d4* __restrict__ slip, const float* __restrict__ x, d4* __restrict__ out) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
@@ -488,7 +490,8 @@ __global__ void k_pre_out(int n, double mu, const int* __restrict__ type, const 
         v[0] = v[1] = v[2] = 0.0;
     } else if (ty == 2) {
         d4 q = ld(nb + j), sl = ld(slip + j);
-        double cz = (q.x - mu * sl.x) * v[0] + (q.y - mu * sl.y) * v[1] + (q.z - mu * sl.z) * v[2];
+        const double mj = mu[j];
+        double cz = (q.x - mj * sl.x) * v[0] + (q.y - mj * sl.y) * v[1] + (q.z - mj * sl.z) * v[2];
         v[0] -= cz * q.x; v[1] -= cz * q.y; v[2] -= cz * q.z;
     }
     st(out + j, v[0], v[1], v[2]);
@@ -505,22 +508,32 @@ size_t frontal_factor_smem(int max_f) {
 
 size_t frontal_solve_smem(int max_f) { return 2 * (size_t)max_f * sizeof(float) + 64; }
 
+// The dynamic shared-memory limit of the front kernels is a per-function
+// attribute shared by every context of the process, so it only ever grows.
 cudaError_t frontal_configure(int max_f) {
+    static std::mutex mu;
+    static int configured = 0;
+    std::lock_guard<std::mutex> lock(mu);
+    if (max_f <= configured) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_front_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)frontal_factor_smem(max_f));
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_msolve_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)frontal_solve_smem(max_f));
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_msolve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)frontal_solve_smem(max_f));
+    e = cudaFuncSetAttribute(k_msolve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)frontal_solve_smem(max_f));
+    if (e == cudaSuccess) configured = max_f;
+    return e;
 }
 
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
                        int max_f, cudaStream_t s, KTimer* kt) {
+    if (kt) kt->begin(DC_KT_ASSEMBLE);
     cudaMemsetAsync(fd.pool, 0, sizeof(float) * fd.pool_size, s);
     dc_note_launch();
     k_pairs<<<nblk(fd.NP, 128), 128, 0, s>>>(dm, ad, fd);
+    if (kt) kt->end(DC_KT_ASSEMBLE);
     for (int l = 0; l < nlev; ++l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
         if (cnt > 0) {

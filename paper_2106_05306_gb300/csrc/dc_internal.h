@@ -18,6 +18,7 @@ struct __align__(32) d4 {
 
 // Host-side count of kernel launches made by the library (all contexts).
 void dc_note_launch();
+void dc_add_launches(long long n);
 long long dc_launch_count();
 
 // CUDA-event timing of one kernel class on a context's stream (classes: DC_KT_*).
@@ -121,18 +122,45 @@ struct DevMesh {
     const int* kptr;                   // L^-T rows (CSR)
     const int* kidx;
     const double* kval;
+    // threads per block of the element / node kernels (picked by the autotuner;
+    // no launch shape changes any result)
+    int bs_local, bs_gather, bs_elem, bs_node;
 };
 
-// Per-step record kept for the adjoint: the contact state of the step.
-// contact[j]: -1 = none, else obstacle index; case_[j] in {0,1,2}.
+// Parameters seen by the kernels.  h, gravity and the contact margin are shared
+// by every instance of a context; friction and obstacles are per instance
+// (node -> instance -> table), the stiffnesses are folded into DevMesh::wt/wb.
 struct DevParams {
-    double k_stretch, k_bend, mu, h;
+    double h;
     double g[3];
     double delta;
-    int n_obst;
-    int kind[DC_MAX_OBSTACLES];
-    double op[DC_MAX_OBSTACLES][7];
+    const int* node_inst;              // [m] instance of each internal node
+    const double* node_mu;             // [m] friction coefficient of the node's instance
+    const int* optr;                   // [n_inst + 1] obstacles of instance i: optr[i] .. optr[i+1]-1
+    const int* okind;                  // [n_obst] DC_PLANE / DC_SPHERE / DC_CAPSULE
+    const double* oprm;                // [n_obst][8] obstacle parameters (normalised plane)
 };
+
+// Instance layout inside a context.  Internal node order is: the free nodes of
+// instance 0, 1, ... (each in its own nested-dissection order), then the pinned
+// nodes of instance 0, 1, ...; external (caller) node order is the concatenation
+// of the instances' own numberings.
+struct InstInfo {
+    int m = 0, mf = 0, T = 0;          // nodes, free nodes, triangles
+    long long ext_off = 0;             // first external node
+    int fo = 0;                        // first internal free node
+    int po = 0;                        // first pinned node, relative to the total free count
+    int to = 0;                        // first triangle
+    int so = 0;                        // first supernode of the adjoint fronts
+    int map(int l, int MF) const { return l < mf ? fo + l : MF + po + (l - mf); }
+};
+
+// Concatenates per-instance meshes into one disconnected mesh (fills the offsets).
+void dc_merge_meshes(const std::vector<HostMesh>& H, std::vector<InstInfo>& I, HostMesh& out);
+// Concatenates per-instance factors (explicit inverse rows only) with node offsets.
+void dc_merge_factors(const std::vector<HostFactor>& F, const std::vector<InstInfo>& I, HostFactor& out);
+// Concatenates per-instance front structures; levels are merged by height.
+void dc_merge_fronts(const std::vector<HostFronts>& F, std::vector<InstInfo>& I, int MF, HostFronts& out);
 
 // ---------------------------------------------------------------- kernel launchers
 // (all asynchronous on the given stream)
@@ -165,7 +193,7 @@ void launch_count_cases(const int* contact, const int* case_, int m_free,
 // Device view of the multifrontal structure and its per-step numeric storage.
 struct FrontDev {
     int S, NP, max_f;
-    float tau;                         // pivots below tau are replaced by +-tau
+    const float* tau;                  // [S] pivots below tau[s] are replaced by +-tau[s]
     long long pool_size;
     const int* begin;
     const int* f;

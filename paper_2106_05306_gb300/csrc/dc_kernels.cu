@@ -20,6 +20,7 @@ std::atomic<long long> g_launches{0};
 }  // namespace
 
 void dc_note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void dc_add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 long long dc_launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
@@ -39,13 +40,14 @@ __device__ __forceinline__ void st(d4* p, double x, double y, double z, double w
 
 // Signed distance and its gradient for one analytic obstacle (reading R4).
 __device__ double sdf(const DevParams& P, int o, double x, double y, double z, double* n) {
-    const double* q = P.op[o];
-    if (P.kind[o] == DC_PLANE) {
+    const double* q = P.oprm + 8 * o;
+    const int kind = P.okind[o];
+    if (kind == DC_PLANE) {
         if (n) { n[0] = q[0]; n[1] = q[1]; n[2] = q[2]; }
         return q[0] * x + q[1] * y + q[2] * z - q[3];
     }
     double cx, cy, cz, r;
-    if (P.kind[o] == DC_SPHERE) {
+    if (kind == DC_SPHERE) {
         cx = q[0]; cy = q[1]; cz = q[2]; r = q[3];
     } else {
         double abx = q[3] - q[0], aby = q[4] - q[1], abz = q[5] - q[2];
@@ -92,7 +94,8 @@ __global__ void k_detect(DevMesh dm, DevParams P, const d4* __restrict__ x_n, co
     double px = x.x + P.h * v.x, py = x.y + P.h * v.y, pz = x.z + P.h * v.z;
     double best = 1e300;
     int bo = -1;
-    for (int o = 0; o < P.n_obst; ++o) {
+    const int inst = P.node_inst[i];
+    for (int o = P.optr[inst]; o < P.optr[inst + 1]; ++o) {
         double ph = sdf(P, o, px, py, pz, nullptr);
         if (ph < best) { best = ph; bo = o; }
     }
@@ -347,7 +350,7 @@ __global__ void k_solve_bwd(DevMesh dm, DevParams P, const d4* __restrict__ y, d
         double n[3] = {q.x, q.y, q.z};
         double vt[3] = {s0 - c * fo.x, s1 - c * fo.y, s2 - c * fo.z};
         double v[3], fn[3];
-        case_[row] = coulomb(P.mu, c, n, q.w, vt, v, fn);
+        case_[row] = coulomb(P.node_mu[row], c, n, q.w, vt, v, fn);
         st(f + row, fn[0], fn[1], fn[2]);
         st(out + row, v[0], v[1], v[2]);
         return;
@@ -391,17 +394,17 @@ void launch_zero_pins(d4* v, int m_free, int m, cudaStream_t s) {
 void launch_detect(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v_n, int* contact,
                    d4* nb, d4* f, d4* ind, cudaStream_t s) {
     dc_note_launch();
-    k_detect<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, P, x_n, v_n, contact, nb, f, ind);
+    k_detect<<<nblk(dm.m_free, dm.bs_node), dm.bs_node, 0, s>>>(dm, P, x_n, v_n, contact, nb, f, ind);
 }
 void launch_local(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* c1, d4* c2,
                   d4* bu, cudaStream_t s) {
     dc_note_launch();
-    k_local<<<nblk((long)dm.T + dm.m, 128), 128, 0, s>>>(dm, P, x_n, v, c1, c2, bu);
+    k_local<<<nblk((long)dm.T + dm.m, dm.bs_local), dm.bs_local, 0, s>>>(dm, P, x_n, v, c1, c2, bu);
 }
 void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, const d4* c1, const d4* c2,
                        const d4* bu, const d4* f, d4* b, cudaStream_t s) {
     dc_note_launch();
-    k_gather_rhs<<<nblk(dm.m_free, 128), 128, 0, s>>>(dm, P, v_n, c1, c2, bu, f, b);
+    k_gather_rhs<<<nblk(dm.m_free, dm.bs_gather), dm.bs_gather, 0, s>>>(dm, P, v_n, c1, c2, bu, f, b);
 }
 void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
     dc_note_launch();
@@ -416,7 +419,7 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* x_np1,
                      cudaStream_t s) {
     dc_note_launch();
-    k_finalize<<<nblk(dm.m, 256), 256, 0, s>>>(dm.m, P.h, x_n, v, x_np1);
+    k_finalize<<<nblk(dm.m, dm.bs_node), dm.bs_node, 0, s>>>(dm.m, P.h, x_n, v, x_np1);
 }
 void launch_count_cases(const int* contact, const int* case_, int m_free, unsigned long long* counters,
                         cudaStream_t s) {

@@ -1,0 +1,332 @@
+// Request server: continuous admission of forward + adjoint rollouts by slot
+// and HBM budget, with host-side preparation pipelined ahead of the GPU.
+//
+//   submit --> [prep threads: mesh ordering, factor, fronts, footprint] -->
+//   ready queue (submission order) --> [slot threads: admit when a slot is free
+//   and the footprint fits the budget; upload, rollout, backward on the slot's
+//   stream; free] --> results, collected by dc_server_wait.
+//
+// Every request is its own one-instance context, so its numbers do not depend
+// on what else runs (bitwise equal to running it alone).
+#include <cuda_runtime.h>
+
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+
+#include "dc_ctx.h"
+
+namespace {
+
+struct Request {
+    int64_t ticket = 0;
+    std::vector<double> rest, x0, v0, gx, gv;
+    std::vector<int32_t> tris, pins;
+    int n_steps = 0;
+    dc_params prm{};
+    // prepared
+    dc_ctx* c = nullptr;
+    MeshPrep mp;
+    ParamPrep pp;
+    size_t bytes = 0;
+    // results
+    bool done = false;
+    dc_status status = DC_OK;
+    std::string err;
+    int slot = -1;
+    std::vector<double> xN, vN, dx0, dv0;
+    double dth[3] = {0, 0, 0};
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    size_t peak = 0;
+    long long adj_iters = 0;
+};
+
+}  // namespace
+
+struct dc_server {
+    dc_server_config cfg{};
+    std::mutex mu;
+    std::condition_variable cv;     // any state change
+    std::deque<Request*> to_prep;
+    std::map<int64_t, Request*> ready;   // prepared, by ticket
+    std::map<int64_t, Request*> all;
+    int64_t next_ticket = 1;
+    size_t reserved = 0, peak_reserved = 0;
+    int64_t in_flight = 0, peak_in_flight = 0, submitted = 0, completed = 0, failed = 0, steps = 0;
+    int preparing = 0;
+    bool stop = false;
+    std::vector<std::thread> threads;
+    std::vector<cudaStream_t> streams;
+    std::vector<double*> pinned;
+    std::chrono::steady_clock::time_point t0;
+    double now() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+namespace {
+
+void finish(dc_server* s, Request* r, dc_status st, const std::string& err) {
+    // caller holds s->mu
+    r->status = st;
+    r->err = err;
+    r->done = true;
+    r->t_done = s->now();
+    if (st == DC_OK) {
+        s->completed++;
+        s->steps += r->n_steps;
+    } else {
+        s->failed++;
+    }
+    s->cv.notify_all();
+}
+
+void prep_loop(dc_server* s) {
+    for (;;) {
+        Request* r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] {
+                return s->stop ||
+                       (!s->to_prep.empty() && (int)s->ready.size() + s->preparing < s->cfg.max_prepared);
+            });
+            if (s->to_prep.empty()) return;   // stop with nothing left
+            r = s->to_prep.front();
+            s->to_prep.pop_front();
+            s->preparing++;
+        }
+        dc_status st = DC_OK;
+        std::string err;
+        dc_ctx* c = new dc_ctx();
+        c->async_alloc = true;
+        c->ihm.resize(1);
+        err = dc_build_mesh(c->ihm[0], (int)(r->rest.size() / 3), r->rest.data(), (int)(r->tris.size() / 3),
+                            r->tris.data(), (int)r->pins.size(), r->pins.empty() ? nullptr : r->pins.data());
+        if (!err.empty()) {
+            st = DC_ERR_INVALID;
+        } else {
+            prep_mesh_host(c, r->mp);
+            st = prep_params_host(c, std::vector<dc_params>(1, r->prm), r->pp);
+            if (st) err = c->err;
+        }
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->preparing--;
+        if (st) {
+            delete c;
+            finish(s, r, st, err);
+            continue;
+        }
+        r->c = c;
+        r->bytes = estimate_device_bytes(c, r->mp, r->pp, r->n_steps);
+        if (r->bytes > (size_t)s->cfg.hbm_budget_bytes) {
+            delete c;
+            r->c = nullptr;
+            finish(s, r, DC_ERR_OOM,
+                   "request needs " + std::to_string(r->bytes) + " device bytes, more than the server's budget");
+            continue;
+        }
+        s->ready[r->ticket] = r;
+        s->cv.notify_all();
+    }
+}
+
+// Runs one admitted request on the slot's stream; returns its status.
+dc_status run_request(dc_server* s, Request* r, int slot, std::string& err) {
+    dc_ctx* c = r->c;
+    c->stream = s->streams[slot];
+    c->kt.stream = c->stream;
+    c->hpin = s->pinned[slot];
+    c->hpin_cap = 1024;
+    c->hpin_external = true;
+    dc_status st = upload_mesh(c, r->mp);
+    if (!st) st = upload_params(c, r->pp);
+    r->mp = MeshPrep();
+    r->pp = ParamPrep();
+    const size_t n3 = r->x0.size();
+    r->xN.resize(n3);
+    r->vN.resize(n3);
+    r->dx0.resize(n3);
+    r->dv0.resize(n3);
+    if (!st)
+        st = dc_rollout(c, r->n_steps, r->x0.data(), r->v0.data(), r->xN.data(), r->vN.data(), nullptr);
+    if (!st)
+        st = dc_backward(c, r->gx.data(), r->gv.empty() ? nullptr : r->gv.data(), nullptr, r->dx0.data(),
+                         r->dv0.data(), r->dth);
+    if (st) err = c->err;
+    r->adj_iters = c->adj_iters;
+    r->peak = c->dev_peak;
+    dc_destroy(c);
+    r->c = nullptr;
+    return st;
+}
+
+void slot_loop(dc_server* s, int slot) {
+    cudaSetDevice(s->cfg.device);
+    for (;;) {
+        Request* r;
+        {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv.wait(lk, [&] {
+                if (!s->ready.empty()) {
+                    Request* h = s->ready.begin()->second;
+                    if (s->reserved + h->bytes <= (size_t)s->cfg.hbm_budget_bytes) return true;
+                }
+                return s->stop && s->ready.empty() && s->to_prep.empty() && s->preparing == 0;
+            });
+            if (s->ready.empty()) return;
+            r = s->ready.begin()->second;
+            s->ready.erase(s->ready.begin());
+            s->reserved += r->bytes;
+            s->peak_reserved = std::max(s->peak_reserved, s->reserved);
+            s->in_flight++;
+            s->peak_in_flight = std::max(s->peak_in_flight, s->in_flight);
+            r->slot = slot;
+            r->t_admit = s->now();
+            s->cv.notify_all();   // a prep thread may now prepare the next request
+        }
+        std::string err;
+        dc_status st = run_request(s, r, slot, err);
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->reserved -= r->bytes;
+        s->in_flight--;
+        finish(s, r, st, err);
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+dc_status dc_server_create(dc_server** out, const dc_server_config* cfg) {
+    if (!out || !cfg || cfg->n_slots < 1 || cfg->n_prep_threads < 1 || cfg->hbm_budget_bytes <= 0 ||
+        cfg->max_prepared < 1)
+        return DC_ERR_INVALID;
+    *out = nullptr;
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return DC_ERR_CUDA;
+    // keep freed blocks in the stream-ordered pool of this process for the next request
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, cfg->device) == cudaSuccess) {
+        uint64_t thr = ~0ull;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+    dc_server* s = new dc_server();
+    s->cfg = *cfg;
+    s->t0 = std::chrono::steady_clock::now();
+    for (int i = 0; i < cfg->n_slots; ++i) {
+        cudaStream_t st;
+        double* h;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaMallocHost(&h, 1024 * sizeof(double)) != cudaSuccess) {
+            for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+            for (double* x : s->pinned) cudaFreeHost(x);
+            delete s;
+            return DC_ERR_CUDA;
+        }
+        s->streams.push_back(st);
+        s->pinned.push_back(h);
+    }
+    for (int i = 0; i < cfg->n_prep_threads; ++i) s->threads.emplace_back(prep_loop, s);
+    for (int i = 0; i < cfg->n_slots; ++i) s->threads.emplace_back(slot_loop, s, i);
+    *out = s;
+    return DC_OK;
+}
+
+dc_status dc_server_submit(dc_server* s, const dc_request* q, int64_t* ticket) {
+    if (!s || !q || !ticket || q->n_nodes <= 0 || q->n_tris <= 0 || q->n_pins < 0 || q->n_steps < 0 ||
+        !q->rest_pos || !q->tris || (q->n_pins > 0 && !q->pins) || !q->x0 || !q->v0 || !q->dL_dx_final)
+        return DC_ERR_INVALID;
+    Request* r = new Request();
+    const size_t n3 = 3 * (size_t)q->n_nodes;
+    r->rest.assign(q->rest_pos, q->rest_pos + n3);
+    r->x0.assign(q->x0, q->x0 + n3);
+    r->v0.assign(q->v0, q->v0 + n3);
+    r->gx.assign(q->dL_dx_final, q->dL_dx_final + n3);
+    if (q->dL_dv_final) r->gv.assign(q->dL_dv_final, q->dL_dv_final + n3);
+    r->tris.assign(q->tris, q->tris + 3 * (size_t)q->n_tris);
+    if (q->n_pins > 0) r->pins.assign(q->pins, q->pins + q->n_pins);
+    r->n_steps = q->n_steps;
+    r->prm = q->params;
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->stop) {
+        delete r;
+        return DC_ERR_STATE;
+    }
+    r->ticket = s->next_ticket++;
+    r->t_submit = s->now();
+    s->all[r->ticket] = r;
+    s->to_prep.push_back(r);
+    s->submitted++;
+    *ticket = r->ticket;
+    s->cv.notify_all();
+    return DC_OK;
+}
+
+dc_status dc_server_wait(dc_server* s, int64_t ticket, dc_result* out) {
+    if (!s || !out) return DC_ERR_INVALID;
+    Request* r;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        auto it = s->all.find(ticket);
+        if (it == s->all.end()) return DC_ERR_INVALID;
+        r = it->second;
+        s->cv.wait(lk, [&] { return r->done; });
+        s->all.erase(it);
+    }
+    const size_t nb = r->xN.size() * sizeof(double);
+    if (r->status == DC_OK) {
+        if (out->x_final) std::memcpy(out->x_final, r->xN.data(), nb);
+        if (out->v_final) std::memcpy(out->v_final, r->vN.data(), nb);
+        if (out->dL_dx0) std::memcpy(out->dL_dx0, r->dx0.data(), nb);
+        if (out->dL_dv0) std::memcpy(out->dL_dv0, r->dv0.data(), nb);
+    }
+    out->status = r->status;
+    out->slot = r->slot;
+    for (int k = 0; k < 3; ++k) out->dL_dparams[k] = r->dth[k];
+    out->t_submit = r->t_submit;
+    out->t_admit = r->t_admit;
+    out->t_done = r->t_done;
+    out->device_bytes = (int64_t)r->bytes;
+    out->device_bytes_peak = (int64_t)r->peak;
+    out->adj_iters = r->adj_iters;
+    std::snprintf(out->message, sizeof(out->message), "%s", r->err.c_str());
+    delete r;
+    return DC_OK;
+}
+
+dc_status dc_server_get_stats(dc_server* s, dc_server_stats* o) {
+    if (!s || !o) return DC_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(s->mu);
+    o->submitted = s->submitted;
+    o->completed = s->completed;
+    o->failed = s->failed;
+    o->in_flight = s->in_flight;
+    o->peak_in_flight = s->peak_in_flight;
+    o->bytes_reserved = (int64_t)s->reserved;
+    o->peak_bytes_reserved = (int64_t)s->peak_reserved;
+    o->cloth_steps = s->steps;
+    return DC_OK;
+}
+
+void dc_server_destroy(dc_server* s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->stop = true;
+        s->cv.notify_all();
+    }
+    for (auto& t : s->threads) t.join();
+    for (auto& kv : s->all) {
+        if (kv.second->c) dc_destroy(kv.second->c);
+        delete kv.second;
+    }
+    for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
+    for (double* x : s->pinned) cudaFreeHost(x);
+    delete s;
+}
+
+}  // extern "C"

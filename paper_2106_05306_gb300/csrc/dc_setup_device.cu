@@ -1,0 +1,496 @@
+// Context setup in two halves: host preparation (merging the instances' meshes,
+// factorising every instance's PD matrix, building the adjoint fronts and the
+// per-instance tables) and the device upload of its results.  A plain context
+// runs both back to back; the request server prepares on host threads and
+// uploads on the stream of the slot that runs the request.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <functional>
+#include <string>
+#include <thread>
+
+#include "dc_ctx.h"
+
+namespace {
+
+constexpr int CHUNK_D = 512;    // doubles per reduction chunk of the Krylov vectors (128 nodes)
+constexpr int CHUNK_E = 1024;   // elements per chunk of the parameter-gradient terms
+
+bool finite_params(const dc_params& p) {
+    const double v[] = {p.k_stretch, p.k_bend, p.density, p.mu, p.h, p.gravity[0], p.gravity[1], p.gravity[2],
+                        p.contact_margin, p.adj_tol};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+// Validates q and normalises its obstacles (unit plane normals).  "" or an error.
+std::string normalise_params(dc_params& q) {
+    if (!finite_params(q) || !(q.h > 0) || q.k_stretch < 0 || q.k_bend < 0 || !(q.density > 0) || q.mu < 0 ||
+        q.n_pd_iters < 0 || q.n_obstacles < 0 || q.n_obstacles > DC_MAX_OBSTACLES || q.checkpoint_every < 1 ||
+        q.adj_max_iters < 1 || q.adj_restart < 1 || !(q.adj_tol > 0) || q.adj_precond < 0 || q.adj_precond > 1)
+        return "invalid or non-finite parameter";
+    for (int o = 0; o < q.n_obstacles; ++o) {
+        dc_obstacle& ob = q.obstacles[o];
+        for (int k = 0; k < 7; ++k)
+            if (!std::isfinite(ob.p[k])) return "non-finite obstacle";
+        if (ob.kind == DC_PLANE) {
+            double nn = std::sqrt(ob.p[0] * ob.p[0] + ob.p[1] * ob.p[1] + ob.p[2] * ob.p[2]);
+            if (!(nn > 0)) return "zero plane normal";
+            for (int k = 0; k < 3; ++k) ob.p[k] /= nn;
+            ob.p[3] /= nn;
+        } else if (ob.kind == DC_SPHERE) {
+            if (!(ob.p[3] > 0)) return "sphere radius must be positive";
+        } else if (ob.kind == DC_CAPSULE) {
+            double L = std::fabs(ob.p[3] - ob.p[0]) + std::fabs(ob.p[4] - ob.p[1]) + std::fabs(ob.p[5] - ob.p[2]);
+            if (!(ob.p[6] > 0) || !(L > 0)) return "bad capsule";
+        } else {
+            return "unknown obstacle kind";
+        }
+    }
+    return "";
+}
+
+// The fields every instance of a batch must share.
+bool same_batch_fields(const dc_params& a, const dc_params& b) {
+    return a.h == b.h && a.gravity[0] == b.gravity[0] && a.gravity[1] == b.gravity[1] &&
+           a.gravity[2] == b.gravity[2] && a.contact_margin == b.contact_margin && a.adj_tol == b.adj_tol &&
+           a.n_pd_iters == b.n_pd_iters && a.adj_max_iters == b.adj_max_iters && a.adj_restart == b.adj_restart &&
+           a.checkpoint_every == b.checkpoint_every && a.adj_precond == b.adj_precond;
+}
+
+template <class T>
+size_t vbytes(const std::vector<T>& v) {
+    return std::max<size_t>(v.size() * sizeof(T), 32);
+}
+
+}  // namespace
+
+void dc_parallel_for(int n, const std::function<void(int)>& f) {
+    int nt = (int)std::min<unsigned>((unsigned)std::max(n, 1), std::max(1u, std::thread::hardware_concurrency()));
+    if (nt <= 1) {
+        for (int i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::atomic<int> next{0};
+    std::vector<std::thread> th;
+    th.reserve(nt);
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&]() {
+            for (int i; (i = next.fetch_add(1)) < n;) f(i);
+        });
+    for (auto& t : th) t.join();
+}
+
+void prep_mesh_host(dc_ctx* c, MeshPrep& mp) {
+    dc_merge_meshes(c->ihm, c->inst, c->hm);
+    c->B = (int)c->ihm.size();
+    const HostMesh& hm = c->hm;
+    const int m = hm.m, T = hm.T, MF = hm.m_free, B = c->B;
+    mp.tri4.resize(T);
+    mp.G4.resize(T);
+    for (int t = 0; t < T; ++t) {
+        mp.tri4[t] = make_int4(hm.tri[3 * t], hm.tri[3 * t + 1], hm.tri[3 * t + 2], 0);
+        mp.G4[t] = d4{hm.G[4 * t], hm.G[4 * t + 1], hm.G[4 * t + 2], hm.G[4 * t + 3]};
+    }
+    mp.qr.resize(m);
+    for (int i = 0; i < m; ++i) mp.qr[i] = d4{hm.qrest[3 * i], hm.qrest[3 * i + 1], hm.qrest[3 * i + 2], 0.0};
+    // node -> triangle incidences and transposed bending stencils (counting sort:
+    // every list keeps ascending triangle / row order)
+    auto& iptr = mp.iptr;
+    auto& tbptr = mp.tbptr;
+    iptr.assign(m + 1, 0);
+    tbptr.assign(m + 1, 0);
+    for (int t = 0; t < T; ++t)
+        for (int a = 0; a < 3; ++a) iptr[hm.tri[3 * t + a] + 1]++;
+    for (int i = 0; i < m; ++i) iptr[i + 1] += iptr[i];
+    mp.iidx.assign(iptr[m], 0);
+    std::vector<int> fill(iptr.begin(), iptr.end() - 1);
+    for (int t = 0; t < T; ++t)
+        for (int a = 0; a < 3; ++a) mp.iidx[fill[hm.tri[3 * t + a]]++] = 3 * t + a;
+    for (int b = 0; b < m; ++b)
+        for (int k = hm.bptr[b]; k < hm.bptr[b + 1]; ++k) tbptr[hm.bidx[k] + 1]++;
+    for (int i = 0; i < m; ++i) tbptr[i + 1] += tbptr[i];
+    mp.tbidx.assign(tbptr[m], 0);
+    mp.tbval.assign(tbptr[m], 0.0);
+    fill.assign(tbptr.begin(), tbptr.end() - 1);
+    for (int b = 0; b < m; ++b)
+        for (int k = hm.bptr[b]; k < hm.bptr[b + 1]; ++k) {
+            int q = fill[hm.bidx[k]]++;
+            mp.tbidx[q] = b;
+            mp.tbval[q] = hm.bval[k];
+        }
+    // instance of every node; reduction chunks counted from each instance's start
+    mp.node_inst.assign(m, 0);
+    mp.cptr.assign(B + 1, 0);
+    mp.pcptr.assign(3 * B + 1, 0);
+    mp.chunks.clear();
+    mp.pchunks.clear();
+    for (int i = 0; i < B; ++i) {
+        const InstInfo& in = c->inst[i];
+        for (int l = 0; l < in.m; ++l) mp.node_inst[in.map(l, MF)] = i;
+        for (int a = 4 * in.fo; a < 4 * (in.fo + in.mf); a += CHUNK_D)
+            mp.chunks.push_back(make_int4(i, a, std::min(4 * (in.fo + in.mf), a + CHUNK_D), 0));
+        mp.cptr[i + 1] = (int)mp.chunks.size();
+        auto add = [&](int kind, int lo, int hi) {
+            for (int a = lo; a < hi; a += CHUNK_E)
+                mp.pchunks.push_back(make_int4(i, kind, a, std::min(hi, a + CHUNK_E)));
+        };
+        add(0, in.to, in.to + in.T);
+        mp.pcptr[3 * i + 1] = (int)mp.pchunks.size();
+        add(1, in.fo, in.fo + in.mf);
+        add(1, MF + in.po, MF + in.po + (in.m - in.mf));
+        mp.pcptr[3 * i + 2] = (int)mp.pchunks.size();
+        add(2, in.fo, in.fo + in.mf);
+        mp.pcptr[3 * i + 3] = (int)mp.pchunks.size();
+    }
+    if (mp.chunks.empty()) mp.chunks.push_back(make_int4(0, 0, 0, 0));   // keeps every launch non-empty
+}
+
+dc_status upload_mesh(dc_ctx* c, MeshPrep& mp) {
+    const HostMesh& hm = c->hm;
+    auto& P = c->mesh_allocs;
+    int4* d_tri;
+    d4 *d_G, *d_qr;
+    double *d_area, *d_bval, *d_abar, *d_sb, *d_tbval;
+    int *d_bptr, *d_bidx, *d_iptr, *d_iidx, *d_tbptr, *d_tbidx, *d_ninst, *d_cptr, *d_pcptr;
+    int4 *d_chunks, *d_pchunks;
+    dc_status s;
+    if ((s = upload(c, P, &d_tri, mp.tri4)) || (s = upload(c, P, &d_G, mp.G4)) ||
+        (s = upload(c, P, &d_area, hm.area)) || (s = upload(c, P, &d_bptr, hm.bptr)) ||
+        (s = upload(c, P, &d_bidx, hm.bidx)) || (s = upload(c, P, &d_bval, hm.bval)) ||
+        (s = upload(c, P, &d_abar, hm.abar)) || (s = upload(c, P, &d_sb, hm.sb)) || (s = upload(c, P, &d_qr, mp.qr)) ||
+        (s = upload(c, P, &d_iptr, mp.iptr)) || (s = upload(c, P, &d_iidx, mp.iidx)) ||
+        (s = upload(c, P, &d_tbptr, mp.tbptr)) || (s = upload(c, P, &d_tbidx, mp.tbidx)) ||
+        (s = upload(c, P, &d_tbval, mp.tbval)) || (s = upload(c, P, &c->d_int2ext, hm.int2ext)) ||
+        (s = upload(c, P, &d_ninst, mp.node_inst)) || (s = upload(c, P, &d_cptr, mp.cptr)) ||
+        (s = upload(c, P, &d_pcptr, mp.pcptr)) || (s = upload(c, P, &d_chunks, mp.chunks)) ||
+        (s = upload(c, P, &d_pchunks, mp.pchunks)))
+        return s;
+    const int m = hm.m, T = hm.T;
+    DevMesh& dm = c->dm;
+    dm.m = m;
+    dm.m_free = hm.m_free;
+    dm.T = T;
+    dm.tri = d_tri;
+    dm.G = d_G;
+    dm.area = d_area;
+    dm.bptr = d_bptr;
+    dm.bidx = d_bidx;
+    dm.bval = d_bval;
+    dm.abar = d_abar;
+    dm.sb = d_sb;
+    dm.qrest = d_qr;
+    dm.iptr = d_iptr;
+    dm.iidx = d_iidx;
+    dm.tbptr = d_tbptr;
+    dm.tbidx = d_tbidx;
+    dm.tbval = d_tbval;
+    dm.bs_local = dm.bs_gather = dm.bs_elem = dm.bs_node = 128;
+    c->dp.node_inst = d_ninst;
+    c->sg.B = c->B;
+    c->sg.nchunk = (int)mp.chunks.size();
+    c->sg.chunk = d_chunks;
+    c->sg.cptr = d_cptr;
+    c->sg.npchunk = (int)mp.pchunks.size();
+    c->sg.pchunk = d_pchunks;
+    c->sg.pcptr = d_pcptr;
+    c->h_cptr = mp.cptr;
+    // work buffers
+    auto& W = c->work_allocs;
+    d4** vecs[] = {&c->xa, &c->va, &c->xb, &c->vb, &c->v, &c->b, &c->y, &c->bu, &c->ind};
+    for (d4** p : vecs) RET(dalloc(c, W, p, m));
+    RET(dalloc(c, W, &c->c1, T));
+    RET(dalloc(c, W, &c->c2, T));
+    RET(dalloc(c, W, &c->cc, m));
+    RET(dalloc(c, W, &c->stage, 3 * (size_t)m));
+    RET(dalloc(c, W, &c->stage2, 3 * (size_t)m));
+    RET(dalloc(c, W, &c->counters, 4));
+    RET(alloc_rec(c, W, c->scratch));
+    if (!c->hpin) {
+        if (cudaMallocHost(&c->hpin, 1024 * sizeof(double)) != cudaSuccess) {
+            c->err = "cudaMallocHost failed";
+            return DC_ERR_OOM;
+        }
+        c->hpin_cap = 1024;
+    }
+    cudaError_t e = c->async_alloc ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        c->err = std::string("device error during context creation: ") + cudaGetErrorString(e);
+        return DC_ERR_CUDA;
+    }
+    return DC_OK;
+}
+
+dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
+    const int B = c->B;
+    for (int i = 0; i < B; ++i) {
+        std::string e = normalise_params(q[i]);
+        if (!e.empty()) {
+            c->err = "dc_set_params: " + e + (B > 1 ? " (instance " + std::to_string(i) + ")" : "");
+            return DC_ERR_INVALID;
+        }
+        if (!same_batch_fields(q[i], q[0])) {
+            c->err = "dc_set_params_batch: instance " + std::to_string(i) +
+                     " differs from instance 0 in a field shared by the batch";
+            return DC_ERR_INVALID;
+        }
+    }
+    std::vector<HostFactor> hf(B);
+    std::vector<HostFronts> fr(B);
+    std::vector<dc_status> st(B, DC_OK);
+    std::vector<std::string> err(B);
+    dc_parallel_for(B, [&](int i) {
+        const HostMesh& h = c->ihm[i];
+        std::vector<double> mass(h.m);
+        for (int l = 0; l < h.m; ++l) mass[l] = q[i].density * h.abar[l];
+        st[i] = dc_build_factor(h, q[i], mass, hf[i], err[i]);
+        if (st[i] == DC_OK) {
+            std::string fe = dc_build_fronts(h, hf[i], fr[i]);
+            if (!fe.empty()) {
+                st[i] = DC_ERR_INVALID;
+                err[i] = fe;
+            }
+        }
+        // only the explicit inverse rows, the size and the largest pivot are kept
+        hf[i].rowidx = std::vector<int>();
+        hf[i].val = std::vector<double>();
+    });
+    for (int i = 0; i < B; ++i)
+        if (st[i]) {
+            c->err = "dc_set_params: " + err[i] + (B > 1 ? " (instance " + std::to_string(i) + ")" : "");
+            return st[i];
+        }
+    const HostMesh& hm = c->hm;
+    const int MF = hm.m_free;
+    std::vector<double> tau_i(B);
+    for (int i = 0; i < B; ++i) tau_i[i] = 1e-7 * hf[i].max_diag;
+    dc_merge_factors(hf, c->inst, pp.hfm);
+    hf.clear();
+    dc_merge_fronts(fr, c->inst, MF, pp.frm);
+    fr.clear();
+    const HostFronts& frm = pp.frm;
+    // per merged node / triangle material, per-instance tables
+    pp.mass.assign(hm.m, 0.0);
+    pp.wt.assign(hm.T, 0.0);
+    pp.wb.assign(hm.m, 0.0);
+    pp.node_mu.assign(hm.m, 0.0);
+    pp.optr.assign(B + 1, 0);
+    pp.okind.clear();
+    pp.oprm.clear();
+    pp.tau.assign(frm.S, 0.0f);
+    for (int i = 0; i < B; ++i) {
+        const InstInfo& in = c->inst[i];
+        const HostMesh& h = c->ihm[i];
+        for (int l = 0; l < in.m; ++l) {
+            const int g = in.map(l, MF);
+            pp.mass[g] = q[i].density * h.abar[l];
+            pp.wb[g] = q[i].k_bend * h.abar[l];
+            pp.node_mu[g] = q[i].mu;
+        }
+        for (int t = 0; t < in.T; ++t) pp.wt[in.to + t] = q[i].k_stretch * h.area[t];
+        for (int o = 0; o < q[i].n_obstacles; ++o) {
+            pp.okind.push_back(q[i].obstacles[o].kind);
+            for (int k = 0; k < 8; ++k) pp.oprm.push_back(k < 7 ? q[i].obstacles[o].p[k] : 0.0);
+        }
+        pp.optr[i + 1] = (int)pp.okind.size();
+        const int S_i = (i + 1 < B ? c->inst[i + 1].so : frm.S) - in.so;
+        for (int s = 0; s < S_i; ++s) pp.tau[in.so + s] = (float)tau_i[i];
+    }
+    pp.long_rows.clear();
+    pp.short_rows.clear();
+    for (int i = 0; i < MF; ++i)
+        (pp.hfm.fptr[i + 1] - pp.hfm.fptr[i] > 1024 ? pp.long_rows : pp.short_rows).push_back(i);
+    pp.front_flops = 0.0;
+    for (int sn = 0; sn < frm.S; ++sn)
+        for (int k = 0; k < frm.p[sn]; ++k) {
+            double r = frm.f[sn] - k - 1;
+            pp.front_flops += r + r * (r + 1.0);
+        }
+    pp.factor_nnz = pp.hfm.colptr.empty() ? 0 : pp.hfm.colptr.back();
+    pp.q = std::move(q);
+    return DC_OK;
+}
+
+dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
+    const HostMesh& hm = c->hm;
+    const int MF = hm.m_free;
+    HostFactor& hfm = pp.hfm;
+    HostFronts& frm = pp.frm;
+    free_pool(c, c->factor_allocs);
+    c->graph_epoch++;
+    c->have_params = false;
+    auto& P = c->factor_allocs;
+    double *d_mass, *d_wt, *d_wb, *d_fval, *d_kval, *d_mu, *d_oprm;
+    int *d_fptr, *d_fidx, *d_kptr, *d_kidx, *d_long, *d_short, *d_optr, *d_okind;
+    dc_status s;
+    if ((s = upload(c, P, &d_mass, pp.mass)) || (s = upload(c, P, &d_wt, pp.wt)) || (s = upload(c, P, &d_wb, pp.wb)) ||
+        (s = upload(c, P, &d_fptr, hfm.fptr)) || (s = upload(c, P, &d_fidx, hfm.fidx)) ||
+        (s = upload(c, P, &d_fval, hfm.fval)) || (s = upload(c, P, &d_kptr, hfm.bptr)) ||
+        (s = upload(c, P, &d_kidx, hfm.bidx)) || (s = upload(c, P, &d_kval, hfm.bval)) ||
+        (s = upload(c, P, &d_long, pp.long_rows)) || (s = upload(c, P, &d_short, pp.short_rows)) ||
+        (s = upload(c, P, &d_mu, pp.node_mu)) || (s = upload(c, P, &d_optr, pp.optr)) ||
+        (s = upload(c, P, &d_okind, pp.okind)) || (s = upload(c, P, &d_oprm, pp.oprm)))
+        return s;
+    DevMesh& dm = c->dm;
+    dm.n_long = (int)pp.long_rows.size();
+    dm.n_short = (int)pp.short_rows.size();
+    dm.long_rows = d_long;
+    dm.short_rows = d_short;
+    dm.mass = d_mass;
+    dm.wt = d_wt;
+    dm.wb = d_wb;
+    dm.fptr = d_fptr;
+    dm.fidx = d_fidx;
+    dm.fval = d_fval;
+    dm.kptr = d_kptr;
+    dm.kidx = d_kidx;
+    dm.kval = d_kval;
+    DevParams& dp = c->dp;
+    dp.h = pp.q[0].h;
+    for (int k = 0; k < 3; ++k) dp.g[k] = pp.q[0].gravity[k];
+    dp.delta = pp.q[0].contact_margin;
+    dp.node_mu = d_mu;
+    dp.optr = d_optr;
+    dp.okind = d_okind;
+    dp.oprm = d_oprm;
+    // multifrontal structure for the adjoint preconditioner
+    int dev = 0, smem_optin = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (frontal_factor_smem(frm.max_f) > (size_t)smem_optin) {
+        c->err = "dc_set_params: the largest front (" + std::to_string(frm.max_f) +
+                 " unknowns) exceeds the shared memory of one CTA";
+        return DC_ERR_INVALID;
+    }
+    CK(frontal_configure(frm.max_f));
+    free_pool(c, c->front_allocs);
+    auto& F = c->front_allocs;
+    FrontDev fd{};
+    fd.S = frm.S;
+    fd.NP = (int)frm.pr_i.size();
+    fd.max_f = frm.max_f;
+    fd.pool_size = frm.pool_size;
+    int *d_begin, *d_f, *d_p, *d_uptr, *d_unode, *d_cptr, *d_child, *d_cmap, *d_lvl, *d_pi, *d_pj, *d_pld, *d_pcp,
+        *d_pcode;
+    long long *d_off, *d_acc_off, *d_pdst, *d_binv_off, *d_linv_off;
+    double* d_pcoef;
+    float* d_tau;
+    const size_t n3 = 3 * (size_t)std::max(MF, 1);
+    if ((s = upload(c, F, &d_begin, frm.begin)) || (s = upload(c, F, &d_f, frm.f)) || (s = upload(c, F, &d_p, frm.p)) ||
+        (s = upload(c, F, &d_off, frm.off)) || (s = upload(c, F, &d_acc_off, frm.acc_off)) ||
+        (s = upload(c, F, &d_binv_off, frm.binv_off)) || (s = dalloc(c, F, &fd.binv, (size_t)frm.binv_size)) ||
+        (s = upload(c, F, &d_linv_off, frm.linv_off)) || (s = dalloc(c, F, &fd.linv, (size_t)frm.linv_size)) ||
+        (s = upload(c, F, &d_uptr, frm.uptr)) || (s = upload(c, F, &d_unode, frm.unode)) ||
+        (s = upload(c, F, &d_cptr, frm.cptr)) || (s = upload(c, F, &d_child, frm.child)) ||
+        (s = upload(c, F, &d_cmap, frm.cmap)) || (s = upload(c, F, &d_lvl, frm.lvl_sn)) ||
+        (s = upload(c, F, &d_pi, frm.pr_i)) || (s = upload(c, F, &d_pj, frm.pr_j)) ||
+        (s = upload(c, F, &d_pdst, frm.pr_dst)) || (s = upload(c, F, &d_pld, frm.pr_ld)) ||
+        (s = upload(c, F, &d_pcp, frm.pr_cptr)) || (s = upload(c, F, &d_pcode, frm.pr_code)) ||
+        (s = upload(c, F, &d_pcoef, frm.pr_coef)) || (s = upload(c, F, &d_tau, pp.tau)) ||
+        (s = dalloc(c, F, &fd.pool, (size_t)frm.pool_size)) || (s = dalloc(c, F, &fd.acc, (size_t)frm.acc_size)) ||
+        (s = dalloc(c, F, &fd.rvec, n3)) || (s = dalloc(c, F, &fd.zvec, n3)) || (s = dalloc(c, F, &fd.xvec, n3)))
+        return s;
+    fd.begin = d_begin;
+    fd.f = d_f;
+    fd.p = d_p;
+    fd.off = d_off;
+    fd.acc_off = d_acc_off;
+    fd.binv_off = d_binv_off;
+    fd.linv_off = d_linv_off;
+    fd.uptr = d_uptr;
+    fd.unode = d_unode;
+    fd.cptr = d_cptr;
+    fd.child = d_child;
+    fd.cmap = d_cmap;
+    fd.lvl_sn = d_lvl;
+    fd.pr_i = d_pi;
+    fd.pr_j = d_pj;
+    fd.pr_dst = d_pdst;
+    fd.pr_ld = d_pld;
+    fd.pr_cptr = d_pcp;
+    fd.pr_code = d_pcode;
+    fd.pr_coef = d_pcoef;
+    fd.tau = d_tau;
+    c->fdv = fd;
+    c->fds[0] = fd;
+    c->fds[1] = fd;   // second slot: its own numeric storage, shared structure
+    if ((s = dalloc(c, F, &c->fds[1].pool, (size_t)frm.pool_size)) ||
+        (s = dalloc(c, F, &c->fds[1].binv, (size_t)frm.binv_size)) ||
+        (s = dalloc(c, F, &c->fds[1].linv, (size_t)frm.linv_size)))
+        return s;
+    c->nlev = (int)frm.lvl_ptr.size() - 1;
+    c->front_flops = pp.front_flops;
+    c->factor_nnz = pp.factor_nnz;
+    c->fwd_nnz = (long long)hfm.fval.size();
+    c->bwd_nnz = (long long)hfm.bval.size();
+    c->hf = HostFactor();
+    c->hf.max_diag = hfm.max_diag;
+    c->fr = std::move(frm);
+    c->prm = pp.q[0];
+    c->iprm = pp.q;
+    c->have_params = true;
+    c->ck_n_steps = -1;
+    if (c->async_alloc) CK(cudaStreamSynchronize(c->stream));
+    return DC_OK;
+}
+
+size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPrep& pp, int n_steps) {
+    const HostMesh& hm = c->hm;
+    const size_t m = hm.m, T = hm.T, MF = hm.m_free, B = c->B;
+    const size_t d4b = sizeof(d4);
+    const dc_params& q = pp.q[0];
+    const size_t k = std::max(1, q.checkpoint_every);
+    const size_t mr = std::max(1, std::min(256, q.adj_restart));
+    size_t b = 0, n = 0;   // bytes and allocation count (each rounded up below)
+    auto add = [&](size_t bytes) {
+        b += std::max<size_t>(bytes, 32);
+        ++n;
+    };
+    // mesh
+    add(vbytes(mp.tri4)); add(vbytes(mp.G4)); add(vbytes(hm.area)); add(vbytes(hm.bptr)); add(vbytes(hm.bidx));
+    add(vbytes(hm.bval)); add(vbytes(hm.abar)); add(vbytes(hm.sb)); add(vbytes(mp.qr)); add(vbytes(mp.iptr));
+    add(vbytes(mp.iidx)); add(vbytes(mp.tbptr)); add(vbytes(mp.tbidx)); add(vbytes(mp.tbval));
+    add(vbytes(hm.int2ext)); add(vbytes(mp.node_inst)); add(vbytes(mp.cptr)); add(vbytes(mp.pcptr));
+    add(vbytes(mp.chunks)); add(vbytes(mp.pchunks));
+    // forward work
+    for (int i = 0; i < 9; ++i) add(m * d4b);
+    add(T * d4b); add(T * d4b); add(m * 8); add(m * 24); add(m * 24); add(32);
+    add(MF * 4); add(MF * 4); add(MF * d4b); add(MF * d4b);
+    // factor and tables
+    const HostFactor& f = pp.hfm;
+    add(vbytes(pp.mass)); add(vbytes(pp.wt)); add(vbytes(pp.wb)); add(vbytes(f.fptr)); add(vbytes(f.fidx));
+    add(vbytes(f.fval)); add(vbytes(f.bptr)); add(vbytes(f.bidx)); add(vbytes(f.bval)); add(vbytes(pp.long_rows));
+    add(vbytes(pp.short_rows)); add(vbytes(pp.node_mu)); add(vbytes(pp.optr)); add(vbytes(pp.okind));
+    add(vbytes(pp.oprm));
+    // fronts (numeric storage twice: two slots)
+    const HostFronts& r = pp.frm;
+    add(vbytes(r.begin)); add(vbytes(r.f)); add(vbytes(r.p)); add(vbytes(r.off)); add(vbytes(r.acc_off));
+    add(vbytes(r.binv_off)); add(vbytes(r.linv_off)); add(vbytes(r.uptr)); add(vbytes(r.unode)); add(vbytes(r.cptr));
+    add(vbytes(r.child)); add(vbytes(r.cmap)); add(vbytes(r.lvl_sn)); add(vbytes(r.pr_i)); add(vbytes(r.pr_j));
+    add(vbytes(r.pr_dst)); add(vbytes(r.pr_ld)); add(vbytes(r.pr_cptr)); add(vbytes(r.pr_code));
+    add(vbytes(r.pr_coef)); add(vbytes(pp.tau));
+    for (int s = 0; s < 2; ++s) {
+        add(4 * (size_t)r.pool_size);
+        add(4 * (size_t)r.binv_size);
+        add(4 * (size_t)r.linv_size);
+    }
+    add(4 * (size_t)r.acc_size); add(12 * MF); add(12 * MF); add(12 * MF);
+    // checkpoints, segment recomputation, adjoint
+    add(((size_t)n_steps / k + 1) * 2 * m * d4b);
+    add((k + 1) * m * d4b); add((k + 1) * m * d4b);
+    for (size_t i = 0; i < k; ++i) { add(MF * 4); add(MF * 4); add(MF * d4b); add(MF * d4b); }
+    add(T * d4b); add(T * d4b); add(m * d4b);
+    for (int s = 0; s < 2; ++s) {
+        add(T * d4b); add(T * d4b); add(T * d4b); add(m * d4b); add(3 * MF * d4b); add(MF * d4b); add(MF * 4);
+    }
+    for (int i = 0; i < 15; ++i) add(m * d4b);
+    add((mr + 1) * 4 * m * 8); add(mr * 4 * m * 8); add((mr + 1) * B * 8); add((mr + 1) * B * 8);
+    add(B * 8); add(B * 8); add((mr + 1) * mp.chunks.size() * 8); add(4 * B * 8); add(mp.pchunks.size() * 8);
+    // allocation granularity of the device pools
+    return b + n * 512;
+}

@@ -42,3 +42,21 @@ def rel_l2(a, b):
 def cuda(a):
     import torch
     return torch.tensor(np.asarray(a, dtype=np.float64), device="cuda")
+
+
+def params_kw(sc, **over):
+    """The set_params keyword arguments of a scene (with overrides)."""
+    p = dataclasses.replace(sc.params, **{k: v for k, v in over.items() if hasattr(sc.params, k)})
+    kw = dict(k_stretch=p.k_stretch, k_bend=p.k_bend, density=p.density, mu=p.mu, h=p.h, gravity=p.gravity,
+              contact_margin=p.contact_margin, n_pd_iters=p.n_pd_iters, obstacles=sc.obstacles)
+    kw.update({k: v for k, v in over.items() if not hasattr(sc.params, k)})
+    return kw
+
+
+def make_batch(scs, device="cuda", **over):
+    import paper_2106_05306_gb300 as dc
+    from paper_2106_05306_gb300 import build
+    build.build()
+    batch = dc.ClothBatch([(s.rest_pos, s.tris, s.pins) for s in scs], device=device)
+    batch.set_params([params_kw(s, **over) for s in scs])
+    return batch
