@@ -1,15 +1,23 @@
 #!/usr/bin/env python3
 """Throughput benchmark of the differentiable cloth hot path on GB300.
 
-Metric: cloth time steps per second, forward + adjoint, FP64.
-One bench step = one full rollout of the draped-cloth workload (61 x 61 grid,
-3721 nodes, 7200 triangles, dropped over a sphere of radius 0.3 m and the
-ground; 125 time steps at h = 1/120 s, 20 PD iterations per step) forward, then
-its gradient w.r.t. (x0, v0, k_stretch, k_bend, mu) through the
-torch.autograd.Function with checkpoints every 25 steps.  Inputs are synthetic
-and seeded (scenes.draped_cloth).
+Metric: cloth time steps per second, forward + adjoint, FP64, batched (and
+served) against the plain one-cloth-at-a-time path.
+
+Workload of one bench step (``--workload batch``, the default): 256 cloths in
+one context (scenes.batch_instance, seeds 0..255): square grids of 16x16 to
+64x64 nodes drawn uniformly, stretch / bending stiffness and friction drawn per
+cloth, each dropped onto its own random sphere (radius 0.2-0.5 m) and the
+ground; 50 time steps at h = 1/120 s with 20 PD iterations each, then the
+gradient w.r.t. (x0, v0, k_stretch, k_bend, mu) of every cloth, in one batched
+rollout and one batched backward.  The same JSON line also reports the plain
+path (the same cloths one at a time, sampled), the single 61x61 draped cloth
+(125 steps, checkpoints every 25), and a short served run (requests of 1k-30k
+DOF and 25-150 steps through the request server) with p50/p99 latency.
+Inputs are synthetic and seeded.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload batch|single] [--no-extras]
 
 For N > 1 it is launched by torch.distributed.run, one rank per GPU; every rank
 runs its own replica of the workload (replicas only: the path has no exchange
@@ -21,11 +29,14 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
 import sys
 import tempfile
+
+import numpy as np
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -34,12 +45,19 @@ if ROOT not in sys.path:
 
 METRIC = "cloth time steps/sec (fwd+adjoint, FP64)"
 UNIT = "cloth_steps/s"
-N_STEPS = 125
-CHECKPOINT_EVERY = 25
 L2_FLUSH_BYTES = 512 << 20        # > 129 MB L2
-WORKLOAD = ("draped cloth 61x61 (3721 nodes, 7200 triangles), sphere r=0.3 m + ground plane, "
-            "125 steps at h=1/120 s, 20 PD iterations/step, forward + checkpointed adjoint (every 25 steps), "
-            "gradient w.r.t. x0, v0, k_stretch, k_bend, mu")
+
+BATCH = 256
+BATCH_STEPS = 50
+BATCH_WORKLOAD = ("batched: 256 cloths in one context, grids 16x16..64x64 (uniform), per-cloth stiffness/friction "
+                  "and random sphere r 0.2-0.5 m + ground plane, 50 steps at h=1/120 s, 20 PD iterations/step, "
+                  "forward + adjoint (all steps recorded, no recomputation), gradient w.r.t. x0, v0, k_stretch, "
+                  "k_bend, mu of every cloth")
+SINGLE_STEPS = 125
+SINGLE_CK = 25
+SINGLE_WORKLOAD = ("draped cloth 61x61 (3721 nodes, 7200 triangles), sphere r=0.3 m + ground plane, "
+                   "125 steps at h=1/120 s, 20 PD iterations/step, forward + checkpointed adjoint (every 25 steps), "
+                   "gradient w.r.t. x0, v0, k_stretch, k_bend, mu")
 
 # FP32 CUDA-core peak from unit counts and the maximum SM clock (GB300: 152 SMs,
 # 128 FP32 lanes per SM, FMA = 2 flops, 2070 MHz); FP64 nominal 1.25 TFLOP/s.
@@ -49,7 +67,7 @@ FP64_PEAK_TFLOPS = 1.25
 
 # DRAM traffic per launch of the roofline kernel from the ncu capture summarised in
 # profiles/ (null when the kernel source changed since the capture).
-TRAFFIC = {"front": {"bytes": None, "source_sha": None}}
+TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None}}
 
 
 def parse_args(argv=None):
@@ -58,10 +76,13 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--roofline-kernel", default="front")
-    ap.add_argument("--rollout-steps", type=int, default=N_STEPS,
-                    help="cloth steps per rollout (125 for the workload; ncu launch lists use a shorter rollout)")
+    ap.add_argument("--workload", choices=["batch", "single"], default="batch")
+    ap.add_argument("--roofline-kernel", default=None, help="kernel class timed for the roofline")
+    ap.add_argument("--rollout-steps", type=int, default=None,
+                    help="cloth steps per rollout (default: the workload's; ncu launch lists use a shorter one)")
+    ap.add_argument("--batch", type=int, default=BATCH, help="cloths in the batch (256 for the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain / single / served side runs")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -144,42 +165,60 @@ class ClockSampler:
 
 # ----------------------------------------------------------------------------- oracle sample
 
-def oracle_sample(n_fwd: int = 5, n_adj: int = 1, start_step: int = 20):
-    """Time the CPU oracle on a bounded sample of the workload: n_fwd forward steps
-    and n_adj adjoint steps of the 61x61 draped cloth starting at `start_step`
-    (reached untimed).  Returns (steps/s for fwd+adjoint, seconds timed, sample text)."""
+def oracle_sample(workload: str):
+    """Time the CPU oracle on a bounded sample of the workload.  batch: 8 of the 256
+    cloths (seeds 0, 32, ..., 224), 2 forward steps and 1 adjoint step each; single:
+    5 forward steps and 1 adjoint step of the 61x61 cloth from step 20 (reached
+    untimed).  Returns (cloth steps/s for fwd + adjoint, seconds timed, sample text)."""
     import scenes
     from oracle import cloth as oc
+    if workload == "batch":
+        per_step = []
+        secs = 0.0
+        for seed in range(0, BATCH, 32):
+            sc = scenes.batch_instance(seed, n_steps=BATCH_STEPS)
+            M = oc.model_from_scene(sc)
+            x, v = sc.x0, sc.v0
+            t0 = time.perf_counter()
+            recs = []
+            for _ in range(2):
+                x, v, rec = oc.step(M, x, v)
+                recs.append(rec)
+            t1 = time.perf_counter()
+            oc.adjoint_step(M, recs[-1], sc.loss_w, sc.loss_w * 0.0)
+            t2 = time.perf_counter()
+            per_step.append((t1 - t0) / 2 + (t2 - t1))
+            secs += t2 - t0
+        sample = ("oracle (numpy/scipy FP64, banded Cholesky + direct sparse KKT adjoint) on 8 of the 256 batched "
+                  "cloths (seeds 0, 32, ..., 224): 2 forward + 1 adjoint step each; steps/s = 1 / mean over the "
+                  "sampled cloths of (forward s/step + adjoint s/step)")
+        return 1.0 / statistics.mean(per_step), secs, sample
     sc = scenes.draped_cloth()
     M = oc.model_from_scene(sc)
     x, v = sc.x0, sc.v0
-    for _ in range(start_step):
+    for _ in range(20):
         x, v, _ = oc.step(M, x, v)
     t0 = time.perf_counter()
     recs = []
-    for _ in range(n_fwd):
+    for _ in range(5):
         x, v, rec = oc.step(M, x, v)
         recs.append(rec)
     t1 = time.perf_counter()
-    gx, gv = sc.loss_w, sc.loss_w * 0.0
-    for rec in recs[::-1][:n_adj]:
-        gx, gv, _, _, _ = oc.adjoint_step(M, rec, gx, gv)
+    oc.adjoint_step(M, recs[-1], sc.loss_w, sc.loss_w * 0.0)
     t2 = time.perf_counter()
-    per_step = (t1 - t0) / n_fwd + (t2 - t1) / n_adj
-    sample = (f"oracle (numpy/scipy FP64, banded Cholesky + direct sparse KKT adjoint) on the 61x61 draped "
-              f"cloth: {n_fwd} forward steps and {n_adj} adjoint step(s) from step {start_step}; "
-              f"steps/s = 1 / (forward s/step + adjoint s/step)")
-    return 1.0 / per_step, t2 - t0, sample
+    sample = ("oracle (numpy/scipy FP64, banded Cholesky + direct sparse KKT adjoint) on the 61x61 draped cloth: "
+              "5 forward steps and 1 adjoint step from step 20; steps/s = 1 / (forward s/step + adjoint s/step)")
+    return 1.0 / ((t1 - t0) / 5 + (t2 - t1)), t2 - t0, sample
 
 
-def cpu_baseline_subprocess():
+def cpu_baseline_subprocess(workload: str):
     """Run the oracle sample single-threaded in a child process."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env.pop("RANK", None)
     env.pop("WORLD_SIZE", None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"], env=env,
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload], env=env,
                        capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
@@ -192,11 +231,186 @@ def kernel_sha(path):
     return hashlib.sha256(open(path, "rb").read()).hexdigest()[:16]
 
 
-def run_ours(args):
+def scene_kw(sc, **over):
+    p = sc.params
+    kw = dict(k_stretch=p.k_stretch, k_bend=p.k_bend, density=p.density, mu=p.mu, h=p.h, gravity=p.gravity,
+              contact_margin=p.contact_margin, n_pd_iters=p.n_pd_iters, obstacles=sc.obstacles)
+    kw.update(over)
+    return kw
+
+
+class Workload:
+    """The timed object of one workload: step() runs one bench step on `stream`."""
+
+    def __init__(self, kind, args, dev):
+        import torch
+
+        import paper_2106_05306_gb300 as dc
+        import scenes
+        self.kind = kind
+        self.dev = dev
+        self.stream = torch.cuda.Stream(dev)
+        with torch.cuda.stream(self.stream):
+            if kind == "batch":
+                self.n_cloth = args.rollout_steps or BATCH_STEPS
+                self.scs = [scenes.batch_instance(seed, n_steps=BATCH_STEPS) for seed in range(args.batch)]
+                self.ctx = dc.ClothBatch([(s.rest_pos, s.tris, s.pins) for s in self.scs], device=dev)
+                self.ctx.set_params([scene_kw(s, checkpoint_every=1) for s in self.scs])
+                self.ctx.autotune()
+                self.ctx.set_graphs(True)
+                cat = lambda k: torch.tensor(np.concatenate([getattr(s, k) for s in self.scs]), device=dev)
+                self.x0, self.v0, self.xi = cat("x0"), cat("v0"), cat("loss_w")
+                self.cloths = len(self.scs)
+            else:
+                self.n_cloth = args.rollout_steps or SINGLE_STEPS
+                sc = scenes.draped_cloth()
+                self.scs = [sc]
+                self.ctx = dc.Cloth(sc.rest_pos, sc.tris, sc.pins, device=dev)
+                self.ctx.set_params(**scene_kw(sc, checkpoint_every=SINGLE_CK))
+                self.x0 = torch.tensor(sc.x0, device=dev)
+                self.v0 = torch.tensor(sc.v0, device=dev)
+                self.xi = torch.tensor(sc.loss_w, device=dev)
+                p = sc.params
+                self.theta = torch.tensor([p.k_stretch, p.k_bend, p.mu], dtype=torch.float64, requires_grad=True)
+                self.cloths = 1
+        self.steps_per_bench_step = self.cloths * self.n_cloth
+
+    def step(self):
+        """One bench step: the rollout and its gradient (device inputs)."""
+        import torch
+
+        import paper_2106_05306_gb300 as dc
+        with torch.cuda.stream(self.stream):
+            if self.kind == "batch":
+                self.ctx.rollout(self.x0, self.v0, self.n_cloth)
+                return self.ctx.backward(self.xi, allow_nonconverged=True)
+            a = self.x0.detach().requires_grad_(True)
+            b = self.v0.detach().requires_grad_(True)
+            xN, vN = dc.rollout_fn(self.ctx, a, b, self.theta, self.n_cloth)
+            (xN * self.xi).sum().backward()
+            return a.grad, b.grad
+
+    def step_host(self, x0h, v0h, xih):
+        """The same step end to end through the public API with pinned host buffers."""
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.ctx.rollout(x0h, v0h, self.n_cloth)
+            if self.kind == "batch":
+                _, _, dth = self.ctx.backward(xih, allow_nonconverged=True)
+            else:
+                _, _, dth = self.ctx.backward(xih)
+            return float(dth.reshape(-1)[0])
+
+
+def plain_sample(args, dev, n_cloth):
+    """The plain path: cloths of the batch one at a time, each its own context
+    (the same parameters, all steps recorded), on a sample of 16 of them."""
     import torch
 
     import paper_2106_05306_gb300 as dc
     import scenes
+    stream = torch.cuda.Stream(dev)
+    tot_s, tot_steps, seeds = 0.0, 0, list(range(0, args.batch, max(1, args.batch // 16)))
+    with torch.cuda.stream(stream):
+        for seed in seeds:
+            sc = scenes.batch_instance(seed, n_steps=BATCH_STEPS)
+            c = dc.Cloth(sc.rest_pos, sc.tris, sc.pins, device=dev)
+            c.set_params(**scene_kw(sc, checkpoint_every=1))
+            x0, v0, xi = (torch.tensor(a, device=dev) for a in (sc.x0, sc.v0, sc.loss_w))
+            c.rollout(x0, v0, n_cloth)
+            c.backward(xi, allow_nonconverged=True)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            c.rollout(x0, v0, n_cloth)
+            c.backward(xi, allow_nonconverged=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot_s += e0.elapsed_time(e1) / 1e3
+            tot_steps += n_cloth
+            c.close()
+    return {"value": tot_steps / tot_s, "unit": UNIT,
+            "sample": f"{len(seeds)} of the batched cloths (seeds 0, {seeds[1] if len(seeds) > 1 else 0}, ...), "
+                      f"each alone in its own context, one after another, {n_cloth} steps fwd+adjoint each"}
+
+
+def single_side_run(args, dev):
+    """The single 61x61 draped cloth (125 steps, checkpoints every 25): 1 warm-up, 1 timed step."""
+    import torch
+    w = Workload("single", argparse.Namespace(rollout_steps=None, batch=1), dev)
+    w.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(w.stream)
+    w.step()
+    e1.record(w.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    w.ctx.close()
+    return {"value": SINGLE_STEPS / (ms / 1e3), "unit": UNIT, "workload": SINGLE_WORKLOAD}
+
+
+def served_side_run(dev, n_req=32, rate=6.0, slots=8, seed0=10000):
+    """A short served run: n_req requests (1k-30k DOF, 25-150 steps, random sphere +
+    ground, mu 0.1-0.6) with Poisson arrivals at `rate` per second into the request
+    server; then the same requests one at a time through the plain path."""
+    import threading
+
+    import torch
+
+    import paper_2106_05306_gb300 as dc
+    import scenes
+    reqs = [scenes.serve_request(seed0 + i) for i in range(n_req)]
+    rng = np.random.default_rng(4242)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    srv = dc.Server(n_slots=slots, n_prep_threads=4, device=dev.index or 0)
+    tickets = [None] * n_req
+
+    def producer():
+        for i, sc in enumerate(reqs):
+            time.sleep(gaps[i])
+            tickets[i] = srv.submit(sc.rest_pos, sc.tris, sc.pins, sc.x0, sc.v0, sc.loss_w, sc.n_steps,
+                                    scene_kw(sc, checkpoint_every=1))
+
+    t0 = time.perf_counter()
+    th = threading.Thread(target=producer)
+    th.start()
+    th.join()
+    res = [srv.wait(t) for t in tickets]
+    makespan = time.perf_counter() - t0
+    st = srv.stats()
+    srv.close()
+    lat = sorted(r["t_done"] - r["t_submit"] for r in res)
+    steps = sum(sc.n_steps for sc in reqs)
+    ok = sum(r["status"] in ("DC_OK", "DC_ERR_NONCONVERGED") for r in res)
+    # the same requests one at a time (plain path, no server)
+    stream = torch.cuda.Stream(dev)
+    plain_s = 0.0
+    with torch.cuda.stream(stream):
+        for sc in reqs:
+            c = dc.Cloth(sc.rest_pos, sc.tris, sc.pins, device=dev)
+            c.set_params(**scene_kw(sc, checkpoint_every=1))
+            x0, v0, xi = (torch.tensor(a, device=dev) for a in (sc.x0, sc.v0, sc.loss_w))
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            c.rollout(x0, v0, sc.n_steps)
+            c.backward(xi, allow_nonconverged=True)
+            torch.cuda.synchronize()
+            plain_s += time.perf_counter() - t
+            c.close()
+    return {"value": steps / makespan, "unit": UNIT, "requests": n_req, "completed": ok,
+            "arrivals": f"Poisson, {rate}/s", "slots": slots,
+            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+            "peak_in_flight": st["peak_in_flight"], "peak_reserved_gb": st["peak_bytes_reserved"] / 1e9,
+            "plain_sequential": {"value": steps / plain_s, "unit": UNIT,
+                                 "note": "same requests one at a time, setup excluded"},
+            "workload": "requests of 1k-30k DOF (log-uniform), 25-150 steps, random sphere + ground, "
+                        "fwd + adjoint, all steps recorded; makespan from first arrival to last result"}
+
+
+def run_ours(args):
+    import torch
+
     from paper_2106_05306_gb300 import build as dcbuild
 
     rank, world, local = dist_env()
@@ -207,114 +421,74 @@ def run_ours(args):
     dcbuild.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    sc = scenes.draped_cloth()
-    p = sc.params
-    cloth = dc.Cloth(sc.rest_pos, sc.tris, sc.pins, device=dev)
-    cloth.set_params(k_stretch=p.k_stretch, k_bend=p.k_bend, density=p.density, mu=p.mu, h=p.h, gravity=p.gravity,
-                     contact_margin=p.contact_margin, n_pd_iters=p.n_pd_iters, obstacles=sc.obstacles,
-                     checkpoint_every=CHECKPOINT_EVERY)
-    x0 = torch.tensor(sc.x0, device=dev)
-    v0 = torch.tensor(sc.v0, device=dev)
-    xi = torch.tensor(sc.loss_w, device=dev)
-    theta = torch.tensor([p.k_stretch, p.k_bend, p.mu], dtype=torch.float64, requires_grad=True)
+    wl = Workload(args.workload, args, dev)
+    roof_cls = args.roofline_kernel or ("solve_fwd" if args.workload == "batch" else "front")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-    n_cloth = args.rollout_steps
-
-    def one_step():
-        a = x0.detach().requires_grad_(True)
-        b = v0.detach().requires_grad_(True)
-        xN, vN = dc.rollout_fn(cloth, a, b, theta, n_cloth)
-        L = (xN * xi).sum()
-        L.backward()
-        return a.grad, b.grad
-
     for _ in range(max(args.warmup, 0)):
-        one_step()
+        wl.step()
     torch.cuda.synchronize()
-    st0 = cloth.stats()
-    cloth.set_kernel_timer(args.roofline_kernel)
+    st0 = wl.ctx.stats()
+    wl.ctx.set_kernel_timer(roof_cls)
     clocks = ClockSampler(local)
     barrier(world)
     clocks.start()
-    stream = torch.cuda.current_stream(dev)
     total_ms = 0.0
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        one_step()
-        e1.record(stream)
+        e0.record(wl.stream)
+        wl.step()
+        e1.record(wl.stream)
         torch.cuda.synchronize()
         total_ms += e0.elapsed_time(e1)
     barrier(world)
     clk = clocks.stop()
-    st1 = cloth.stats()
-    cloth.set_kernel_timer("none")
+    st1 = wl.ctx.stats()
+    wl.ctx.set_kernel_timer("none")
     max_ms = aggregate(total_ms, world)
-    value = world * args.steps * n_cloth / (max_ms / 1e3)
+    value = world * args.steps * wl.steps_per_bench_step / (max_ms / 1e3)
 
-    # end to end through the C ABI with pinned host buffers (copies inside the timed region)
-    x0h = x0.cpu().pin_memory()
-    v0h = v0.cpu().pin_memory()
-    xih = xi.cpu().pin_memory()
+    # end to end through the public API with pinned host buffers (copies inside the timed region)
+    x0h, v0h, xih = (t.cpu().pin_memory() for t in (wl.x0, wl.v0, wl.xi))
     e2e_s = 0.0
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        xN, vN = cloth.rollout(x0h, v0h, n_cloth)
-        dx0, dv0, dth = cloth.backward(xih)
-        _ = float(dth[0])
+        wl.step_host(x0h, v0h, xih)
         e2e_s += time.perf_counter() - t0
     e2e_max = aggregate(e2e_s * 1e3, world) / 1e3
-    m = sc.m
-    e2e = {"value": world * args.steps * n_cloth / e2e_max, "unit": UNIT,
-           "h2d_bytes_per_step": 3 * m * 3 * 8, "d2h_bytes_per_step": 4 * m * 3 * 8 + 3 * 8}
+    m = wl.ctx.m
+    e2e = {"value": world * args.steps * wl.steps_per_bench_step / e2e_max, "unit": UNIT,
+           "h2d_bytes_per_step": 3 * m * 3 * 8,
+           "d2h_bytes_per_step": 4 * m * 3 * 8 + 3 * 8 * wl.cloths}
 
-    # roofline of the dominant kernel (live CUDA-event timing over the timed region)
-    launches = st1["timer_launches"]
-    kern_ms = st1["timer_ms"] / max(launches, 1)
-    if args.roofline_kernel == "front":
-        n_fact = launches / max(st1["front_levels"], 1)
-        work = st1["front_flops"] * n_fact / max(launches, 1)          # flops per launch (mean)
-        achieved = work / (kern_ms / 1e3) / 1e12
-        roof = {"kernel": "k_front_level (one level of the FP32 multifrontal LDL^T)", "bound": "alu",
-                "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz"}
-        tr = TRAFFIC["front"]
-        src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_frontal.cu")
-        roof["traffic"] = tr["bytes"] if tr["source_sha"] == kernel_sha(src) else None
-    else:
-        nnz = st1["fwd_solve_nnz"] if args.roofline_kernel == "solve_fwd" else st1["bwd_solve_nnz"]
-        work = 6.0 * nnz                                                # 3 RHS FMAs per nonzero
-        achieved = work / (kern_ms / 1e3) / 1e12
-        roof = {"kernel": f"k_{args.roofline_kernel}", "bound": "alu", "achieved": achieved,
-                "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s",
-                "traffic": None}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["mean_launch_us"] = kern_ms * 1e3
-    roof["launches_timed"] = launches
-
+    roof = roofline(roof_cls, st1)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD if n_cloth == N_STEPS else WORKLOAD.replace("125 steps", f"{n_cloth} steps"),
-                   "cloth_steps_per_bench_step": n_cloth, "nodes": m,
-                   "triangles": int(sc.tris.shape[0]), "pd_iters": p.n_pd_iters,
-                   "checkpoint_every": CHECKPOINT_EVERY, "parallelism": f"replicas x{world}",
-                   "l2": "flushed (512 MB write) before every timed step"},
+        "config": workload_config(wl, world),
         "e2e": e2e,
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
         "roofline": roof,
         "clocks": clk,
-        "adjoint": {"gmres_iters_per_step": (st1["adj_iters"] - st0["adj_iters"]) / max(
-            st1["adj_steps"] - st0["adj_steps"], 1), "nonconverged_steps": st1["adj_nonconverged"]},
+        "adjoint": {"gmres_iters_per_cloth_step": (st1["adj_iters"] - st0["adj_iters"]) / max(
+            st1["adj_steps"] - st0["adj_steps"], 1),
+            "lockstep_iters_per_step": (st1["adj_batch_iters"] - st0["adj_batch_iters"]) / max(
+                args.steps * wl.n_cloth, 1),
+            "nonconverged_cloth_steps": st1["adj_nonconverged"] - st0["adj_nonconverged"]},
     }
+    wl.ctx.close()
+    if rank == 0 and not args.no_extras and args.workload == "batch":
+        out["plain"] = plain_sample(args, dev, wl.n_cloth)
+        out["batched_vs_plain"] = value / out["plain"]["value"]
+        out["single_61x61"] = single_side_run(args, dev)
+        out["served"] = served_side_run(dev)
+        out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline_subprocess()
-    cloth.close()
+        out["cpu_baseline"] = cpu_baseline_subprocess(args.workload)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -322,24 +496,72 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def roofline(cls, st):
+    """Roofline of the dominant kernel from the live CUDA-event timing of its launches."""
+    launches = st["timer_launches"]
+    kern_ms = st["timer_ms"] / max(launches, 1)
+    if cls == "front":
+        n_fact = launches / max(st["front_levels"], 1)
+        work = st["front_flops"] * n_fact / max(launches, 1)          # flops per launch (mean)
+        roof = {"kernel": "k_front_level (one level of the FP32 multifrontal LDL^T)", "bound": "alu",
+                "achieved": work / (kern_ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", "traffic": None}
+        tr = TRAFFIC["front"]
+        src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_frontal.cu")
+        if tr["source_sha"] == kernel_sha(src):
+            roof["traffic"] = tr["bytes"]
+    else:
+        nnz = st["fwd_solve_nnz"] if cls == "solve_fwd" else st["bwd_solve_nnz"]
+        work = 6.0 * nnz                                  # 3 right-hand sides: one FMA each per nonzero
+        roof = {"kernel": f"k_{cls} (P^-1 sweep with the explicit inverse factor rows, FP64, 3 right-hand sides)",
+                "bound": "alu", "achieved": work / (kern_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 table of the profiling recipe)",
+                "traffic": None, "algorithmic_flops_per_launch": work}
+        tr = TRAFFIC.get(cls)
+        src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_kernels.cu")
+        if tr and tr["bytes_per_nnz"] and tr["source_sha"] == kernel_sha(src):
+            roof["traffic"] = tr["bytes_per_nnz"] * nnz
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["mean_launch_us"] = kern_ms * 1e3
+    roof["launches_timed"] = launches
+    return roof
+
+
+def workload_config(wl, world):
+    if wl.kind == "batch":
+        sizes = [s.n for s in wl.scs]
+        return {"workload": BATCH_WORKLOAD if wl.n_cloth == BATCH_STEPS else
+                BATCH_WORKLOAD.replace("50 steps", f"{wl.n_cloth} steps"),
+                "cloths": len(wl.scs), "grid_n_min": min(sizes), "grid_n_max": max(sizes),
+                "nodes": int(wl.ctx.m), "triangles": int(sum(s.tris.shape[0] for s in wl.scs)),
+                "cloth_steps_per_bench_step": wl.steps_per_bench_step, "pd_iters": 20, "checkpoint_every": 1,
+                "graphs": "captured per rollout; bypassed while the roofline kernel timer runs (timed region)",
+                "autotuned": True, "parallelism": f"replicas x{world}",
+                "l2": "flushed (512 MB write) before every timed step; inputs also larger than L2"}
+    return {"workload": SINGLE_WORKLOAD if wl.n_cloth == SINGLE_STEPS else
+            SINGLE_WORKLOAD.replace("125 steps", f"{wl.n_cloth} steps"),
+            "cloth_steps_per_bench_step": wl.n_cloth, "nodes": int(wl.ctx.m),
+            "triangles": int(wl.scs[0].tris.shape[0]), "pd_iters": 20, "checkpoint_every": SINGLE_CK,
+            "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) before every timed step"}
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
     # each step: one bounded oracle sample of the workload (single-threaded child process)
-    vals, secs = [], 0.0
-    info = None
+    vals, info = [], None
     for k in range(args.warmup + args.steps):
-        info = cpu_baseline_subprocess()
+        info = cpu_baseline_subprocess(args.workload)
         if k >= args.warmup:
             vals.append(info["value"])
-            secs += info.get("seconds", 0.0)
     value = statistics.mean(vals) if vals and None not in vals else None
+    wl = BATCH_WORKLOAD if args.workload == "batch" else SINGLE_WORKLOAD
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": (1e3 / value) if value else None, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "l2": "n/a (CPU)"},
+           "config": {"workload": wl, "l2": "n/a (CPU)"},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": info["sample"] if info else None},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -349,7 +571,7 @@ def run_reference(args):
 def main():
     args = parse_args()
     if args.cpu_sample:
-        v, secs, sample = oracle_sample()
+        v, secs, sample = oracle_sample(args.workload)
         print(json.dumps({"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
                           "seconds": secs}))
         return

@@ -211,6 +211,7 @@ __global__ void k_adj_elem(DevMesh dm, AdjDev ad, const d4* __restrict__ z, d4* 
     const double h2 = ad.h * ad.h;
     if (id < dm.T) {
         int4 tr = dm.tri[id];
+        if (ad.mask && ad.mask[ad.node_inst[tr.x]] == 0.0) return;
         d4 g = ld(dm.G + id);
         d4 z0 = ld(z + tr.x), z1 = ld(z + tr.y), z2 = ld(z + tr.z);
         double e1[3] = {z1.x - z0.x, z1.y - z0.y, z1.z - z0.z};
@@ -244,6 +245,7 @@ __global__ void k_adj_elem(DevMesh dm, AdjDev ad, const d4* __restrict__ z, d4* 
     }
     int b = id - dm.T;
     if (b >= dm.m) return;
+    if (ad.mask && ad.mask[ad.node_inst[b]] == 0.0) return;
     double dq[3] = {0, 0, 0};
     for (int k = dm.bptr[b]; k < dm.bptr[b + 1]; ++k) {
         d4 zz = ld(z + dm.bidx[k]);
@@ -268,6 +270,7 @@ __global__ void k_adj_gather(DevMesh dm, AdjDev ad, int mode, const d4* __restri
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int n = (mode == 3) ? dm.m : dm.m_free;
     if (i >= n) return;
+    if (ad.mask && ad.mask[ad.node_inst[i]] == 0.0) return;
     double r0 = 0, r1 = 0, r2 = 0;
     for (int k = dm.iptr[i]; k < dm.iptr[i + 1]; ++k) {
         int e = dm.iidx[k];
@@ -382,10 +385,15 @@ constexpr int DOT_THREADS = 128;
 // partial[j * nchunk + c] = sum over chunk c of V_j . w   (grid: chunks x vectors)
 __global__ void __launch_bounds__(DOT_THREADS) k_bmdot(const double* __restrict__ V, long ldv,
                                                        const double* __restrict__ w, const int4* __restrict__ chunk,
-                                                       int nchunk, double* __restrict__ partial) {
+                                                       int nchunk, double* __restrict__ partial,
+                                                       const double* __restrict__ mask) {
     __shared__ double sh[DOT_THREADS / 32];
     const int c = blockIdx.x, j = blockIdx.y;
     const int4 ch = chunk[c];
+    if (mask && mask[ch.x] == 0.0) {
+        if (threadIdx.x == 0) partial[(long)j * nchunk + c] = 0.0;
+        return;
+    }
     const double* v = V + j * ldv;
     double s = 0.0;
     for (int i = ch.y + threadIdx.x; i < ch.z; i += DOT_THREADS) s += v[i] * w[i];
@@ -413,8 +421,10 @@ __global__ void k_breduce(const double* __restrict__ partial, int nchunk, const 
 
 // w += sign * sum_j V_j coef[j * B + inst]   (one block per chunk)
 __global__ void k_bvupdate(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ coef, int B,
-                           const int4* __restrict__ chunk, double* __restrict__ w, double sign) {
+                           const int4* __restrict__ chunk, double* __restrict__ w, double sign,
+                           const double* __restrict__ mask) {
     const int4 ch = chunk[blockIdx.x];
+    if (mask && mask[ch.x] == 0.0) return;
     for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
         double s = 0.0;
         for (int j = 0; j < nvec; ++j) s += V[j * ldv + i] * coef[j * B + ch.x];
@@ -427,7 +437,7 @@ __global__ void k_bscale(const double* __restrict__ a, const double* __restrict_
                          const int4* __restrict__ chunk, double* __restrict__ out) {
     const int4 ch = chunk[blockIdx.x];
     const double f = sc[ch.x];
-    for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) out[i] = a[i] * f;
+    for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) out[i] = f == 0.0 ? 0.0 : a[i] * f;
 }
 
 // ----------------------------------------------------------------- gradient outputs
@@ -684,16 +694,16 @@ void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytm
     k_adj_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, ad, ytmp, base, out);
 }
 void adj_bdot(const Segs& sg, const double* V, long ldv, int nvec, const double* w, double* partial, double* out,
-              cudaStream_t s) {
+              cudaStream_t s, const double* mask) {
     dc_note_launch();
-    k_bmdot<<<dim3(sg.nchunk, nvec), DOT_THREADS, 0, s>>>(V, ldv, w, sg.chunk, sg.nchunk, partial);
+    k_bmdot<<<dim3(sg.nchunk, nvec), DOT_THREADS, 0, s>>>(V, ldv, w, sg.chunk, sg.nchunk, partial, mask);
     dc_note_launch();
     k_breduce<<<nblk((long)sg.B * nvec, 128), 128, 0, s>>>(partial, sg.nchunk, sg.cptr, sg.B, nvec, out);
 }
 void adj_bvupdate(const Segs& sg, const double* V, long ldv, int nvec, const double* coef, double* w, double sign,
-                  cudaStream_t s) {
+                  cudaStream_t s, const double* mask) {
     dc_note_launch();
-    k_bvupdate<<<sg.nchunk, 128, 0, s>>>(V, ldv, nvec, coef, sg.B, sg.chunk, w, sign);
+    k_bvupdate<<<sg.nchunk, 128, 0, s>>>(V, ldv, nvec, coef, sg.B, sg.chunk, w, sign, mask);
 }
 void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s) {
     dc_note_launch();

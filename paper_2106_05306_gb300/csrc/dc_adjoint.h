@@ -17,6 +17,9 @@ struct AdjDev {
     const int* case_;     // step record: 0 take-off, 1 stick, 2 slip
     const d4* nb;         // step record: (normal, beta)
     const d4* f;          // step record: contact force
+    const int* node_inst; // [m] instance of each node
+    const double* mask;   // [n_inst] or NULL: instances with mask 0 are skipped (their
+                          // outputs keep stale, finite values that are only ever scaled by 0)
     d4* c1;               // element-pass scratch [T]
     d4* c2;               // [T]
     d4* bu;               // [m]
@@ -39,11 +42,11 @@ struct Segs {
 };
 // out[j * B + i] = V_j . w over instance i's free nodes, j < nvec
 void adj_bdot(const Segs& sg, const double* V, long ldv, int nvec, const double* w, double* partial, double* out,
-              cudaStream_t s);
+              cudaStream_t s, const double* mask = nullptr);
 // w += sign * sum_j V_j coef[j * B + i] on instance i's free nodes
 void adj_bvupdate(const Segs& sg, const double* V, long ldv, int nvec, const double* coef, double* w, double sign,
-                  cudaStream_t s);
-// out = a * sc[i] on instance i's free nodes
+                  cudaStream_t s, const double* mask = nullptr);
+// out = a * sc[i] on instance i's free nodes (exactly 0 where sc[i] == 0)
 void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s);
 void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
                  const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
@@ -57,7 +60,9 @@ void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream
 size_t frontal_factor_smem(int max_f);
 size_t frontal_solve_smem(int max_f);
 cudaError_t frontal_configure(int max_f);
+// lvl_ptr / lvl_maxf: host arrays, the fronts of level l are lvl_sn[lvl_ptr[l] ..
+// lvl_ptr[l+1]) and the largest has lvl_maxf[l] unknowns.
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
-                       int max_f, cudaStream_t s, KTimer* kt = nullptr);
-void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, int max_f, int n_free,
-                     const d4* w, d4* out, cudaStream_t s, KTimer* kt = nullptr);
+                       const int* lvl_maxf, cudaStream_t s, KTimer* kt = nullptr);
+void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, const int* lvl_maxf,
+                     int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt = nullptr);

@@ -200,6 +200,7 @@ dc_status dc_rollout(dc_ctx* c, int32_t n_steps, const double* x0, const double*
     const int k = c->prm.checkpoint_every;
     const int n_ck = n_steps / k + 1;
     RET(ensure_checkpoints(c, n_ck));
+    if (k == 1) RET(ensure_records(c, n_steps));
     bool host_io = false;
     d4* X = c->ck;              // checkpoint 0 holds (x0, v0)
     d4* Vv = c->ck + m;
@@ -227,7 +228,7 @@ dc_status dc_rollout(dc_ctx* c, int32_t n_steps, const double* x0, const double*
                     nv = bufv[(s + 1) & 1];
                 }
             }
-            run_step(c, cx, cv, nx, nv, c->scratch);
+            run_step(c, cx, cv, nx, nv, k == 1 ? c->rec_all[s] : c->scratch);
             RET(store_vec(c, nx, traj_x + (size_t)(s + 1) * 3 * m, h2));
             host_io |= h2;
             cx = nx;
@@ -261,7 +262,9 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
     }
     const int N = c->ck_n_steps, k = c->ck_every, m = c->hm.m, B = c->B;
     cudaStream_t s = c->stream;
-    RET(ensure_segment(c, k));
+    // k == 1: every step's state and record were kept by the rollout
+    const bool direct = k == 1;
+    if (!direct) RET(ensure_segment(c, k));
     RET(ensure_adjoint(c));
     bool host_io = false;
     RET(load_vec(c, dL_dx_final, c->gx, host_io));
@@ -282,33 +285,44 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
     CK(cudaMemsetAsync(c->dparam_acc, 0, 4 * sizeof(double) * B, s));
     bool noncv = false;
     dc_status st = DC_OK;
-    int n_seg = (N + k - 1) / k;
+    // direct: one segment over the whole rollout, so that the preparation of every
+    // step overlaps the GMRES of the step after it
+    const int n_seg = direct ? (N > 0 ? 1 : 0) : (N + k - 1) / k;
     for (int seg = n_seg - 1; seg >= 0 && st == DC_OK; --seg) {
-        int s0 = seg * k, s1 = std::min(N, s0 + k);
-        st = recompute_segment(c, seg, s0, s1);
-        if (st) break;
-        // step q's data is prepared on stream2 while the GMRES of step q+1 runs on
-        // the main stream; slot (s0 + q) % 2 alternates between consecutive steps
+        const int s0 = direct ? 0 : seg * k, s1 = direct ? N : std::min(N, s0 + k);
+        if (!direct) {
+            st = recompute_segment(c, seg, s0, s1);
+            if (st) break;
+        }
+        // state x_t / v_t and the record of step t (t -> t+1), t in [s0, s1]
+        auto X = [&](int t) -> const d4* {
+            return direct ? c->ck + (size_t)t * 2 * m : c->segX + (size_t)(t - s0) * m;
+        };
+        auto V = [&](int t) -> const d4* {
+            return direct ? c->ck + (size_t)t * 2 * m + m : c->segV + (size_t)(t - s0) * m;
+        };
+        auto R = [&](int t) -> const StepRec& { return direct ? c->rec_all[t] : c->seg_rec[t - s0]; };
+        // step t's data is prepared on stream2 while the GMRES of step t+1 runs on
+        // the main stream; slot t % 2 alternates between consecutive steps
         CK(cudaEventRecord(c->ev_seg, s));
         CK(cudaStreamWaitEvent(c->stream2, c->ev_seg, 0));
         {
-            const int q = s1 - s0 - 1, k2 = (s0 + q) % 2;
+            const int t = s1 - 1, k2 = t % 2;
             CK(cudaStreamWaitEvent(c->stream2, c->ev_free[k2], 0));
-            prepare_step(c, q, k2, c->stream2);
+            prepare_step(c, R(t), X(t + 1), V(t + 1), k2, c->stream2);
             CK(cudaEventRecord(c->ev_fact[k2], c->stream2));
         }
-        for (int q = s1 - s0 - 1; q >= 0; --q) {
-            const int k2 = (s0 + q) % 2;
-            if (q > 0) {
-                const int kn = (s0 + q - 1) % 2;
+        for (int t = s1 - 1; t >= s0; --t) {
+            const int k2 = t % 2;
+            if (t > s0) {
+                const int kn = (t - 1) % 2;
                 CK(cudaStreamWaitEvent(c->stream2, c->ev_free[kn], 0));
-                prepare_step(c, q - 1, kn, c->stream2);
+                prepare_step(c, R(t - 1), X(t), V(t), kn, c->stream2);
                 CK(cudaEventRecord(c->ev_fact[kn], c->stream2));
             }
             CK(cudaStreamWaitEvent(s, c->ev_fact[k2], 0));
-            if (traj) adj_add_ext(c->gx, traj + (size_t)(s0 + q + 1) * 3 * m, c->d_int2ext, m, s);
-            st = adjoint_step(c, c->segX + (size_t)q * m, c->segX + (size_t)(q + 1) * m,
-                              c->segV + (size_t)(q + 1) * m, k2, noncv);
+            if (traj) adj_add_ext(c->gx, traj + (size_t)(t + 1) * 3 * m, c->d_int2ext, m, s);
+            st = adjoint_step(c, X(t), X(t + 1), V(t + 1), k2, noncv);
             if (st) break;
         }
     }
@@ -435,6 +449,7 @@ void dc_destroy(dc_ctx* c) {
         if (g->exec) cudaGraphExecDestroy(g->exec);
     free_pool(c, c->adj_allocs);
     free_pool(c, c->seg_allocs);
+    free_pool(c, c->rec_allocs);
     free_pool(c, c->ck_allocs);
     free_pool(c, c->work_allocs);
     free_pool(c, c->factor_allocs);

@@ -69,6 +69,7 @@ struct dc_ctx {
     HostFronts fr;
     FrontDev fdv{};
     int nlev = 0;
+    std::vector<int> lvl_maxf;     // largest front of every level
     int* d_int2ext = nullptr;
     // forward work
     d4 *xa = nullptr, *va = nullptr, *xb = nullptr, *vb = nullptr, *v = nullptr, *b = nullptr, *y = nullptr;
@@ -81,6 +82,11 @@ struct dc_ctx {
     // rollout checkpoints
     int ck_n_steps = -1, ck_every = 1, ck_cap = 0;
     d4* ck = nullptr;              // [(cap)][2][m]
+    // with checkpoint_every == 1 the rollout keeps every step's contact record, and
+    // the backward reads states and records directly (no recomputation)
+    std::vector<StepRec> rec_all;
+    Pool rec_allocs;
+    int rec_cap = 0;
     // backward segment buffers
     int seg_cap = 0;
     d4* segX = nullptr;            // [(cap+1)][m]
@@ -230,6 +236,8 @@ dc_status ensure_segment(dc_ctx* c, int k);
 dc_status ensure_adjoint(dc_ctx* c);
 // Recomputes steps [s0, s1) from the checkpoint into the segment buffers.
 dc_status recompute_segment(dc_ctx* c, int seg, int s0, int s1);
-void prepare_step(dc_ctx* c, int q, int k, cudaStream_t s);
+dc_status ensure_records(dc_ctx* c, int n_steps);
+// Per-step adjoint data of the step with record r, ending at (x1, v1), into slot k.
+void prepare_step(dc_ctx* c, const StepRec& r, const d4* x1, const d4* v1, int k, cudaStream_t s);
 dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv);
 dc_status autotune(dc_ctx* c);

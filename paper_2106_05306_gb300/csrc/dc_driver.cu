@@ -186,7 +186,7 @@ dc_status rollout_steps(dc_ctx* c, int n_steps, int k) {
                     nv = bufv[(s + 1) & 1];
                 }
             }
-            run_step(c, cx, cv, nx, nv, c->scratch);
+            run_step(c, cx, cv, nx, nv, k == 1 ? c->rec_all[s] : c->scratch);
             cx = nx;
             cv = nv;
         }
@@ -201,6 +201,16 @@ dc_status ensure_checkpoints(dc_ctx* c, int n_ck) {
     free_pool(c, c->ck_allocs);
     RET(dalloc(c, c->ck_allocs, &c->ck, (size_t)n_ck * 2 * c->hm.m));
     c->ck_cap = n_ck;
+    c->graph_epoch++;
+    return DC_OK;
+}
+
+dc_status ensure_records(dc_ctx* c, int n_steps) {
+    if (n_steps <= c->rec_cap) return DC_OK;
+    free_pool(c, c->rec_allocs);
+    c->rec_all.assign(n_steps, StepRec{});
+    for (int i = 0; i < n_steps; ++i) RET(alloc_rec(c, c->rec_allocs, c->rec_all[i]));
+    c->rec_cap = n_steps;
     c->graph_epoch++;
     return DC_OK;
 }
@@ -296,12 +306,12 @@ namespace {
 inline d4* vcol(double* base, int j, int m) { return reinterpret_cast<d4*>(base + (size_t)j * 4 * m); }
 
 // Preconditioner K(w) -> out.
-void precond(dc_ctx* c, const d4* w, d4* out) {
+void precond(dc_ctx* c, const AdjDev& ad, const d4* w, d4* out) {
     cudaStream_t s = c->stream;
     const DevMesh& dm = c->dm;
-    const AdjDev& ad = c->ad;
     if (c->prm.adj_precond == 0) {
-        frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, dm.m_free, w, out, s, &c->kt);
+        frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->lvl_maxf.data(), dm.m_free, w, out, s,
+                        &c->kt);
         return;
     }
     // node-block inverse, projected P^-1, node-block inverse
@@ -410,21 +420,26 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
         adj_bscale(c->sg, rr, c->dscale, c->V, s);
         c->kt.end(DC_KT_KRYLOV);
         int jmax = 0;
+        // inside the Arnoldi loop the instances whose scale is 0 (finished) are
+        // skipped by every kernel
+        AdjDev adm = c->ad;
+        const double* mask = c->dscale;
+        adm.mask = mask;
         for (int j = 0; j < mr; ++j) {
             d4* vj = vcol(c->V, j, m);
             d4* zj = vcol(c->Zb, j, m);
-            precond(c, vj, zj);
+            precond(c, adm, vj, zj);
             c->kt.begin(DC_KT_APPLYH);
-            adj_apply_H(c->dm, c->ad, 0, zj, nullptr, c->wv, s);
+            adj_apply_H(c->dm, adm, 0, zj, nullptr, c->wv, s);
             c->kt.end(DC_KT_APPLYH);
             double* w = reinterpret_cast<double*>(c->wv);
             // classical Gram-Schmidt, twice
             c->kt.begin(DC_KT_KRYLOV);
-            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef, s);
-            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef, w, -1.0, s);
-            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef2, s);
-            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef2, w, -1.0, s);
-            adj_bdot(c->sg, w, 0, 1, w, c->partial, c->dnorm, s);
+            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef, s, mask);
+            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef, w, -1.0, s, mask);
+            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef2, s, mask);
+            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef2, w, -1.0, s, mask);
+            adj_bdot(c->sg, w, 0, 1, w, c->partial, c->dnorm, s, mask);
             c->kt.end(DC_KT_KRYLOV);
             double* h1 = c->hpin;
             double* h2 = c->hpin + (size_t)(mr + 1) * B;
@@ -531,22 +546,22 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
 // Per-step adjoint data of step q into slot k: the element linearisation, node
 // types and (with the multifrontal preconditioner) the factorised fronts.  Runs on
 // stream2 so that it overlaps the GMRES of the step after q.
-void prepare_step(dc_ctx* c, int q, int k, cudaStream_t s) {
+void prepare_step(dc_ctx* c, const StepRec& r, const d4* x1, const d4* v1, int k, cudaStream_t s) {
     AdjDev& ad = c->ads[k];
-    const StepRec& r = c->seg_rec[q];
-    const int m = c->hm.m;
     ad.h = c->prm.h;
     ad.mu = c->dp.node_mu;
+    ad.node_inst = c->dp.node_inst;
+    ad.mask = nullptr;
     ad.contact = r.contact;
     ad.case_ = r.case_;
     ad.nb = r.nb;
     ad.f = r.f;
     KTimer* kt = s == c->stream ? &c->kt : &c->kt2;
     kt->begin(DC_KT_ASSEMBLE);
-    adj_setup(c->dm, ad, c->segX + (size_t)(q + 1) * m, c->segV + (size_t)(q + 1) * m, s);
+    adj_setup(c->dm, ad, x1, v1, s);
     kt->end(DC_KT_ASSEMBLE);
     if (c->prm.adj_precond == 0) {
-        frontal_factorize(c->dm, ad, c->fds[k], c->fr.lvl_ptr.data(), c->nlev, c->fr.max_f, s,
+        frontal_factorize(c->dm, ad, c->fds[k], c->fr.lvl_ptr.data(), c->nlev, c->lvl_maxf.data(), s,
                           s == c->stream ? &c->kt : &c->kt2);
         c->n_factorisations++;
     }
@@ -603,6 +618,8 @@ dc_status autotune(dc_ctx* c) {
     AdjDev ad = c->ads[0];
     ad.h = c->prm.h;
     ad.mu = c->dp.node_mu;
+    ad.node_inst = c->dp.node_inst;
+    ad.mask = nullptr;
     ad.contact = c->scratch.contact;
     ad.case_ = c->scratch.case_;
     ad.nb = c->scratch.nb;

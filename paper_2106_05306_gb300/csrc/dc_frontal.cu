@@ -145,17 +145,17 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
 // below the block against that inverse; the trailing matrix is updated with
 // TM x TM register tiles whose operands come from a transposed, zero-padded
 // copy of the panel (128-bit shared-memory loads).
-__global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin) {
+__global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin, int mf) {
     extern __shared__ __align__(16) float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     float* F = fd.pool + fd.off[s];
     const int f = fd.f[s], p = fd.p[s];
-    const int ldt = (fd.max_f + 7) / 8 * 8;          // row stride of the transposed panel
+    const int ldt = (mf + 7) / 8 * 8;                // row stride of the transposed panel
     float* Ls = sm;                                  // [f][LDS] panel, row-major
-    float* Xs = sm + (long)fd.max_f * LDS;           // [PB][LDS] diagonal-block inverse
+    float* Xs = sm + (long)mf * LDS;                 // [PB][LDS] diagonal-block inverse
     float* Dd = Xs + PB * LDS;                       // [PB] pivots of the panel
-    float* Lt = sm + ((long)fd.max_f * LDS + PB * LDS + PB + 3) / 4 * 4;   // [PB][ldt], 16-byte aligned
+    float* Lt = sm + ((long)mf * LDS + PB * LDS + PB + 3) / 4 * 4;   // [PB][ldt], 16-byte aligned
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
         const int c = fd.child[q];
         const float* Fc = fd.pool + fd.off[c];
@@ -388,9 +388,10 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin)
 // Forward substitution L y = r over one level (CTA per front), then z = D^-1 y.
 // y_s = L_ss^-1 w_s with the stored explicit inverse; the rows below accumulate
 // -L_Us y_s into the front's update vector, which the parent adds in.
-__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
+__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin, const double* __restrict__ mask) {
     extern __shared__ float w[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    if (mask && mask[fd.sn_inst[s]] == 0.0) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
     const float* X = fd.linv + fd.linv_off[s];
@@ -428,9 +429,10 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin) {
 
 // Backward substitution L^T x = z over one level (CTA per front), top-down:
 // x_s = L_ss^-T (z_s - L_Us^T x_U).
-__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
+__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin, const double* __restrict__ mask) {
     extern __shared__ float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    if (mask && mask[fd.sn_inst[s]] == 0.0) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
     const float* X = fd.linv + fd.linv_off[s];
@@ -461,9 +463,10 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin) {
 
 // r = Pi_B w in single precision (DOF order 3*node + c).
 __global__ void k_pre_in(int n, const int* __restrict__ type, const d4* __restrict__ nb, const d4* __restrict__ w,
-                         float* __restrict__ r) {
+                         float* __restrict__ r, const int* __restrict__ node_inst, const double* __restrict__ mask) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if (mask && mask[node_inst[j]] == 0.0) return;
     d4 a = ld(w + j);
     double v[3] = {a.x, a.y, a.z};
     int ty = type[j];
@@ -481,9 +484,11 @@ __global__ void k_pre_in(int n, const int* __restrict__ type, const d4* __restri
 
 // out = S_C x in double precision: stick -> 0, slip -> x - n ((n - mu t).x).
 __global__ void k_pre_out(int n, const double* __restrict__ mu, const int* __restrict__ type, const d4* __restrict__ nb,
-                          const d4* __restrict__ slip, const float* __restrict__ x, d4* __restrict__ out) {
+                          const d4* __restrict__ slip, const float* __restrict__ x, d4* __restrict__ out,
+                          const int* __restrict__ node_inst, const double* __restrict__ mask) {
     int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
+    if (mask && mask[node_inst[j]] == 0.0) return;
     double v[3] = {(double)x[3 * j], (double)x[3 * j + 1], (double)x[3 * j + 2]};
     int ty = type[j];
     if (ty == 1) {
@@ -527,8 +532,13 @@ cudaError_t frontal_configure(int max_f) {
     return e;
 }
 
+// Threads per CTA for a level whose largest front has mf unknowns: small fronts
+// get small CTAs (and, with the level's own shared-memory size, many CTAs per SM).
+static int factor_threads(int mf) { return mf <= 96 ? 128 : (mf <= 192 ? 256 : FT2); }
+static int solve_threads(int mf) { return mf <= 128 ? 128 : (mf <= 256 ? 256 : (mf <= 512 ? 512 : FT)); }
+
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
-                       int max_f, cudaStream_t s, KTimer* kt) {
+                       const int* lvl_maxf, cudaStream_t s, KTimer* kt) {
     if (kt) kt->begin(DC_KT_ASSEMBLE);
     cudaMemsetAsync(fd.pool, 0, sizeof(float) * fd.pool_size, s);
     dc_note_launch();
@@ -537,36 +547,40 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
     for (int l = 0; l < nlev; ++l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
         if (cnt > 0) {
+            const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_FRONT);
-            k_front_level<<<cnt, FT2, frontal_factor_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            k_front_level<<<cnt, factor_threads(mf), frontal_factor_smem(mf), s>>>(fd, lvl_ptr[l], mf);
             if (kt) kt->end(DC_KT_FRONT);
         }
     }
 }
 
-void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, int max_f, int n_free,
-                     const d4* w, d4* out, cudaStream_t s, KTimer* kt) {
+void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, const int* lvl_maxf,
+                     int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt) {
     dc_note_launch();
-    k_pre_in<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.type, ad.nb, w, fd.rvec);
+    k_pre_in<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.type, ad.nb, w, fd.rvec, ad.node_inst, ad.mask);
     for (int l = 0; l < nlev; ++l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
         if (cnt > 0) {
+            const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_MSOLVE);
-            k_msolve_fwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            k_msolve_fwd<<<cnt, solve_threads(mf), frontal_solve_smem(mf), s>>>(fd, lvl_ptr[l], ad.mask);
             if (kt) kt->end(DC_KT_MSOLVE);
         }
     }
     for (int l = nlev - 1; l >= 0; --l) {
         int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
         if (cnt > 0) {
+            const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_MSOLVE);
-            k_msolve_bwd<<<cnt, FT, frontal_solve_smem(max_f), s>>>(fd, lvl_ptr[l]);
+            k_msolve_bwd<<<cnt, solve_threads(mf), frontal_solve_smem(mf), s>>>(fd, lvl_ptr[l], ad.mask);
             if (kt) kt->end(DC_KT_MSOLVE);
         }
     }
     dc_note_launch();
-    k_pre_out<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.mu, ad.type, ad.nb, ad.slip, fd.xvec, out);
+    k_pre_out<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.mu, ad.type, ad.nb, ad.slip, fd.xvec, out,
+                                                  ad.node_inst, ad.mask);
 }

@@ -194,6 +194,7 @@ void launch_count_cases(const int* contact, const int* case_, int m_free,
 struct FrontDev {
     int S, NP, max_f;
     const float* tau;                  // [S] pivots below tau[s] are replaced by +-tau[s]
+    const int* sn_inst;                // [S] instance of each front
     long long pool_size;
     const int* begin;
     const int* f;

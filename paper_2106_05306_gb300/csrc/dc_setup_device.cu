@@ -381,6 +381,12 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     double* d_pcoef;
     float* d_tau;
     const size_t n3 = 3 * (size_t)std::max(MF, 1);
+    std::vector<int> sn_inst(frm.S, 0);
+    for (int i = 0; i < c->B; ++i) {
+        const int end = i + 1 < c->B ? c->inst[i + 1].so : frm.S;
+        for (int q = c->inst[i].so; q < end; ++q) sn_inst[q] = i;
+    }
+    int* d_sninst;
     if ((s = upload(c, F, &d_begin, frm.begin)) || (s = upload(c, F, &d_f, frm.f)) || (s = upload(c, F, &d_p, frm.p)) ||
         (s = upload(c, F, &d_off, frm.off)) || (s = upload(c, F, &d_acc_off, frm.acc_off)) ||
         (s = upload(c, F, &d_binv_off, frm.binv_off)) || (s = dalloc(c, F, &fd.binv, (size_t)frm.binv_size)) ||
@@ -392,6 +398,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         (s = upload(c, F, &d_pdst, frm.pr_dst)) || (s = upload(c, F, &d_pld, frm.pr_ld)) ||
         (s = upload(c, F, &d_pcp, frm.pr_cptr)) || (s = upload(c, F, &d_pcode, frm.pr_code)) ||
         (s = upload(c, F, &d_pcoef, frm.pr_coef)) || (s = upload(c, F, &d_tau, pp.tau)) ||
+        (s = upload(c, F, &d_sninst, sn_inst)) ||
         (s = dalloc(c, F, &fd.pool, (size_t)frm.pool_size)) || (s = dalloc(c, F, &fd.acc, (size_t)frm.acc_size)) ||
         (s = dalloc(c, F, &fd.rvec, n3)) || (s = dalloc(c, F, &fd.zvec, n3)) || (s = dalloc(c, F, &fd.xvec, n3)))
         return s;
@@ -416,6 +423,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     fd.pr_code = d_pcode;
     fd.pr_coef = d_pcoef;
     fd.tau = d_tau;
+    fd.sn_inst = d_sninst;
     c->fdv = fd;
     c->fds[0] = fd;
     c->fds[1] = fd;   // second slot: its own numeric storage, shared structure
@@ -424,6 +432,10 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         (s = dalloc(c, F, &c->fds[1].linv, (size_t)frm.linv_size)))
         return s;
     c->nlev = (int)frm.lvl_ptr.size() - 1;
+    c->lvl_maxf.assign(std::max(c->nlev, 0), 0);
+    for (int l = 0; l < c->nlev; ++l)
+        for (int q = frm.lvl_ptr[l]; q < frm.lvl_ptr[l + 1]; ++q)
+            c->lvl_maxf[l] = std::max(c->lvl_maxf[l], frm.f[frm.lvl_sn[q]]);
     c->front_flops = pp.front_flops;
     c->factor_nnz = pp.factor_nnz;
     c->fwd_nnz = (long long)hfm.fval.size();
@@ -473,7 +485,7 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     add(vbytes(r.binv_off)); add(vbytes(r.linv_off)); add(vbytes(r.uptr)); add(vbytes(r.unode)); add(vbytes(r.cptr));
     add(vbytes(r.child)); add(vbytes(r.cmap)); add(vbytes(r.lvl_sn)); add(vbytes(r.pr_i)); add(vbytes(r.pr_j));
     add(vbytes(r.pr_dst)); add(vbytes(r.pr_ld)); add(vbytes(r.pr_cptr)); add(vbytes(r.pr_code));
-    add(vbytes(r.pr_coef)); add(vbytes(pp.tau));
+    add(vbytes(r.pr_coef)); add(vbytes(pp.tau)); add(vbytes(pp.tau));
     for (int s = 0; s < 2; ++s) {
         add(4 * (size_t)r.pool_size);
         add(4 * (size_t)r.binv_size);
@@ -482,6 +494,8 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     add(4 * (size_t)r.acc_size); add(12 * MF); add(12 * MF); add(12 * MF);
     // checkpoints, segment recomputation, adjoint
     add(((size_t)n_steps / k + 1) * 2 * m * d4b);
+    if (k == 1)
+        for (int i = 0; i < n_steps; ++i) { add(MF * 4); add(MF * 4); add(MF * d4b); add(MF * d4b); }
     add((k + 1) * m * d4b); add((k + 1) * m * d4b);
     for (size_t i = 0; i < k; ++i) { add(MF * 4); add(MF * 4); add(MF * d4b); add(MF * d4b); }
     add(T * d4b); add(T * d4b); add(m * d4b);

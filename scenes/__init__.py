@@ -210,3 +210,26 @@ def small_scene(n: int = 4, seed: int = 0, contact: str = "sphere", pinned: bool
         prm.mu = float(rng.uniform(0.8, 1.5))
     return Scene(f"small_{n}_{contact}", n, pos, tris, pins, obst, prm, x0, v0, n_steps,
                  loss_weights(n * n, seed))
+
+
+def serve_request(seed: int, dof_lo: float = 1e3, dof_hi: float = 3e4, steps_lo: int = 25,
+                  steps_hi: int = 150) -> Scene:
+    """One request of the served workload: a square cloth of log-uniform DOF count
+    (3 n^2 in [dof_lo, dof_hi]), a uniform step count, random material and friction,
+    dropped onto a random sphere and the ground."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5E4E]))
+    dof = _log_uniform(rng, dof_lo, dof_hi)
+    n = max(4, int(round(np.sqrt(dof / 3.0))))
+    n_steps = int(rng.integers(steps_lo, steps_hi + 1))
+    mu = float(rng.uniform(0.1, 0.6))
+    ks = _log_uniform(rng, 1e2, 1e4)
+    kb = _log_uniform(rng, 1e-4, 1e-2)
+    r = float(rng.uniform(0.2, 0.5))
+    cy = r + float(rng.uniform(0.0, 0.2))
+    cx, cz = float(rng.uniform(-0.2, 0.2)), float(rng.uniform(0.3, 0.7))
+    pos, tris = grid_mesh(n, side=1.0, height=cy + r + 0.1)
+    obst = [Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.0),
+            Obstacle("sphere", center=(cx, cy, cz), radius=r)]
+    prm = Params(k_stretch=ks, k_bend=kb, density=0.1, mu=mu, h=1.0 / 120.0)
+    return Scene(f"request_{seed}_{n}_{n_steps}", n, pos, tris, np.zeros(0, np.int32), obst, prm,
+                 pos.copy(), np.zeros_like(pos), n_steps, loss_weights(n * n, seed))
