@@ -386,9 +386,10 @@ constexpr int DOT_THREADS = 128;
 __global__ void __launch_bounds__(DOT_THREADS) k_bmdot(const double* __restrict__ V, long ldv,
                                                        const double* __restrict__ w, const int4* __restrict__ chunk,
                                                        int nchunk, double* __restrict__ partial,
-                                                       const double* __restrict__ mask) {
+                                                       const double* __restrict__ mask,
+                                                       const int* __restrict__ clist) {
     __shared__ double sh[DOT_THREADS / 32];
-    const int c = blockIdx.x, j = blockIdx.y;
+    const int c = clist ? clist[blockIdx.x] : blockIdx.x, j = blockIdx.y;
     const int4 ch = chunk[c];
     if (mask && mask[ch.x] == 0.0) {
         if (threadIdx.x == 0) partial[(long)j * nchunk + c] = 0.0;
@@ -422,8 +423,8 @@ __global__ void k_breduce(const double* __restrict__ partial, int nchunk, const 
 // w += sign * sum_j V_j coef[j * B + inst]   (one block per chunk)
 __global__ void k_bvupdate(const double* __restrict__ V, long ldv, int nvec, const double* __restrict__ coef, int B,
                            const int4* __restrict__ chunk, double* __restrict__ w, double sign,
-                           const double* __restrict__ mask) {
-    const int4 ch = chunk[blockIdx.x];
+                           const double* __restrict__ mask, const int* __restrict__ clist) {
+    const int4 ch = chunk[clist ? clist[blockIdx.x] : blockIdx.x];
     if (mask && mask[ch.x] == 0.0) return;
     for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) {
         double s = 0.0;
@@ -434,8 +435,8 @@ __global__ void k_bvupdate(const double* __restrict__ V, long ldv, int nvec, con
 
 // out = a * sc[inst]   (one block per chunk)
 __global__ void k_bscale(const double* __restrict__ a, const double* __restrict__ sc,
-                         const int4* __restrict__ chunk, double* __restrict__ out) {
-    const int4 ch = chunk[blockIdx.x];
+                         const int4* __restrict__ chunk, double* __restrict__ out, const int* __restrict__ clist) {
+    const int4 ch = chunk[clist ? clist[blockIdx.x] : blockIdx.x];
     const double f = sc[ch.x];
     for (int i = ch.y + threadIdx.x; i < ch.z; i += blockDim.x) out[i] = f == 0.0 ? 0.0 : a[i] * f;
 }
@@ -694,20 +695,25 @@ void adj_solve_project(const DevMesh& dm, const AdjDev& ad, const d4* r, d4* ytm
     k_adj_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, ad, ytmp, base, out);
 }
 void adj_bdot(const Segs& sg, const double* V, long ldv, int nvec, const double* w, double* partial, double* out,
-              cudaStream_t s, const double* mask) {
+              cudaStream_t s, const double* mask, const int* clist, int ncl) {
+    if (clist && ncl == 0) return;
     dc_note_launch();
-    k_bmdot<<<dim3(sg.nchunk, nvec), DOT_THREADS, 0, s>>>(V, ldv, w, sg.chunk, sg.nchunk, partial, mask);
+    k_bmdot<<<dim3(clist ? ncl : sg.nchunk, nvec), DOT_THREADS, 0, s>>>(V, ldv, w, sg.chunk, sg.nchunk, partial, mask,
+                                                                        clist);
     dc_note_launch();
     k_breduce<<<nblk((long)sg.B * nvec, 128), 128, 0, s>>>(partial, sg.nchunk, sg.cptr, sg.B, nvec, out);
 }
 void adj_bvupdate(const Segs& sg, const double* V, long ldv, int nvec, const double* coef, double* w, double sign,
-                  cudaStream_t s, const double* mask) {
+                  cudaStream_t s, const double* mask, const int* clist, int ncl) {
+    if (clist && ncl == 0) return;
     dc_note_launch();
-    k_bvupdate<<<sg.nchunk, 128, 0, s>>>(V, ldv, nvec, coef, sg.B, sg.chunk, w, sign, mask);
+    k_bvupdate<<<clist ? ncl : sg.nchunk, 128, 0, s>>>(V, ldv, nvec, coef, sg.B, sg.chunk, w, sign, mask, clist);
 }
-void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s) {
+void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s, const int* clist,
+                int ncl) {
+    if (clist && ncl == 0) return;
     dc_note_launch();
-    k_bscale<<<sg.nchunk, 128, 0, s>>>(a, sc, sg.chunk, out);
+    k_bscale<<<clist ? ncl : sg.nchunk, 128, 0, s>>>(a, sc, sg.chunk, out, clist);
 }
 void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
                  const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,

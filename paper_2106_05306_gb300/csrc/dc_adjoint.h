@@ -41,13 +41,16 @@ struct Segs {
     const int* pcptr = nullptr;      // [3 B + 1] chunks of (instance i, kind q) at 3 i + q
 };
 // out[j * B + i] = V_j . w over instance i's free nodes, j < nvec
+// clist (optional): device list of the ncl chunks to process (others keep stale
+// partial sums / values that callers must not use).
 void adj_bdot(const Segs& sg, const double* V, long ldv, int nvec, const double* w, double* partial, double* out,
-              cudaStream_t s, const double* mask = nullptr);
+              cudaStream_t s, const double* mask = nullptr, const int* clist = nullptr, int ncl = 0);
 // w += sign * sum_j V_j coef[j * B + i] on instance i's free nodes
 void adj_bvupdate(const Segs& sg, const double* V, long ldv, int nvec, const double* coef, double* w, double sign,
-                  cudaStream_t s, const double* mask = nullptr);
+                  cudaStream_t s, const double* mask = nullptr, const int* clist = nullptr, int ncl = 0);
 // out = a * sc[i] on instance i's free nodes (exactly 0 where sc[i] == 0)
-void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s);
+void adj_bscale(const Segs& sg, const double* a, const double* sc, double* out, cudaStream_t s,
+                const int* clist = nullptr, int ncl = 0);
 void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const d4* z, const d4* E,
                  const d4* resid, const d4* x_n, const d4* v1, const d4* gx, d4* gx_out, d4* gv_out,
                  cudaStream_t s);
@@ -64,5 +67,9 @@ cudaError_t frontal_configure(int max_f);
 // lvl_ptr[l+1]) and the largest has lvl_maxf[l] unknowns.
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
                        const int* lvl_maxf, cudaStream_t s, KTimer* kt = nullptr);
+// act_sn / act_ptr (optional): device list of the fronts to solve, level l at
+// act_sn[act_ptr[l] .. act_ptr[l+1]) (act_ptr on the host); fronts of masked
+// instances may be listed (they exit at once), active ones must be.
 void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, const int* lvl_maxf,
-                     int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt = nullptr);
+                     int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt = nullptr,
+                     const int* act_sn = nullptr, const int* act_ptr = nullptr);

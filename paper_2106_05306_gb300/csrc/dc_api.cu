@@ -456,6 +456,8 @@ void dc_destroy(dc_ctx* c) {
     free_pool(c, c->front_allocs);
     free_pool(c, c->mesh_allocs);
     if (c->hpin && !c->hpin_external) cudaFreeHost(c->hpin);
+    if (c->h_act_sn) cudaFreeHost(c->h_act_sn);
+    if (c->h_act_ch) cudaFreeHost(c->h_act_ch);
     if (c->async_alloc) cudaStreamSynchronize(c->stream);
     delete c;
 }

@@ -109,6 +109,18 @@ struct dc_ctx {
     size_t hpin_cap = 0;           // doubles
     bool hpin_external = false;    // hpin belongs to the caller (a server slot)
     std::vector<GState> gs;
+    // fronts and reduction chunks of the instances still iterating (batches):
+    // level l's fronts are act_sn[act_ptr[l] .. act_ptr[l+1]); rebuilt when the
+    // active set has shrunk by a quarter (the mask keeps results exact between)
+    std::vector<int> lvl_inst_ptr;  // [nlev][B + 1]: instance i's fronts in level l start at this lvl_sn index
+    int* d_act_sn = nullptr;
+    int* h_act_sn = nullptr;        // pinned
+    int* d_act_ch = nullptr;
+    int* h_act_ch = nullptr;        // pinned
+    int n_act_ch = 0;
+    std::vector<int> act_ptr;
+    bool act_on = false;
+    int act_built = 0;
     // CUDA graphs
     bool use_graphs = false;
     long long graph_epoch = 0;     // bumped whenever a captured pointer or launch shape may change

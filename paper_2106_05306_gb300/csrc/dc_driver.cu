@@ -288,6 +288,15 @@ dc_status ensure_adjoint(dc_ctx* c) {
     RET(dalloc(c, P, &c->partial, (size_t)(mr + 1) * c->sg.nchunk));
     RET(dalloc(c, P, &c->dparam_acc, 4 * (size_t)B));
     RET(dalloc(c, P, &c->dparam_part, (size_t)c->sg.npchunk));
+    if (B > 1 && c->prm.adj_precond == 0) {
+        RET(dalloc(c, P, &c->d_act_sn, (size_t)std::max(c->fr.S, 1)));
+        RET(dalloc(c, P, &c->d_act_ch, (size_t)std::max(c->sg.nchunk, 1)));
+        if (c->h_act_sn) cudaFreeHost(c->h_act_sn);
+        if (c->h_act_ch) cudaFreeHost(c->h_act_ch);
+        c->h_act_sn = c->h_act_ch = nullptr;
+        CK(cudaMallocHost(&c->h_act_sn, sizeof(int) * (size_t)std::max(c->fr.S, 1)));
+        CK(cudaMallocHost(&c->h_act_ch, sizeof(int) * (size_t)std::max(c->sg.nchunk, 1)));
+    }
     const size_t need = 3 * (size_t)(mr + 1) * B + 4 * (size_t)B + 64;
     if (need > c->hpin_cap) {
         if (c->hpin && !c->hpin_external) cudaFreeHost(c->hpin);
@@ -311,7 +320,7 @@ void precond(dc_ctx* c, const AdjDev& ad, const d4* w, d4* out) {
     const DevMesh& dm = c->dm;
     if (c->prm.adj_precond == 0) {
         frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->lvl_maxf.data(), dm.m_free, w, out, s,
-                        &c->kt);
+                        &c->kt, c->act_on ? c->d_act_sn : nullptr, c->act_ptr.data());
         return;
     }
     // node-block inverse, projected P^-1, node-block inverse
@@ -320,6 +329,34 @@ void precond(dc_ctx* c, const AdjDev& ad, const d4* w, d4* out) {
     adj_solve_project(dm, ad, c->r1, c->ytmp, c->x1, c->x2, s);
     adj_apply_H(dm, ad, 1, c->x2, w, c->r2, s);
     adj_dplus(dm, ad, c->x2, c->r2, out, s);
+}
+
+// Compacted front and chunk lists of the instances with gs[i].act (batches only).
+dc_status build_active_lists(dc_ctx* c) {
+    const int B = c->B, nl = c->nlev;
+    c->act_ptr.assign(nl + 1, 0);
+    int pos = 0, cnt = 0;
+    for (int i = 0; i < B; ++i) cnt += c->gs[i].act;
+    for (int l = 0; l < nl; ++l) {
+        c->act_ptr[l] = pos;
+        const int* P = c->lvl_inst_ptr.data() + (size_t)l * (B + 1);
+        for (int i = 0; i < B; ++i)
+            if (c->gs[i].act)
+                for (int q = P[i]; q < P[i + 1]; ++q) c->h_act_sn[pos++] = c->fr.lvl_sn[q];
+    }
+    c->act_ptr[nl] = pos;
+    if (pos > 0)
+        CK(cudaMemcpyAsync(c->d_act_sn, c->h_act_sn, sizeof(int) * pos, cudaMemcpyHostToDevice, c->stream));
+    int nch = 0;
+    for (int i = 0; i < B; ++i)
+        if (c->gs[i].act)
+            for (int q = c->h_cptr[i]; q < c->h_cptr[i + 1]; ++q) c->h_act_ch[nch++] = q;
+    c->n_act_ch = nch;
+    if (nch > 0)
+        CK(cudaMemcpyAsync(c->d_act_ch, c->h_act_ch, sizeof(int) * nch, cudaMemcpyHostToDevice, c->stream));
+    c->act_on = true;
+    c->act_built = cnt;
+    return DC_OK;
 }
 
 // Per-instance |a|^2-style dot products a . b into out[0 .. B).
@@ -414,10 +451,13 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
             done[i] = 0;
         }
         if (!active) break;
+        if (c->h_act_sn) RET(build_active_lists(c));
         for (int i = 0; i < B; ++i) sc[i] = gs[i].act ? 1.0 / gs[i].res : 0.0;
         RET(upload_scale(c, sc));
+        // chunk list of the active instances (batches), else all chunks
+        const int* cl = c->h_act_sn ? c->d_act_ch : nullptr;
         c->kt.begin(DC_KT_KRYLOV);
-        adj_bscale(c->sg, rr, c->dscale, c->V, s);
+        adj_bscale(c->sg, rr, c->dscale, c->V, s, cl, c->n_act_ch);
         c->kt.end(DC_KT_KRYLOV);
         int jmax = 0;
         // inside the Arnoldi loop the instances whose scale is 0 (finished) are
@@ -435,11 +475,12 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
             double* w = reinterpret_cast<double*>(c->wv);
             // classical Gram-Schmidt, twice
             c->kt.begin(DC_KT_KRYLOV);
-            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef, s, mask);
-            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef, w, -1.0, s, mask);
-            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef2, s, mask);
-            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef2, w, -1.0, s, mask);
-            adj_bdot(c->sg, w, 0, 1, w, c->partial, c->dnorm, s, mask);
+            const int ncl = c->n_act_ch;
+            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef, s, mask, cl, ncl);
+            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef, w, -1.0, s, mask, cl, ncl);
+            adj_bdot(c->sg, c->V, ldv, j + 1, w, c->partial, c->dcoef2, s, mask, cl, ncl);
+            adj_bvupdate(c->sg, c->V, ldv, j + 1, c->dcoef2, w, -1.0, s, mask, cl, ncl);
+            adj_bdot(c->sg, w, 0, 1, w, c->partial, c->dnorm, s, mask, cl, ncl);
             c->kt.end(DC_KT_KRYLOV);
             double* h1 = c->hpin;
             double* h2 = c->hpin + (size_t)(mr + 1) * B;
@@ -490,9 +531,14 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
             jmax = j + 1;
             c->adj_batch_iters++;
             if (!still) break;
+            if (c->h_act_sn) {
+                int cnt = 0;
+                for (int i = 0; i < B; ++i) cnt += gs[i].act;
+                if (4 * cnt <= 3 * c->act_built) RET(build_active_lists(c));
+            }
             RET(upload_scale(c, sc));
             c->kt.begin(DC_KT_KRYLOV);
-            adj_bscale(c->sg, w, c->dscale, reinterpret_cast<double*>(vcol(c->V, j + 1, m)), s);
+            adj_bscale(c->sg, w, c->dscale, reinterpret_cast<double*>(vcol(c->V, j + 1, m)), s, cl, c->n_act_ch);
             c->kt.end(DC_KT_KRYLOV);
         }
         // z += sum_j Zb_j y_j per instance (columns past an instance's own count are 0)
@@ -533,6 +579,7 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
         }
         for (int i = 0; i < B; ++i) gs[i].used = 0;
     }
+    c->act_on = false;
     for (int i = 0; i < B; ++i) {
         iters[i] = gs[i].total;
         rel[i] = gs[i].beta0 > 0.0 ? gs[i].res / gs[i].beta0 : 0.0;

@@ -385,12 +385,51 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
     }
 }
 
-// Forward substitution L y = r over one level (CTA per front), then z = D^-1 y.
-// y_s = L_ss^-1 w_s with the stored explicit inverse; the rows below accumulate
-// -L_Us y_s into the front's update vector, which the parent adds in.
-__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin, const double* __restrict__ mask) {
+// Column-major matrix-vector product on one CTA: t_i = sum_k A[k * lda + i] v_k for
+// rows i < nrows and k < K (k <= i when tri).  The k range is cut into G
+// contiguous chunks, one per thread group (consecutive threads of a group take
+// consecutive rows: coalesced), and the G partial sums of a row are added in
+// group order, so the result does not depend on timing.  fin(i, t_i) stores.
+template <class Fin>
+__device__ __forceinline__ void cm_gemv(const float* __restrict__ A, long lda, int nrows, int K, bool tri,
+                                        const float* __restrict__ v, float* __restrict__ red, Fin fin) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    // rows per pass: at least 4 groups share the k range when the CTA is large enough
+    const int R = min((nrows + 31) & ~31, max(32, nt / 4));
+    const int G = nt / R;
+    const int C = (K + G - 1) / G;
+    const int r = tid % R, g = tid / R;
+    for (int i0 = 0; i0 < nrows; i0 += R) {
+        const int i = i0 + r;
+        if (g < G) {
+            float acc = 0.0f;
+            if (i < nrows) {
+                const int k0 = g * C;
+                int k1 = min(K, k0 + C);
+                if (tri) k1 = min(k1, i + 1);
+                const float* a = A + i;
+#pragma unroll 4
+                for (int k = k0; k < k1; ++k) acc += a[(long)k * lda] * v[k];
+            }
+            red[g * R + r] = acc;
+        }
+        __syncthreads();
+        if (tid < R && i0 + tid < nrows) {
+            float t = 0.0f;
+            for (int q = 0; q < G; ++q) t += red[q * R + tid];
+            fin(i0 + tid, t);
+        }
+        __syncthreads();
+    }
+}
+
+// Forward substitution L y = r over one level (CTA per front of sn_list), then
+// z = D^-1 y.  y_s = L_ss^-1 w_s with the stored explicit inverse; the rows below
+// accumulate -L_Us y_s into the front's update vector, which the parent adds in.
+__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __restrict__ sn_list,
+                                                    const double* __restrict__ mask) {
     extern __shared__ float w[];
-    const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    const int s = sn_list[blockIdx.x];
     if (mask && mask[fd.sn_inst[s]] == 0.0) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
@@ -398,6 +437,7 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin, c
     const int f = fd.f[s], p = fd.p[s];
     const int base = 3 * fd.begin[s];
     float* y = w + f;
+    float* red = y + f;                // [nt] partial sums
     for (int t = tid; t < f; t += nt) w[t] = 0.0f;
     __syncthreads();
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
@@ -410,28 +450,19 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, int lvl_begin, c
     }
     for (int t = tid; t < p; t += nt) w[t] += fd.rvec[base + t];
     __syncthreads();
-    for (int i = tid; i < p; i += nt) {
-        float sum = 0.0f;
-#pragma unroll 8
-        for (int k = 0; k <= i; ++k) sum += X[(long)k * p + i] * w[k];
-        y[i] = sum;
-    }
-    __syncthreads();
+    cm_gemv(X, p, p, p, true, w, red, [&](int i, float t) { y[i] = t; });
     float* acc = fd.acc + fd.acc_off[s];
-    for (int i = p + tid; i < f; i += nt) {
-        float sum = 0.0f;
-#pragma unroll 8
-        for (int k = 0; k < p; ++k) sum += F[(long)k * f + i] * y[k];
-        acc[i - p] = w[i] - sum;
-    }
+    cm_gemv(F + p, f, f - p, p, false, y, red, [&](int i, float t) { acc[i] = w[p + i] - t; });
     for (int t = tid; t < p; t += nt) fd.zvec[base + t] = y[t] / F[(long)t * f + t];
 }
 
 // Backward substitution L^T x = z over one level (CTA per front), top-down:
-// x_s = L_ss^-T (z_s - L_Us^T x_U).
-__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin, const double* __restrict__ mask) {
+// x_s = L_ss^-T (z_s - L_Us^T x_U).  One warp per row (lanes along the row),
+// two rows per warp at a time.
+__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, const int* __restrict__ sn_list,
+                                                    const double* __restrict__ mask) {
     extern __shared__ float sm[];
-    const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
+    const int s = sn_list[blockIdx.x];
     if (mask && mask[fd.sn_inst[s]] == 0.0) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
@@ -445,19 +476,44 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, int lvl_begin, c
     for (int k = tid; k < nu; k += nt) xu[k] = fd.xvec[3 * un[k / 3] + k % 3];
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    for (int t = warp; t < p; t += nw) {
-        float sum = 0.0f;
-        for (int k = lane; k < nu; k += 32) sum += F[(long)t * f + p + k] * xu[k];
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) w[t] -= sum;
+    for (int t = warp; t < p; t += 2 * nw) {
+        const int t2 = t + nw;
+        const bool two = t2 < p;
+        const float* r1 = F + (long)t * f + p;
+        const float* r2 = F + (long)(two ? t2 : t) * f + p;
+        float s1 = 0.0f, s2 = 0.0f;
+        for (int k = lane; k < nu; k += 32) {
+            const float x = xu[k];
+            s1 += r1[k] * x;
+            s2 += r2[k] * x;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            w[t] -= s1;
+            if (two) w[t2] -= s2;
+        }
     }
     __syncthreads();
-    for (int i = warp; i < p; i += nw) {
-        float sum = 0.0f;
-        const float* xc = X + (long)i * p;   // column i of L_ss^-1 = row i of L_ss^-T
-        for (int k = i + lane; k < p; k += 32) sum += xc[k] * w[k];
-        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-        if (lane == 0) fd.xvec[base + i] = sum;
+    for (int i = warp; i < p; i += 2 * nw) {
+        const int i2 = i + nw;
+        const bool two = i2 < p;
+        const float* c1 = X + (long)i * p;   // column i of L_ss^-1 = row i of L_ss^-T
+        const float* c2 = X + (long)(two ? i2 : i) * p;
+        float s1 = 0.0f, s2 = 0.0f;
+        for (int k = i + lane; k < p; k += 32) s1 += c1[k] * w[k];
+        if (two)
+            for (int k = i2 + lane; k < p; k += 32) s2 += c2[k] * w[k];
+        for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        }
+        if (lane == 0) {
+            fd.xvec[base + i] = s1;
+            if (two) fd.xvec[base + i2] = s2;
+        }
     }
 }
 
@@ -511,7 +567,7 @@ size_t frontal_factor_smem(int max_f) {
     return (panel > inverse ? panel : inverse) * sizeof(float) + 64;
 }
 
-size_t frontal_solve_smem(int max_f) { return 2 * (size_t)max_f * sizeof(float) + 64; }
+size_t frontal_solve_smem(int max_f) { return (2 * (size_t)max_f + FT) * sizeof(float) + 64; }
 
 // The dynamic shared-memory limit of the front kernels is a per-function
 // attribute shared by every context of the process, so it only ever grows.
@@ -535,7 +591,7 @@ cudaError_t frontal_configure(int max_f) {
 // Threads per CTA for a level whose largest front has mf unknowns: small fronts
 // get small CTAs (and, with the level's own shared-memory size, many CTAs per SM).
 static int factor_threads(int mf) { return mf <= 96 ? 128 : (mf <= 192 ? 256 : FT2); }
-static int solve_threads(int mf) { return mf <= 128 ? 128 : (mf <= 256 ? 256 : (mf <= 512 ? 512 : FT)); }
+static int solve_threads(int mf) { return mf <= 64 ? 128 : (mf <= 128 ? 256 : (mf <= 256 ? 512 : FT)); }
 
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
                        const int* lvl_maxf, cudaStream_t s, KTimer* kt) {
@@ -557,26 +613,38 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
 }
 
 void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, const int* lvl_maxf,
-                     int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt) {
+                     int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt, const int* act_sn,
+                     const int* act_ptr) {
     dc_note_launch();
     k_pre_in<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.type, ad.nb, w, fd.rvec, ad.node_inst, ad.mask);
+    // level l's fronts: the compacted list of the active instances' fronts, or all of them
+    auto level = [&](int l, int& cnt) -> const int* {
+        if (act_sn) {
+            cnt = act_ptr[l + 1] - act_ptr[l];
+            return act_sn + act_ptr[l];
+        }
+        cnt = lvl_ptr[l + 1] - lvl_ptr[l];
+        return fd.lvl_sn + lvl_ptr[l];
+    };
     for (int l = 0; l < nlev; ++l) {
-        int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
+        int cnt;
+        const int* sn = level(l, cnt);
         if (cnt > 0) {
             const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_MSOLVE);
-            k_msolve_fwd<<<cnt, solve_threads(mf), frontal_solve_smem(mf), s>>>(fd, lvl_ptr[l], ad.mask);
+            k_msolve_fwd<<<cnt, solve_threads(mf), frontal_solve_smem(mf), s>>>(fd, sn, ad.mask);
             if (kt) kt->end(DC_KT_MSOLVE);
         }
     }
     for (int l = nlev - 1; l >= 0; --l) {
-        int cnt = lvl_ptr[l + 1] - lvl_ptr[l];
+        int cnt;
+        const int* sn = level(l, cnt);
         if (cnt > 0) {
             const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_MSOLVE);
-            k_msolve_bwd<<<cnt, solve_threads(mf), frontal_solve_smem(mf), s>>>(fd, lvl_ptr[l], ad.mask);
+            k_msolve_bwd<<<cnt, solve_threads(mf), frontal_solve_smem(mf), s>>>(fd, sn, ad.mask);
             if (kt) kt->end(DC_KT_MSOLVE);
         }
     }

@@ -443,6 +443,21 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     c->hf = HostFactor();
     c->hf.max_diag = hfm.max_diag;
     c->fr = std::move(frm);
+    {
+        // per level, where each instance's fronts start in lvl_sn (an instance's
+        // fronts are contiguous and ascending inside a level)
+        const int B = c->B, nl = c->nlev;
+        c->lvl_inst_ptr.assign((size_t)nl * (B + 1), 0);
+        for (int l = 0; l < nl; ++l) {
+            int* P = c->lvl_inst_ptr.data() + (size_t)l * (B + 1);
+            int q = c->fr.lvl_ptr[l];
+            for (int i = 0; i <= B; ++i) {
+                while (q < c->fr.lvl_ptr[l + 1] && sn_inst[c->fr.lvl_sn[q]] < i) ++q;
+                P[i] = q;
+            }
+            P[B] = c->fr.lvl_ptr[l + 1];
+        }
+    }
     c->prm = pp.q[0];
     c->iprm = pp.q;
     c->have_params = true;
