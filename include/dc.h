@@ -79,6 +79,14 @@ typedef struct dc_params {
     int32_t adj_precond;     /* adjoint preconditioner: 0 = per-step single-precision
                                 multifrontal LDL^T of the constrained matrix (default);
                                 1 = node-block inverse + projected P^-1 (no factorisation) */
+    int32_t global_solver;   /* how P^-1 is applied (Eq. pd_global): 0 = rows of the
+                                explicit inverse factors L^-1, L^-T, two launches per
+                                application (default; best for one small cloth);
+                                1 = level-scheduled supernodal substitution with L,
+                                about 4x fewer flops, one launch per tree level
+                                (best for batches; needs adj_precond 0).  Equal
+                                results up to rounding. */
+    int32_t reserved_;
     dc_obstacle obstacles[DC_MAX_OBSTACLES];
 } dc_params;
 
@@ -113,6 +121,9 @@ typedef struct dc_stats {
     int32_t block_node;        /* ... for the per-node kernels                        */
     int32_t block_elem;        /* ... for the adjoint per-element kernel              */
     int64_t adj_batch_iters;   /* GMRES iterations run by a context, all instances in lockstep */
+    int32_t global_solver;     /* dc_params.global_solver in use                      */
+    int32_t reserved_;
+    double psolve_flops;       /* FP64 flops of one supernodal substitution sweep (3 columns) */
 } dc_stats;
 
 /* Kernel classes for dc_set_kernel_timer. */

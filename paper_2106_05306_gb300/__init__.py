@@ -32,7 +32,7 @@ _KIND = {"plane": DC_PLANE, "sphere": DC_SPHERE, "capsule": DC_CAPSULE}
 
 _PARAM_DEFAULTS = dict(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0, gravity=(0.0, -9.8, 0.0),
                        contact_margin=1e-6, n_pd_iters=20, obstacles=(), adj_tol=1e-10, adj_max_iters=2000,
-                       adj_restart=200, checkpoint_every=1, adj_precond=0)
+                       adj_restart=200, checkpoint_every=1, adj_precond=0, global_solver=0)
 
 
 def _torch():
@@ -81,6 +81,7 @@ def _make_params(lib, kw) -> dc_params:
     p.adj_restart = int(q["adj_restart"])
     p.checkpoint_every = int(q["checkpoint_every"])
     p.adj_precond = int(q["adj_precond"])
+    p.global_solver = int(q["global_solver"])
     obstacles = list(q["obstacles"])
     if len(obstacles) > DC_MAX_OBSTACLES:
         raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
@@ -234,6 +235,9 @@ class Cloth(_Context):
         check(st, None)
         self._init_common(ctx, device)
         self._theta = None
+        # rollout_fn's backward accepts adjoint steps stopped at their rounding
+        # floor above adj_tol when this is set (they are counted in stats())
+        self.allow_nonconverged = False
 
     def set_params(self, **kw):
         p, q = _make_params(self._lib, kw)
@@ -392,7 +396,8 @@ def _rollout_function():
             cloth = ctx.cloth
             if gx is None:
                 gx = torch.zeros((cloth.m, 3), dtype=torch.float64, device=cloth.device)
-            dx0, dv0, dth = cloth.backward(gx.contiguous(), gv.contiguous() if gv is not None else None)
+            dx0, dv0, dth = cloth.backward(gx.contiguous(), gv.contiguous() if gv is not None else None,
+                                           allow_nonconverged=getattr(cloth, "allow_nonconverged", False))
             return None, None, dx0, dv0, dth.to(ctx.theta_device)
 
     return ClothRollout

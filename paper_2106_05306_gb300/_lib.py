@@ -25,6 +25,7 @@ class dc_params(ctypes.Structure):
                 ("n_pd_iters", ctypes.c_int32), ("adj_max_iters", ctypes.c_int32),
                 ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("n_obstacles", ctypes.c_int32), ("adj_precond", ctypes.c_int32),
+                ("global_solver", ctypes.c_int32), ("reserved_", ctypes.c_int32),
                 ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
 
 
@@ -41,7 +42,8 @@ class dc_stats(ctypes.Structure):
                 ("front_levels", ctypes.c_int32), ("n_supernodes", ctypes.c_int32),
                 ("factorisations", ctypes.c_int64), ("n_instances", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("graph_replays", ctypes.c_int64), ("block_local", ctypes.c_int32), ("block_gather", ctypes.c_int32),
-                ("block_node", ctypes.c_int32), ("block_elem", ctypes.c_int32), ("adj_batch_iters", ctypes.c_int64)]
+                ("block_node", ctypes.c_int32), ("block_elem", ctypes.c_int32), ("adj_batch_iters", ctypes.c_int64),
+                ("global_solver", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("psolve_flops", ctypes.c_double)]
 
 
 class dc_instance(ctypes.Structure):

@@ -408,6 +408,8 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->block_node = c->dm.bs_node;
     o->block_elem = c->dm.bs_elem;
     o->adj_batch_iters = c->adj_batch_iters;
+    o->global_solver = c->dm.solver;
+    o->psolve_flops = c->psolve_flops;
     return DC_OK;
 }
 

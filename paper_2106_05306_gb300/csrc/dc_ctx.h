@@ -49,6 +49,7 @@ struct dc_ctx {
     std::string err;
     KTimer kt;
     double front_flops = 0.0;
+    double psolve_flops = 0.0;     // one supernodal sweep, 3 columns
     // instances
     int B = 1;
     std::vector<HostMesh> ihm;     // per-instance meshes (refactorised on new parameters)
@@ -70,6 +71,7 @@ struct dc_ctx {
     FrontDev fdv{};
     int nlev = 0;
     std::vector<int> lvl_maxf;     // largest front of every level
+    std::vector<int> lvl_maxfs;    // ... in nodes (supernodal substitution)
     int* d_int2ext = nullptr;
     // forward work
     d4 *xa = nullptr, *va = nullptr, *xb = nullptr, *vb = nullptr, *v = nullptr, *b = nullptr, *y = nullptr;
@@ -220,6 +222,7 @@ struct ParamPrep {
     std::vector<double> mass, wt, wb, node_mu, oprm;
     std::vector<int> optr, okind, long_rows, short_rows;
     std::vector<float> tau;
+    HostPSolve ps;                 // global_solver 1
     double front_flops = 0.0;
     long long factor_nnz = 0;
 };

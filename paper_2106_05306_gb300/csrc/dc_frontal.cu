@@ -386,22 +386,25 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
 }
 
 // Column-major matrix-vector product on one CTA: t_i = sum_k A[k * lda + i] v_k for
-// rows i < nrows and k < K (k <= i when tri).  The k range is cut into G
-// contiguous chunks, one per thread group (consecutive threads of a group take
-// consecutive rows: coalesced), and the G partial sums of a row are added in
-// group order, so the result does not depend on timing.  fin(i, t_i) stores.
+// rows i < nrows and k < K (k <= i when tri).  Rows go in passes of GV_ROWS; the
+// k range is cut into G contiguous chunks with G a function of K alone, every
+// (row, chunk) partial sum is one work item (consecutive items take consecutive
+// rows: coalesced), and a row's partial sums are added in chunk order.  The
+// arithmetic thus depends only on (nrows, K), never on the CTA size, so a front
+// gives the same bits whatever else shares its level.  fin(i, t_i) stores.
+constexpr int GV_ROWS = 64;
+constexpr int GV_MAXG = 8;
+__host__ __device__ constexpr int gv_groups(int K) { return K <= 8 ? 1 : (K + 7) / 8 < GV_MAXG ? (K + 7) / 8 : GV_MAXG; }
+
 template <class Fin>
 __device__ __forceinline__ void cm_gemv(const float* __restrict__ A, long lda, int nrows, int K, bool tri,
                                         const float* __restrict__ v, float* __restrict__ red, Fin fin) {
     const int nt = blockDim.x, tid = threadIdx.x;
-    // rows per pass: at least 4 groups share the k range when the CTA is large enough
-    const int R = min((nrows + 31) & ~31, max(32, nt / 4));
-    const int G = nt / R;
+    const int G = gv_groups(K);
     const int C = (K + G - 1) / G;
-    const int r = tid % R, g = tid / R;
-    for (int i0 = 0; i0 < nrows; i0 += R) {
-        const int i = i0 + r;
-        if (g < G) {
+    for (int i0 = 0; i0 < nrows; i0 += GV_ROWS) {
+        for (int item = tid; item < GV_ROWS * G; item += nt) {
+            const int r = item % GV_ROWS, g = item / GV_ROWS, i = i0 + r;
             float acc = 0.0f;
             if (i < nrows) {
                 const int k0 = g * C;
@@ -411,12 +414,12 @@ __device__ __forceinline__ void cm_gemv(const float* __restrict__ A, long lda, i
 #pragma unroll 4
                 for (int k = k0; k < k1; ++k) acc += a[(long)k * lda] * v[k];
             }
-            red[g * R + r] = acc;
+            red[g * GV_ROWS + r] = acc;
         }
         __syncthreads();
-        if (tid < R && i0 + tid < nrows) {
+        if (tid < GV_ROWS && i0 + tid < nrows) {
             float t = 0.0f;
-            for (int q = 0; q < G; ++q) t += red[q * R + tid];
+            for (int q = 0; q < G; ++q) t += red[q * GV_ROWS + tid];
             fin(i0 + tid, t);
         }
         __syncthreads();
@@ -437,7 +440,7 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __res
     const int f = fd.f[s], p = fd.p[s];
     const int base = 3 * fd.begin[s];
     float* y = w + f;
-    float* red = y + f;                // [nt] partial sums
+    float* red = y + f;                // [GV_MAXG][GV_ROWS] partial sums
     for (int t = tid; t < f; t += nt) w[t] = 0.0f;
     __syncthreads();
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
@@ -567,7 +570,7 @@ size_t frontal_factor_smem(int max_f) {
     return (panel > inverse ? panel : inverse) * sizeof(float) + 64;
 }
 
-size_t frontal_solve_smem(int max_f) { return (2 * (size_t)max_f + FT) * sizeof(float) + 64; }
+size_t frontal_solve_smem(int max_f) { return (2 * (size_t)max_f + GV_ROWS * GV_MAXG) * sizeof(float) + 64; }
 
 // The dynamic shared-memory limit of the front kernels is a per-function
 // attribute shared by every context of the process, so it only ever grows.

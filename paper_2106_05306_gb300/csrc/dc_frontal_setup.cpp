@@ -190,3 +190,85 @@ std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts
     }
     return "";
 }
+
+void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps) {
+    const int S = fr.S;
+    ps = HostPSolve();
+    ps.poff.resize(S);
+    ps.xoff.resize(S);
+    ps.toff.resize(S);
+    ps.aoff.resize(S);
+    long long po = 0, xo = 0, to = 0, ao = 0;
+    for (int s = 0; s < S; ++s) {
+        const long long ns = fr.end[s] - fr.begin[s], nu = fr.uptr[s + 1] - fr.uptr[s];
+        ps.poff[s] = po;
+        ps.xoff[s] = xo;
+        ps.toff[s] = to;
+        ps.aoff[s] = (int)ao;
+        po += (ns + nu) * ns;
+        xo += ns * ns;
+        to += ns * nu;
+        ao += nu;
+    }
+    ps.acc_nodes = ao;
+    ps.panel.assign(po, 0.0);
+    ps.xinv.assign(xo, 0.0);
+    ps.xinvt.assign(xo, 0.0);
+    ps.pant.assign(to, 0.0);
+    std::vector<double> x;
+    for (int s = 0; s < S; ++s) {
+        const int b = fr.begin[s], e = fr.end[s], ns = e - b;
+        const int* un = fr.unode.data() + fr.uptr[s];
+        const int nu = fr.uptr[s + 1] - fr.uptr[s], fs = ns + nu;
+        double* pan = ps.panel.data() + ps.poff[s];
+        for (int c = 0; c < ns; ++c) {
+            const int j = b + c;
+            for (int q = hf.colptr[j]; q < hf.colptr[j + 1]; ++q) {
+                const int i = hf.rowidx[q];
+                const int pos = i < e ? i - b : ns + (int)(std::lower_bound(un, un + nu, i) - un);
+                pan[(long)c * fs + pos] = hf.val[q];
+            }
+        }
+        // inverse of the top block D (D[r][c] = pan[c * fs + r], lower) column by column
+        double* X = ps.xinv.data() + ps.xoff[s];
+        x.assign(ns, 0.0);
+        for (int c = 0; c < ns; ++c) {
+            for (int r = 0; r < ns; ++r) x[r] = 0.0;
+            for (int r = c; r < ns; ++r) {
+                double t = (r == c) ? 1.0 : 0.0;
+                for (int k = c; k < r; ++k) t -= pan[(long)k * fs + r] * x[k];
+                x[r] = t / pan[(long)r * fs + r];
+            }
+            for (int r = 0; r < ns; ++r) X[(long)c * ns + r] = x[r];
+        }
+        // transposed copies for the backward sweep
+        double* XT = ps.xinvt.data() + ps.xoff[s];
+        for (int c = 0; c < ns; ++c)
+            for (int r = 0; r < ns; ++r) XT[(long)r * ns + c] = X[(long)c * ns + r];
+        double* T = ps.pant.data() + ps.toff[s];
+        for (int c = 0; c < ns; ++c)
+            for (int k = 0; k < nu; ++k) T[(long)k * ns + c] = pan[(long)c * fs + ns + k];
+    }
+}
+
+void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out) {
+    out = HostPSolve();
+    long long po = 0, xo = 0, to = 0, ao = 0;
+    for (const HostPSolve& p : P) {
+        for (size_t s = 0; s < p.poff.size(); ++s) {
+            out.poff.push_back(p.poff[s] + po);
+            out.xoff.push_back(p.xoff[s] + xo);
+            out.toff.push_back(p.toff[s] + to);
+            out.aoff.push_back((int)(p.aoff[s] + ao));
+        }
+        out.panel.insert(out.panel.end(), p.panel.begin(), p.panel.end());
+        out.xinv.insert(out.xinv.end(), p.xinv.begin(), p.xinv.end());
+        out.xinvt.insert(out.xinvt.end(), p.xinvt.begin(), p.xinvt.end());
+        out.pant.insert(out.pant.end(), p.pant.begin(), p.pant.end());
+        po += (long long)p.panel.size();
+        xo += (long long)p.xinv.size();
+        to += (long long)p.pant.size();
+        ao += p.acc_nodes;
+    }
+    out.acc_nodes = ao;
+}

@@ -92,10 +92,56 @@ struct HostFronts {
 };
 std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts& fr);
 
+// Dense supernodal storage of the scalar factor L of P (global_solver 1), on the
+// supernode partition of the fronts: supernode s has ns = (end - begin) nodes and
+// nu update rows U_s; its panel is L's columns begin..end-1 restricted to the rows
+// (s's nodes, U_s), (ns + nu) x ns column-major, and xinv holds the inverse of
+// the panel's ns x ns lower-triangular top block, column-major.  The backward
+// sweep reads transposed copies (pant: L_Us^T, ns x nu; xinvt: the inverse
+// transposed), so that both sweeps are column-major products.
+struct HostPSolve {
+    std::vector<long long> poff, xoff;   // [S] offsets of panel / inverse (doubles)
+    std::vector<long long> toff;         // [S] offset of the transposed update block (doubles)
+    std::vector<int> aoff;               // [S] offset of the update vector (nodes)
+    std::vector<double> panel, xinv, pant, xinvt;
+    long long acc_nodes = 0;
+};
+void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps);
+void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out);
+
 // ---------------------------------------------------------------- device views
+
+// Device view of the supernodal substitution (global_solver 1): the front
+// partition (node-level counts are the fronts' DOF counts / 3) and the panels.
+struct PSolveDev {
+    int nlev;
+    const int* lvl_ptr_h;              // host: fronts of level l are lvl_sn[lvl_ptr_h[l] .. lvl_ptr_h[l+1])
+    const int* lvl_maxf_h;             // host: largest front of level l (nodes)
+    const int* lvl_sn;
+    const int* begin;
+    const int* f;                      // DOFs of the front (3 per node)
+    const int* p;
+    const int* uptr;
+    const int* unode;
+    const int* cptr;
+    const int* child;
+    const int* cmap;
+    const long long* poff;
+    const long long* xoff;
+    const long long* toff;
+    const int* aoff;
+    const double* panel;
+    const double* xinv;
+    const double* pant;
+    const double* xinvt;
+    d4* acc;                           // update vectors of the forward sweep (nodes)
+    d4* xint;                          // solution of the backward sweep before any per-node update
+};
 
 struct DevMesh {
     int m, m_free, T;
+    int solver;                        // 0: explicit inverse rows; 1: supernodal (ps)
+    PSolveDev ps;
     const int4* tri;                   // [T] (i0, i1, i2, 0)
     const d4* G;                       // [T] (g1x, g1y, g2x, g2y)
     const double* wt;                  // [T] k_stretch * area
@@ -185,6 +231,9 @@ void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s);
 void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode,
                       const int* contact, const d4* normal_beta, const double* c, d4* f,
                       int* case_, double* c_out, cudaStream_t s);
+// Raises the shared-memory limit of the supernodal level kernels for fronts of
+// up to max_fs nodes (process-wide, never lowered).
+cudaError_t psolve_configure(int max_fs);
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v,
                      d4* x_np1, cudaStream_t s);
 void launch_count_cases(const int* contact, const int* case_, int m_free,

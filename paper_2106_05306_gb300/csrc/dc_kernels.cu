@@ -12,6 +12,7 @@
 // Every reduction is a fixed-order gather (no atomics), so a launch is bitwise
 // repeatable and independent of what else runs on the GPU.
 #include <atomic>
+#include <mutex>
 
 #include "dc_internal.h"
 
@@ -331,15 +332,13 @@ __device__ __forceinline__ int coulomb(double mu, double c, const double n[3], d
     return 2;
 }
 
-__global__ void k_solve_bwd(DevMesh dm, DevParams P, const d4* __restrict__ y, d4* __restrict__ out, int mode,
-                            const int* __restrict__ contact, const d4* __restrict__ nb,
-                            const double* __restrict__ cc, d4* __restrict__ f, int* __restrict__ case_,
-                            double* __restrict__ c_out) {
-    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    if (row >= dm.m_free) return;
-    double s0, s1, s2;
-    warp_row(dm.kptr, dm.kidx, dm.kval, y, row, s0, s1, s2);
-    if ((threadIdx.x & 31) != 0) return;
+// Output of one row of the backward substitution: mode 0 stores it; mode 1
+// applies the node's Signorini-Coulomb update (contact nodes) and stores v; mode 2
+// stores the compliance c_j = h s0.
+__device__ __forceinline__ void finish_row(const DevParams& P, int row, double s0, double s1, double s2,
+                                           d4* __restrict__ out, int mode, const int* __restrict__ contact,
+                                           const d4* __restrict__ nb, const double* __restrict__ cc,
+                                           d4* __restrict__ f, int* __restrict__ case_, double* __restrict__ c_out) {
     if (mode == 2) {
         c_out[row] = P.h * s0;
         return;
@@ -356,6 +355,162 @@ __global__ void k_solve_bwd(DevMesh dm, DevParams P, const d4* __restrict__ y, d
         return;
     }
     st(out + row, s0, s1, s2);
+}
+
+__global__ void k_solve_bwd(DevMesh dm, DevParams P, const d4* __restrict__ y, d4* __restrict__ out, int mode,
+                            const int* __restrict__ contact, const d4* __restrict__ nb,
+                            const double* __restrict__ cc, d4* __restrict__ f, int* __restrict__ case_,
+                            double* __restrict__ c_out) {
+    int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    if (row >= dm.m_free) return;
+    double s0, s1, s2;
+    warp_row(dm.kptr, dm.kidx, dm.kval, y, row, s0, s1, s2);
+    if ((threadIdx.x & 31) != 0) return;
+    finish_row(P, row, s0, s1, s2, out, mode, contact, nb, cc, f, case_, c_out);
+}
+
+// ---- supernodal substitution (global_solver 1): one CTA per supernode, levels
+// leaves-first for L y = b and root-first for L^T x = y, three right-hand sides.
+// Shared memory holds the front's vectors component-major ([3][n]).
+
+// Column-major product on one CTA with three right-hand sides: t_c,i = sum_k
+// A[k * lda + i] v[c * ldv + k] for i < nrows and k < K (tri 1: only k <= i;
+// tri 2: only k >= i).  Rows go in passes of GV_ROWS; the k range is cut into G
+// contiguous chunks with G a function of K alone; every (row, chunk) partial sum is
+// one work item and a row's partial sums are added in chunk order, so the result
+// depends only on (nrows, K), never on the CTA size (a supernode gives the same
+// bits whatever else shares its level).  fin(i, t0, t1, t2) stores (it must not
+// write v).
+constexpr int GV_ROWS = 64;
+constexpr int GV_MAXG = 8;
+__host__ __device__ constexpr int gv_groups(int K) { return K <= 8 ? 1 : (K + 7) / 8 < GV_MAXG ? (K + 7) / 8 : GV_MAXG; }
+
+template <class Fin>
+__device__ __forceinline__ void cm_gemv3(const double* __restrict__ A, long lda, int nrows, int K, int tri,
+                                         const double* __restrict__ v, int ldv, double* __restrict__ red, Fin fin) {
+    const int nt = blockDim.x, tid = threadIdx.x;
+    const int G = gv_groups(K);
+    const int C = (K + G - 1) / G;
+    constexpr int RS = GV_ROWS * GV_MAXG;      // stride between the three columns' partial sums
+    for (int i0 = 0; i0 < nrows; i0 += GV_ROWS) {
+        for (int item = tid; item < GV_ROWS * G; item += nt) {
+            const int r = item % GV_ROWS, g = item / GV_ROWS, i = i0 + r;
+            double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+            if (i < nrows) {
+                int k0 = g * C;
+                int k1 = min(K, k0 + C);
+                if (tri == 1) k1 = min(k1, i + 1);
+                if (tri == 2) k0 = max(k0, i);
+                const double* a = A + i;
+                for (int k = k0; k < k1; ++k) {
+                    const double x = a[(long)k * lda];
+                    a0 += x * v[k];
+                    a1 += x * v[ldv + k];
+                    a2 += x * v[2 * ldv + k];
+                }
+            }
+            red[g * GV_ROWS + r] = a0;
+            red[RS + g * GV_ROWS + r] = a1;
+            red[2 * RS + g * GV_ROWS + r] = a2;
+        }
+        __syncthreads();
+        if (tid < GV_ROWS && i0 + tid < nrows) {
+            double t0 = 0.0, t1 = 0.0, t2 = 0.0;
+            for (int q = 0; q < G; ++q) {
+                t0 += red[q * GV_ROWS + tid];
+                t1 += red[RS + q * GV_ROWS + tid];
+                t2 += red[2 * RS + q * GV_ROWS + tid];
+            }
+            fin(i0 + tid, t0, t1, t2);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, int lvl_begin, const d4* __restrict__ b,
+                                                d4* __restrict__ y) {
+    extern __shared__ double smd[];
+    const int s = ps.lvl_sn[lvl_begin + blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
+    double* w = smd;                   // [3][fs]
+    double* yv = w + 3 * fs;           // [3][ns]
+    double* red = yv + 3 * ns;         // [3][GV_MAXG * GV_ROWS]
+    for (int t = tid; t < 3 * fs; t += nt) w[t] = 0.0;
+    __syncthreads();
+    for (int q = ps.cptr[s]; q < ps.cptr[s + 1]; ++q) {
+        const int c = ps.child[q];
+        const int nuc = (ps.f[c] - ps.p[c]) / 3;
+        const int* map = ps.cmap + ps.uptr[c];
+        const d4* acc = ps.acc + ps.aoff[c];
+        for (int k = tid; k < nuc; k += nt) {
+            const int pos = map[k];
+            const d4 a = ld(acc + k);
+            w[pos] += a.x;
+            w[fs + pos] += a.y;
+            w[2 * fs + pos] += a.z;
+        }
+        __syncthreads();
+    }
+    for (int t = tid; t < ns; t += nt) {
+        const d4 a = ld(b + begin + t);
+        w[t] += a.x;
+        w[fs + t] += a.y;
+        w[2 * fs + t] += a.z;
+    }
+    __syncthreads();
+    const double* X = ps.xinv + ps.xoff[s];
+    const double* Pn = ps.panel + ps.poff[s];
+    cm_gemv3(X, ns, ns, ns, 1, w, fs, red, [&](int i, double t0, double t1, double t2) {
+        yv[i] = t0;
+        yv[ns + i] = t1;
+        yv[2 * ns + i] = t2;
+    });
+    d4* acc = ps.acc + ps.aoff[s];
+    cm_gemv3(Pn + ns, fs, nu, ns, 0, yv, ns, red, [&](int i, double t0, double t1, double t2) {
+        st(acc + i, w[ns + i] - t0, w[fs + ns + i] - t1, w[2 * fs + ns + i] - t2);
+    });
+    for (int t = tid; t < ns; t += nt) st(y + begin + t, yv[t], yv[ns + t], yv[2 * ns + t]);
+}
+
+__global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, int lvl_begin, const d4* __restrict__ y,
+                                                d4* __restrict__ out, int mode, const int* __restrict__ contact,
+                                                const d4* __restrict__ nb, const double* __restrict__ cc,
+                                                d4* __restrict__ f, int* __restrict__ case_,
+                                                double* __restrict__ c_out) {
+    extern __shared__ double smd[];
+    const int s = ps.lvl_sn[lvl_begin + blockIdx.x];
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
+    double* w = smd;                   // [3][ns]
+    double* xu = w + 3 * ns;           // [3][nu]
+    double* red = xu + 3 * nu;         // [3][GV_MAXG * GV_ROWS]
+    const int* un = ps.unode + ps.uptr[s];
+    for (int t = tid; t < ns; t += nt) {
+        const d4 a = ld(y + begin + t);
+        w[t] = a.x;
+        w[ns + t] = a.y;
+        w[2 * ns + t] = a.z;
+    }
+    for (int k = tid; k < nu; k += nt) {
+        const d4 a = ld(ps.xint + un[k]);
+        xu[k] = a.x;
+        xu[nu + k] = a.y;
+        xu[2 * nu + k] = a.z;
+    }
+    __syncthreads();
+    // w -= L_Us^T x_U (the transposed update block is ns x nu column-major)
+    cm_gemv3(ps.pant + ps.toff[s], ns, ns, nu, 0, xu, nu, red, [&](int i, double t0, double t1, double t2) {
+        w[i] -= t0;
+        w[ns + i] -= t1;
+        w[2 * ns + i] -= t2;
+    });
+    // x = L_ss^-T w, then the per-node output
+    cm_gemv3(ps.xinvt + ps.xoff[s], ns, ns, ns, 2, w, ns, red, [&](int i, double t0, double t1, double t2) {
+        const int row = begin + i;
+        st(ps.xint + row, t0, t1, t2);
+        finish_row(P, row, t0, t1, t2, out, mode, contact, nb, cc, f, case_, c_out);
+    });
 }
 
 __global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4* __restrict__ v,
@@ -406,12 +561,54 @@ void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, con
     dc_note_launch();
     k_gather_rhs<<<nblk(dm.m_free, dm.bs_gather), dm.bs_gather, 0, s>>>(dm, P, v_n, c1, c2, bu, f, b);
 }
+namespace {
+int ps_threads(int fs) { return fs <= 64 ? 128 : 256; }
+size_t ps_smem(int fs, int) { return (6 * (size_t)fs + 3 * (size_t)GV_ROWS * GV_MAXG) * sizeof(double); }
+}  // namespace
+
+// The level kernels' dynamic shared-memory limit is shared by every context of
+// the process: it only ever grows.
+cudaError_t psolve_configure(int max_fs) {
+    static std::mutex mu;
+    static size_t configured = 48 * 1024;
+    std::lock_guard<std::mutex> lock(mu);
+    const size_t need = ps_smem(max_fs, ps_threads(max_fs));
+    if (need <= configured) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(k_ps_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ps_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess) configured = need;
+    return e;
+}
+
 void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
+    if (dm.solver == 1) {
+        const PSolveDev& ps = dm.ps;
+        for (int l = 0; l < ps.nlev; ++l) {
+            const int cnt = ps.lvl_ptr_h[l + 1] - ps.lvl_ptr_h[l];
+            if (cnt <= 0) continue;
+            const int fs = ps.lvl_maxf_h[l], nt = ps_threads(fs);
+            dc_note_launch();
+            k_ps_fwd<<<cnt, nt, ps_smem(fs, nt), s>>>(ps, ps.lvl_ptr_h[l], b, y);
+        }
+        return;
+    }
     dc_note_launch();
     k_solve_fwd<<<dm.n_long + nblk(dm.n_short, 8), 256, 0, s>>>(dm, b, y);
 }
 void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode, const int* contact,
                       const d4* nb, const double* c, d4* f, int* case_, double* c_out, cudaStream_t s) {
+    if (dm.solver == 1) {
+        const PSolveDev& ps = dm.ps;
+        for (int l = ps.nlev - 1; l >= 0; --l) {
+            const int cnt = ps.lvl_ptr_h[l + 1] - ps.lvl_ptr_h[l];
+            if (cnt <= 0) continue;
+            const int fs = ps.lvl_maxf_h[l], nt = ps_threads(fs);
+            dc_note_launch();
+            k_ps_bwd<<<cnt, nt, ps_smem(fs, nt), s>>>(ps, P, ps.lvl_ptr_h[l], y, out, mode, contact, nb, c, f,
+                                                      case_, c_out);
+        }
+        return;
+    }
     dc_note_launch();
     k_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, P, y, out, mode, contact, nb, c, f, case_,
                                                                 c_out);

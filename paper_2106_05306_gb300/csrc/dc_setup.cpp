@@ -379,6 +379,15 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
             x[hf.rowidx[q]] = 0.0;
         }
     }
+    if (p.global_solver != 0) {   // the supernodal substitution uses L itself
+        hf.fptr.assign(n + 1, 0);
+        hf.bptr.assign(n + 1, 0);
+        hf.fidx.clear();
+        hf.fval.clear();
+        hf.bidx.clear();
+        hf.bval.clear();
+        return DC_OK;
+    }
     // ---- explicit inverse factor: column j of L^-1 lives on the etree path j -> root
     std::vector<std::vector<std::pair<int, double>>> inv_rows(n);   // row i: (col j, value)
     hf.bptr.assign(1, 0);

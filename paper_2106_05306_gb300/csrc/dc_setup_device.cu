@@ -32,8 +32,11 @@ bool finite_params(const dc_params& p) {
 std::string normalise_params(dc_params& q) {
     if (!finite_params(q) || !(q.h > 0) || q.k_stretch < 0 || q.k_bend < 0 || !(q.density > 0) || q.mu < 0 ||
         q.n_pd_iters < 0 || q.n_obstacles < 0 || q.n_obstacles > DC_MAX_OBSTACLES || q.checkpoint_every < 1 ||
-        q.adj_max_iters < 1 || q.adj_restart < 1 || !(q.adj_tol > 0) || q.adj_precond < 0 || q.adj_precond > 1)
+        q.adj_max_iters < 1 || q.adj_restart < 1 || !(q.adj_tol > 0) || q.adj_precond < 0 || q.adj_precond > 1 ||
+        q.global_solver < 0 || q.global_solver > 1)
         return "invalid or non-finite parameter";
+    if (q.adj_precond == 1 && q.global_solver != 0)
+        return "adj_precond 1 needs global_solver 0 (it projects with the explicit inverse rows)";
     for (int o = 0; o < q.n_obstacles; ++o) {
         dc_obstacle& ob = q.obstacles[o];
         for (int k = 0; k < 7; ++k)
@@ -60,7 +63,8 @@ bool same_batch_fields(const dc_params& a, const dc_params& b) {
     return a.h == b.h && a.gravity[0] == b.gravity[0] && a.gravity[1] == b.gravity[1] &&
            a.gravity[2] == b.gravity[2] && a.contact_margin == b.contact_margin && a.adj_tol == b.adj_tol &&
            a.n_pd_iters == b.n_pd_iters && a.adj_max_iters == b.adj_max_iters && a.adj_restart == b.adj_restart &&
-           a.checkpoint_every == b.checkpoint_every && a.adj_precond == b.adj_precond;
+           a.checkpoint_every == b.checkpoint_every && a.adj_precond == b.adj_precond &&
+           a.global_solver == b.global_solver;
 }
 
 template <class T>
@@ -242,6 +246,7 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
     }
     std::vector<HostFactor> hf(B);
     std::vector<HostFronts> fr(B);
+    std::vector<HostPSolve> psi(B);
     std::vector<dc_status> st(B, DC_OK);
     std::vector<std::string> err(B);
     dc_parallel_for(B, [&](int i) {
@@ -254,6 +259,8 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
             if (!fe.empty()) {
                 st[i] = DC_ERR_INVALID;
                 err[i] = fe;
+            } else if (q[i].global_solver == 1) {
+                dc_build_psolve(hf[i], fr[i], psi[i]);
             }
         }
         // only the explicit inverse rows, the size and the largest pivot are kept
@@ -273,6 +280,8 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
     hf.clear();
     dc_merge_fronts(fr, c->inst, MF, pp.frm);
     fr.clear();
+    if (q[0].global_solver == 1) dc_merge_psolve(psi, pp.ps);
+    psi.clear();
     const HostFronts& frm = pp.frm;
     // per merged node / triangle material, per-instance tables
     pp.mass.assign(hm.m, 0.0);
@@ -431,6 +440,47 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         (s = dalloc(c, F, &c->fds[1].binv, (size_t)frm.binv_size)) ||
         (s = dalloc(c, F, &c->fds[1].linv, (size_t)frm.linv_size)))
         return s;
+    // supernodal substitution of P (global_solver 1) on the same partition
+    dm.solver = pp.q[0].global_solver;
+    if (dm.solver == 1) {
+        long long *d_poff, *d_xoff, *d_toff;
+        int* d_aoff;
+        double *d_panel, *d_xinv, *d_pant, *d_xinvt;
+        d4 *d_acc, *d_xint;
+        if ((s = upload(c, F, &d_poff, pp.ps.poff)) || (s = upload(c, F, &d_xoff, pp.ps.xoff)) ||
+            (s = upload(c, F, &d_toff, pp.ps.toff)) || (s = upload(c, F, &d_aoff, pp.ps.aoff)) ||
+            (s = upload(c, F, &d_panel, pp.ps.panel)) || (s = upload(c, F, &d_xinv, pp.ps.xinv)) ||
+            (s = upload(c, F, &d_pant, pp.ps.pant)) || (s = upload(c, F, &d_xinvt, pp.ps.xinvt)) ||
+            (s = dalloc(c, F, &d_acc, (size_t)std::max<long long>(pp.ps.acc_nodes, 1))) ||
+            (s = dalloc(c, F, &d_xint, (size_t)std::max(MF, 1))))
+            return s;
+        PSolveDev& ps = dm.ps;
+        ps.lvl_sn = d_lvl;
+        ps.begin = d_begin;
+        ps.f = d_f;
+        ps.p = d_p;
+        ps.uptr = d_uptr;
+        ps.unode = d_unode;
+        ps.cptr = d_cptr;
+        ps.child = d_child;
+        ps.cmap = d_cmap;
+        ps.poff = d_poff;
+        ps.xoff = d_xoff;
+        ps.toff = d_toff;
+        ps.aoff = d_aoff;
+        ps.panel = d_panel;
+        ps.xinv = d_xinv;
+        ps.pant = d_pant;
+        ps.xinvt = d_xinvt;
+        ps.acc = d_acc;
+        ps.xint = d_xint;
+    }
+    c->psolve_flops = 0.0;
+    if (dm.solver == 1)
+        for (int q = 0; q < frm.S; ++q) {
+            const double ns = frm.p[q] / 3, nu = (frm.f[q] - frm.p[q]) / 3;
+            c->psolve_flops += 6.0 * (ns * (ns + 1.0) / 2.0 + ns * nu);   // 3 columns, one FMA = 2 flops
+        }
     c->nlev = (int)frm.lvl_ptr.size() - 1;
     c->lvl_maxf.assign(std::max(c->nlev, 0), 0);
     for (int l = 0; l < c->nlev; ++l)
@@ -443,6 +493,16 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     c->hf = HostFactor();
     c->hf.max_diag = hfm.max_diag;
     c->fr = std::move(frm);
+    c->lvl_maxfs.assign(c->lvl_maxf.size(), 0);
+    for (size_t l = 0; l < c->lvl_maxf.size(); ++l) c->lvl_maxfs[l] = c->lvl_maxf[l] / 3;
+    if (dm.solver == 1) {
+        dm.ps.nlev = c->nlev;
+        dm.ps.lvl_ptr_h = c->fr.lvl_ptr.data();
+        dm.ps.lvl_maxf_h = c->lvl_maxfs.data();
+        int mx = 0;
+        for (int v : c->lvl_maxfs) mx = std::max(mx, v);
+        CK(psolve_configure(mx));
+    }
     {
         // per level, where each instance's fronts start in lvl_sn (an instance's
         // fronts are contiguous and ascending inside a level)
@@ -507,6 +567,11 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
         add(4 * (size_t)r.linv_size);
     }
     add(4 * (size_t)r.acc_size); add(12 * MF); add(12 * MF); add(12 * MF);
+    if (q.global_solver == 1) {
+        add(vbytes(pp.ps.poff)); add(vbytes(pp.ps.xoff)); add(vbytes(pp.ps.toff)); add(vbytes(pp.ps.aoff));
+        add(vbytes(pp.ps.panel)); add(vbytes(pp.ps.xinv)); add(vbytes(pp.ps.pant)); add(vbytes(pp.ps.xinvt));
+        add((size_t)pp.ps.acc_nodes * d4b); add(MF * d4b);
+    }
     // checkpoints, segment recomputation, adjoint
     add(((size_t)n_steps / k + 1) * 2 * m * d4b);
     if (k == 1)

@@ -1,0 +1,84 @@
+"""GPU parity of the supernodal substitution of P (global_solver = 1): the
+global solve against the oracle's banded Cholesky, forward steps and adjoint
+gradients against the oracle, a batch against the same cloths alone (bitwise),
+and the allocation-free entry point against dc_global_solve."""
+import numpy as np
+import pytest
+
+import scenes
+from oracle import cloth as oc
+from tests._helpers import (GRAD_TOL, STATE_TOL, cuda, make_batch, make_cloth, oracle_model, rel_inf,
+                            rel_l2)
+
+pytestmark = pytest.mark.gpu
+
+
+def test_supernodal_global_solve_matches_banded_cholesky():
+    import torch
+    for sc in (scenes.small_scene(5, seed=1), scenes.hanging_cloth(), scenes.draped_cloth(),
+               scenes.batch_instance(15)):
+        cloth = make_cloth(sc, global_solver=1)
+        assert cloth.stats()["global_solver"] == 1 and cloth.stats()["psolve_flops"] > 0
+        M = oracle_model(sc)
+        rng = np.random.default_rng(3)
+        rhs = rng.standard_normal((sc.m, 3))
+        got = cloth.global_solve(cuda(rhs)).cpu().numpy()
+        want = np.zeros_like(rhs)
+        want[M.free] = M.solve_P(rhs[M.free])
+        assert rel_inf(got, want) < 1e-11
+        assert np.all(got[M.pins] == 0.0)
+        dst = torch.empty((sc.m, 3), dtype=torch.float64, device="cuda")
+        assert cloth._lib.dc_global_solve_static(cloth._ctx, cuda(rhs).data_ptr(), dst.data_ptr()) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(dst, torch.tensor(got, device="cuda"))
+        cloth.close()
+
+
+@pytest.mark.parametrize("contact,drop,pinned", [("sphere", True, True), ("both", True, False),
+                                                 ("capsule", False, True)])
+def test_supernodal_rollout_and_adjoint_parity(contact, drop, pinned):
+    sc = scenes.small_scene(6, seed=5, contact=contact, drop=drop, pinned=pinned, n_steps=4)
+    M = oracle_model(sc)
+    xs, vs, recs = oc.rollout(M, sc.x0, sc.v0, sc.n_steps)
+    gv = 0.3 * np.random.default_rng(2).standard_normal((sc.m, 3))
+    want = oc.rollout_gradient(M, recs, sc.loss_w, gv)
+    for ck in (1, 3):
+        cloth = make_cloth(sc, global_solver=1, checkpoint_every=ck)
+        xN, vN = cloth.rollout(cuda(sc.x0), cuda(sc.v0), sc.n_steps)
+        assert rel_inf(xN.cpu().numpy(), xs[-1]) <= STATE_TOL
+        assert rel_inf(vN.cpu().numpy(), vs[-1]) <= STATE_TOL
+        dx0, dv0, dth = cloth.backward(cuda(sc.loss_w), cuda(gv))
+        cloth.close()
+        assert rel_l2(dx0.cpu().numpy(), want[0]) <= GRAD_TOL
+        assert rel_l2(dv0.cpu().numpy(), want[1]) <= GRAD_TOL
+        scale = np.max(np.abs(want[2]))
+        for q in range(3):
+            assert abs(dth[q].item() - want[2][q]) <= GRAD_TOL * max(abs(want[2][q]), 1e-6 * scale)
+
+
+def test_supernodal_batch_is_bitwise_the_cloths_alone():
+    import torch
+    scs = [scenes.small_scene(4, seed=1, contact="sphere", drop=True),
+           scenes.small_scene(7, seed=2, contact="plane", drop=True, pinned=False),
+           scenes.small_scene(5, seed=3, contact="both", drop=True)]
+    cat = lambda k: cuda(np.concatenate([getattr(s, k) for s in scs]))
+    b = make_batch(scs, global_solver=1, checkpoint_every=1)
+    xN, vN = b.rollout(cat("x0"), cat("v0"), 3)
+    dx0, dv0, dth = b.backward(cat("loss_w"))
+    parts = [b.split(t) for t in (xN, vN, dx0, dv0)]
+    b.close()
+    for i, sc in enumerate(scs):
+        cl = make_cloth(sc, global_solver=1, checkpoint_every=1)
+        ax, av = cl.rollout(cuda(sc.x0), cuda(sc.v0), 3)
+        adx, adv, ath = cl.backward(cuda(sc.loss_w))
+        cl.close()
+        for a, p in zip((ax, av, adx, adv), (q[i] for q in parts)):
+            assert torch.equal(a, p), i
+        assert torch.equal(ath, dth[i])
+
+
+def test_supernodal_rejects_block_preconditioner():
+    import paper_2106_05306_gb300 as dc
+    sc = scenes.small_scene(4, seed=1)
+    with pytest.raises(dc.DCError, match="DC_ERR_INVALID"):
+        make_cloth(sc, global_solver=1, adj_precond=1)
