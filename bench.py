@@ -68,7 +68,9 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic per launch of the roofline kernel from the ncu capture summarised in
 # profiles/ (null when the kernel source changed since the capture).
 TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None},
-           "ps_solve_fwd": {"bytes": None, "source_sha": None}}
+           # k_ps_fwd: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
+           # profiles/k_ps_fwd_batched_96cloths.md), scaled by the sweep's flops
+           "ps_solve_fwd": {"bytes_per_flop": 140359680.0 / 62559690.0, "source_sha": "861a24732cf079b0"}}
 
 
 def parse_args(argv=None):
@@ -523,8 +525,10 @@ def roofline(cls, st):
                 "traffic": None, "algorithmic_flops_per_launch": work}
         tr = TRAFFIC.get("ps_" + cls)
         src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_kernels.cu")
-        if tr and tr["bytes"] and tr["source_sha"] == kernel_sha(src):
-            roof["traffic"] = tr["bytes"]
+        if tr and tr["source_sha"] == kernel_sha(src):
+            roof["traffic"] = tr["bytes_per_flop"] * work
+            roof["traffic_note"] = ("DRAM read+write of one sweep measured by ncu on 96 cloths, scaled to this "
+                                    "sweep by its flops (profiles/k_ps_fwd_batched_96cloths.md)")
     else:
         nnz = st["fwd_solve_nnz"] if cls == "solve_fwd" else st["bwd_solve_nnz"]
         work = 6.0 * nnz                                  # 3 right-hand sides: one FMA each per nonzero
