@@ -72,6 +72,7 @@ struct dc_ctx {
     int nlev = 0;
     std::vector<int> lvl_maxf;     // largest front of every level
     std::vector<int> lvl_maxfs;    // ... in nodes (supernodal substitution)
+    std::vector<int> ps_lvl_ptr, ps_nbig, ps_nsmall, ps_maxbig;   // supernodal level lists (large, then small)
     int* d_int2ext = nullptr;
     // forward work
     d4 *xa = nullptr, *va = nullptr, *xb = nullptr, *vb = nullptr, *v = nullptr, *b = nullptr, *y = nullptr;

@@ -385,6 +385,14 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
     }
 }
 
+// Issues L2 prefetches for [p, p + bytes) (128-byte lines, spread over the CTA),
+// so that a front's blocks stream in from HBM while the CTA gathers its inputs.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const char* c = static_cast<const char*>(p);
+    for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // Column-major matrix-vector product on one CTA: t_i = sum_k A[k * lda + i] v_k for
 // rows i < nrows and k < K (k <= i when tri).  Rows go in passes of GV_ROWS; the
 // k range is cut into G contiguous chunks with G a function of K alone, every
@@ -392,7 +400,7 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
 // rows: coalesced), and a row's partial sums are added in chunk order.  The
 // arithmetic thus depends only on (nrows, K), never on the CTA size, so a front
 // gives the same bits whatever else shares its level.  fin(i, t_i) stores.
-constexpr int GV_ROWS = 64;
+constexpr int GV_ROWS = 128;
 constexpr int GV_MAXG = 8;
 __host__ __device__ constexpr int gv_groups(int K) { return K <= 8 ? 1 : (K + 7) / 8 < GV_MAXG ? (K + 7) / 8 : GV_MAXG; }
 
@@ -441,6 +449,8 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __res
     const int base = 3 * fd.begin[s];
     float* y = w + f;
     float* red = y + f;                // [GV_MAXG][GV_ROWS] partial sums
+    prefetch_l2(X, sizeof(float) * p * p);
+    prefetch_l2(F, sizeof(float) * (size_t)p * f);
     for (int t = tid; t < f; t += nt) w[t] = 0.0f;
     __syncthreads();
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
@@ -475,6 +485,8 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, const int* __res
     float* w = sm;
     float* xu = sm + p;
     const int* un = fd.unode + fd.uptr[s];
+    prefetch_l2(F, sizeof(float) * (size_t)p * f);
+    prefetch_l2(X, sizeof(float) * p * p);
     for (int t = tid; t < p; t += nt) w[t] = fd.zvec[base + t];
     for (int k = tid; k < nu; k += nt) xu[k] = fd.xvec[3 * un[k / 3] + k % 3];
     __syncthreads();

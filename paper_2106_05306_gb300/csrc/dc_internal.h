@@ -111,13 +111,21 @@ void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out);
 
 // ---------------------------------------------------------------- device views
 
+// Supernodal substitution: fronts of at most this many nodes are solved by one
+// warp each, larger ones by a whole CTA.
+constexpr int DC_PS_SMALL = 64;
+
 // Device view of the supernodal substitution (global_solver 1): the front
 // partition (node-level counts are the fronts' DOF counts / 3) and the panels.
 struct PSolveDev {
     int nlev;
-    const int* lvl_ptr_h;              // host: fronts of level l are lvl_sn[lvl_ptr_h[l] .. lvl_ptr_h[l+1])
-    const int* lvl_maxf_h;             // host: largest front of level l (nodes)
-    const int* lvl_sn;
+    // level l's fronts are sn[lvl_ptr_h[l] ..): first nbig_h[l] large ones (CTA
+    // path, the largest maxbig_h[l] nodes), then nsmall_h[l] small ones (warp path)
+    const int* lvl_ptr_h;              // host
+    const int* nbig_h;                 // host
+    const int* nsmall_h;               // host
+    const int* maxbig_h;               // host
+    const int* sn;
     const int* begin;
     const int* f;                      // DOFs of the front (3 per node)
     const int* p;

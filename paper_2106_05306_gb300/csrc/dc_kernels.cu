@@ -369,6 +369,14 @@ __global__ void k_solve_bwd(DevMesh dm, DevParams P, const d4* __restrict__ y, d
     finish_row(P, row, s0, s1, s2, out, mode, contact, nb, cc, f, case_, c_out);
 }
 
+// Issues L2 prefetches for [p, p + bytes) (128-byte lines, spread over the CTA),
+// so that a front's blocks stream in from HBM while the CTA gathers its inputs.
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+    const char* c = static_cast<const char*>(p);
+    for (size_t o = (size_t)threadIdx.x * 128; o < bytes; o += (size_t)blockDim.x * 128)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(c + o));
+}
+
 // ---- supernodal substitution (global_solver 1): one CTA per supernode, levels
 // leaves-first for L y = b and root-first for L^T x = y, three right-hand sides.
 // Shared memory holds the front's vectors component-major ([3][n]).
@@ -402,6 +410,7 @@ __device__ __forceinline__ void cm_gemv3(const double* __restrict__ A, long lda,
                 if (tri == 1) k1 = min(k1, i + 1);
                 if (tri == 2) k0 = max(k0, i);
                 const double* a = A + i;
+#pragma unroll 4
                 for (int k = k0; k < k1; ++k) {
                     const double x = a[(long)k * lda];
                     a0 += x * v[k];
@@ -427,15 +436,22 @@ __device__ __forceinline__ void cm_gemv3(const double* __restrict__ A, long lda,
     }
 }
 
-__global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, int lvl_begin, const d4* __restrict__ b,
-                                                d4* __restrict__ y) {
-    extern __shared__ double smd[];
-    const int s = ps.lvl_sn[lvl_begin + blockIdx.x];
+// Fronts of at most PS_SMALL nodes take the warp path: one warp per front,
+// warp-synchronous, sums in plain k order; larger fronts take the CTA path.  A
+// front's path depends only on its own size, so its bits do not depend on what
+// else shares its level.
+constexpr int PS_SMALL = DC_PS_SMALL;
+constexpr int PS_WARPS = 8;    // small fronts per CTA
+
+__device__ __forceinline__ void ps_fwd_cta(const PSolveDev& ps, int s, const d4* __restrict__ b,
+                                           d4* __restrict__ y, double* __restrict__ smd) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
     double* w = smd;                   // [3][fs]
     double* yv = w + 3 * fs;           // [3][ns]
     double* red = yv + 3 * ns;         // [3][GV_MAXG * GV_ROWS]
+    prefetch_l2(ps.xinv + ps.xoff[s], sizeof(double) * ns * ns);
+    prefetch_l2(ps.panel + ps.poff[s], sizeof(double) * fs * ns);
     for (int t = tid; t < 3 * fs; t += nt) w[t] = 0.0;
     __syncthreads();
     for (int q = ps.cptr[s]; q < ps.cptr[s + 1]; ++q) {
@@ -473,19 +489,95 @@ __global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, int lvl_begin, con
     for (int t = tid; t < ns; t += nt) st(y + begin + t, yv[t], yv[ns + t], yv[2 * ns + t]);
 }
 
-__global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, int lvl_begin, const d4* __restrict__ y,
-                                                d4* __restrict__ out, int mode, const int* __restrict__ contact,
-                                                const d4* __restrict__ nb, const double* __restrict__ cc,
-                                                d4* __restrict__ f, int* __restrict__ case_,
-                                                double* __restrict__ c_out) {
+// w: this warp's [3][PS_SMALL] gathered right-hand side, then [3][PS_SMALL] of y_s
+__device__ __forceinline__ void ps_fwd_warp(const PSolveDev& ps, int s, const d4* __restrict__ b,
+                                            d4* __restrict__ y, double* __restrict__ w) {
+    constexpr int L = PS_SMALL;
+    const int lane = threadIdx.x & 31;
+    const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
+    double* yv = w + 3 * L;
+    for (int t = lane; t < fs; t += 32) w[t] = w[L + t] = w[2 * L + t] = 0.0;
+    __syncwarp();
+    for (int q = ps.cptr[s]; q < ps.cptr[s + 1]; ++q) {
+        const int c = ps.child[q];
+        const int nuc = (ps.f[c] - ps.p[c]) / 3;
+        const int* map = ps.cmap + ps.uptr[c];
+        const d4* acc = ps.acc + ps.aoff[c];
+        for (int k = lane; k < nuc; k += 32) {
+            const int pos = map[k];
+            const d4 a = ld(acc + k);
+            w[pos] += a.x;
+            w[L + pos] += a.y;
+            w[2 * L + pos] += a.z;
+        }
+        __syncwarp();
+    }
+    for (int t = lane; t < ns; t += 32) {
+        const d4 a = ld(b + begin + t);
+        w[t] += a.x;
+        w[L + t] += a.y;
+        w[2 * L + t] += a.z;
+    }
+    __syncwarp();
+    const double* X = ps.xinv + ps.xoff[s];
+    for (int i = lane; i < ns; i += 32) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
+        for (int k = 0; k <= i; ++k) {
+            const double x = X[(long)k * ns + i];
+            a0 += x * w[k];
+            a1 += x * w[L + k];
+            a2 += x * w[2 * L + k];
+        }
+        yv[i] = a0;
+        yv[L + i] = a1;
+        yv[2 * L + i] = a2;
+    }
+    __syncwarp();
+    const double* Pn = ps.panel + ps.poff[s] + ns;
+    d4* acc = ps.acc + ps.aoff[s];
+    for (int i = lane; i < nu; i += 32) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < ns; ++k) {
+            const double x = Pn[(long)k * fs + i];
+            a0 += x * yv[k];
+            a1 += x * yv[L + k];
+            a2 += x * yv[2 * L + k];
+        }
+        st(acc + i, w[ns + i] - a0, w[L + ns + i] - a1, w[2 * L + ns + i] - a2);
+    }
+    for (int t = lane; t < ns; t += 32) st(y + begin + t, yv[t], yv[L + t], yv[2 * L + t]);
+}
+
+// Level kernel of L y = b: CTAs [0, n_big) take one large front each, the others
+// PS_WARPS small fronts each (one per warp).
+__global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, const int* __restrict__ big, int n_big,
+                                                const int* __restrict__ small, int n_small,
+                                                const d4* __restrict__ b, d4* __restrict__ y) {
     extern __shared__ double smd[];
-    const int s = ps.lvl_sn[lvl_begin + blockIdx.x];
+    if ((int)blockIdx.x < n_big) {
+        ps_fwd_cta(ps, big[blockIdx.x], b, y, smd);
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    const int q = ((int)blockIdx.x - n_big) * PS_WARPS + warp;
+    if (q < n_small) ps_fwd_warp(ps, small[q], b, y, smd + warp * 6 * PS_SMALL);
+}
+
+__device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams& P, int s, const d4* __restrict__ y,
+                                           d4* __restrict__ out, int mode, const int* __restrict__ contact,
+                                           const d4* __restrict__ nb, const double* __restrict__ cc,
+                                           d4* __restrict__ f, int* __restrict__ case_, double* __restrict__ c_out,
+                                           double* __restrict__ smd) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
     double* w = smd;                   // [3][ns]
     double* xu = w + 3 * ns;           // [3][nu]
     double* red = xu + 3 * nu;         // [3][GV_MAXG * GV_ROWS]
     const int* un = ps.unode + ps.uptr[s];
+    prefetch_l2(ps.pant + ps.toff[s], sizeof(double) * ns * nu);
+    prefetch_l2(ps.xinvt + ps.xoff[s], sizeof(double) * ns * ns);
     for (int t = tid; t < ns; t += nt) {
         const d4 a = ld(y + begin + t);
         w[t] = a.x;
@@ -511,6 +603,80 @@ __global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, int l
         st(ps.xint + row, t0, t1, t2);
         finish_row(P, row, t0, t1, t2, out, mode, contact, nb, cc, f, case_, c_out);
     });
+}
+
+// w: this warp's [3][PS_SMALL] right-hand side, then [3][PS_SMALL] of x_U
+__device__ __forceinline__ void ps_bwd_warp(const PSolveDev& ps, const DevParams& P, int s, const d4* __restrict__ y,
+                                            d4* __restrict__ out, int mode, const int* __restrict__ contact,
+                                            const d4* __restrict__ nb, const double* __restrict__ cc,
+                                            d4* __restrict__ f, int* __restrict__ case_,
+                                            double* __restrict__ c_out, double* __restrict__ w) {
+    constexpr int L = PS_SMALL;
+    const int lane = threadIdx.x & 31;
+    const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
+    double* xu = w + 3 * L;
+    const int* un = ps.unode + ps.uptr[s];
+    for (int t = lane; t < ns; t += 32) {
+        const d4 a = ld(y + begin + t);
+        w[t] = a.x;
+        w[L + t] = a.y;
+        w[2 * L + t] = a.z;
+    }
+    for (int k = lane; k < nu; k += 32) {
+        const d4 a = ld(ps.xint + un[k]);
+        xu[k] = a.x;
+        xu[L + k] = a.y;
+        xu[2 * L + k] = a.z;
+    }
+    __syncwarp();
+    const double* T = ps.pant + ps.toff[s];
+    for (int i = lane; i < ns; i += 32) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
+        for (int k = 0; k < nu; ++k) {
+            const double x = T[(long)k * ns + i];
+            a0 += x * xu[k];
+            a1 += x * xu[L + k];
+            a2 += x * xu[2 * L + k];
+        }
+        w[i] -= a0;
+        w[L + i] -= a1;
+        w[2 * L + i] -= a2;
+    }
+    __syncwarp();
+    const double* XT = ps.xinvt + ps.xoff[s];
+    for (int i = lane; i < ns; i += 32) {
+        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+#pragma unroll 4
+        for (int k = i; k < ns; ++k) {
+            const double x = XT[(long)k * ns + i];
+            a0 += x * w[k];
+            a1 += x * w[L + k];
+            a2 += x * w[2 * L + k];
+        }
+        const int row = begin + i;
+        st(ps.xint + row, a0, a1, a2);
+        finish_row(P, row, a0, a1, a2, out, mode, contact, nb, cc, f, case_, c_out);
+    }
+}
+
+// Level kernel of L^T x = y (and the per-node output): large fronts per CTA, small
+// fronts per warp, as for the forward sweep.
+__global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, const int* __restrict__ big, int n_big,
+                                                const int* __restrict__ small, int n_small, const d4* __restrict__ y,
+                                                d4* __restrict__ out, int mode, const int* __restrict__ contact,
+                                                const d4* __restrict__ nb, const double* __restrict__ cc,
+                                                d4* __restrict__ f, int* __restrict__ case_,
+                                                double* __restrict__ c_out) {
+    extern __shared__ double smd[];
+    if ((int)blockIdx.x < n_big) {
+        ps_bwd_cta(ps, P, big[blockIdx.x], y, out, mode, contact, nb, cc, f, case_, c_out, smd);
+        return;
+    }
+    const int warp = threadIdx.x >> 5;
+    const int q = ((int)blockIdx.x - n_big) * PS_WARPS + warp;
+    if (q < n_small)
+        ps_bwd_warp(ps, P, small[q], y, out, mode, contact, nb, cc, f, case_, c_out, smd + warp * 6 * PS_SMALL);
 }
 
 __global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4* __restrict__ v,
@@ -562,8 +728,14 @@ void launch_gather_rhs(const DevMesh& dm, const DevParams& P, const d4* v_n, con
     k_gather_rhs<<<nblk(dm.m_free, dm.bs_gather), dm.bs_gather, 0, s>>>(dm, P, v_n, c1, c2, bu, f, b);
 }
 namespace {
-int ps_threads(int fs) { return fs <= 64 ? 128 : 256; }
-size_t ps_smem(int fs, int) { return (6 * (size_t)fs + 3 * (size_t)GV_ROWS * GV_MAXG) * sizeof(double); }
+size_t ps_smem(int fs) { return (6 * (size_t)fs + 3 * (size_t)GV_ROWS * GV_MAXG) * sizeof(double); }
+// CTA-path fronts get 128 threads up to 96 nodes, else 256; the warp path needs 256
+int ps_threads(int big_fs, int n_small) { return (n_small > 0 || big_fs > 96) ? 256 : 128; }
+size_t ps_level_smem(int big_fs, int n_small) {
+    const size_t a = big_fs > 0 ? ps_smem(big_fs) : 0;
+    const size_t b = n_small > 0 ? (size_t)PS_WARPS * 6 * PS_SMALL * sizeof(double) : 0;
+    return a > b ? a : b;
+}
 }  // namespace
 
 // The level kernels' dynamic shared-memory limit is shared by every context of
@@ -572,7 +744,7 @@ cudaError_t psolve_configure(int max_fs) {
     static std::mutex mu;
     static size_t configured = 48 * 1024;
     std::lock_guard<std::mutex> lock(mu);
-    const size_t need = ps_smem(max_fs, ps_threads(max_fs));
+    const size_t need = ps_level_smem(max_fs, 1);
     if (need <= configured) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_ps_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ps_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
@@ -584,11 +756,13 @@ void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
     if (dm.solver == 1) {
         const PSolveDev& ps = dm.ps;
         for (int l = 0; l < ps.nlev; ++l) {
-            const int cnt = ps.lvl_ptr_h[l + 1] - ps.lvl_ptr_h[l];
-            if (cnt <= 0) continue;
-            const int fs = ps.lvl_maxf_h[l], nt = ps_threads(fs);
+            const int nb = ps.nbig_h[l], nsm = ps.nsmall_h[l];
+            if (nb + nsm <= 0) continue;
+            const int* big = ps.sn + ps.lvl_ptr_h[l];
+            const int grid = nb + (nsm + PS_WARPS - 1) / PS_WARPS;
             dc_note_launch();
-            k_ps_fwd<<<cnt, nt, ps_smem(fs, nt), s>>>(ps, ps.lvl_ptr_h[l], b, y);
+            k_ps_fwd<<<grid, ps_threads(ps.maxbig_h[l], nsm), ps_level_smem(ps.maxbig_h[l], nsm), s>>>(
+                ps, big, nb, big + nb, nsm, b, y);
         }
         return;
     }
@@ -600,12 +774,13 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
     if (dm.solver == 1) {
         const PSolveDev& ps = dm.ps;
         for (int l = ps.nlev - 1; l >= 0; --l) {
-            const int cnt = ps.lvl_ptr_h[l + 1] - ps.lvl_ptr_h[l];
-            if (cnt <= 0) continue;
-            const int fs = ps.lvl_maxf_h[l], nt = ps_threads(fs);
+            const int nbg = ps.nbig_h[l], nsm = ps.nsmall_h[l];
+            if (nbg + nsm <= 0) continue;
+            const int* big = ps.sn + ps.lvl_ptr_h[l];
+            const int grid = nbg + (nsm + PS_WARPS - 1) / PS_WARPS;
             dc_note_launch();
-            k_ps_bwd<<<cnt, nt, ps_smem(fs, nt), s>>>(ps, P, ps.lvl_ptr_h[l], y, out, mode, contact, nb, c, f,
-                                                      case_, c_out);
+            k_ps_bwd<<<grid, ps_threads(ps.maxbig_h[l], nsm), ps_level_smem(ps.maxbig_h[l], nsm), s>>>(
+                ps, P, big, nbg, big + nbg, nsm, y, out, mode, contact, nb, c, f, case_, c_out);
         }
         return;
     }

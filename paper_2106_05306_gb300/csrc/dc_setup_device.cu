@@ -454,8 +454,35 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
             (s = dalloc(c, F, &d_acc, (size_t)std::max<long long>(pp.ps.acc_nodes, 1))) ||
             (s = dalloc(c, F, &d_xint, (size_t)std::max(MF, 1))))
             return s;
+        // per level: the large fronts (CTA path) first, then the small ones (warp path)
+        std::vector<int> psn(frm.S);
+        const int nl = (int)frm.lvl_ptr.size() - 1;
+        c->ps_lvl_ptr.assign(nl + 1, 0);
+        c->ps_nbig.assign(nl, 0);
+        c->ps_nsmall.assign(nl, 0);
+        c->ps_maxbig.assign(nl, 0);
+        int pos = 0;
+        for (int l = 0; l < nl; ++l) {
+            c->ps_lvl_ptr[l] = pos;
+            for (int q = frm.lvl_ptr[l]; q < frm.lvl_ptr[l + 1]; ++q) {
+                const int sn = frm.lvl_sn[q], fsn = frm.f[sn] / 3;
+                if (fsn > DC_PS_SMALL) {
+                    psn[pos++] = sn;
+                    c->ps_maxbig[l] = std::max(c->ps_maxbig[l], fsn);
+                }
+            }
+            c->ps_nbig[l] = pos - c->ps_lvl_ptr[l];
+            for (int q = frm.lvl_ptr[l]; q < frm.lvl_ptr[l + 1]; ++q) {
+                const int sn = frm.lvl_sn[q];
+                if (frm.f[sn] / 3 <= DC_PS_SMALL) psn[pos++] = sn;
+            }
+            c->ps_nsmall[l] = pos - c->ps_lvl_ptr[l] - c->ps_nbig[l];
+        }
+        c->ps_lvl_ptr[nl] = pos;
+        int* d_psn;
+        if ((s = upload(c, F, &d_psn, psn))) return s;
         PSolveDev& ps = dm.ps;
-        ps.lvl_sn = d_lvl;
+        ps.sn = d_psn;
         ps.begin = d_begin;
         ps.f = d_f;
         ps.p = d_p;
@@ -497,10 +524,12 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     for (size_t l = 0; l < c->lvl_maxf.size(); ++l) c->lvl_maxfs[l] = c->lvl_maxf[l] / 3;
     if (dm.solver == 1) {
         dm.ps.nlev = c->nlev;
-        dm.ps.lvl_ptr_h = c->fr.lvl_ptr.data();
-        dm.ps.lvl_maxf_h = c->lvl_maxfs.data();
+        dm.ps.lvl_ptr_h = c->ps_lvl_ptr.data();
+        dm.ps.nbig_h = c->ps_nbig.data();
+        dm.ps.nsmall_h = c->ps_nsmall.data();
+        dm.ps.maxbig_h = c->ps_maxbig.data();
         int mx = 0;
-        for (int v : c->lvl_maxfs) mx = std::max(mx, v);
+        for (int v : c->ps_maxbig) mx = std::max(mx, v);
         CK(psolve_configure(mx));
     }
     {
@@ -570,6 +599,7 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     if (q.global_solver == 1) {
         add(vbytes(pp.ps.poff)); add(vbytes(pp.ps.xoff)); add(vbytes(pp.ps.toff)); add(vbytes(pp.ps.aoff));
         add(vbytes(pp.ps.panel)); add(vbytes(pp.ps.xinv)); add(vbytes(pp.ps.pant)); add(vbytes(pp.ps.xinvt));
+        add(vbytes(pp.ps.aoff));
         add((size_t)pp.ps.acc_nodes * d4b); add(MF * d4b);
     }
     // checkpoints, segment recomputation, adjoint
