@@ -70,7 +70,7 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None},
            # k_ps_fwd: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
            # profiles/k_ps_fwd_batched_96cloths.md), scaled by the sweep's flops
-           "ps_solve_fwd": {"bytes_per_flop": 140359680.0 / 62559690.0, "source_sha": "861a24732cf079b0"}}
+           "ps_solve_fwd": {"bytes_per_flop": (155440640.0 + 59392.0) / 62559690.0, "source_sha": "42369b81075ae49c"}}
 
 
 def parse_args(argv=None):

@@ -76,18 +76,19 @@ def test_batch_forward_and_adjoint_match_oracle_and_alone():
     assert n_contacts > 0
 
 
-def test_batch_graphs_and_autotune_change_no_bit():
+@pytest.mark.parametrize("solver", [0, 1])
+def test_batch_graphs_and_autotune_change_no_bit(solver):
     import torch
     scs = _mixed_scenes()[:3]
     rng = np.random.default_rng(8)
     gvs = [0.3 * rng.standard_normal((s.m, 3)) for s in scs]
-    ref = make_batch(scs, checkpoint_every=2)
+    ref = make_batch(scs, checkpoint_every=2, global_solver=solver)
     want = _run_batch(ref, scs, 5, gvs)
     ref.close()
     # graphs need a capturable (non-default) stream
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
-        b = make_batch(scs, checkpoint_every=2)
+        b = make_batch(scs, checkpoint_every=2, global_solver=solver)
         b.set_graphs(True)
         b.autotune()
         got = _run_batch(b, scs, 5, gvs)
