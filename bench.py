@@ -354,10 +354,11 @@ def single_side_run(args, dev):
             "nonconverged_cloth_steps": st["adj_nonconverged"]}
 
 
-def served_side_run(dev, n_req=32, rate=6.0, slots=8, seed0=10000):
-    """A short served run: n_req requests (1k-30k DOF, 25-150 steps, random sphere +
-    ground, mu 0.1-0.6) with Poisson arrivals at `rate` per second into the request
-    server; then the same requests one at a time through the plain path."""
+def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=16, seed0=10000):
+    """Served runs: n_req requests (1k-30k DOF, 25-150 steps, random sphere + ground,
+    mu 0.1-0.6) with Poisson arrivals into the request server, one run per arrival
+    rate; then the same requests one at a time through the plain path.  The served
+    value is the best throughput of the sweep (the server saturated)."""
     import threading
 
     import torch
@@ -365,28 +366,33 @@ def served_side_run(dev, n_req=32, rate=6.0, slots=8, seed0=10000):
     import paper_2106_05306_gb300 as dc
     import scenes
     reqs = [scenes.serve_request(seed0 + i) for i in range(n_req)]
-    rng = np.random.default_rng(4242)
-    gaps = rng.exponential(1.0 / rate, n_req)
-    srv = dc.Server(n_slots=slots, n_prep_threads=4, device=dev.index or 0)
-    tickets = [None] * n_req
-
-    def producer():
-        for i, sc in enumerate(reqs):
-            time.sleep(gaps[i])
-            tickets[i] = srv.submit(sc.rest_pos, sc.tris, sc.pins, sc.x0, sc.v0, sc.loss_w, sc.n_steps,
-                                    scene_kw(sc, checkpoint_every=1))
-
-    t0 = time.perf_counter()
-    th = threading.Thread(target=producer)
-    th.start()
-    th.join()
-    res = [srv.wait(t) for t in tickets]
-    makespan = time.perf_counter() - t0
-    st = srv.stats()
-    srv.close()
-    lat = sorted(r["t_done"] - r["t_submit"] for r in res)
     steps = sum(sc.n_steps for sc in reqs)
-    ok = sum(r["status"] in ("DC_OK", "DC_ERR_NONCONVERGED") for r in res)
+    sweep = []
+    for rate in rates:
+        rng = np.random.default_rng(4242)
+        gaps = rng.exponential(1.0 / rate, n_req)
+        srv = dc.Server(n_slots=slots, n_prep_threads=4, device=dev.index or 0)
+        tickets = [None] * n_req
+
+        def producer():
+            for i, sc in enumerate(reqs):
+                time.sleep(gaps[i])
+                tickets[i] = srv.submit(sc.rest_pos, sc.tris, sc.pins, sc.x0, sc.v0, sc.loss_w, sc.n_steps,
+                                        scene_kw(sc, checkpoint_every=1))
+
+        t0 = time.perf_counter()
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        res = [srv.wait(t) for t in tickets]
+        makespan = time.perf_counter() - t0
+        st = srv.stats()
+        srv.close()
+        lat = sorted(r["t_done"] - r["t_submit"] for r in res)
+        ok = sum(r["status"] in ("DC_OK", "DC_ERR_NONCONVERGED") for r in res)
+        sweep.append({"rate_per_s": rate, "value": steps / makespan, "completed": ok,
+                      "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
+                      "peak_in_flight": st["peak_in_flight"], "peak_reserved_gb": st["peak_bytes_reserved"] / 1e9})
     # the same requests one at a time (plain path, no server)
     stream = torch.cuda.Stream(dev)
     plain_s = 0.0
@@ -402,14 +408,15 @@ def served_side_run(dev, n_req=32, rate=6.0, slots=8, seed0=10000):
             torch.cuda.synchronize()
             plain_s += time.perf_counter() - t
             c.close()
-    return {"value": steps / makespan, "unit": UNIT, "requests": n_req, "completed": ok,
-            "arrivals": f"Poisson, {rate}/s", "slots": slots,
-            "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
-            "peak_in_flight": st["peak_in_flight"], "peak_reserved_gb": st["peak_bytes_reserved"] / 1e9,
+    best = max(sweep, key=lambda r: r["value"])
+    return {"value": best["value"], "unit": UNIT, "requests": n_req, "slots": slots,
+            "p50_latency_s": best["p50_latency_s"], "p99_latency_s": best["p99_latency_s"],
+            "at_rate_per_s": best["rate_per_s"], "rate_sweep": sweep,
             "plain_sequential": {"value": steps / plain_s, "unit": UNIT,
                                  "note": "same requests one at a time, setup excluded"},
             "workload": "requests of 1k-30k DOF (log-uniform), 25-150 steps, random sphere + ground, "
-                        "fwd + adjoint, all steps recorded; makespan from first arrival to last result"}
+                        "fwd + adjoint, all steps recorded; Poisson arrivals; throughput = steps / makespan "
+                        "from the first arrival to the last result"}
 
 
 def run_ours(args):

@@ -421,6 +421,7 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
     std::vector<double> sc(B, 0.0), yv;
     CK(cudaMemcpyAsync(c->r1, c->rhs, sizeof(d4) * m, cudaMemcpyDeviceToDevice, s));
     const bool debug = std::getenv("DC_DEBUG_GMRES") != nullptr;
+    const long long lock0 = c->adj_batch_iters;
     for (int cycle = 0;; ++cycle) {
         RET(bdot_host(c, rr, rr, nrm));
         bool active = false;
@@ -580,6 +581,12 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
         for (int i = 0; i < B; ++i) gs[i].used = 0;
     }
     c->act_on = false;
+    if (debug && std::getenv("DC_DEBUG_GMRES")[0] == '2') {
+        int mx = 0;
+        for (int i = 0; i < B; ++i) mx = std::max(mx, gs[i].total);
+        std::fprintf(stderr, "[dc gmres] step: %lld lockstep iterations, largest instance total %d\n",
+                     c->adj_batch_iters - lock0, mx);
+    }
     for (int i = 0; i < B; ++i) {
         iters[i] = gs[i].total;
         rel[i] = gs[i].beta0 > 0.0 ? gs[i].res / gs[i].beta0 : 0.0;
