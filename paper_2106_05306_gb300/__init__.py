@@ -298,6 +298,21 @@ class ClothBatch(_Context):
         self.params = [b[1] for b in built]
         return self
 
+    def set_theta(self, theta):
+        """Per-instance differentiable parameters, shape (n_instances, 3) = (k_stretch,
+        k_bend, mu); refactorises when they change."""
+        th = [tuple(float(v) for v in row) for row in np.asarray(theta, dtype=np.float64).reshape(-1, 3)]
+        if len(th) != self.n_instances:
+            raise ValueError(f"theta: expected {self.n_instances} x 3 values")
+        cur = [(q["k_stretch"], q["k_bend"], q["mu"]) for q in self.params]
+        if th != cur:
+            kws = []
+            for q, (ks, kb, mu) in zip(self.params, th):
+                kw = dict(q)
+                kw.update(k_stretch=ks, k_bend=kb, mu=mu)
+                kws.append(kw)
+            self.set_params(kws)
+
     def backward(self, dL_dx, dL_dv=None, dL_dtraj=None, allow_nonconverged=False):
         return self._backward(dL_dx, dL_dv, dL_dtraj, allow_nonconverged, (self.n_instances, 3))
 
@@ -384,8 +399,11 @@ def _rollout_function():
 
         @staticmethod
         def forward(ctx, cloth, n_steps, x0, v0, theta):
-            th = theta.detach().cpu().tolist()
-            cloth.set_theta(*th)
+            th = theta.detach().cpu()
+            if isinstance(cloth, ClothBatch):
+                cloth.set_theta(th.numpy())
+            else:
+                cloth.set_theta(*th.tolist())
             xN, vN = cloth.rollout(x0.detach(), v0.detach(), n_steps)
             ctx.cloth = cloth
             ctx.theta_device = theta.device
@@ -406,8 +424,10 @@ def _rollout_function():
 _FN = None
 
 
-def rollout_fn(cloth: Cloth, x0, v0, theta, n_steps: int):
-    """Differentiable rollout: returns (x_N, v_N); gradients flow to x0, v0 and theta."""
+def rollout_fn(cloth, x0, v0, theta, n_steps: int):
+    """Differentiable rollout: returns (x_N, v_N); gradients flow to x0, v0 and theta.
+    For a Cloth theta is (k_stretch, k_bend, mu); for a ClothBatch it is one such
+    row per instance, shape (n_instances, 3), and x0 / v0 are concatenated."""
     global _FN
     if _FN is None:
         _FN = _rollout_function()

@@ -128,3 +128,23 @@ def test_batch_parameter_checks():
     with pytest.raises(dc.DCError, match="DC_ERR_INVALID"):
         batch.set_params([params_kw(scs[0])] * 3)
     batch.close()
+
+
+def test_batch_autograd_function_matches_backward():
+    """rollout_fn over a ClothBatch: per-instance theta (B, 3) gets each instance's
+    dL/d(k_stretch, k_bend, mu), equal to dc_backward's."""
+    import torch
+    import paper_2106_05306_gb300 as dc
+    scs = _mixed_scenes()[:3]
+    b = make_batch(scs, checkpoint_every=1)
+    x0 = _cat([s.x0 for s in scs]).requires_grad_(True)
+    v0 = _cat([s.v0 for s in scs]).requires_grad_(True)
+    th = torch.tensor([[s.params.k_stretch, s.params.k_bend, s.params.mu] for s in scs], dtype=torch.float64,
+                      requires_grad=True)
+    xi = _cat([s.loss_w for s in scs])
+    xN, vN = dc.rollout_fn(b, x0, v0, th, 3)
+    gx0, gv0, gth = torch.autograd.grad((xN * xi).sum(), (x0, v0, th))
+    b.rollout(x0.detach(), v0.detach(), 3)
+    dx0, dv0, dth = b.backward(xi)
+    b.close()
+    assert torch.equal(gx0, dx0) and torch.equal(gv0, dv0) and torch.equal(gth, dth.cpu())

@@ -85,3 +85,29 @@ def test_server_hbm_budget_bounds_admission():
     r = srv.wait(srv.submit(sc.rest_pos, sc.tris, sc.pins, sc.x0, sc.v0, sc.loss_w, sc.n_steps, kw))
     srv.close()
     assert r["status"] == "DC_ERR_OOM" and r["slot"] == -1
+
+
+def test_server_bad_request_fails_alone():
+    """A request with an out-of-range triangle index fails with DC_ERR_INVALID; the
+    requests around it still finish with the same results as alone."""
+    import paper_2106_05306_gb300 as dc
+    reqs = _requests()[:3]
+    srv = dc.Server(n_slots=2, n_prep_threads=2)
+    t_ok1 = _submit_all(srv, reqs[:1])[0]
+    sc, gv, kw = reqs[1]
+    bad_tris = sc.tris.copy()
+    bad_tris[0, 0] = sc.m + 5
+    t_bad = srv.submit(sc.rest_pos, bad_tris, sc.pins, sc.x0, sc.v0, sc.loss_w, sc.n_steps, kw)
+    t_ok2 = _submit_all(srv, reqs[2:3])[0]
+    r1, rb, r2 = srv.wait(t_ok1), srv.wait(t_bad), srv.wait(t_ok2)
+    st = srv.stats()
+    srv.close()
+    assert rb["status"] == "DC_ERR_INVALID" and rb["slot"] == -1, rb
+    assert r1["status"] == "DC_OK" and r2["status"] == "DC_OK"
+    assert st["failed"] == 1 and st["completed"] == 2
+    for (sc, gv, kw), r in ((reqs[0], r1), (reqs[2], r2)):
+        cl = make_cloth(sc, checkpoint_every=2)
+        xN, _ = cl.rollout(cuda(sc.x0), cuda(sc.v0), sc.n_steps)
+        dx0, _, _ = cl.backward(cuda(sc.loss_w), cuda(gv))
+        cl.close()
+        assert np.array_equal(r["x_final"], xN.cpu().numpy()) and np.array_equal(r["dL_dx0"], dx0.cpu().numpy())
