@@ -68,9 +68,10 @@ FP64_PEAK_TFLOPS = 1.25
 # DRAM traffic per launch of the roofline kernel from the ncu capture summarised in
 # profiles/ (null when the kernel source changed since the capture).
 TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None},
-           # k_ps_fwd: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
-           # profiles/k_ps_fwd_batched_96cloths.md), scaled by the sweep's flops
-           "ps_solve_fwd": {"bytes_per_flop": (155440640.0 + 59392.0) / 62559690.0, "source_sha": "42369b81075ae49c"}}
+           # k_ps_fwd_tree: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
+           # profiles/k_ps_fwd_tree_batched_96cloths.md), scaled by the sweep's flops
+           "ps_solve_fwd": {"bytes_per_flop": (132945920.0 + 11691008.0) / 62559690.0,
+                            "source_sha": "0c6de9d063ed26e7"}}
 
 
 def parse_args(argv=None):
@@ -524,9 +525,9 @@ def roofline(cls, st):
             roof["traffic"] = tr["bytes"]
     elif st.get("global_solver", 0) == 1:
         work = st["psolve_flops"]                         # exact count of one sweep, 3 right-hand sides
-        name = "k_ps_fwd" if cls == "solve_fwd" else "k_ps_bwd"
-        roof = {"kernel": f"{name} (P^-1 sweep, level-scheduled supernodal substitution, FP64, 3 right-hand sides; "
-                          f"one launch here = the {st['front_levels']} level launches of one sweep)",
+        name = "k_ps_fwd_tree" if cls == "solve_fwd" else "k_ps_bwd_tree"
+        roof = {"kernel": f"{name} (P^-1 sweep, supernodal substitution, FP64, 3 right-hand sides; one launch per "
+                          f"sweep, fronts of the {st['front_levels']}-level trees taken in dependency order)",
                 "bound": "alu", "achieved": work / (kern_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 table of the profiling recipe)",
                 "traffic": None, "algorithmic_flops_per_launch": work}
@@ -535,7 +536,7 @@ def roofline(cls, st):
         if tr and tr["source_sha"] == kernel_sha(src):
             roof["traffic"] = tr["bytes_per_flop"] * work
             roof["traffic_note"] = ("DRAM read+write of one sweep measured by ncu on 96 cloths, scaled to this "
-                                    "sweep by its flops (profiles/k_ps_fwd_batched_96cloths.md)")
+                                    "sweep by its flops (profiles/k_ps_fwd_tree_batched_96cloths.md)")
     else:
         nnz = st["fwd_solve_nnz"] if cls == "solve_fwd" else st["bwd_solve_nnz"]
         work = 6.0 * nnz                                  # 3 right-hand sides: one FMA each per nonzero

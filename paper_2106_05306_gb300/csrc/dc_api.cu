@@ -44,7 +44,7 @@ dc_status finish_create(dc_ctx* c, dc_ctx** out, void* stream) {
 dc_status apply_params(dc_ctx* c, std::vector<dc_params> q) {
     ParamPrep pp;
     RET(prep_params_host(c, std::move(q), pp));
-    CK(cudaStreamSynchronize(c->stream));   // earlier work may still read the old factor
+    CK(ctx_sync(c, c->stream));   // earlier work may still read the old factor
     return upload_params(c, pp);
 }
 
@@ -181,7 +181,7 @@ dc_status dc_step(dc_ctx* c, const double* x_n, const double* v_n, double* x_np1
     RET(store_vec(c, c->xb, x_np1, host_io));
     RET(store_vec(c, c->vb, v_np1, host_io));
     CK(cudaGetLastError());
-    if (host_io) CK(cudaStreamSynchronize(c->stream));
+    if (host_io) CK(ctx_sync(c, c->stream));
     return DC_OK;
 }
 
@@ -245,7 +245,22 @@ dc_status dc_rollout(dc_ctx* c, int32_t n_steps, const double* x0, const double*
     CK(cudaGetLastError());
     c->ck_n_steps = n_steps;
     c->ck_every = k;
-    if (host_io) CK(cudaStreamSynchronize(c->stream));
+    if (host_io) CK(ctx_sync(c, c->stream));
+    return DC_OK;
+}
+
+// The tree-scheduled sweeps' sticky fault word (counters[3]) is set when a
+// dependency wait gave up; every result computed since is invalid.  Call with
+// the stream idle.
+static dc_status check_sweep_fault(dc_ctx* c) {
+    if (!c->counters || c->dm.solver != 1) return DC_OK;
+    unsigned long long w = 0;
+    CK(cudaMemcpyAsync(&w, c->counters + 3, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+    CK(ctx_sync(c, c->stream));
+    if (w) {
+        c->err = "supernodal sweep: a dependency wait timed out; results since then are invalid";
+        return DC_ERR_CUDA;
+    }
     return DC_OK;
 }
 
@@ -336,11 +351,12 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
                              B, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
         host_io |= !dev;
     }
-    CK(cudaStreamSynchronize(s));
-    if (c->stream2) CK(cudaStreamSynchronize(c->stream2));
+    CK(ctx_sync(c, s));
+    if (c->stream2) CK(ctx_sync(c, c->stream2));
     free_pool(c, tmp);
     CK(cudaGetLastError());
     if (st) return st;
+    RET(check_sweep_fault(c));
     if (noncv) {
         c->err = "dc_backward: an adjoint step reached adj_max_iters above adj_tol";
         return DC_ERR_NONCONVERGED;
@@ -365,16 +381,16 @@ dc_status dc_global_solve(dc_ctx* c, const double* rhs, double* out) {
     launch_solve_bwd(c->dm, c->dp, c->y, c->v, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, c->stream);
     RET(store_vec(c, c->v, out, host_io));
     CK(cudaGetLastError());
-    if (host_io) CK(cudaStreamSynchronize(c->stream));
+    if (host_io) CK(ctx_sync(c, c->stream));
     return DC_OK;
 }
 
 dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     if (!c || !o) return DC_ERR_INVALID;
-    CK(cudaStreamSynchronize(c->stream));
+    CK(ctx_sync(c, c->stream));
     unsigned long long cnt[4] = {0, 0, 0, 0};
     CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(ctx_sync(c, c->stream));
     std::memset(o, 0, sizeof(*o));
     o->steps = c->steps;
     o->contacts_takeoff = (int64_t)cnt[0];
@@ -410,6 +426,10 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->adj_batch_iters = c->adj_batch_iters;
     o->global_solver = c->dm.solver;
     o->psolve_flops = c->psolve_flops;
+    if (cnt[3] && c->dm.solver == 1) {
+        c->err = "supernodal sweep: a dependency wait timed out; results since then are invalid";
+        return DC_ERR_CUDA;
+    }
     return DC_OK;
 }
 
@@ -429,15 +449,15 @@ dc_status dc_set_kernel_timer(dc_ctx* c, int32_t kernel_class) {
 
 dc_status dc_sync(dc_ctx* c) {
     if (!c) return DC_ERR_INVALID;
-    CK(cudaStreamSynchronize(c->stream));
+    CK(ctx_sync(c, c->stream));
     CK(cudaGetLastError());
-    return DC_OK;
+    return check_sweep_fault(c);
 }
 
 void dc_destroy(dc_ctx* c) {
     if (!c) return;
-    cudaStreamSynchronize(c->stream);
-    if (c->stream2) cudaStreamSynchronize(c->stream2);
+    ctx_sync(c, c->stream);
+    if (c->stream2) ctx_sync(c, c->stream2);
     c->kt.release();
     c->kt2.release();
     for (int k = 0; k < 2; ++k) {
@@ -445,6 +465,7 @@ void dc_destroy(dc_ctx* c) {
         if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
     }
     if (c->ev_seg) cudaEventDestroy(c->ev_seg);
+    if (c->ev_block) cudaEventDestroy(c->ev_block);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     GraphCache* gcs[] = {&c->g_roll, &c->g_seg[0], &c->g_seg[1]};
     for (GraphCache* g : gcs)
@@ -460,7 +481,7 @@ void dc_destroy(dc_ctx* c) {
     if (c->hpin && !c->hpin_external) cudaFreeHost(c->hpin);
     if (c->h_act_sn) cudaFreeHost(c->h_act_sn);
     if (c->h_act_ch) cudaFreeHost(c->h_act_ch);
-    if (c->async_alloc) cudaStreamSynchronize(c->stream);
+    if (c->async_alloc) ctx_sync(c, c->stream);
     delete c;
 }
 

@@ -66,6 +66,8 @@ struct dc_ctx {
     std::vector<int> h_cptr;       // host copy of sg.cptr
     Pool mesh_allocs, factor_allocs, work_allocs, ck_allocs, seg_allocs, adj_allocs, front_allocs;
     bool async_alloc = false;      // stream-ordered allocation on `stream` (contexts of the request server)
+    bool blocking_sync = false;    // waits block the thread instead of spinning (contexts of the request server)
+    cudaEvent_t ev_block = nullptr;
     size_t dev_bytes = 0, dev_peak = 0;   // device bytes held now / at most
     HostFronts fr;
     FrontDev fdv{};
@@ -151,6 +153,20 @@ struct dc_ctx {
         if (s_ != DC_OK) return s_; \
     } while (0)
 
+// Waits for the work queued on s so far.  With blocking_sync the thread sleeps
+// on an event created with cudaEventBlockingSync instead of spinning, so that
+// the request server's many slot threads leave the host's cores to the threads
+// preparing the next requests.
+inline cudaError_t ctx_sync(dc_ctx* c, cudaStream_t s) {
+    if (!c->blocking_sync) return cudaStreamSynchronize(s);
+    if (!c->ev_block) {
+        cudaError_t e = cudaEventCreateWithFlags(&c->ev_block, cudaEventBlockingSync | cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaEventRecord(c->ev_block, s);
+    return e != cudaSuccess ? e : cudaEventSynchronize(c->ev_block);
+}
+
 // Allocates count T's (zeroed unless zero = false) into pool.  With
 // async_alloc the memory comes from the device's stream-ordered pool on the
 // context's stream, so that a context being set up does not synchronise the
@@ -187,7 +203,7 @@ dc_status upload(dc_ctx* c, Pool& pool, T** p, const std::vector<T>& h) {
         if (c->async_alloc) {
             // h is pageable and may die after the return: wait for the copy
             CK(cudaMemcpyAsync(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, c->stream));
-            CK(cudaStreamSynchronize(c->stream));
+            CK(ctx_sync(c, c->stream));
         } else {
             CK(cudaMemcpy(*p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
         }

@@ -365,7 +365,7 @@ dc_status bdot_host(dc_ctx* c, const double* a, const double* b, std::vector<dou
     adj_bdot(c->sg, a, 0, 1, b, c->partial, c->dnorm, c->stream);
     c->kt.end(DC_KT_KRYLOV);
     CK(cudaMemcpyAsync(c->hpin, c->dnorm, sizeof(double) * c->B, cudaMemcpyDeviceToHost, c->stream));
-    CK(cudaStreamSynchronize(c->stream));
+    CK(ctx_sync(c, c->stream));
     out.assign(c->hpin, c->hpin + c->B);
     return DC_OK;
 }
@@ -373,7 +373,7 @@ dc_status bdot_host(dc_ctx* c, const double* a, const double* b, std::vector<dou
 dc_status upload_scale(dc_ctx* c, const std::vector<double>& sc) {
     double* h = c->hpin + 3 * (size_t)(c->adj_restart_cap + 1) * c->B;
     // the previous upload from this buffer must have been consumed
-    CK(cudaStreamSynchronize(c->stream));
+    CK(ctx_sync(c, c->stream));
     std::memcpy(h, sc.data(), sizeof(double) * c->B);
     CK(cudaMemcpyAsync(c->dscale, h, sizeof(double) * c->B, cudaMemcpyHostToDevice, c->stream));
     return DC_OK;
@@ -489,7 +489,7 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
             CK(cudaMemcpyAsync(h1, c->dcoef, sizeof(double) * (j + 1) * B, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(h2, c->dcoef2, sizeof(double) * (j + 1) * B, cudaMemcpyDeviceToHost, s));
             CK(cudaMemcpyAsync(hn_all, c->dnorm, sizeof(double) * B, cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
+            CK(ctx_sync(c, s));
             bool still = false;
             for (int i = 0; i < B; ++i) {
                 GState& g = gs[i];
@@ -544,7 +544,7 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
         }
         // z += sum_j Zb_j y_j per instance (columns past an instance's own count are 0)
         double* hy = c->hpin;
-        CK(cudaStreamSynchronize(s));
+        CK(ctx_sync(c, s));
         std::memset(hy, 0, sizeof(double) * (size_t)jmax * B);
         for (int i = 0; i < B; ++i) {
             const GState& g = gs[i];
@@ -667,7 +667,7 @@ dc_status autotune(dc_ctx* c) {
         CK(cudaMemsetAsync(c->va, 0, sizeof(d4) * m, s));
         CK(cudaMemsetAsync(c->v, 0, sizeof(d4) * m, s));
         CK(cudaMemsetAsync(c->scratch.f, 0, sizeof(d4) * c->hm.m_free, s));
-        CK(cudaStreamSynchronize(s));
+        CK(ctx_sync(c, s));
     }
     AdjDev ad = c->ads[0];
     ad.h = c->prm.h;
@@ -716,7 +716,7 @@ dc_status autotune(dc_ctx* c) {
     pick(&dm.bs_elem, [&]() { adj_apply_H(dm, ad, 0, c->v, nullptr, c->wv, s); });
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    CK(cudaStreamSynchronize(s));
+    CK(ctx_sync(c, s));
     CK(cudaGetLastError());
     c->graph_epoch++;
     return DC_OK;

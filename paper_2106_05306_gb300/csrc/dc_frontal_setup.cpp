@@ -272,3 +272,34 @@ void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out) {
     }
     out.acc_nodes = ao;
 }
+
+// Work items of the tree-scheduled sweeps, in a topological order (every front
+// after its children): fronts farther from their root come first, so the longest
+// remaining chains start earliest.  A front of more than DC_PS_SMALL nodes is an
+// item alone (one CTA); smaller fronts of equal depth go up to DC_PS_WARPS to an
+// item (one warp each).  Item q is tq_sn[tq_ptr[q] .. tq_ptr[q + 1]).
+void dc_build_tree_items(const HostFronts& fr, std::vector<int>& tq_ptr, std::vector<int>& tq_sn) {
+    std::vector<int> depth(fr.S, 0), order(fr.S);
+    for (int s = 0; s < fr.S; ++s) {
+        order[s] = s;
+        for (int a = fr.parent[s]; a >= 0; a = fr.parent[a]) depth[s]++;
+    }
+    auto large = [&](int s) { return fr.f[s] / 3 > DC_PS_SMALL; };
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        if (depth[a] != depth[b]) return depth[a] > depth[b];
+        return large(a) && !large(b);
+    });
+    tq_ptr.assign(1, 0);
+    tq_sn.clear();
+    for (size_t k = 0; k < order.size();) {
+        const int s = order[k];
+        if (large(s)) {
+            tq_sn.push_back(s);
+            ++k;
+        } else {
+            for (int n = 0; k < order.size() && n < DC_PS_WARPS && !large(order[k]) && depth[order[k]] == depth[s]; ++n)
+                tq_sn.push_back(order[k++]);
+        }
+        tq_ptr.push_back((int)tq_sn.size());
+    }
+}

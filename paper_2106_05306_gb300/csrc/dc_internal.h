@@ -108,12 +108,16 @@ struct HostPSolve {
 };
 void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps);
 void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out);
+// Work items of the tree-scheduled sweeps (see PSolveDev::tq_ptr)
+void dc_build_tree_items(const HostFronts& fr, std::vector<int>& tq_ptr, std::vector<int>& tq_sn);
 
 // ---------------------------------------------------------------- device views
 
 // Supernodal substitution: fronts of at most this many nodes are solved by one
 // warp each, larger ones by a whole CTA.
 constexpr int DC_PS_SMALL = 64;
+// small fronts solved together by one CTA (one per warp)
+constexpr int DC_PS_WARPS = 8;
 
 // Device view of the supernodal substitution (global_solver 1): the front
 // partition (node-level counts are the fronts' DOF counts / 3) and the panels.
@@ -144,6 +148,18 @@ struct PSolveDev {
     const double* xinvt;
     d4* acc;                           // update vectors of the forward sweep (nodes)
     d4* xint;                          // solution of the backward sweep before any per-node update
+    // tree-scheduled sweeps (one launch per sweep): work items in a topological
+    // order, children first; item q is the fronts tq_sn[tq_ptr[q] .. tq_ptr[q+1]),
+    // one large front or up to DC_PS_WARPS small ones of equal depth
+    int tree;                          // 1: tree-scheduled sweeps, 0: one launch per level
+    int S, n_items;
+    const int* parent;                 // [S] parent front, -1 at a root
+    const int* tq_ptr;
+    const int* tq_sn;
+    int* sched;                        // [2][S + 1]: ticket counter, then per-front done flags (fwd; bwd)
+    unsigned long long* fault;         // sticky: set when a dependency wait gave up
+    int tree_grid_f, tree_grid_b;      // host: CTAs of a tree-scheduled launch (fwd, bwd)
+    size_t tree_smem;                  // host: its dynamic shared memory
 };
 
 struct DevMesh {
@@ -242,6 +258,10 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
 // Raises the shared-memory limit of the supernodal level kernels for fronts of
 // up to max_fs nodes (process-wide, never lowered).
 cudaError_t psolve_configure(int max_fs);
+// Launch shape of the tree-scheduled sweeps whose largest CTA-path front has
+// max_fs nodes: the CTAs of each kernel that fit on the device at once, and the
+// dynamic shared memory
+cudaError_t psolve_tree_grid(int max_fs, int* grid_f, int* grid_b, size_t* smem);
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v,
                      d4* x_np1, cudaStream_t s);
 void launch_count_cases(const int* contact, const int* case_, int m_free,

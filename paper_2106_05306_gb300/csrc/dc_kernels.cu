@@ -11,6 +11,7 @@
 //              backward sweep (Eq. contact_all).
 // Every reduction is a fixed-order gather (no atomics), so a launch is bitwise
 // repeatable and independent of what else runs on the GPU.
+#include <algorithm>
 #include <atomic>
 #include <mutex>
 
@@ -29,6 +30,14 @@ namespace {
 __device__ __forceinline__ d4 ld(const d4* p) {
     const double2* q = reinterpret_cast<const double2*>(p);
     double2 a = q[0], b = q[1];
+    d4 r;
+    r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
+    return r;
+}
+// a load through L2 only, for data that other CTAs of the same launch write
+__device__ __forceinline__ d4 ld_cg(const d4* p) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+    double2 a = __ldcg(q), b = __ldcg(q + 1);
     d4 r;
     r.x = a.x; r.y = a.y; r.z = b.x; r.w = b.y;
     return r;
@@ -441,7 +450,19 @@ __device__ __forceinline__ void cm_gemv3(const double* __restrict__ A, long lda,
 // front's path depends only on its own size, so its bits do not depend on what
 // else shares its level.
 constexpr int PS_SMALL = DC_PS_SMALL;
-constexpr int PS_WARPS = 8;    // small fronts per CTA
+constexpr int PS_WARPS = DC_PS_WARPS;    // small fronts per CTA
+
+// The static blocks a front's forward sweep reads, fetched into L2 ahead of use.
+__device__ __forceinline__ void ps_fwd_prefetch(const PSolveDev& ps, int s) {
+    const int ns = ps.p[s] / 3, fs = ps.f[s] / 3;
+    prefetch_l2(ps.xinv + ps.xoff[s], sizeof(double) * ns * ns);
+    prefetch_l2(ps.panel + ps.poff[s], sizeof(double) * fs * ns);
+}
+__device__ __forceinline__ void ps_bwd_prefetch(const PSolveDev& ps, int s) {
+    const int ns = ps.p[s] / 3, nu = ps.f[s] / 3 - ns;
+    prefetch_l2(ps.pant + ps.toff[s], sizeof(double) * ns * nu);
+    prefetch_l2(ps.xinvt + ps.xoff[s], sizeof(double) * ns * ns);
+}
 
 __device__ __forceinline__ void ps_fwd_cta(const PSolveDev& ps, int s, const d4* __restrict__ b,
                                            d4* __restrict__ y, double* __restrict__ smd) {
@@ -450,8 +471,6 @@ __device__ __forceinline__ void ps_fwd_cta(const PSolveDev& ps, int s, const d4*
     double* w = smd;                   // [3][fs]
     double* yv = w + 3 * fs;           // [3][ns]
     double* red = yv + 3 * ns;         // [3][GV_MAXG * GV_ROWS]
-    prefetch_l2(ps.xinv + ps.xoff[s], sizeof(double) * ns * ns);
-    prefetch_l2(ps.panel + ps.poff[s], sizeof(double) * fs * ns);
     for (int t = tid; t < 3 * fs; t += nt) w[t] = 0.0;
     __syncthreads();
     for (int q = ps.cptr[s]; q < ps.cptr[s + 1]; ++q) {
@@ -461,7 +480,7 @@ __device__ __forceinline__ void ps_fwd_cta(const PSolveDev& ps, int s, const d4*
         const d4* acc = ps.acc + ps.aoff[c];
         for (int k = tid; k < nuc; k += nt) {
             const int pos = map[k];
-            const d4 a = ld(acc + k);
+            const d4 a = ld_cg(acc + k);
             w[pos] += a.x;
             w[fs + pos] += a.y;
             w[2 * fs + pos] += a.z;
@@ -505,7 +524,7 @@ __device__ __forceinline__ void ps_fwd_warp(const PSolveDev& ps, int s, const d4
         const d4* acc = ps.acc + ps.aoff[c];
         for (int k = lane; k < nuc; k += 32) {
             const int pos = map[k];
-            const d4 a = ld(acc + k);
+            const d4 a = ld_cg(acc + k);
             w[pos] += a.x;
             w[L + pos] += a.y;
             w[2 * L + pos] += a.z;
@@ -557,6 +576,7 @@ __global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, const int* __restr
                                                 const d4* __restrict__ b, d4* __restrict__ y) {
     extern __shared__ double smd[];
     if ((int)blockIdx.x < n_big) {
+        ps_fwd_prefetch(ps, big[blockIdx.x]);
         ps_fwd_cta(ps, big[blockIdx.x], b, y, smd);
         return;
     }
@@ -576,8 +596,6 @@ __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams&
     double* xu = w + 3 * ns;           // [3][nu]
     double* red = xu + 3 * nu;         // [3][GV_MAXG * GV_ROWS]
     const int* un = ps.unode + ps.uptr[s];
-    prefetch_l2(ps.pant + ps.toff[s], sizeof(double) * ns * nu);
-    prefetch_l2(ps.xinvt + ps.xoff[s], sizeof(double) * ns * ns);
     for (int t = tid; t < ns; t += nt) {
         const d4 a = ld(y + begin + t);
         w[t] = a.x;
@@ -585,7 +603,7 @@ __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams&
         w[2 * ns + t] = a.z;
     }
     for (int k = tid; k < nu; k += nt) {
-        const d4 a = ld(ps.xint + un[k]);
+        const d4 a = ld_cg(ps.xint + un[k]);
         xu[k] = a.x;
         xu[nu + k] = a.y;
         xu[2 * nu + k] = a.z;
@@ -623,7 +641,7 @@ __device__ __forceinline__ void ps_bwd_warp(const PSolveDev& ps, const DevParams
         w[2 * L + t] = a.z;
     }
     for (int k = lane; k < nu; k += 32) {
-        const d4 a = ld(ps.xint + un[k]);
+        const d4 a = ld_cg(ps.xint + un[k]);
         xu[k] = a.x;
         xu[L + k] = a.y;
         xu[2 * L + k] = a.z;
@@ -670,6 +688,7 @@ __global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, const
                                                 double* __restrict__ c_out) {
     extern __shared__ double smd[];
     if ((int)blockIdx.x < n_big) {
+        ps_bwd_prefetch(ps, big[blockIdx.x]);
         ps_bwd_cta(ps, P, big[blockIdx.x], y, out, mode, contact, nb, cc, f, case_, c_out, smd);
         return;
     }
@@ -677,6 +696,144 @@ __global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, const
     const int q = ((int)blockIdx.x - n_big) * PS_WARPS + warp;
     if (q < n_small)
         ps_bwd_warp(ps, P, small[q], y, out, mode, contact, nb, cc, f, case_, c_out, smd + warp * 6 * PS_SMALL);
+}
+
+// ---- tree-scheduled sweeps: one launch per sweep instead of one per level.
+// CTAs take work items from a ticket counter in a topological order (children
+// before parents for L y = b, the reverse for L^T x = y) and, before an item,
+// wait for the done flags of the fronts it reads: its children's update vectors
+// (forward) or its parent's solution (backward; the parent's own wait covers the
+// ancestors above it).  An item only waits on items with smaller tickets, which
+// CTAs already running hold, and the smallest unfinished ticket never waits, so
+// the launch makes progress whatever the number of CTAs resident.  A front's
+// arithmetic is that of the level kernels, so the results are the same bits.
+// Every wait is bounded: after PS_SPIN_LIMIT polls it sets the sticky fault word,
+// and every CTA stops taking items once the word is set.
+constexpr int PS_SPIN_LIMIT = 1 << 20;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool fault_set(const unsigned long long* fault) {
+    return *reinterpret_cast<const volatile unsigned long long*>(fault) != 0ull;
+}
+// Waits until *flag is nonzero; false when the fault word is (or gets) set.
+__device__ bool ps_wait(const int* flag, unsigned long long* fault) {
+    for (int i = 0; i < PS_SPIN_LIMIT; ++i) {
+        if (ld_acquire(flag)) {
+            __threadfence();
+            return true;
+        }
+        if ((i & 31) == 31 && fault_set(fault)) return false;
+        __nanosleep(i < 64 ? 32 : 256);
+    }
+    atomicExch(fault, 1ull);
+    return false;
+}
+
+// One thread takes the next ticket for the CTA; n_items once the fault word is set.
+__device__ __forceinline__ int ps_take(const PSolveDev& ps, int* ticket, int* s_item) {
+    if (threadIdx.x == 0) *s_item = fault_set(ps.fault) ? ps.n_items : atomicAdd(ticket, 1);
+    __syncthreads();
+    return *s_item;
+}
+
+__global__ void __launch_bounds__(256) k_ps_fwd_tree(PSolveDev ps, const d4* __restrict__ b, d4* __restrict__ y) {
+    extern __shared__ double smd[];
+    __shared__ int s_item, s_ok;
+    int* ticket = ps.sched;
+    int* done = ps.sched + 1;
+    for (;;) {
+        const int it = ps_take(ps, ticket, &s_item);
+        if (it >= ps.n_items) return;
+        const int q0 = ps.tq_ptr[it], nq = ps.tq_ptr[it + 1] - q0;
+        const int s0 = ps.tq_sn[q0];
+        if (ps.f[s0] / 3 > PS_SMALL) {
+            ps_fwd_prefetch(ps, s0);
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                for (int q = ps.cptr[s0]; ok && q < ps.cptr[s0 + 1]; ++q) ok = ps_wait(done + ps.child[q], ps.fault);
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            ps_fwd_cta(ps, s0, b, y, smd);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) st_release(done + s0, 1);
+        } else {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (warp < nq) {
+                const int s = ps.tq_sn[q0 + warp];
+                int ok = 1;
+                if (lane == 0)
+                    for (int q = ps.cptr[s]; ok && q < ps.cptr[s + 1]; ++q) ok = ps_wait(done + ps.child[q], ps.fault);
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    ps_fwd_warp(ps, s, b, y, smd + warp * 6 * PS_SMALL);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) st_release(done + s, 1);
+                }
+            }
+            __syncthreads();   // every warp has read s_item before it is rewritten
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_ps_bwd_tree(PSolveDev ps, DevParams P, const d4* __restrict__ y,
+                                                     d4* __restrict__ out, int mode, const int* __restrict__ contact,
+                                                     const d4* __restrict__ nb, const double* __restrict__ cc,
+                                                     d4* __restrict__ f, int* __restrict__ case_,
+                                                     double* __restrict__ c_out) {
+    extern __shared__ double smd[];
+    __shared__ int s_item, s_ok;
+    int* ticket = ps.sched + ps.S + 1;
+    int* done = ps.sched + ps.S + 2;
+    for (;;) {
+        const int t = ps_take(ps, ticket, &s_item);
+        if (t >= ps.n_items) return;
+        const int it = ps.n_items - 1 - t;   // the forward order reversed: parents first
+        const int q0 = ps.tq_ptr[it], nq = ps.tq_ptr[it + 1] - q0;
+        const int s0 = ps.tq_sn[q0];
+        if (ps.f[s0] / 3 > PS_SMALL) {
+            ps_bwd_prefetch(ps, s0);
+            if (threadIdx.x == 0) {
+                const int par = ps.parent[s0];
+                s_ok = par < 0 || ps_wait(done + par, ps.fault);
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            ps_bwd_cta(ps, P, s0, y, out, mode, contact, nb, cc, f, case_, c_out, smd);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) st_release(done + s0, 1);
+        } else {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (warp < nq) {
+                const int s = ps.tq_sn[q0 + warp];
+                int ok = 1;
+                if (lane == 0) {
+                    const int par = ps.parent[s];
+                    ok = par < 0 || ps_wait(done + par, ps.fault);
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    ps_bwd_warp(ps, P, s, y, out, mode, contact, nb, cc, f, case_, c_out,
+                                smd + warp * 6 * PS_SMALL);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) st_release(done + s, 1);
+                }
+            }
+            __syncthreads();
+        }
+    }
 }
 
 __global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4* __restrict__ v,
@@ -748,13 +905,38 @@ cudaError_t psolve_configure(int max_fs) {
     if (need <= configured) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(k_ps_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess) e = cudaFuncSetAttribute(k_ps_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ps_fwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ps_bwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess) configured = need;
     return e;
+}
+
+cudaError_t psolve_tree_grid(int max_fs, int* grid_f, int* grid_b, size_t* smem_out) {
+    const size_t smem = ps_level_smem(max_fs, 1);
+    *smem_out = smem;
+    int dev = 0, sms = 0, nf = 0, nb = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nf, k_ps_fwd_tree, 256, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_ps_bwd_tree, 256, smem);
+    if (e != cudaSuccess) return e;
+    *grid_f = sms * std::max(1, nf);
+    *grid_b = sms * std::max(1, nb);
+    return cudaSuccess;
 }
 
 void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
     if (dm.solver == 1) {
         const PSolveDev& ps = dm.ps;
+        if (ps.tree) {
+            if (ps.n_items == 0) return;
+            cudaMemsetAsync(ps.sched, 0, sizeof(int) * (ps.S + 1), s);
+            dc_note_launch();
+            k_ps_fwd_tree<<<std::min(ps.tree_grid_f, ps.n_items), 256, ps.tree_smem, s>>>(ps, b, y);
+            return;
+        }
         for (int l = 0; l < ps.nlev; ++l) {
             const int nb = ps.nbig_h[l], nsm = ps.nsmall_h[l];
             if (nb + nsm <= 0) continue;
@@ -773,6 +955,14 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
                       const d4* nb, const double* c, d4* f, int* case_, double* c_out, cudaStream_t s) {
     if (dm.solver == 1) {
         const PSolveDev& ps = dm.ps;
+        if (ps.tree) {
+            if (ps.n_items == 0) return;
+            cudaMemsetAsync(ps.sched + ps.S + 1, 0, sizeof(int) * (ps.S + 1), s);
+            dc_note_launch();
+            k_ps_bwd_tree<<<std::min(ps.tree_grid_b, ps.n_items), 256, ps.tree_smem, s>>>(
+                ps, P, y, out, mode, contact, nb, c, f, case_, c_out);
+            return;
+        }
         for (int l = ps.nlev - 1; l >= 0; --l) {
             const int nbg = ps.nbig_h[l], nsm = ps.nsmall_h[l];
             if (nbg + nsm <= 0) continue;

@@ -104,6 +104,7 @@ void prep_loop(dc_server* s) {
         std::string err;
         dc_ctx* c = new dc_ctx();
         c->async_alloc = true;
+        c->blocking_sync = true;
         c->ihm.resize(1);
         err = dc_build_mesh(c->ihm[0], (int)(r->rest.size() / 3), r->rest.data(), (int)(r->tris.size() / 3),
                             r->tris.data(), (int)r->pins.size(), r->pins.empty() ? nullptr : r->pins.data());

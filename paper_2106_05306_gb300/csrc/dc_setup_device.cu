@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <string>
@@ -222,7 +223,7 @@ dc_status upload_mesh(dc_ctx* c, MeshPrep& mp) {
         }
         c->hpin_cap = 1024;
     }
-    cudaError_t e = c->async_alloc ? cudaStreamSynchronize(c->stream) : cudaDeviceSynchronize();
+    cudaError_t e = c->async_alloc ? ctx_sync(c, c->stream) : cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         c->err = std::string("device error during context creation: ") + cudaGetErrorString(e);
         return DC_ERR_CUDA;
@@ -481,7 +482,21 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         c->ps_lvl_ptr[nl] = pos;
         int* d_psn;
         if ((s = upload(c, F, &d_psn, psn))) return s;
+        std::vector<int> tq_ptr, tq_sn;
+        dc_build_tree_items(frm, tq_ptr, tq_sn);
+        int *d_parent, *d_tq_ptr, *d_tq_sn, *d_sched;
+        if ((s = upload(c, F, &d_parent, frm.parent)) || (s = upload(c, F, &d_tq_ptr, tq_ptr)) ||
+            (s = upload(c, F, &d_tq_sn, tq_sn)) || (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))))
+            return s;
         PSolveDev& ps = dm.ps;
+        ps.S = frm.S;
+        ps.n_items = (int)tq_ptr.size() - 1;
+        ps.parent = d_parent;
+        ps.tq_ptr = d_tq_ptr;
+        ps.tq_sn = d_tq_sn;
+        ps.sched = d_sched;
+        ps.fault = c->counters + 3;
+        ps.tree = std::getenv("DC_PS_LEVELS") ? 0 : 1;
         ps.sn = d_psn;
         ps.begin = d_begin;
         ps.f = d_f;
@@ -531,6 +546,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         int mx = 0;
         for (int v : c->ps_maxbig) mx = std::max(mx, v);
         CK(psolve_configure(mx));
+        CK(psolve_tree_grid(mx, &dm.ps.tree_grid_f, &dm.ps.tree_grid_b, &dm.ps.tree_smem));
     }
     {
         // per level, where each instance's fronts start in lvl_sn (an instance's
@@ -551,7 +567,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     c->iprm = pp.q;
     c->have_params = true;
     c->ck_n_steps = -1;
-    if (c->async_alloc) CK(cudaStreamSynchronize(c->stream));
+    if (c->async_alloc) CK(ctx_sync(c, c->stream));
     return DC_OK;
 }
 
@@ -601,6 +617,8 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
         add(vbytes(pp.ps.panel)); add(vbytes(pp.ps.xinv)); add(vbytes(pp.ps.pant)); add(vbytes(pp.ps.xinvt));
         add(vbytes(pp.ps.aoff));
         add((size_t)pp.ps.acc_nodes * d4b); add(MF * d4b);
+        // tree schedule: parents, items (at most one per front), two ticket/flag arrays
+        add(4 * (size_t)r.S); add(4 * ((size_t)r.S + 1)); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));
     }
     // checkpoints, segment recomputation, adjoint
     add(((size_t)n_steps / k + 1) * 2 * m * d4b);

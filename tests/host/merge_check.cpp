@@ -26,6 +26,36 @@ static void grid(int n, std::vector<double>& pos, std::vector<int>& tri) {
         }
 }
 
+// The tree-scheduled sweeps' work items: every front in exactly one item, a
+// large front alone, small fronts at most DC_PS_WARPS to an item and of one
+// depth, and every child in an earlier item than its parent.  "" when valid.
+static const char* check_items(const HostFronts& fr, int* n_large) {
+    std::vector<int> tq_ptr, tq_sn;
+    dc_build_tree_items(fr, tq_ptr, tq_sn);
+    if ((int)tq_sn.size() != fr.S || tq_ptr.front() != 0 || tq_ptr.back() != fr.S) return "item sizes";
+    std::vector<int> item(fr.S, -1), depth(fr.S, 0);
+    for (int s = 0; s < fr.S; ++s)
+        for (int a = fr.parent[s]; a >= 0; a = fr.parent[a]) depth[s]++;
+    *n_large = 0;
+    for (int q = 0; q + 1 < (int)tq_ptr.size(); ++q) {
+        const int n = tq_ptr[q + 1] - tq_ptr[q];
+        if (n < 1 || n > DC_PS_WARPS) return "item width";
+        for (int k = tq_ptr[q]; k < tq_ptr[q + 1]; ++k) {
+            const int s = tq_sn[k];
+            if (s < 0 || s >= fr.S || item[s] >= 0) return "each front in one item";
+            item[s] = q;
+            const bool large = fr.f[s] / 3 > DC_PS_SMALL;
+            if (large && n != 1) return "a large front is an item alone";
+            *n_large += large;
+            if (depth[s] != depth[tq_sn[tq_ptr[q]]]) return "one depth per item";
+        }
+    }
+    for (int s = 0; s < fr.S; ++s)
+        for (int k = fr.cptr[s]; k < fr.cptr[s + 1]; ++k)
+            if (item[fr.child[k]] >= item[s]) return "children before parents";
+    return "";
+}
+
 #define REQUIRE(cond, msg)                         \
     do {                                           \
         if (!(cond)) {                             \
@@ -122,6 +152,30 @@ int main() {
             REQUIRE(FR.begin[g] == R[i].begin[s] + I[i].fo, "front nodes");
             REQUIRE(FR.parent[g] == (R[i].parent[s] < 0 ? -1 : R[i].parent[s] + I[i].so), "front parents");
         }
+    int n_large = 0;
+    const char* bad = check_items(FR, &n_large);
+    REQUIRE(!*bad, bad);
+    {
+        // one larger cloth, so that fronts of more than DC_PS_SMALL nodes occur
+        std::vector<double> pos;
+        std::vector<int> tri;
+        grid(40, pos, tri);
+        HostMesh h;
+        HostFactor hf;
+        HostFronts hr;
+        REQUIRE(dc_build_mesh(h, (int)pos.size() / 3, pos.data(), (int)tri.size() / 3, tri.data(), 0, nullptr)
+                    .empty(),
+                "mesh 40");
+        std::vector<double> mass(h.m);
+        for (int l = 0; l < h.m; ++l) mass[l] = p.density * h.abar[l];
+        std::string err;
+        REQUIRE(dc_build_factor(h, p, mass, hf, err) == DC_OK, "factor 40");
+        REQUIRE(dc_build_fronts(h, hf, hr).empty(), "fronts 40");
+        int nl = 0;
+        bad = check_items(hr, &nl);
+        REQUIRE(!*bad, bad);
+        REQUIRE(nl > 0, "large fronts in the 40 x 40 cloth");
+    }
     // supernodal panels: offsets concatenated in instance order
     HostPSolve PM;
     dc_merge_psolve(PS, PM);

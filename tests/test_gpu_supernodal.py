@@ -1,7 +1,8 @@
 """GPU parity of the supernodal substitution of P (global_solver = 1): the
 global solve against the oracle's banded Cholesky, forward steps and adjoint
 gradients against the oracle, a batch against the same cloths alone (bitwise),
-and the allocation-free entry point against dc_global_solve."""
+the tree-scheduled sweeps against one launch per level (bitwise), and the
+allocation-free entry point against dc_global_solve."""
 import numpy as np
 import pytest
 
@@ -75,6 +76,33 @@ def test_supernodal_batch_is_bitwise_the_cloths_alone():
         for a, p in zip((ax, av, adx, adv), (q[i] for q in parts)):
             assert torch.equal(a, p), i
         assert torch.equal(ath, dth[i])
+
+
+def test_supernodal_tree_schedule_is_bitwise_the_level_launches(monkeypatch):
+    """One launch per sweep, fronts taken in dependency order by whichever CTA is
+    free, gives the bits of one launch per tree level: a front's arithmetic does
+    not depend on when or where it runs.  Cloths of 35-49 nodes a side have fronts
+    on both the CTA path and the warp path."""
+    import torch
+    scs = [scenes.batch_instance(s, n_steps=3) for s in (0, 1, 2, 5)]
+    assert max(sc.n for sc in scs) >= 40
+    cat = lambda k: cuda(np.concatenate([getattr(s, k) for s in scs]))
+    runs = []
+    for levels in (True, False):
+        if levels:
+            monkeypatch.setenv("DC_PS_LEVELS", "1")
+        else:
+            monkeypatch.delenv("DC_PS_LEVELS", raising=False)
+        b = make_batch(scs, global_solver=1, checkpoint_every=1)
+        xN, vN = b.rollout(cat("x0"), cat("v0"), 3)
+        dx0, dv0, dth = b.backward(cat("loss_w"), allow_nonconverged=True)
+        rhs = cuda(np.random.default_rng(9).standard_normal((sum(sc.m for sc in scs), 3)))
+        sol = b.global_solve(rhs)
+        b.stats()   # raises if a dependency wait of a sweep gave up
+        b.close()
+        runs.append((xN, vN, dx0, dv0, dth, sol))
+    for a, c in zip(*runs):
+        assert torch.equal(a, c)
 
 
 def test_supernodal_rejects_block_preconditioner():
