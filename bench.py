@@ -70,8 +70,8 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None},
            # k_ps_fwd_tree: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
            # profiles/k_ps_fwd_tree_batched_96cloths.md), scaled by the sweep's flops
-           "ps_solve_fwd": {"bytes_per_flop": (132945920.0 + 11691008.0) / 62559690.0,
-                            "source_sha": "0c6de9d063ed26e7"}}
+           "ps_solve_fwd": {"bytes_per_flop": (140546048.0 + 11526656.0) / 62559690.0,
+                            "source_sha": "c4d8e738a0c3ccc0"}}
 
 
 def parse_args(argv=None):
@@ -355,7 +355,7 @@ def single_side_run(args, dev):
             "nonconverged_cloth_steps": st["adj_nonconverged"]}
 
 
-def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=16, seed0=10000):
+def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=8, seed0=10000):
     """Served runs: n_req requests (1k-30k DOF, 25-150 steps, random sphere + ground,
     mu 0.1-0.6) with Poisson arrivals into the request server, one run per arrival
     rate; then the same requests one at a time through the plain path.  The served

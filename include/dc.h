@@ -19,10 +19,12 @@
  *  - All GPU work is enqueued on the CUDA stream given to dc_create_mesh.
  *    Errors found on the device (non-finite values) are reported by the next
  *    synchronising call (dc_sync, dc_get_stats, or any call with host buffers).
- *    With global_solver 1 a substitution sweep is one launch whose CTAs wait
- *    for one another's fronts; every such wait is bounded, and one that gives up
- *    sets a sticky device flag that dc_sync, dc_get_stats and dc_backward
- *    report as DC_ERR_CUDA (the context's results are invalid from then on).
+ *    A triangular-solve sweep over the elimination trees (the supernodal
+ *    substitution of global_solver 1, the preconditioner solves of the adjoint)
+ *    is one launch whose CTAs wait for one another's fronts; every such wait is
+ *    bounded, and one that gives up sets a sticky device flag that dc_sync,
+ *    dc_get_stats and dc_backward report as DC_ERR_CUDA (the context's results
+ *    are invalid from then on).
  *  - A context is not thread-safe.
  *  - Batches.  dc_create_batch packs several cloths (instances) of any sizes
  *    into one context; every call below then works on all of them at once,

@@ -63,13 +63,20 @@ void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream
 size_t frontal_factor_smem(int max_f);
 size_t frontal_solve_smem(int max_f);
 cudaError_t frontal_configure(int max_f);
+// Launch shape of the tree-scheduled solves for fronts of at most max_f
+// unknowns: the CTAs of each kernel that fit on the device at once, and the
+// dynamic shared memory.
+cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem);
 // lvl_ptr / lvl_maxf: host arrays, the fronts of level l are lvl_sn[lvl_ptr[l] ..
 // lvl_ptr[l+1]) and the largest has lvl_maxf[l] unknowns.
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
                        const int* lvl_maxf, cudaStream_t s, KTimer* kt = nullptr);
 // act_sn / act_ptr (optional): device list of the fronts to solve, level l at
 // act_sn[act_ptr[l] .. act_ptr[l+1]) (act_ptr on the host); fronts of masked
-// instances may be listed (they exit at once), active ones must be.
+// instances may be listed (they exit at once), active ones must be.  With
+// fd.tree the two solves are one launch each over act_tq[0 .. n_act_tq) (the
+// same fronts in fd.tq's order), or over fd.tq when act_tq is null.
 void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, const int* lvl_maxf,
                      int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt = nullptr,
-                     const int* act_sn = nullptr, const int* act_ptr = nullptr);
+                     const int* act_sn = nullptr, const int* act_ptr = nullptr, const int* act_tq = nullptr,
+                     int n_act_tq = 0);

@@ -249,16 +249,16 @@ dc_status dc_rollout(dc_ctx* c, int32_t n_steps, const double* x0, const double*
     return DC_OK;
 }
 
-// The tree-scheduled sweeps' sticky fault word (counters[3]) is set when a
+// The tree-scheduled solves' sticky fault word (counters[3]) is set when a
 // dependency wait gave up; every result computed since is invalid.  Call with
 // the stream idle.
 static dc_status check_sweep_fault(dc_ctx* c) {
-    if (!c->counters || c->dm.solver != 1) return DC_OK;
+    if (!c->counters) return DC_OK;
     unsigned long long w = 0;
     CK(cudaMemcpyAsync(&w, c->counters + 3, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
     CK(ctx_sync(c, c->stream));
     if (w) {
-        c->err = "supernodal sweep: a dependency wait timed out; results since then are invalid";
+        c->err = "tree-scheduled solve: a dependency wait timed out; results since then are invalid";
         return DC_ERR_CUDA;
     }
     return DC_OK;
@@ -426,8 +426,8 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->adj_batch_iters = c->adj_batch_iters;
     o->global_solver = c->dm.solver;
     o->psolve_flops = c->psolve_flops;
-    if (cnt[3] && c->dm.solver == 1) {
-        c->err = "supernodal sweep: a dependency wait timed out; results since then are invalid";
+    if (cnt[3]) {
+        c->err = "tree-scheduled solve: a dependency wait timed out; results since then are invalid";
         return DC_ERR_CUDA;
     }
     return DC_OK;
@@ -465,7 +465,6 @@ void dc_destroy(dc_ctx* c) {
         if (c->ev_free[k]) cudaEventDestroy(c->ev_free[k]);
     }
     if (c->ev_seg) cudaEventDestroy(c->ev_seg);
-    if (c->ev_block) cudaEventDestroy(c->ev_block);
     if (c->stream2) cudaStreamDestroy(c->stream2);
     GraphCache* gcs[] = {&c->g_roll, &c->g_seg[0], &c->g_seg[1]};
     for (GraphCache* g : gcs)
@@ -481,7 +480,8 @@ void dc_destroy(dc_ctx* c) {
     if (c->hpin && !c->hpin_external) cudaFreeHost(c->hpin);
     if (c->h_act_sn) cudaFreeHost(c->h_act_sn);
     if (c->h_act_ch) cudaFreeHost(c->h_act_ch);
-    if (c->async_alloc) ctx_sync(c, c->stream);
+    if (c->async_alloc) ctx_sync(c, c->stream);   // the stream-ordered frees above
+    if (c->ev_block) cudaEventDestroy(c->ev_block);   // after the last wait on it
     delete c;
 }
 

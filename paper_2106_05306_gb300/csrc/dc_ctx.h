@@ -118,6 +118,10 @@ struct dc_ctx {
     // level l's fronts are act_sn[act_ptr[l] .. act_ptr[l+1]); rebuilt when the
     // active set has shrunk by a quarter (the mask keeps results exact between)
     std::vector<int> lvl_inst_ptr;  // [nlev][B + 1]: instance i's fronts in level l start at this lvl_sn index
+    // with tree-scheduled solves d_act_sn instead holds the active instances'
+    // fronts in the tree order (tq_h filtered), n_act_tq of them
+    std::vector<int> tq_h, sn_inst_h;   // fronts in tree order; instance of each front
+    int n_act_tq = 0;
     int* d_act_sn = nullptr;
     int* h_act_sn = nullptr;        // pinned
     int* d_act_ch = nullptr;

@@ -320,7 +320,8 @@ void precond(dc_ctx* c, const AdjDev& ad, const d4* w, d4* out) {
     const DevMesh& dm = c->dm;
     if (c->prm.adj_precond == 0) {
         frontal_precond(ad, c->fdv, c->fr.lvl_ptr.data(), c->nlev, c->lvl_maxf.data(), dm.m_free, w, out, s,
-                        &c->kt, c->act_on ? c->d_act_sn : nullptr, c->act_ptr.data());
+                        &c->kt, c->act_on ? c->d_act_sn : nullptr, c->act_ptr.data(),
+                        c->act_on ? c->d_act_sn : nullptr, c->n_act_tq);
         return;
     }
     // node-block inverse, projected P^-1, node-block inverse
@@ -337,14 +338,20 @@ dc_status build_active_lists(dc_ctx* c) {
     c->act_ptr.assign(nl + 1, 0);
     int pos = 0, cnt = 0;
     for (int i = 0; i < B; ++i) cnt += c->gs[i].act;
-    for (int l = 0; l < nl; ++l) {
-        c->act_ptr[l] = pos;
-        const int* P = c->lvl_inst_ptr.data() + (size_t)l * (B + 1);
-        for (int i = 0; i < B; ++i)
-            if (c->gs[i].act)
-                for (int q = P[i]; q < P[i + 1]; ++q) c->h_act_sn[pos++] = c->fr.lvl_sn[q];
+    if (c->fdv.tree) {
+        for (int s : c->tq_h)
+            if (c->gs[c->sn_inst_h[s]].act) c->h_act_sn[pos++] = s;
+        c->n_act_tq = pos;
+    } else {
+        for (int l = 0; l < nl; ++l) {
+            c->act_ptr[l] = pos;
+            const int* P = c->lvl_inst_ptr.data() + (size_t)l * (B + 1);
+            for (int i = 0; i < B; ++i)
+                if (c->gs[i].act)
+                    for (int q = P[i]; q < P[i + 1]; ++q) c->h_act_sn[pos++] = c->fr.lvl_sn[q];
+        }
+        c->act_ptr[nl] = pos;
     }
-    c->act_ptr[nl] = pos;
     if (pos > 0)
         CK(cudaMemcpyAsync(c->d_act_sn, c->h_act_sn, sizeof(int) * pos, cudaMemcpyHostToDevice, c->stream));
     int nch = 0;

@@ -15,6 +15,7 @@
 
 #include "dc_adjoint.h"
 #include "dc_internal.h"
+#include "dc_wait.cuh"
 
 namespace {
 
@@ -434,14 +435,19 @@ __device__ __forceinline__ void cm_gemv(const float* __restrict__ A, long lda, i
     }
 }
 
-// Forward substitution L y = r over one level (CTA per front of sn_list), then
-// z = D^-1 y.  y_s = L_ss^-1 w_s with the stored explicit inverse; the rows below
-// accumulate -L_Us y_s into the front's update vector, which the parent adds in.
-__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __restrict__ sn_list,
-                                                    const double* __restrict__ mask) {
-    extern __shared__ float w[];
-    const int s = sn_list[blockIdx.x];
-    if (mask && mask[fd.sn_inst[s]] == 0.0) return;
+// The blocks a front's solves read, fetched into L2 ahead of use.
+__device__ __forceinline__ void msolve_prefetch(const FrontDev& fd, int s) {
+    const int f = fd.f[s], p = fd.p[s];
+    prefetch_l2(fd.linv + fd.linv_off[s], sizeof(float) * p * p);
+    prefetch_l2(fd.pool + fd.off[s], sizeof(float) * (size_t)p * f);
+}
+
+// Forward substitution L y = r for front s (one CTA), then z = D^-1 y.  y_s =
+// L_ss^-1 w_s with the stored explicit inverse; the rows below accumulate
+// -L_Us y_s into the front's update vector, which the parent adds in.  The
+// children's update vectors are read through L2 (other CTAs of a tree-scheduled
+// launch write them).
+__device__ __forceinline__ void msolve_fwd_front(const FrontDev& fd, int s, float* __restrict__ w) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
     const float* X = fd.linv + fd.linv_off[s];
@@ -449,8 +455,6 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __res
     const int base = 3 * fd.begin[s];
     float* y = w + f;
     float* red = y + f;                // [GV_MAXG][GV_ROWS] partial sums
-    prefetch_l2(X, sizeof(float) * p * p);
-    prefetch_l2(F, sizeof(float) * (size_t)p * f);
     for (int t = tid; t < f; t += nt) w[t] = 0.0f;
     __syncthreads();
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
@@ -458,7 +462,7 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __res
         const int nu = fd.f[c] - fd.p[c];
         const int* map = fd.cmap + fd.uptr[c];
         const float* acc = fd.acc + fd.acc_off[c];
-        for (int k = tid; k < nu; k += nt) w[3 * map[k / 3] + k % 3] += acc[k];
+        for (int k = tid; k < nu; k += nt) w[3 * map[k / 3] + k % 3] += __ldcg(acc + k);
         __syncthreads();
     }
     for (int t = tid; t < p; t += nt) w[t] += fd.rvec[base + t];
@@ -469,14 +473,21 @@ __global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __res
     for (int t = tid; t < p; t += nt) fd.zvec[base + t] = y[t] / F[(long)t * f + t];
 }
 
-// Backward substitution L^T x = z over one level (CTA per front), top-down:
-// x_s = L_ss^-T (z_s - L_Us^T x_U).  One warp per row (lanes along the row),
-// two rows per warp at a time.
-__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, const int* __restrict__ sn_list,
+// Forward substitution over one level (CTA per front of sn_list).
+__global__ void __launch_bounds__(FT) k_msolve_fwd(FrontDev fd, const int* __restrict__ sn_list,
                                                     const double* __restrict__ mask) {
-    extern __shared__ float sm[];
+    extern __shared__ float w[];
     const int s = sn_list[blockIdx.x];
     if (mask && mask[fd.sn_inst[s]] == 0.0) return;
+    msolve_prefetch(fd, s);
+    msolve_fwd_front(fd, s, w);
+}
+
+// Backward substitution L^T x = z for front s (one CTA), top-down: x_s =
+// L_ss^-T (z_s - L_Us^T x_U).  One warp per row (lanes along the row), two rows
+// per warp at a time; a row's sum does not depend on the CTA size.  x_U is read
+// through L2 (the ancestors' CTAs of a tree-scheduled launch write it).
+__device__ __forceinline__ void msolve_bwd_front(const FrontDev& fd, int s, float* __restrict__ sm) {
     const int tid = threadIdx.x, nt = blockDim.x;
     const float* F = fd.pool + fd.off[s];
     const float* X = fd.linv + fd.linv_off[s];
@@ -485,10 +496,8 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, const int* __res
     float* w = sm;
     float* xu = sm + p;
     const int* un = fd.unode + fd.uptr[s];
-    prefetch_l2(F, sizeof(float) * (size_t)p * f);
-    prefetch_l2(X, sizeof(float) * p * p);
     for (int t = tid; t < p; t += nt) w[t] = fd.zvec[base + t];
-    for (int k = tid; k < nu; k += nt) xu[k] = fd.xvec[3 * un[k / 3] + k % 3];
+    for (int k = tid; k < nu; k += nt) xu[k] = __ldcg(fd.xvec + 3 * un[k / 3] + k % 3);
     __syncthreads();
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     for (int t = warp; t < p; t += 2 * nw) {
@@ -529,6 +538,85 @@ __global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, const int* __res
             fd.xvec[base + i] = s1;
             if (two) fd.xvec[base + i2] = s2;
         }
+    }
+}
+
+// Backward substitution over one level (CTA per front of sn_list).
+__global__ void __launch_bounds__(FT) k_msolve_bwd(FrontDev fd, const int* __restrict__ sn_list,
+                                                    const double* __restrict__ mask) {
+    extern __shared__ float sm[];
+    const int s = sn_list[blockIdx.x];
+    if (mask && mask[fd.sn_inst[s]] == 0.0) return;
+    msolve_prefetch(fd, s);
+    msolve_bwd_front(fd, s, sm);
+}
+
+// Tree-scheduled solves: one launch per sweep.  Persistent CTAs take the fronts
+// of items[0 .. n_items) (a topological order, children first) from a ticket
+// counter; the backward sweep takes them in reverse.  Before a front a CTA waits
+// (bounded, dc_wait.cuh) for its children's done flags (forward) or its
+// parent's (backward).  A front is only ever waited on by fronts of its own
+// instance, and an instance is masked whole, so a masked front is skipped
+// without a flag.  An item waits only on items with smaller tickets, held by
+// CTAs already running, so the launch completes whatever the number resident.
+constexpr int MT = 256;   // threads per CTA of a tree-scheduled solve
+
+__device__ __forceinline__ int ms_take(const FrontDev& fd, int* ticket, int n_items, int* s_item) {
+    if (threadIdx.x == 0) *s_item = dc_fault_set(fd.fault) ? n_items : atomicAdd(ticket, 1);
+    __syncthreads();
+    const int t = *s_item;
+    __syncthreads();   // every thread has read the ticket before it is rewritten
+    return t;
+}
+
+__global__ void __launch_bounds__(MT) k_msolve_fwd_tree(FrontDev fd, const int* __restrict__ items, int n_items,
+                                                        const double* __restrict__ mask) {
+    extern __shared__ float w[];
+    __shared__ int s_item, s_ok;
+    int* ticket = fd.sched;
+    int* done = fd.sched + 1;
+    for (;;) {
+        const int t = ms_take(fd, ticket, n_items, &s_item);
+        if (t >= n_items) return;
+        const int s = items[t];
+        if (mask && mask[fd.sn_inst[s]] == 0.0) continue;
+        msolve_prefetch(fd, s);
+        if (threadIdx.x == 0) {
+            bool ok = true;
+            for (int q = fd.cptr[s]; ok && q < fd.cptr[s + 1]; ++q) ok = dc_wait_flag(done + fd.child[q], fd.fault);
+            s_ok = ok;
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        msolve_fwd_front(fd, s, w);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) dc_st_release(done + s, 1);
+    }
+}
+
+__global__ void __launch_bounds__(MT) k_msolve_bwd_tree(FrontDev fd, const int* __restrict__ items, int n_items,
+                                                        const double* __restrict__ mask) {
+    extern __shared__ float sm[];
+    __shared__ int s_item, s_ok;
+    int* ticket = fd.sched + fd.S + 1;
+    int* done = fd.sched + fd.S + 2;
+    for (;;) {
+        const int t = ms_take(fd, ticket, n_items, &s_item);
+        if (t >= n_items) return;
+        const int s = items[n_items - 1 - t];
+        if (mask && mask[fd.sn_inst[s]] == 0.0) continue;
+        msolve_prefetch(fd, s);
+        if (threadIdx.x == 0) {
+            const int par = fd.parent[s];
+            s_ok = par < 0 || dc_wait_flag(done + par, fd.fault);
+        }
+        __syncthreads();
+        if (!s_ok) return;
+        msolve_bwd_front(fd, s, sm);
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) dc_st_release(done + s, 1);
     }
 }
 
@@ -599,8 +687,28 @@ cudaError_t frontal_configure(int max_f) {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(k_msolve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)frontal_solve_smem(max_f));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_msolve_fwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)frontal_solve_smem(max_f));
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_msolve_bwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)frontal_solve_smem(max_f));
     if (e == cudaSuccess) configured = max_f;
     return e;
+}
+
+cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_out) {
+    const size_t smem = frontal_solve_smem(max_f);
+    *smem_out = smem;
+    int dev = 0, sms = 0, nf = 0, nb = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nf, k_msolve_fwd_tree, MT, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_msolve_bwd_tree, MT, smem);
+    if (e != cudaSuccess) return e;
+    *grid_f = sms * (nf > 0 ? nf : 1);
+    *grid_b = sms * (nb > 0 ? nb : 1);
+    return cudaSuccess;
 }
 
 // Threads per CTA for a level whose largest front has mf unknowns: small fronts
@@ -629,9 +737,26 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
 
 void frontal_precond(const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev, const int* lvl_maxf,
                      int n_free, const d4* w, d4* out, cudaStream_t s, KTimer* kt, const int* act_sn,
-                     const int* act_ptr) {
+                     const int* act_ptr, const int* act_tq, int n_act_tq) {
     dc_note_launch();
     k_pre_in<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.type, ad.nb, w, fd.rvec, ad.node_inst, ad.mask);
+    if (fd.tree) {
+        const int* items = act_tq ? act_tq : fd.tq;
+        const int n = act_tq ? n_act_tq : fd.S;
+        if (n > 0) {
+            cudaMemsetAsync(fd.sched, 0, sizeof(int) * 2 * ((size_t)fd.S + 1), s);
+            if (kt) kt->begin(DC_KT_MSOLVE);
+            dc_note_launch();
+            k_msolve_fwd_tree<<<n < fd.tree_grid_f ? n : fd.tree_grid_f, MT, fd.tree_smem, s>>>(fd, items, n, ad.mask);
+            dc_note_launch();
+            k_msolve_bwd_tree<<<n < fd.tree_grid_b ? n : fd.tree_grid_b, MT, fd.tree_smem, s>>>(fd, items, n, ad.mask);
+            if (kt) kt->end(DC_KT_MSOLVE);
+        }
+        dc_note_launch();
+        k_pre_out<<<nblk(n_free, 128), 128, 0, s>>>(n_free, ad.mu, ad.type, ad.nb, ad.slip, fd.xvec, out,
+                                                      ad.node_inst, ad.mask);
+        return;
+    }
     // level l's fronts: the compacted list of the active instances' fronts, or all of them
     auto level = [&](int l, int& cnt) -> const int* {
         if (act_sn) {

@@ -300,4 +300,14 @@ struct FrontDev {
     float* rvec;                       // [3 m_free] right-hand side
     float* zvec;                       // [3 m_free] D^-1 L^-1 r
     float* xvec;                       // [3 m_free] solution
+    // tree-scheduled solves (one launch per sweep): the fronts in a topological
+    // order (children first), their parents, and the launches' ticket counters
+    // and done flags
+    int tree;                          // 1: tree-scheduled solves, 0: one launch per level
+    const int* tq;                     // [S]
+    const int* parent;                 // [S] -1 at a root
+    int* sched;                        // [2][S + 1]: ticket, then per-front done flags (fwd; bwd)
+    unsigned long long* fault;         // sticky: set when a dependency wait gave up
+    int tree_grid_f, tree_grid_b;      // host: CTAs of a tree-scheduled launch
+    size_t tree_smem;                  // host: its dynamic shared memory
 };

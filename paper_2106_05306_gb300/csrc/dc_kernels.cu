@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "dc_internal.h"
+#include "dc_wait.cuh"
 
 namespace {
 std::atomic<long long> g_launches{0};
@@ -393,11 +394,12 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 // Column-major product on one CTA with three right-hand sides: t_c,i = sum_k
 // A[k * lda + i] v[c * ldv + k] for i < nrows and k < K (tri 1: only k <= i;
 // tri 2: only k >= i).  Rows go in passes of GV_ROWS; the k range is cut into G
-// contiguous chunks with G a function of K alone; every (row, chunk) partial sum is
-// one work item and a row's partial sums are added in chunk order, so the result
-// depends only on (nrows, K), never on the CTA size (a supernode gives the same
-// bits whatever else shares its level).  fin(i, t0, t1, t2) stores (it must not
-// write v).
+// contiguous chunks with G a function of K alone.  Every (row, chunk) pair with
+// a nonempty k range is one work item -- the pairs are numbered chunk by chunk,
+// so that the triangle's empty pairs take no lanes -- and a row's partial sums
+// are added in chunk order.  The result depends only on (nrows, K), never on the
+// CTA size (a supernode gives the same bits whatever else shares its launch).
+// fin(i, t0, t1, t2) stores (it must not write v).
 constexpr int GV_ROWS = 64;
 constexpr int GV_MAXG = 8;
 __host__ __device__ constexpr int gv_groups(int K) { return K <= 8 ? 1 : (K + 7) / 8 < GV_MAXG ? (K + 7) / 8 : GV_MAXG; }
@@ -410,31 +412,42 @@ __device__ __forceinline__ void cm_gemv3(const double* __restrict__ A, long lda,
     const int C = (K + G - 1) / G;
     constexpr int RS = GV_ROWS * GV_MAXG;      // stride between the three columns' partial sums
     for (int i0 = 0; i0 < nrows; i0 += GV_ROWS) {
-        for (int item = tid; item < GV_ROWS * G; item += nt) {
-            const int r = item % GV_ROWS, g = item / GV_ROWS, i = i0 + r;
+        const int R = min(GV_ROWS, nrows - i0);
+        // rows [lo(g), hi(g)) of this pass have a nonempty k range in chunk g
+        auto lo = [&](int g) { return tri == 1 ? min(R, max(0, g * C - i0)) : 0; };
+        auto hi = [&](int g) { return tri == 2 ? max(0, min(R, (g + 1) * C - i0)) : R; };
+        int n_items = 0;
+        for (int g = 0; g < G; ++g) n_items += max(0, hi(g) - lo(g));
+        for (int item = tid; item < n_items; item += nt) {
+            int g = 0, base = 0;
+            for (;; ++g) {
+                const int n = max(0, hi(g) - lo(g));
+                if (item < base + n) break;
+                base += n;
+            }
+            const int r = lo(g) + item - base, i = i0 + r;
+            int k0 = g * C;
+            int k1 = min(K, k0 + C);
+            if (tri == 1) k1 = min(k1, i + 1);
+            if (tri == 2) k0 = max(k0, i);
+            const double* a = A + i;
             double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-            if (i < nrows) {
-                int k0 = g * C;
-                int k1 = min(K, k0 + C);
-                if (tri == 1) k1 = min(k1, i + 1);
-                if (tri == 2) k0 = max(k0, i);
-                const double* a = A + i;
 #pragma unroll 4
-                for (int k = k0; k < k1; ++k) {
-                    const double x = a[(long)k * lda];
-                    a0 += x * v[k];
-                    a1 += x * v[ldv + k];
-                    a2 += x * v[2 * ldv + k];
-                }
+            for (int k = k0; k < k1; ++k) {
+                const double x = a[(long)k * lda];
+                a0 += x * v[k];
+                a1 += x * v[ldv + k];
+                a2 += x * v[2 * ldv + k];
             }
             red[g * GV_ROWS + r] = a0;
             red[RS + g * GV_ROWS + r] = a1;
             red[2 * RS + g * GV_ROWS + r] = a2;
         }
         __syncthreads();
-        if (tid < GV_ROWS && i0 + tid < nrows) {
+        if (tid < R) {
             double t0 = 0.0, t1 = 0.0, t2 = 0.0;
             for (int q = 0; q < G; ++q) {
+                if (tid < lo(q) || tid >= hi(q)) continue;
                 t0 += red[q * GV_ROWS + tid];
                 t1 += red[RS + q * GV_ROWS + tid];
                 t2 += red[2 * RS + q * GV_ROWS + tid];
@@ -451,6 +464,7 @@ __device__ __forceinline__ void cm_gemv3(const double* __restrict__ A, long lda,
 // else shares its level.
 constexpr int PS_SMALL = DC_PS_SMALL;
 constexpr int PS_WARPS = DC_PS_WARPS;    // small fronts per CTA
+constexpr int PS_LD = PS_SMALL + 1;       // shared-memory column stride of the warp path (no bank conflicts)
 
 // The static blocks a front's forward sweep reads, fetched into L2 ahead of use.
 __device__ __forceinline__ void ps_fwd_prefetch(const PSolveDev& ps, int s) {
@@ -508,10 +522,14 @@ __device__ __forceinline__ void ps_fwd_cta(const PSolveDev& ps, int s, const d4*
     for (int t = tid; t < ns; t += nt) st(y + begin + t, yv[t], yv[ns + t], yv[2 * ns + t]);
 }
 
-// w: this warp's [3][PS_SMALL] gathered right-hand side, then [3][PS_SMALL] of y_s
+// Warp path, forward: w is this warp's [3][PS_LD] gathered right-hand side, then
+// [3][PS_LD] of y_s.  Both products give one lane to each (row, column) pair, so
+// that a front of ns or nu rows keeps 3 ns or 3 nu lanes busy instead of ns or
+// nu (the fronts here have 4-24 pivot rows); a pair's sum runs over k in
+// ascending order, as with one lane per row.
 __device__ __forceinline__ void ps_fwd_warp(const PSolveDev& ps, int s, const d4* __restrict__ b,
                                             d4* __restrict__ y, double* __restrict__ w) {
-    constexpr int L = PS_SMALL;
+    constexpr int L = PS_LD;
     const int lane = threadIdx.x & 31;
     const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
     double* yv = w + 3 * L;
@@ -538,33 +556,27 @@ __device__ __forceinline__ void ps_fwd_warp(const PSolveDev& ps, int s, const d4
         w[2 * L + t] += a.z;
     }
     __syncwarp();
+    // y_s = L_ss^-1 w_s (lower triangle)
     const double* X = ps.xinv + ps.xoff[s];
-    for (int i = lane; i < ns; i += 32) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int q = lane; q < 3 * ns; q += 32) {
+        const int i = q / 3, col = q - 3 * i;
+        const double* wc = w + col * L;
+        double a = 0.0;
 #pragma unroll 4
-        for (int k = 0; k <= i; ++k) {
-            const double x = X[(long)k * ns + i];
-            a0 += x * w[k];
-            a1 += x * w[L + k];
-            a2 += x * w[2 * L + k];
-        }
-        yv[i] = a0;
-        yv[L + i] = a1;
-        yv[2 * L + i] = a2;
+        for (int k = 0; k <= i; ++k) a += X[(long)k * ns + i] * wc[k];
+        yv[col * L + i] = a;
     }
     __syncwarp();
+    // update vector: w_U - L_Us y_s
     const double* Pn = ps.panel + ps.poff[s] + ns;
-    d4* acc = ps.acc + ps.aoff[s];
-    for (int i = lane; i < nu; i += 32) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    double* acc = reinterpret_cast<double*>(ps.acc + ps.aoff[s]);
+    for (int q = lane; q < 3 * nu; q += 32) {
+        const int i = q / 3, col = q - 3 * i;
+        const double* yc = yv + col * L;
+        double a = 0.0;
 #pragma unroll 4
-        for (int k = 0; k < ns; ++k) {
-            const double x = Pn[(long)k * fs + i];
-            a0 += x * yv[k];
-            a1 += x * yv[L + k];
-            a2 += x * yv[2 * L + k];
-        }
-        st(acc + i, w[ns + i] - a0, w[L + ns + i] - a1, w[2 * L + ns + i] - a2);
+        for (int k = 0; k < ns; ++k) a += Pn[(long)k * fs + i] * yc[k];
+        acc[4 * i + col] = w[col * L + ns + i] - a;
     }
     for (int t = lane; t < ns; t += 32) st(y + begin + t, yv[t], yv[L + t], yv[2 * L + t]);
 }
@@ -582,7 +594,7 @@ __global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, const int* __restr
     }
     const int warp = threadIdx.x >> 5;
     const int q = ((int)blockIdx.x - n_big) * PS_WARPS + warp;
-    if (q < n_small) ps_fwd_warp(ps, small[q], b, y, smd + warp * 6 * PS_SMALL);
+    if (q < n_small) ps_fwd_warp(ps, small[q], b, y, smd + warp * 6 * PS_LD);
 }
 
 __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams& P, int s, const d4* __restrict__ y,
@@ -623,13 +635,14 @@ __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams&
     });
 }
 
-// w: this warp's [3][PS_SMALL] right-hand side, then [3][PS_SMALL] of x_U
+// Warp path, backward: w is this warp's [3][PS_LD] right-hand side, then
+// [3][PS_LD] of x_U, later of x_s.  One lane per (row, column) pair, as forward.
 __device__ __forceinline__ void ps_bwd_warp(const PSolveDev& ps, const DevParams& P, int s, const d4* __restrict__ y,
                                             d4* __restrict__ out, int mode, const int* __restrict__ contact,
                                             const d4* __restrict__ nb, const double* __restrict__ cc,
                                             d4* __restrict__ f, int* __restrict__ case_,
                                             double* __restrict__ c_out, double* __restrict__ w) {
-    constexpr int L = PS_SMALL;
+    constexpr int L = PS_LD;
     const int lane = threadIdx.x & 31;
     const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
     double* xu = w + 3 * L;
@@ -647,32 +660,31 @@ __device__ __forceinline__ void ps_bwd_warp(const PSolveDev& ps, const DevParams
         xu[2 * L + k] = a.z;
     }
     __syncwarp();
+    // w_s -= L_Us^T x_U (the transposed update block is ns x nu column-major)
     const double* T = ps.pant + ps.toff[s];
-    for (int i = lane; i < ns; i += 32) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int q = lane; q < 3 * ns; q += 32) {
+        const int i = q / 3, col = q - 3 * i;
+        const double* xc = xu + col * L;
+        double a = 0.0;
 #pragma unroll 4
-        for (int k = 0; k < nu; ++k) {
-            const double x = T[(long)k * ns + i];
-            a0 += x * xu[k];
-            a1 += x * xu[L + k];
-            a2 += x * xu[2 * L + k];
-        }
-        w[i] -= a0;
-        w[L + i] -= a1;
-        w[2 * L + i] -= a2;
+        for (int k = 0; k < nu; ++k) a += T[(long)k * ns + i] * xc[k];
+        w[col * L + i] -= a;
     }
     __syncwarp();
+    // x_s = L_ss^-T w_s (upper triangle of the transposed inverse), into xu
     const double* XT = ps.xinvt + ps.xoff[s];
-    for (int i = lane; i < ns; i += 32) {
-        double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int q = lane; q < 3 * ns; q += 32) {
+        const int i = q / 3, col = q - 3 * i;
+        const double* wc = w + col * L;
+        double a = 0.0;
 #pragma unroll 4
-        for (int k = i; k < ns; ++k) {
-            const double x = XT[(long)k * ns + i];
-            a0 += x * w[k];
-            a1 += x * w[L + k];
-            a2 += x * w[2 * L + k];
-        }
-        const int row = begin + i;
+        for (int k = i; k < ns; ++k) a += XT[(long)k * ns + i] * wc[k];
+        xu[col * L + i] = a;
+    }
+    __syncwarp();
+    for (int t = lane; t < ns; t += 32) {
+        const double a0 = xu[t], a1 = xu[L + t], a2 = xu[2 * L + t];
+        const int row = begin + t;
         st(ps.xint + row, a0, a1, a2);
         finish_row(P, row, a0, a1, a2, out, mode, contact, nb, cc, f, case_, c_out);
     }
@@ -695,7 +707,7 @@ __global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, const
     const int warp = threadIdx.x >> 5;
     const int q = ((int)blockIdx.x - n_big) * PS_WARPS + warp;
     if (q < n_small)
-        ps_bwd_warp(ps, P, small[q], y, out, mode, contact, nb, cc, f, case_, c_out, smd + warp * 6 * PS_SMALL);
+        ps_bwd_warp(ps, P, small[q], y, out, mode, contact, nb, cc, f, case_, c_out, smd + warp * 6 * PS_LD);
 }
 
 // ---- tree-scheduled sweeps: one launch per sweep instead of one per level.
@@ -707,38 +719,12 @@ __global__ void __launch_bounds__(256) k_ps_bwd(PSolveDev ps, DevParams P, const
 // CTAs already running hold, and the smallest unfinished ticket never waits, so
 // the launch makes progress whatever the number of CTAs resident.  A front's
 // arithmetic is that of the level kernels, so the results are the same bits.
-// Every wait is bounded: after PS_SPIN_LIMIT polls it sets the sticky fault word,
-// and every CTA stops taking items once the word is set.
-constexpr int PS_SPIN_LIMIT = 1 << 20;
-
-__device__ __forceinline__ int ld_acquire(const int* p) {
-    int v;
-    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ bool fault_set(const unsigned long long* fault) {
-    return *reinterpret_cast<const volatile unsigned long long*>(fault) != 0ull;
-}
-// Waits until *flag is nonzero; false when the fault word is (or gets) set.
-__device__ bool ps_wait(const int* flag, unsigned long long* fault) {
-    for (int i = 0; i < PS_SPIN_LIMIT; ++i) {
-        if (ld_acquire(flag)) {
-            __threadfence();
-            return true;
-        }
-        if ((i & 31) == 31 && fault_set(fault)) return false;
-        __nanosleep(i < 64 ? 32 : 256);
-    }
-    atomicExch(fault, 1ull);
-    return false;
-}
+// Every wait is bounded (dc_wait.cuh): one that gives up sets the sticky fault
+// word, and every CTA stops taking items once the word is set.
 
 // One thread takes the next ticket for the CTA; n_items once the fault word is set.
 __device__ __forceinline__ int ps_take(const PSolveDev& ps, int* ticket, int* s_item) {
-    if (threadIdx.x == 0) *s_item = fault_set(ps.fault) ? ps.n_items : atomicAdd(ticket, 1);
+    if (threadIdx.x == 0) *s_item = dc_fault_set(ps.fault) ? ps.n_items : atomicAdd(ticket, 1);
     __syncthreads();
     return *s_item;
 }
@@ -757,7 +743,7 @@ __global__ void __launch_bounds__(256) k_ps_fwd_tree(PSolveDev ps, const d4* __r
             ps_fwd_prefetch(ps, s0);
             if (threadIdx.x == 0) {
                 bool ok = true;
-                for (int q = ps.cptr[s0]; ok && q < ps.cptr[s0 + 1]; ++q) ok = ps_wait(done + ps.child[q], ps.fault);
+                for (int q = ps.cptr[s0]; ok && q < ps.cptr[s0 + 1]; ++q) ok = dc_wait_flag(done + ps.child[q], ps.fault);
                 s_ok = ok;
             }
             __syncthreads();
@@ -765,20 +751,20 @@ __global__ void __launch_bounds__(256) k_ps_fwd_tree(PSolveDev ps, const d4* __r
             ps_fwd_cta(ps, s0, b, y, smd);
             __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0) st_release(done + s0, 1);
+            if (threadIdx.x == 0) dc_st_release(done + s0, 1);
         } else {
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             if (warp < nq) {
                 const int s = ps.tq_sn[q0 + warp];
                 int ok = 1;
                 if (lane == 0)
-                    for (int q = ps.cptr[s]; ok && q < ps.cptr[s + 1]; ++q) ok = ps_wait(done + ps.child[q], ps.fault);
+                    for (int q = ps.cptr[s]; ok && q < ps.cptr[s + 1]; ++q) ok = dc_wait_flag(done + ps.child[q], ps.fault);
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (ok) {
-                    ps_fwd_warp(ps, s, b, y, smd + warp * 6 * PS_SMALL);
+                    ps_fwd_warp(ps, s, b, y, smd + warp * 6 * PS_LD);
                     __threadfence();
                     __syncwarp();
-                    if (lane == 0) st_release(done + s, 1);
+                    if (lane == 0) dc_st_release(done + s, 1);
                 }
             }
             __syncthreads();   // every warp has read s_item before it is rewritten
@@ -805,14 +791,14 @@ __global__ void __launch_bounds__(256) k_ps_bwd_tree(PSolveDev ps, DevParams P, 
             ps_bwd_prefetch(ps, s0);
             if (threadIdx.x == 0) {
                 const int par = ps.parent[s0];
-                s_ok = par < 0 || ps_wait(done + par, ps.fault);
+                s_ok = par < 0 || dc_wait_flag(done + par, ps.fault);
             }
             __syncthreads();
             if (!s_ok) return;
             ps_bwd_cta(ps, P, s0, y, out, mode, contact, nb, cc, f, case_, c_out, smd);
             __threadfence();
             __syncthreads();
-            if (threadIdx.x == 0) st_release(done + s0, 1);
+            if (threadIdx.x == 0) dc_st_release(done + s0, 1);
         } else {
             const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
             if (warp < nq) {
@@ -820,15 +806,15 @@ __global__ void __launch_bounds__(256) k_ps_bwd_tree(PSolveDev ps, DevParams P, 
                 int ok = 1;
                 if (lane == 0) {
                     const int par = ps.parent[s];
-                    ok = par < 0 || ps_wait(done + par, ps.fault);
+                    ok = par < 0 || dc_wait_flag(done + par, ps.fault);
                 }
                 ok = __shfl_sync(0xffffffffu, ok, 0);
                 if (ok) {
                     ps_bwd_warp(ps, P, s, y, out, mode, contact, nb, cc, f, case_, c_out,
-                                smd + warp * 6 * PS_SMALL);
+                                smd + warp * 6 * PS_LD);
                     __threadfence();
                     __syncwarp();
-                    if (lane == 0) st_release(done + s, 1);
+                    if (lane == 0) dc_st_release(done + s, 1);
                 }
             }
             __syncthreads();
@@ -890,7 +876,7 @@ size_t ps_smem(int fs) { return (6 * (size_t)fs + 3 * (size_t)GV_ROWS * GV_MAXG)
 int ps_threads(int big_fs, int n_small) { return (n_small > 0 || big_fs > 96) ? 256 : 128; }
 size_t ps_level_smem(int big_fs, int n_small) {
     const size_t a = big_fs > 0 ? ps_smem(big_fs) : 0;
-    const size_t b = n_small > 0 ? (size_t)PS_WARPS * 6 * PS_SMALL * sizeof(double) : 0;
+    const size_t b = n_small > 0 ? (size_t)PS_WARPS * 6 * PS_LD * sizeof(double) : 0;
     return a > b ? a : b;
 }
 }  // namespace

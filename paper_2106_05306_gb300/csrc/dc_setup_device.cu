@@ -434,6 +434,25 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     fd.pr_coef = d_pcoef;
     fd.tau = d_tau;
     fd.sn_inst = d_sninst;
+    // tree-scheduled solves: the fronts in a topological order (children first);
+    // DC_LEVEL_SOLVES=1 in the environment selects one launch per tree level
+    // instead (same results)
+    {
+        std::vector<int> tq_ptr, tq_sn;
+        dc_build_tree_items(frm, tq_ptr, tq_sn);
+        int *d_tq, *d_parent, *d_sched;
+        if ((s = upload(c, F, &d_tq, tq_sn)) || (s = upload(c, F, &d_parent, frm.parent)) ||
+            (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))))
+            return s;
+        fd.tq = d_tq;
+        fd.parent = d_parent;
+        fd.sched = d_sched;
+        fd.fault = c->counters + 3;
+        fd.tree = std::getenv("DC_LEVEL_SOLVES") ? 0 : 1;
+        CK(frontal_tree_grid(frm.max_f, &fd.tree_grid_f, &fd.tree_grid_b, &fd.tree_smem));
+        c->tq_h = std::move(tq_sn);
+        c->sn_inst_h = sn_inst;
+    }
     c->fdv = fd;
     c->fds[0] = fd;
     c->fds[1] = fd;   // second slot: its own numeric storage, shared structure
@@ -484,19 +503,19 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         if ((s = upload(c, F, &d_psn, psn))) return s;
         std::vector<int> tq_ptr, tq_sn;
         dc_build_tree_items(frm, tq_ptr, tq_sn);
-        int *d_parent, *d_tq_ptr, *d_tq_sn, *d_sched;
-        if ((s = upload(c, F, &d_parent, frm.parent)) || (s = upload(c, F, &d_tq_ptr, tq_ptr)) ||
-            (s = upload(c, F, &d_tq_sn, tq_sn)) || (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))))
+        int *d_tq_ptr, *d_tq_sn, *d_sched;
+        if ((s = upload(c, F, &d_tq_ptr, tq_ptr)) || (s = upload(c, F, &d_tq_sn, tq_sn)) ||
+            (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))))
             return s;
         PSolveDev& ps = dm.ps;
         ps.S = frm.S;
         ps.n_items = (int)tq_ptr.size() - 1;
-        ps.parent = d_parent;
+        ps.parent = fd.parent;
         ps.tq_ptr = d_tq_ptr;
         ps.tq_sn = d_tq_sn;
         ps.sched = d_sched;
         ps.fault = c->counters + 3;
-        ps.tree = std::getenv("DC_PS_LEVELS") ? 0 : 1;
+        ps.tree = fd.tree;
         ps.sn = d_psn;
         ps.begin = d_begin;
         ps.f = d_f;
@@ -612,13 +631,14 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
         add(4 * (size_t)r.linv_size);
     }
     add(4 * (size_t)r.acc_size); add(12 * MF); add(12 * MF); add(12 * MF);
+    add(4 * (size_t)r.S); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));   // tree order, parents, tickets/flags
     if (q.global_solver == 1) {
         add(vbytes(pp.ps.poff)); add(vbytes(pp.ps.xoff)); add(vbytes(pp.ps.toff)); add(vbytes(pp.ps.aoff));
         add(vbytes(pp.ps.panel)); add(vbytes(pp.ps.xinv)); add(vbytes(pp.ps.pant)); add(vbytes(pp.ps.xinvt));
         add(vbytes(pp.ps.aoff));
         add((size_t)pp.ps.acc_nodes * d4b); add(MF * d4b);
-        // tree schedule: parents, items (at most one per front), two ticket/flag arrays
-        add(4 * (size_t)r.S); add(4 * ((size_t)r.S + 1)); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));
+        // tree schedule: items (at most one per front), two ticket/flag arrays
+        add(4 * ((size_t)r.S + 1)); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));
     }
     // checkpoints, segment recomputation, adjoint
     add(((size_t)n_steps / k + 1) * 2 * m * d4b);

@@ -81,8 +81,10 @@ def test_supernodal_batch_is_bitwise_the_cloths_alone():
 def test_supernodal_tree_schedule_is_bitwise_the_level_launches(monkeypatch):
     """One launch per sweep, fronts taken in dependency order by whichever CTA is
     free, gives the bits of one launch per tree level: a front's arithmetic does
-    not depend on when or where it runs.  Cloths of 35-49 nodes a side have fronts
-    on both the CTA path and the warp path."""
+    not depend on when or where it runs.  This holds for the supernodal sweeps of
+    the forward step and for the multifrontal solves of the adjoint's
+    preconditioner (the gradients).  Cloths of 35-49 nodes a side have fronts on
+    both the CTA path and the warp path."""
     import torch
     scs = [scenes.batch_instance(s, n_steps=3) for s in (0, 1, 2, 5)]
     assert max(sc.n for sc in scs) >= 40
@@ -90,9 +92,9 @@ def test_supernodal_tree_schedule_is_bitwise_the_level_launches(monkeypatch):
     runs = []
     for levels in (True, False):
         if levels:
-            monkeypatch.setenv("DC_PS_LEVELS", "1")
+            monkeypatch.setenv("DC_LEVEL_SOLVES", "1")
         else:
-            monkeypatch.delenv("DC_PS_LEVELS", raising=False)
+            monkeypatch.delenv("DC_LEVEL_SOLVES", raising=False)
         b = make_batch(scs, global_solver=1, checkpoint_every=1)
         xN, vN = b.rollout(cat("x0"), cat("v0"), 3)
         dx0, dv0, dth = b.backward(cat("loss_w"), allow_nonconverged=True)
