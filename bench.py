@@ -70,8 +70,8 @@ FP64_PEAK_TFLOPS = 1.25
 TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None},
            # k_ps_fwd_tree: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
            # profiles/k_ps_fwd_tree_batched_96cloths.md), scaled by the sweep's flops
-           "ps_solve_fwd": {"bytes_per_flop": (140546048.0 + 11526656.0) / 62559690.0,
-                            "source_sha": "c4d8e738a0c3ccc0"}}
+           "ps_solve_fwd": {"bytes_per_flop": (143285504.0 + 12266240.0) / 62559690.0,
+                            "source_sha": "b62290a3bd33d00b"}}
 
 
 def parse_args(argv=None):

@@ -455,17 +455,16 @@ __device__ __forceinline__ void msolve_fwd_front(const FrontDev& fd, int s, floa
     const int base = 3 * fd.begin[s];
     float* y = w + f;
     float* red = y + f;                // [GV_MAXG][GV_ROWS] partial sums
-    for (int t = tid; t < f; t += nt) w[t] = 0.0f;
-    __syncthreads();
-    for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
-        const int c = fd.child[q];
-        const int nu = fd.f[c] - fd.p[c];
-        const int* map = fd.cmap + fd.uptr[c];
-        const float* acc = fd.acc + fd.acc_off[c];
-        for (int k = tid; k < nu; k += nt) w[3 * map[k / 3] + k % 3] += __ldcg(acc + k);
-        __syncthreads();
+    // w = the children's update entries (pull lists: children in order), then r
+    // on the pivots -- the sums of a child-by-child scatter into zeroed storage
+    const int* pp = fd.pull_ptr + fd.pull_off[s];
+    for (int t = tid; t < f; t += nt) {
+        const int node = t / 3, comp = t - 3 * node;
+        float a = 0.0f;
+        for (int e = pp[node]; e < pp[node + 1]; ++e) a += __ldcg(fd.acc + fd.pull_idx[e] + comp);
+        if (t < p) a += fd.rvec[base + t];
+        w[t] = a;
     }
-    for (int t = tid; t < p; t += nt) w[t] += fd.rvec[base + t];
     __syncthreads();
     cm_gemv(X, p, p, p, true, w, red, [&](int i, float t) { y[i] = t; });
     float* acc = fd.acc + fd.acc_off[s];
@@ -711,13 +710,26 @@ cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_
     return cudaSuccess;
 }
 
-// Threads per CTA for a level whose largest front has mf unknowns: small fronts
-// get small CTAs (and, with the level's own shared-memory size, many CTAs per SM).
-static int factor_threads(int mf) { return mf <= 96 ? 128 : (mf <= 192 ? 256 : FT2); }
+// Threads per CTA for a level of cnt fronts whose largest has mf unknowns: small
+// fronts get small CTAs (and, with the level's own shared-memory size, many CTAs
+// per SM).  The kernel takes 128 registers a thread, so a 512-thread CTA fills an
+// SM's register file; a level with at least two fronts per SM uses 256 threads
+// instead when two CTAs fit in shared memory, so that one CTA's serial phases
+// (the diagonal block on one warp) overlap the other's updates.  The results do
+// not depend on the CTA size.
+static int factor_threads(int mf, int cnt, int sms) {
+    if (mf <= 96) return 128;
+    if (mf <= 192) return 256;
+    if (cnt >= 2 * sms && 2 * frontal_factor_smem(mf) <= 227 * 1024) return 256;
+    return FT2;
+}
 static int solve_threads(int mf) { return mf <= 64 ? 128 : (mf <= 128 ? 256 : (mf <= 256 ? 512 : FT)); }
 
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
                        const int* lvl_maxf, cudaStream_t s, KTimer* kt) {
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (kt) kt->begin(DC_KT_ASSEMBLE);
     cudaMemsetAsync(fd.pool, 0, sizeof(float) * fd.pool_size, s);
     dc_note_launch();
@@ -729,7 +741,7 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
             const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_FRONT);
-            k_front_level<<<cnt, factor_threads(mf), frontal_factor_smem(mf), s>>>(fd, lvl_ptr[l], mf);
+            k_front_level<<<cnt, factor_threads(mf, cnt, sms), frontal_factor_smem(mf), s>>>(fd, lvl_ptr[l], mf);
             if (kt) kt->end(DC_KT_FRONT);
         }
     }

@@ -303,3 +303,34 @@ void dc_build_tree_items(const HostFronts& fr, std::vector<int>& tq_ptr, std::ve
         tq_ptr.push_back((int)tq_sn.size());
     }
 }
+
+// For every front s and node position t of s (t < f_s / 3, pivots first): the
+// update-vector entries of s's children that add into t, children in cptr order
+// and entries in ascending order (entry j of child c is aoff[c] + stride j), so that a gather summing them in list order
+// adds exactly what a child-by-child scatter adds.
+void dc_build_pull_lists(const HostFronts& fr, const std::vector<int>& aoff, int stride, std::vector<int>& pull_off,
+                         std::vector<int>& pull_ptr, std::vector<int>& pull_idx) {
+    pull_off.assign(fr.S, 0);
+    pull_ptr.clear();
+    pull_idx.clear();
+    std::vector<int> fill;
+    for (int s = 0; s < fr.S; ++s) {
+        const int fs = fr.f[s] / 3;
+        pull_off[s] = (int)pull_ptr.size();
+        const size_t base = pull_ptr.size();
+        pull_ptr.resize(base + fs + 1, 0);
+        for (int q = fr.cptr[s]; q < fr.cptr[s + 1]; ++q) {
+            const int c = fr.child[q];
+            for (int k = fr.uptr[c]; k < fr.uptr[c + 1]; ++k) pull_ptr[base + fr.cmap[k] + 1]++;
+        }
+        pull_ptr[base] = (int)pull_idx.size();
+        for (int t = 0; t < fs; ++t) pull_ptr[base + t + 1] += pull_ptr[base + t];
+        pull_idx.resize(pull_ptr[base + fs]);
+        fill.assign(pull_ptr.begin() + base, pull_ptr.begin() + base + fs);
+        for (int q = fr.cptr[s]; q < fr.cptr[s + 1]; ++q) {
+            const int c = fr.child[q];
+            for (int k = fr.uptr[c]; k < fr.uptr[c + 1]; ++k)
+                pull_idx[fill[fr.cmap[k]]++] = aoff[c] + stride * (k - fr.uptr[c]);
+        }
+    }
+}

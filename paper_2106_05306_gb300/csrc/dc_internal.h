@@ -110,6 +110,10 @@ void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps)
 void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out);
 // Work items of the tree-scheduled sweeps (see PSolveDev::tq_ptr)
 void dc_build_tree_items(const HostFronts& fr, std::vector<int>& tq_ptr, std::vector<int>& tq_sn);
+// Pull lists of the forward solves' child gather (see PSolveDev::pull_off and
+// FrontDev::pull_off): entry j of child c's update vector is aoff[c] + stride j
+void dc_build_pull_lists(const HostFronts& fr, const std::vector<int>& aoff, int stride, std::vector<int>& pull_off,
+                         std::vector<int>& pull_ptr, std::vector<int>& pull_idx);
 
 // ---------------------------------------------------------------- device views
 
@@ -156,6 +160,12 @@ struct PSolveDev {
     const int* parent;                 // [S] parent front, -1 at a root
     const int* tq_ptr;
     const int* tq_sn;
+    // gather of the children's update vectors into front s: position t < fs/3
+    // sums acc[pull_idx[e]] for e in [pull_ptr[pull_off[s] + t], pull_ptr[pull_off[s] + t + 1]),
+    // children in cptr order
+    const int* pull_off;               // [S]
+    const int* pull_ptr;
+    const int* pull_idx;
     int* sched;                        // [2][S + 1]: ticket counter, then per-front done flags (fwd; bwd)
     unsigned long long* fault;         // sticky: set when a dependency wait gave up
     int tree_grid_f, tree_grid_b;      // host: CTAs of a tree-scheduled launch (fwd, bwd)
@@ -304,6 +314,12 @@ struct FrontDev {
     // order (children first), their parents, and the launches' ticket counters
     // and done flags
     int tree;                          // 1: tree-scheduled solves, 0: one launch per level
+    // gather of the children's update vectors into front s: node t < f/3 sums the
+    // 3-float entries acc[pull_idx[e] ..] for e in [pull_ptr[pull_off[s] + t],
+    // pull_ptr[pull_off[s] + t + 1]), children in cptr order
+    const int* pull_off;               // [S]
+    const int* pull_ptr;
+    const int* pull_idx;
     const int* tq;                     // [S]
     const int* parent;                 // [S] -1 at a root
     int* sched;                        // [2][S + 1]: ticket, then per-front done flags (fwd; bwd)

@@ -400,7 +400,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
 // are added in chunk order.  The result depends only on (nrows, K), never on the
 // CTA size (a supernode gives the same bits whatever else shares its launch).
 // fin(i, t0, t1, t2) stores (it must not write v).
-constexpr int GV_ROWS = 64;
+constexpr int GV_ROWS = 128;
 constexpr int GV_MAXG = 8;
 __host__ __device__ constexpr int gv_groups(int K) { return K <= 8 ? 1 : (K + 7) / 8 < GV_MAXG ? (K + 7) / 8 : GV_MAXG; }
 
@@ -466,6 +466,30 @@ constexpr int PS_SMALL = DC_PS_SMALL;
 constexpr int PS_WARPS = DC_PS_WARPS;    // small fronts per CTA
 constexpr int PS_LD = PS_SMALL + 1;       // shared-memory column stride of the warp path (no bank conflicts)
 
+// Right-hand side of position t of a front: the children's update entries that
+// add into t (pull list pp, children in order), then b_t for a pivot (bt not
+// null); the three columns go to w[0], w[stride], w[2 stride].  The sums are
+// those of a child-by-child scatter into zeroed storage, in the same order.
+__device__ __forceinline__ void ps_gather(const PSolveDev& ps, const int* __restrict__ pp, int t,
+                                          const d4* __restrict__ bt, double* __restrict__ w, int stride) {
+    double x = 0.0, y = 0.0, z = 0.0;
+    for (int e = pp[t]; e < pp[t + 1]; ++e) {
+        const d4 a = ld_cg(ps.acc + ps.pull_idx[e]);
+        x += a.x;
+        y += a.y;
+        z += a.z;
+    }
+    if (bt) {
+        const d4 a = ld(bt);
+        x += a.x;
+        y += a.y;
+        z += a.z;
+    }
+    w[0] = x;
+    w[stride] = y;
+    w[2 * stride] = z;
+}
+
 // The static blocks a front's forward sweep reads, fetched into L2 ahead of use.
 __device__ __forceinline__ void ps_fwd_prefetch(const PSolveDev& ps, int s) {
     const int ns = ps.p[s] / 3, fs = ps.f[s] / 3;
@@ -485,28 +509,8 @@ __device__ __forceinline__ void ps_fwd_cta(const PSolveDev& ps, int s, const d4*
     double* w = smd;                   // [3][fs]
     double* yv = w + 3 * fs;           // [3][ns]
     double* red = yv + 3 * ns;         // [3][GV_MAXG * GV_ROWS]
-    for (int t = tid; t < 3 * fs; t += nt) w[t] = 0.0;
-    __syncthreads();
-    for (int q = ps.cptr[s]; q < ps.cptr[s + 1]; ++q) {
-        const int c = ps.child[q];
-        const int nuc = (ps.f[c] - ps.p[c]) / 3;
-        const int* map = ps.cmap + ps.uptr[c];
-        const d4* acc = ps.acc + ps.aoff[c];
-        for (int k = tid; k < nuc; k += nt) {
-            const int pos = map[k];
-            const d4 a = ld_cg(acc + k);
-            w[pos] += a.x;
-            w[fs + pos] += a.y;
-            w[2 * fs + pos] += a.z;
-        }
-        __syncthreads();
-    }
-    for (int t = tid; t < ns; t += nt) {
-        const d4 a = ld(b + begin + t);
-        w[t] += a.x;
-        w[fs + t] += a.y;
-        w[2 * fs + t] += a.z;
-    }
+    const int* pp = ps.pull_ptr + ps.pull_off[s];
+    for (int t = tid; t < fs; t += nt) ps_gather(ps, pp, t, t < ns ? b + begin + t : nullptr, w + t, fs);
     __syncthreads();
     const double* X = ps.xinv + ps.xoff[s];
     const double* Pn = ps.panel + ps.poff[s];
@@ -533,28 +537,8 @@ __device__ __forceinline__ void ps_fwd_warp(const PSolveDev& ps, int s, const d4
     const int lane = threadIdx.x & 31;
     const int begin = ps.begin[s], ns = ps.p[s] / 3, fs = ps.f[s] / 3, nu = fs - ns;
     double* yv = w + 3 * L;
-    for (int t = lane; t < fs; t += 32) w[t] = w[L + t] = w[2 * L + t] = 0.0;
-    __syncwarp();
-    for (int q = ps.cptr[s]; q < ps.cptr[s + 1]; ++q) {
-        const int c = ps.child[q];
-        const int nuc = (ps.f[c] - ps.p[c]) / 3;
-        const int* map = ps.cmap + ps.uptr[c];
-        const d4* acc = ps.acc + ps.aoff[c];
-        for (int k = lane; k < nuc; k += 32) {
-            const int pos = map[k];
-            const d4 a = ld_cg(acc + k);
-            w[pos] += a.x;
-            w[L + pos] += a.y;
-            w[2 * L + pos] += a.z;
-        }
-        __syncwarp();
-    }
-    for (int t = lane; t < ns; t += 32) {
-        const d4 a = ld(b + begin + t);
-        w[t] += a.x;
-        w[L + t] += a.y;
-        w[2 * L + t] += a.z;
-    }
+    const int* pp = ps.pull_ptr + ps.pull_off[s];
+    for (int t = lane; t < fs; t += 32) ps_gather(ps, pp, t, t < ns ? b + begin + t : nullptr, w + t, L);
     __syncwarp();
     // y_s = L_ss^-1 w_s (lower triangle)
     const double* X = ps.xinv + ps.xoff[s];

@@ -440,10 +440,18 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     {
         std::vector<int> tq_ptr, tq_sn;
         dc_build_tree_items(frm, tq_ptr, tq_sn);
-        int *d_tq, *d_parent, *d_sched;
+        // pull lists of the children's update vectors (float offsets of each node's x)
+        std::vector<int> acc_base(frm.S), pull_off, pull_ptr, pull_idx;
+        for (int q = 0; q < frm.S; ++q) acc_base[q] = (int)frm.acc_off[q];
+        dc_build_pull_lists(frm, acc_base, 3, pull_off, pull_ptr, pull_idx);
+        int *d_tq, *d_parent, *d_sched, *d_pull_off, *d_pull_ptr, *d_pull_idx;
         if ((s = upload(c, F, &d_tq, tq_sn)) || (s = upload(c, F, &d_parent, frm.parent)) ||
-            (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))))
+            (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))) || (s = upload(c, F, &d_pull_off, pull_off)) ||
+            (s = upload(c, F, &d_pull_ptr, pull_ptr)) || (s = upload(c, F, &d_pull_idx, pull_idx)))
             return s;
+        fd.pull_off = d_pull_off;
+        fd.pull_ptr = d_pull_ptr;
+        fd.pull_idx = d_pull_idx;
         fd.tq = d_tq;
         fd.parent = d_parent;
         fd.sched = d_sched;
@@ -503,9 +511,12 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         if ((s = upload(c, F, &d_psn, psn))) return s;
         std::vector<int> tq_ptr, tq_sn;
         dc_build_tree_items(frm, tq_ptr, tq_sn);
-        int *d_tq_ptr, *d_tq_sn, *d_sched;
+        std::vector<int> pull_off, pull_ptr, pull_idx;
+        dc_build_pull_lists(frm, pp.ps.aoff, 1, pull_off, pull_ptr, pull_idx);
+        int *d_tq_ptr, *d_tq_sn, *d_sched, *d_pull_off, *d_pull_ptr, *d_pull_idx;
         if ((s = upload(c, F, &d_tq_ptr, tq_ptr)) || (s = upload(c, F, &d_tq_sn, tq_sn)) ||
-            (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))))
+            (s = dalloc(c, F, &d_sched, 2 * ((size_t)frm.S + 1))) || (s = upload(c, F, &d_pull_off, pull_off)) ||
+            (s = upload(c, F, &d_pull_ptr, pull_ptr)) || (s = upload(c, F, &d_pull_idx, pull_idx)))
             return s;
         PSolveDev& ps = dm.ps;
         ps.S = frm.S;
@@ -514,6 +525,9 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         ps.tq_ptr = d_tq_ptr;
         ps.tq_sn = d_tq_sn;
         ps.sched = d_sched;
+        ps.pull_off = d_pull_off;
+        ps.pull_ptr = d_pull_ptr;
+        ps.pull_idx = d_pull_idx;
         ps.fault = c->counters + 3;
         ps.tree = fd.tree;
         ps.sn = d_psn;
@@ -632,6 +646,11 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     }
     add(4 * (size_t)r.acc_size); add(12 * MF); add(12 * MF); add(12 * MF);
     add(4 * (size_t)r.S); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));   // tree order, parents, tickets/flags
+    {
+        size_t nodes = 0;   // pull lists of the children's update vectors
+        for (int q = 0; q < r.S; ++q) nodes += r.f[q] / 3 + 1;
+        add(4 * (size_t)r.S); add(4 * nodes); add(4 * (size_t)r.acc_size / 3 + 4);
+    }
     if (q.global_solver == 1) {
         add(vbytes(pp.ps.poff)); add(vbytes(pp.ps.xoff)); add(vbytes(pp.ps.toff)); add(vbytes(pp.ps.aoff));
         add(vbytes(pp.ps.panel)); add(vbytes(pp.ps.xinv)); add(vbytes(pp.ps.pant)); add(vbytes(pp.ps.xinvt));
@@ -639,6 +658,10 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
         add((size_t)pp.ps.acc_nodes * d4b); add(MF * d4b);
         // tree schedule: items (at most one per front), two ticket/flag arrays
         add(4 * ((size_t)r.S + 1)); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));
+        // pull lists of the child gather
+        size_t nodes = 0;
+        for (int q = 0; q < r.S; ++q) nodes += r.f[q] / 3 + 1;
+        add(4 * (size_t)r.S); add(4 * nodes); add(4 * (size_t)pp.ps.acc_nodes);
     }
     // checkpoints, segment recomputation, adjoint
     add(((size_t)n_steps / k + 1) * 2 * m * d4b);

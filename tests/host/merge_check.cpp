@@ -56,6 +56,38 @@ static const char* check_items(const HostFronts& fr, int* n_large) {
     return "";
 }
 
+// The pull lists of the forward solves' child gather: summing a front's lists in
+// order gives bitwise the child-by-child scatter into zeroed storage.  stride 1:
+// one entry per node (the supernodal sweep's d4 vectors, aoff in nodes); stride
+// 3: three floats per node (the multifrontal solve, aoff in floats, padded).
+static const char* check_pull(const HostFronts& fr, const std::vector<int>& aoff, int stride, long long acc_len) {
+    std::vector<int> off, ptr, idx;
+    dc_build_pull_lists(fr, aoff, stride, off, ptr, idx);
+    std::vector<double> acc(acc_len);
+    unsigned long long st = 12345;
+    for (double& a : acc) {
+        st = st * 6364136223846793005ull + 1442695040888963407ull;
+        a = (double)(long long)(st >> 11) * 0x1.0p-40 - 4096.0;
+    }
+    for (int s = 0; s < fr.S; ++s) {
+        const int fs = fr.f[s] / 3;
+        for (int comp = 0; comp < stride; ++comp) {
+            std::vector<double> scat(fs, 0.0);
+            for (int q = fr.cptr[s]; q < fr.cptr[s + 1]; ++q) {
+                const int c = fr.child[q];
+                for (int k = fr.uptr[c]; k < fr.uptr[c + 1]; ++k)
+                    scat[fr.cmap[k]] += acc[aoff[c] + stride * (k - fr.uptr[c]) + comp];
+            }
+            for (int t = 0; t < fs; ++t) {
+                double x = 0.0;
+                for (int e = ptr[off[s] + t]; e < ptr[off[s] + t + 1]; ++e) x += acc[idx[e] + comp];
+                if (x != scat[t]) return "pull gather differs from the scatter";
+            }
+        }
+    }
+    return "";
+}
+
 #define REQUIRE(cond, msg)                         \
     do {                                           \
         if (!(cond)) {                             \
@@ -192,6 +224,12 @@ int main() {
                             PS[i].panel[PS[i].poff[s] + (long)k * (ns + R[i].uptr[s + 1] - R[i].uptr[s]) + k],
                         "panel values");
         }
+    bad = check_pull(FR, PM.aoff, 1, PM.acc_nodes);
+    REQUIRE(!*bad, bad);
+    std::vector<int> acc_base(FR.S);
+    for (int q = 0; q < FR.S; ++q) acc_base[q] = (int)FR.acc_off[q];
+    bad = check_pull(FR, acc_base, 3, FR.acc_size);
+    REQUIRE(!*bad, bad);
     std::printf("ok %d %d %d\n", M.m, MF, S);
     return 0;
 }
