@@ -60,17 +60,18 @@ void adj_params(const DevMesh& dm, const AdjDev& ad, const Segs& sg, const d4* z
 void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s);
 
 // Per-step multifrontal LDL^T preconditioner (dc_frontal.cu).
-size_t frontal_factor_smem(int max_f);
+size_t frontal_factor_smem(int max_f, int max_p);
 size_t frontal_solve_smem(int max_f);
-cudaError_t frontal_configure(int max_f);
+cudaError_t frontal_configure(int max_f, int max_p);
 // Launch shape of the tree-scheduled solves for fronts of at most max_f
 // unknowns: the CTAs of each kernel that fit on the device at once, and the
 // dynamic shared memory.
 cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem);
-// lvl_ptr / lvl_maxf: host arrays, the fronts of level l are lvl_sn[lvl_ptr[l] ..
-// lvl_ptr[l+1]) and the largest has lvl_maxf[l] unknowns.
+// lvl_ptr / lvl_maxf / lvl_maxp: host arrays, the fronts of level l are
+// lvl_sn[lvl_ptr[l] .. lvl_ptr[l+1]), the largest has lvl_maxf[l] unknowns and
+// the largest pivot block lvl_maxp[l].
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
-                       const int* lvl_maxf, cudaStream_t s, KTimer* kt = nullptr);
+                       const int* lvl_maxf, const int* lvl_maxp, cudaStream_t s, KTimer* kt = nullptr);
 // act_sn / act_ptr (optional): device list of the fronts to solve, level l at
 // act_sn[act_ptr[l] .. act_ptr[l+1]) (act_ptr on the host); fronts of masked
 // instances may be listed (they exit at once), active ones must be.  With

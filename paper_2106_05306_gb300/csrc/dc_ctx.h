@@ -73,6 +73,7 @@ struct dc_ctx {
     FrontDev fdv{};
     int nlev = 0;
     std::vector<int> lvl_maxf;     // largest front of every level
+    std::vector<int> lvl_maxp;     // largest pivot block of every level
     std::vector<int> lvl_maxfs;    // ... in nodes (supernodal substitution)
     std::vector<int> ps_lvl_ptr, ps_nbig, ps_nsmall, ps_maxbig;   // supernodal level lists (large, then small)
     int* d_int2ext = nullptr;

@@ -622,7 +622,7 @@ void prepare_step(dc_ctx* c, const StepRec& r, const d4* x1, const d4* v1, int k
     adj_setup(c->dm, ad, x1, v1, s);
     kt->end(DC_KT_ASSEMBLE);
     if (c->prm.adj_precond == 0) {
-        frontal_factorize(c->dm, ad, c->fds[k], c->fr.lvl_ptr.data(), c->nlev, c->lvl_maxf.data(), s,
+        frontal_factorize(c->dm, ad, c->fds[k], c->fr.lvl_ptr.data(), c->nlev, c->lvl_maxf.data(), c->lvl_maxp.data(), s,
                           s == c->stream ? &c->kt : &c->kt2);
         c->n_factorisations++;
     }

@@ -141,11 +141,13 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
 
 // Extend-add of the children's update blocks, then the partial LDL^T of the
 // front's pivot columns; the trailing lower triangle becomes the update block.
-// Per panel of PB pivot columns: warp 0 factorises the PB x PB diagonal block in
-// registers (shuffles only) and inverts it; every thread then solves its rows
-// below the block against that inverse; the trailing matrix is updated with
-// TM x TM register tiles whose operands come from a transposed, zero-padded
-// copy of the panel (128-bit shared-memory loads).
+// Per panel of PB pivot columns: the panel's diagonal block is staged row-major
+// and its rows below transposed and zero-padded (the only copy of them, so that
+// shared memory grows with one panel width, not two); warp 0 factorises the
+// diagonal block in registers (shuffles only) and inverts it; every thread then
+// solves its rows below the block against that inverse, in place; the trailing
+// matrix is updated with TM x TM register tiles whose operands come from the
+// transposed rows (128-bit shared-memory loads).
 __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin, int mf) {
     extern __shared__ __align__(16) float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
@@ -153,10 +155,10 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
     float* F = fd.pool + fd.off[s];
     const int f = fd.f[s], p = fd.p[s];
     const int ldt = (mf + 7) / 8 * 8;                // row stride of the transposed panel
-    float* Ls = sm;                                  // [f][LDS] panel, row-major
-    float* Xs = sm + (long)mf * LDS;                 // [PB][LDS] diagonal-block inverse
+    float* Db = sm;                                  // [PB][LDS] diagonal block, row-major
+    float* Xs = Db + PB * LDS;                       // [PB][LDS] diagonal-block inverse
     float* Dd = Xs + PB * LDS;                       // [PB] pivots of the panel
-    float* Lt = sm + ((long)mf * LDS + PB * LDS + PB + 3) / 4 * 4;   // [PB][ldt], 16-byte aligned
+    float* Lt = sm + (2 * PB * LDS + PB + 3) / 4 * 4;   // [PB][ldt] rows below the block, 16-byte aligned
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
         const int c = fd.child[q];
         const float* Fc = fd.pool + fd.off[c];
@@ -190,16 +192,23 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
     for (int k0 = 0; k0 < p; k0 += PB) {
         const int kb = min(PB, p - k0);
         const int nr = f - k0;
+        const int n2 = nr - kb;                          // rows below the diagonal block
+        const int n2p = (n2 + TM - 1) / TM * TM;
         for (int c = warp; c < kb; c += nw) {
             const float* src = F + (long)(k0 + c) * f + k0;
-            for (int r = lane; r < nr; r += 32) Ls[r * LDS + c] = src[r];
+            for (int r = lane; r < nr; r += 32) {
+                const float v = src[r];
+                if (r < kb) Db[r * LDS + c] = v;
+                else Lt[c * ldt + r - kb] = v;
+            }
+            for (int r = n2 + lane; r < n2p; r += 32) Lt[c * ldt + r] = 0.0f;
         }
         __syncthreads();
         if (warp == 0) {
             // lane r holds row r of the diagonal block
             float row[PB];
 #pragma unroll
-            for (int j = 0; j < PB; ++j) row[j] = (lane < kb && j < kb) ? Ls[lane * LDS + j] : 0.0f;
+            for (int j = 0; j < PB; ++j) row[j] = (lane < kb && j < kb) ? Db[lane * LDS + j] : 0.0f;
 #pragma unroll
             for (int c = 0; c < PB; ++c) {
                 if (c < kb) {
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
                 float dl = 0.0f;
 #pragma unroll
                 for (int j = 0; j < PB; ++j) {
-                    if (j <= lane && j < kb) Ls[lane * LDS + j] = row[j];
+                    if (j <= lane && j < kb) Db[lane * LDS + j] = row[j];
                     if (j == lane) dl = row[j];
                 }
                 Dd[lane] = dl;
@@ -243,34 +252,29 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
             for (int i = 0; i < PB; ++i) Bi[lane * PB + i] = (lane < kb && i < kb) ? xc[i] : (i == lane ? 1.0f : 0.0f);
         }
         __syncthreads();
-        // rows below the diagonal block: l_r = D^-1 L_dd^-1 a_r (one row per thread)
-        for (int r = kb + tid; r < nr; r += nt) {
+        // rows below the diagonal block: l_r = D^-1 L_dd^-1 a_r (one row per thread,
+        // in place in the transposed rows)
+        for (int r = tid; r < n2; r += nt) {
             float a[PB];
 #pragma unroll
-            for (int j = 0; j < PB; ++j) a[j] = (j < kb) ? Ls[r * LDS + j] : 0.0f;
+            for (int j = 0; j < PB; ++j) a[j] = (j < kb) ? Lt[j * ldt + r] : 0.0f;
 #pragma unroll
             for (int c = 0; c < PB; ++c) {
                 if (c < kb) {
                     float sum = 0.0f;
 #pragma unroll
                     for (int j = 0; j <= c; ++j) sum += Xs[c * LDS + j] * a[j];
-                    Ls[r * LDS + c] = sum / Dd[c];
+                    Lt[c * ldt + r] = sum / Dd[c];
                 }
             }
         }
         __syncthreads();
-        const int n2 = nr - kb;
-        const int n2p = (n2 + TM - 1) / TM * TM;
+        // the panel's columns back to the front (disjoint from what the trailing
+        // update below reads and writes, so no barrier between the two)
         for (int c = warp; c < kb; c += nw) {
             float* dst = F + (long)(k0 + c) * f + k0;
-            for (int r = c + lane; r < nr; r += 32) dst[r] = Ls[r * LDS + c];
+            for (int r = c + lane; r < nr; r += 32) dst[r] = r < kb ? Db[r * LDS + c] : Lt[c * ldt + r - kb];
         }
-        // transposed, zero-padded copy of the trailing rows of the panel
-        for (long e = tid; e < (long)PB * n2p; e += nt) {
-            const int c = (int)(e / n2p), r = (int)(e % n2p);
-            Lt[c * ldt + r] = (c < kb && r < n2) ? Ls[(kb + r) * LDS + c] : 0.0f;
-        }
-        __syncthreads();
         // trailing update in TM x 4 half-tiles of the TM x TM tiles of the lower
         // triangle; each thread prefetches its tile's current values before the FMA
         // loop so that the memory latency overlaps the arithmetic
@@ -662,10 +666,13 @@ __global__ void k_pre_out(int n, const double* __restrict__ mu, const int* __res
 
 }  // namespace
 
-size_t frontal_factor_smem(int max_f) {
+// Shared memory of a factorisation CTA: the diagonal block, its inverse, the
+// pivots and the transposed rows below the block (one panel width of the front),
+// or the scratch of the explicit inverse of a pivot block of up to max_p rows.
+size_t frontal_factor_smem(int max_f, int max_p) {
     const size_t ldt = ((size_t)max_f + 7) / 8 * 8;
-    size_t panel = ((size_t)max_f * LDS + PB * LDS + PB + 3) / 4 * 4 + PB * ldt;
-    size_t inverse = 2 * (size_t)PB * (max_f + 1) + (size_t)PB * PB;
+    size_t panel = (2 * (size_t)PB * LDS + PB + 3) / 4 * 4 + PB * ldt;
+    size_t inverse = 2 * (size_t)PB * (max_p + 1) + (size_t)PB * PB;
     return (panel > inverse ? panel : inverse) * sizeof(float) + 64;
 }
 
@@ -673,27 +680,25 @@ size_t frontal_solve_smem(int max_f) { return (2 * (size_t)max_f + GV_ROWS * GV_
 
 // The dynamic shared-memory limit of the front kernels is a per-function
 // attribute shared by every context of the process, so it only ever grows.
-cudaError_t frontal_configure(int max_f) {
+cudaError_t frontal_configure(int max_f, int max_p) {
     static std::mutex mu;
-    static int configured = 0;
+    static size_t factor_bytes = 48 * 1024, solve_bytes = 48 * 1024;
     std::lock_guard<std::mutex> lock(mu);
-    if (max_f <= configured) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_front_level, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)frontal_factor_smem(max_f));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_msolve_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)frontal_solve_smem(max_f));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_msolve_bwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)frontal_solve_smem(max_f));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_msolve_fwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)frontal_solve_smem(max_f));
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_msolve_bwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)frontal_solve_smem(max_f));
-    if (e == cudaSuccess) configured = max_f;
-    return e;
+    const size_t fb = frontal_factor_smem(max_f, max_p), sb = frontal_solve_smem(max_f);
+    if (fb > factor_bytes) {
+        cudaError_t e = cudaFuncSetAttribute(k_front_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb);
+        if (e != cudaSuccess) return e;
+        factor_bytes = fb;
+    }
+    if (sb > solve_bytes) {
+        for (const void* k : {(const void*)k_msolve_fwd, (const void*)k_msolve_bwd, (const void*)k_msolve_fwd_tree,
+                              (const void*)k_msolve_bwd_tree}) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb);
+            if (e != cudaSuccess) return e;
+        }
+        solve_bytes = sb;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_out) {
@@ -717,16 +722,16 @@ cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_
 // instead when two CTAs fit in shared memory, so that one CTA's serial phases
 // (the diagonal block on one warp) overlap the other's updates.  The results do
 // not depend on the CTA size.
-static int factor_threads(int mf, int cnt, int sms) {
+static int factor_threads(int mf, int mp, int cnt, int sms) {
     if (mf <= 96) return 128;
     if (mf <= 192) return 256;
-    if (cnt >= 2 * sms && 2 * frontal_factor_smem(mf) <= 227 * 1024) return 256;
+    if (cnt >= 2 * sms && 2 * frontal_factor_smem(mf, mp) <= 227 * 1024) return 256;
     return FT2;
 }
 static int solve_threads(int mf) { return mf <= 64 ? 128 : (mf <= 128 ? 256 : (mf <= 256 ? 512 : FT)); }
 
 void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, const int* lvl_ptr, int nlev,
-                       const int* lvl_maxf, cudaStream_t s, KTimer* kt) {
+                       const int* lvl_maxf, const int* lvl_maxp, cudaStream_t s, KTimer* kt) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -741,7 +746,9 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
             const int mf = lvl_maxf[l];
             dc_note_launch();
             if (kt) kt->begin(DC_KT_FRONT);
-            k_front_level<<<cnt, factor_threads(mf, cnt, sms), frontal_factor_smem(mf), s>>>(fd, lvl_ptr[l], mf);
+            const int mp = lvl_maxp[l];
+            k_front_level<<<cnt, factor_threads(mf, mp, cnt, sms), frontal_factor_smem(mf, mp), s>>>(fd, lvl_ptr[l],
+                                                                                                  mf);
             if (kt) kt->end(DC_KT_FRONT);
         }
     }

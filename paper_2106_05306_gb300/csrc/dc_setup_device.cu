@@ -372,12 +372,14 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     int dev = 0, smem_optin = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (frontal_factor_smem(frm.max_f) > (size_t)smem_optin) {
+    int max_p = 0;
+    for (int q = 0; q < frm.S; ++q) max_p = std::max(max_p, frm.p[q]);
+    if (frontal_factor_smem(frm.max_f, max_p) > (size_t)smem_optin) {
         c->err = "dc_set_params: the largest front (" + std::to_string(frm.max_f) +
                  " unknowns) exceeds the shared memory of one CTA";
         return DC_ERR_INVALID;
     }
-    CK(frontal_configure(frm.max_f));
+    CK(frontal_configure(frm.max_f, max_p));
     free_pool(c, c->front_allocs);
     auto& F = c->front_allocs;
     FrontDev fd{};
@@ -558,9 +560,13 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         }
     c->nlev = (int)frm.lvl_ptr.size() - 1;
     c->lvl_maxf.assign(std::max(c->nlev, 0), 0);
+    c->lvl_maxp.assign(std::max(c->nlev, 0), 0);
     for (int l = 0; l < c->nlev; ++l)
         for (int q = frm.lvl_ptr[l]; q < frm.lvl_ptr[l + 1]; ++q)
             c->lvl_maxf[l] = std::max(c->lvl_maxf[l], frm.f[frm.lvl_sn[q]]);
+    for (int l = 0; l < c->nlev; ++l)
+        for (int q = frm.lvl_ptr[l]; q < frm.lvl_ptr[l + 1]; ++q)
+            c->lvl_maxp[l] = std::max(c->lvl_maxp[l], frm.p[frm.lvl_sn[q]]);
     c->front_flops = pp.front_flops;
     c->factor_nnz = pp.factor_nnz;
     c->fwd_nnz = (long long)hfm.fval.size();
