@@ -718,14 +718,15 @@ cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_
 // Threads per CTA for a level of cnt fronts whose largest has mf unknowns: small
 // fronts get small CTAs (and, with the level's own shared-memory size, many CTAs
 // per SM).  The kernel takes 128 registers a thread, so a 512-thread CTA fills an
-// SM's register file; a level with at least two fronts per SM uses 256 threads
-// instead when two CTAs fit in shared memory, so that one CTA's serial phases
-// (the diagonal block on one warp) overlap the other's updates.  The results do
-// not depend on the CTA size.
+// SM's register file; a level with at least four fronts per SM (two waves of two
+// CTAs) uses 256 threads instead when two CTAs fit in shared memory, so that one
+// CTA's serial phases (the diagonal block on one warp) overlap the other's
+// updates.  With fewer fronts the halved CTAs only lengthen the one wave.  The
+// results do not depend on the CTA size.
 static int factor_threads(int mf, int mp, int cnt, int sms) {
     if (mf <= 96) return 128;
     if (mf <= 192) return 256;
-    if (cnt >= 2 * sms && 2 * frontal_factor_smem(mf, mp) <= 227 * 1024) return 256;
+    if (cnt >= 4 * sms && 2 * frontal_factor_smem(mf, mp) <= 227 * 1024) return 256;
     return FT2;
 }
 static int solve_threads(int mf) { return mf <= 64 ? 128 : (mf <= 128 ? 256 : (mf <= 256 ? 512 : FT)); }
