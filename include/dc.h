@@ -262,6 +262,17 @@ dc_status dc_set_kernel_timer(dc_ctx* ctx, int32_t kernel_class);
  * serialised by the caller.  Asynchronous on the context's stream. */
 dc_status dc_global_solve_static(dc_ctx* ctx, const double* rhs, double* out);
 
+/* Testing the bounded waits of the tree-scheduled sweeps (global_solver 1).
+ * Runs one forward supernodal sweep of P^-1 on the context's work vectors with
+ * the first skip_items work items never executed, so that a front whose child
+ * is among them waits for a flag that nothing sets.  The wait gives up after
+ * about a second, sets the context's sticky fault flag and the launch ends; the
+ * call synchronises and returns DC_ERR_CUDA when the fault was raised (DC_OK if
+ * no skipped item had a waiting parent).  The context's results are invalid
+ * afterwards: destroy it.  DC_ERR_INVALID without global_solver 1 or with
+ * skip_items outside [1, number of items). */
+dc_status dc_debug_sweep_wait_timeout(dc_ctx* ctx, int32_t skip_items);
+
 /* Counters and factor sizes (synchronises the stream). */
 dc_status dc_get_stats(dc_ctx* ctx, dc_stats* out);
 

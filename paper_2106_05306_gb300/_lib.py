@@ -99,6 +99,7 @@ SIGNATURES = {
     "dc_backward": (ctypes.c_int32, [_P, _P, _P, _P, _P, _P, _P]),
     "dc_global_solve": (ctypes.c_int32, [_P, _P, _P]),
     "dc_global_solve_static": (ctypes.c_int32, [_P, _P, _P]),
+    "dc_debug_sweep_wait_timeout": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_stats)]),
     "dc_set_kernel_timer": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_sync": (ctypes.c_int32, [_P]),

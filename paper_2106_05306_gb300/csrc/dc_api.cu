@@ -385,6 +385,22 @@ dc_status dc_global_solve(dc_ctx* c, const double* rhs, double* out) {
     return DC_OK;
 }
 
+dc_status dc_debug_sweep_wait_timeout(dc_ctx* c, int32_t skip_items) {
+    if (!c) return DC_ERR_INVALID;
+    if (!c->have_params || c->dm.solver != 1 || !c->dm.ps.tree) {
+        c->err = "dc_debug_sweep_wait_timeout: needs global_solver 1 with tree-scheduled sweeps";
+        return DC_ERR_INVALID;
+    }
+    if (skip_items < 1 || skip_items >= c->dm.ps.n_items) {
+        c->err = "dc_debug_sweep_wait_timeout: skip_items outside [1, " + std::to_string(c->dm.ps.n_items) + ")";
+        return DC_ERR_INVALID;
+    }
+    launch_solve_fwd_skip(c->dm, c->b, c->y, skip_items, c->stream);
+    CK(ctx_sync(c, c->stream));
+    CK(cudaGetLastError());
+    return check_sweep_fault(c);
+}
+
 dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     if (!c || !o) return DC_ERR_INVALID;
     CK(ctx_sync(c, c->stream));

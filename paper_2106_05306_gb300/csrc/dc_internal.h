@@ -268,6 +268,9 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
 // Raises the shared-memory limit of the supernodal level kernels for fronts of
 // up to max_fs nodes (process-wide, never lowered).
 cudaError_t psolve_configure(int max_fs);
+// The tree-scheduled forward sweep with its first `skip` tickets taken before
+// the launch (testing the bounded waits: those items never run).
+void launch_solve_fwd_skip(const DevMesh& dm, const d4* b, d4* y, int skip, cudaStream_t s);
 // Launch shape of the tree-scheduled sweeps whose largest CTA-path front has
 // max_fs nodes: the CTAs of each kernel that fit on the device at once, and the
 // dynamic shared memory

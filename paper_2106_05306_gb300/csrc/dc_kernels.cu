@@ -921,6 +921,14 @@ void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s) {
     dc_note_launch();
     k_solve_fwd<<<dm.n_long + nblk(dm.n_short, 8), 256, 0, s>>>(dm, b, y);
 }
+void launch_solve_fwd_skip(const DevMesh& dm, const d4* b, d4* y, int skip, cudaStream_t s) {
+    const PSolveDev& ps = dm.ps;
+    cudaMemsetAsync(ps.sched, 0, sizeof(int) * (ps.S + 1), s);
+    const int ticket = skip;   // pageable source: copied before the call returns
+    cudaMemcpyAsync(ps.sched, &ticket, sizeof(int), cudaMemcpyHostToDevice, s);
+    dc_note_launch();
+    k_ps_fwd_tree<<<std::min(ps.tree_grid_f, ps.n_items), 256, ps.tree_smem, s>>>(ps, b, y);
+}
 void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode, const int* contact,
                       const d4* nb, const double* c, d4* f, int* case_, double* c_out, cudaStream_t s) {
     if (dm.solver == 1) {

@@ -112,3 +112,36 @@ def test_supernodal_rejects_block_preconditioner():
     sc = scenes.small_scene(4, seed=1)
     with pytest.raises(dc.DCError, match="DC_ERR_INVALID"):
         make_cloth(sc, global_solver=1, adj_precond=1)
+
+
+def test_supernodal_sweep_wait_gives_up_and_reports():
+    """A sweep started past its first work item leaves a parent waiting for a child
+    that never runs (a flag that nothing sets): the bounded wait gives up after
+    about a second, the context reports DC_ERR_CUDA from then on, and the GPU
+    stays usable for a new context."""
+    import time
+
+    import paper_2106_05306_gb300 as dc
+    from paper_2106_05306_gb300._lib import check
+    sc = scenes.batch_instance(0, n_steps=2)     # 43 x 43 nodes: a 9-level tree
+    cloth = make_cloth(sc, global_solver=1)
+    with pytest.raises(dc.DCError, match="DC_ERR_INVALID"):
+        check(cloth._lib.dc_debug_sweep_wait_timeout(cloth._ctx, 0), cloth._ctx)
+    t0 = time.perf_counter()
+    st = cloth._lib.dc_debug_sweep_wait_timeout(cloth._ctx, 1)
+    elapsed = time.perf_counter() - t0
+    with pytest.raises(dc.DCError, match="DC_ERR_CUDA.*timed out"):
+        check(st, cloth._ctx)
+    assert elapsed < 60.0
+    with pytest.raises(dc.DCError, match="timed out"):
+        cloth.stats()
+    cloth.close()
+    fresh = make_cloth(sc, global_solver=1)
+    M = oracle_model(sc)
+    rhs = np.random.default_rng(4).standard_normal((sc.m, 3))
+    got = fresh.global_solve(cuda(rhs)).cpu().numpy()
+    want = np.zeros_like(rhs)
+    want[M.free] = M.solve_P(rhs[M.free])
+    assert rel_inf(got, want) < 1e-11
+    fresh.stats()
+    fresh.close()
