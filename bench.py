@@ -71,7 +71,7 @@ TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_pe
            # k_ps_fwd_tree: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
            # profiles/k_ps_fwd_tree_batched_96cloths.md), scaled by the sweep's flops
            "ps_solve_fwd": {"bytes_per_flop": (143285504.0 + 12266240.0) / 62559690.0,
-                            "source_sha": "b62290a3bd33d00b"}}
+                            "source_sha": "7d84422f04d8e204"}}
 
 
 def parse_args(argv=None):
