@@ -38,7 +38,7 @@ inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
 // Per triangle at x_{n+1}: R (polar factor), S^-1, 1/tr S (reading R1).
 __global__ void k_adj_setup_tri(DevMesh dm, const d4* __restrict__ x1, d4* __restrict__ tr0,
-                                d4* __restrict__ tr1, d4* __restrict__ tr2) {
+                                d4* __restrict__ tr1, d4* __restrict__ tr2, d4* __restrict__ tav) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= dm.T) return;
     int4 tr = dm.tri[t];
@@ -65,9 +65,24 @@ __global__ void k_adj_setup_tri(DevMesh dm, const d4* __restrict__ x1, d4* __res
         R[q] = s00 * F[q] + s01 * F[3 + q];
         R[3 + q] = s01 * F[q] + s11 * F[3 + q];
     }
+    // per vertex v of the triangle: a_v = (g_v0 R1 - g_v1 R0) / tr S, and the
+    // projector P = I - R0 R0^T - R1 R1^T (the front assembly reads them for
+    // every pair of the triangle's vertices instead of forming them again)
+    for (int v = 0; v < 3; ++v) {
+        double gv0, gv1;
+        if (v == 1) { gv0 = g.x; gv1 = g.y; }
+        else if (v == 2) { gv0 = g.z; gv1 = g.w; }
+        else { gv0 = -(g.x + g.z); gv1 = -(g.y + g.w); }
+        st(tav + 4 * (long)t + v, (gv0 * R[3] - gv1 * R[0]) * it, (gv0 * R[4] - gv1 * R[1]) * it,
+           (gv0 * R[5] - gv1 * R[2]) * it);
+    }
+    double P[9];
+    for (int r = 0; r < 3; ++r)
+        for (int c2 = 0; c2 < 3; ++c2) P[3 * r + c2] = ((r == c2) ? 1.0 : 0.0) - R[r] * R[c2] - R[3 + r] * R[3 + c2];
+    st(tav + 4 * (long)t + 3, P[0], P[1], P[2], P[4]);
     st(tr0 + t, R[0], R[1], R[2], s00);
     st(tr1 + t, R[3], R[4], R[5], s01);
-    st(tr2 + t, s11, it, 0.0, 0.0);   // tr S = t, so 1/tr S = it
+    st(tr2 + t, s11, it, P[5], P[8]);   // tr S = t, so 1/tr S = it
 }
 
 // Per vertex at x_{n+1}: sphere-projection derivative data (q_hat, kappa = s/|q|)
@@ -667,7 +682,7 @@ __global__ void k_adj_rhs(DevMesh dm, AdjDev ad, const d4* __restrict__ gx, cons
 
 void adj_setup(const DevMesh& dm, const AdjDev& ad, const d4* x1, const d4* v1, cudaStream_t s) {
     dc_note_launch();
-    k_adj_setup_tri<<<nblk(dm.T, 128), 128, 0, s>>>(dm, x1, ad.tr0, ad.tr1, ad.tr2);
+    k_adj_setup_tri<<<nblk(dm.T, 128), 128, 0, s>>>(dm, x1, ad.tr0, ad.tr1, ad.tr2, ad.tav);
     dc_note_launch();
     k_adj_setup_bend<<<nblk(dm.m, 128), 128, 0, s>>>(dm, x1, ad.bq);
     dc_note_launch();

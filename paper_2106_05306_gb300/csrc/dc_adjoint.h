@@ -8,7 +8,9 @@ struct AdjDev {
     const double* mu;     // [m] friction coefficient of each node's instance
     d4* tr0;              // [T] (R col 0, S^-1_00)
     d4* tr1;              // [T] (R col 1, S^-1_01)
-    d4* tr2;              // [T] (S^-1_11, 1/tr S, -, -)
+    d4* tr2;              // [T] (S^-1_11, 1/tr S, P_12, P_22)
+    d4* tav;              // [4T] per triangle: a_v (xyz) of its 3 vertices, then (P_00, P_01, P_02, P_11);
+                          // a_v = (g_v0 R1 - g_v1 R0) / tr S, P = I - R0 R0^T - R1 R1^T
     d4* bq;               // [m] (q_hat, s/|q|)
     d4* dinv;             // [3 m_free] rows of the constrained block inverse D+
     d4* slip;             // [m_free] (t_hat, h mu f_N / |u_T|) for slip nodes

@@ -257,6 +257,7 @@ dc_status ensure_adjoint(dc_ctx* c) {
         RET(dalloc(c, P, &a.tr0, T));
         RET(dalloc(c, P, &a.tr1, T));
         RET(dalloc(c, P, &a.tr2, T));
+        RET(dalloc(c, P, &a.tav, 4 * (size_t)T));
         RET(dalloc(c, P, &a.bq, m));
         RET(dalloc(c, P, &a.dinv, 3 * (size_t)mf));
         RET(dalloc(c, P, &a.slip, mf));

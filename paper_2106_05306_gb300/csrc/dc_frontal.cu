@@ -67,24 +67,22 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
             else { ga0 = -(g.x + g.z); ga1 = -(g.y + g.w); }
             if (b == 1) { gb0 = g.x; gb1 = g.y; } else if (b == 2) { gb0 = g.z; gb1 = g.w; }
             else { gb0 = -(g.x + g.z); gb1 = -(g.y + g.w); }
-            d4 A0 = ld(ad.tr0 + t), A1 = ld(ad.tr1 + t), A2 = ld(ad.tr2 + t);
-            double R0[3] = {A0.x, A0.y, A0.z}, R1[3] = {A1.x, A1.y, A1.z};
-            double s00 = A0.w, s01 = A1.w, s11 = A2.x, itr = A2.y;
+            const d4 A0 = ld(ad.tr0 + t), A1 = ld(ad.tr1 + t), A2 = ld(ad.tr2 + t);
+            const double s00 = A0.w, s01 = A1.w, s11 = A2.x, itr = A2.y;
+            // the triangle's a_a, a_b and projector P, formed once per triangle
+            const d4 va = ld(ad.tav + 4 * (long)t + a), vb = ld(ad.tav + 4 * (long)t + b);
+            const d4 pp = ld(ad.tav + 4 * (long)t + 3);
+            const double aa[3] = {va.x, va.y, va.z}, ab[3] = {vb.x, vb.y, vb.z};
+            const double P[9] = {pp.x, pp.y, pp.z, pp.y, pp.w, A2.z, pp.z, A2.z, A2.w};
             double w = h2 * dm.wt[t];
             double gg = ga0 * gb0 + ga1 * gb1;
             double gam = ga0 * gb0 * s00 + (ga0 * gb1 + ga1 * gb0) * s01 + ga1 * gb1 * s11;
-            double aa[3], ab[3];
-            for (int q = 0; q < 3; ++q) {
-                aa[q] = (ga0 * R1[q] - ga1 * R0[q]) * itr;
-                ab[q] = (gb0 * R1[q] - gb1 * R0[q]) * itr;
-            }
             double trS = 1.0 / itr;
-            // block = w ((g_a.g_b) I - trS a_a a_b^T - gam (I - R0 R0^T - R1 R1^T))
+            // block = w ((g_a.g_b) I - trS a_a a_b^T - gam P)
             for (int r = 0; r < 3; ++r)
                 for (int c = 0; c < 3; ++c) {
                     double dl = (r == c) ? 1.0 : 0.0;
-                    H[3 * r + c] += w * (gg * dl - trS * aa[r] * ab[c] -
-                                         gam * (dl - R0[r] * R0[c] - R1[r] * R1[c]));
+                    H[3 * r + c] += w * (gg * dl - trS * aa[r] * ab[c] - gam * P[3 * r + c]);
                 }
         } else {
             int b = -code - 1;

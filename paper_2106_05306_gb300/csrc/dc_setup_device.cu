@@ -677,7 +677,8 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     for (size_t i = 0; i < k; ++i) { add(MF * 4); add(MF * 4); add(MF * d4b); add(MF * d4b); }
     add(T * d4b); add(T * d4b); add(m * d4b);
     for (int s = 0; s < 2; ++s) {
-        add(T * d4b); add(T * d4b); add(T * d4b); add(m * d4b); add(3 * MF * d4b); add(MF * d4b); add(MF * 4);
+        add(T * d4b); add(T * d4b); add(T * d4b); add(4 * T * d4b); add(m * d4b); add(3 * MF * d4b); add(MF * d4b);
+        add(MF * 4);
     }
     for (int i = 0; i < 15; ++i) add(m * d4b);
     add((mr + 1) * 4 * m * 8); add(mr * 4 * m * 8); add((mr + 1) * B * 8); add((mr + 1) * B * 8);
