@@ -590,10 +590,16 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
     }
     c->act_on = false;
     if (debug && std::getenv("DC_DEBUG_GMRES")[0] == '2') {
-        int mx = 0;
-        for (int i = 0; i < B; ++i) mx = std::max(mx, gs[i].total);
-        std::fprintf(stderr, "[dc gmres] step: %lld lockstep iterations, largest instance total %d\n",
-                     c->adj_batch_iters - lock0, mx);
+        int mx = 0, arg = 0, over8 = 0;
+        for (int i = 0; i < B; ++i) {
+            if (gs[i].total > mx) mx = gs[i].total, arg = i;
+            over8 += gs[i].total > 8;
+        }
+        const double r = gs[arg].beta0 > 0.0 ? gs[arg].res / gs[arg].beta0 : 0.0;
+        std::fprintf(stderr,
+                     "[dc gmres] step: %lld lockstep iterations, largest instance total %d (instance %d, rel "
+                     "residual %.3e), %d instances above 8\n",
+                     c->adj_batch_iters - lock0, mx, arg, r, over8);
     }
     for (int i = 0; i < B; ++i) {
         iters[i] = gs[i].total;
