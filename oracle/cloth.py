@@ -23,10 +23,13 @@ Paper passages followed (section / equation labels of the paper):
   * Sec. 4.1-4.2, Eq. adjoint / adjoint_pd / adjoint_vv / adjoint_v /
     ppr_adjoint, and "Extensions" (curved obstacles): the adjoint.
 
-Readings of passages the paper leaves open (each also listed in the design doc):
+Readings of passages the paper leaves open (the CUDA path implements the same ones):
   R1 stretch: A_t maps a triangle to its deformation gradient F = X G (3x2),
      w_t = k_stretch * rest area, projection onto matrices with orthonormal
-     columns (the polar factor of F).
+     columns (the polar factor of F).  A collapsed triangle
+     (det F^T F <= 1e-30 (tr F^T F)^2) gets a polar factor built from the
+     singular vectors of F with a fixed choice of the missing one, and its
+     projection is treated as locally constant in the adjoint (dR = 0).
   R2 bending: A_b is the cotangent Laplacian row of vertex b divided by its
      barycentric area, w_b = k_bend * area, projection onto the sphere of radius
      s_b = |A_b x_rest| (p_b = 0 where the rest shape is flat, s_b = 0).
@@ -270,17 +273,64 @@ class Contacts:
 def polar(F):
     """Polar factor R and stretch S of 3x2 matrices F = R S (R1).
 
-    S = sqrt(F^T F) in closed form for 2x2 SPD C: S = (C + sqrt(det C) I) /
-    sqrt(tr C + 2 sqrt(det C)), then R = F S^-1.
+    S = sqrt(F^T F) in closed form for 2x2 SPD C = F^T F:
+    S = (C + sqrt(det C) I) / sqrt(tr C + 2 sqrt(det C)), then R = F S^-1.
+    sqrt(det C) is taken as |f_1 x f_2| (Lagrange's identity,
+    det F^T F = |f_1 x f_2|^2 for the columns f_1, f_2 of F), which is exact
+    for a triangle collapsed onto a line.  A collapsed triangle
+    (det C <= 1e-30 (tr C)^2, see ``polar_degenerate``) has no unique polar
+    factor; it gets the one of ``_polar_collapsed`` and S is left singular.
     """
     C = np.einsum("tck,tcl->tkl", F, F)
-    det = C[:, 0, 0] * C[:, 1, 1] - C[:, 0, 1] * C[:, 1, 0]
-    sd = np.sqrt(np.maximum(det, 0.0))
+    cr = np.cross(F[:, :, 0], F[:, :, 1])
+    sd = np.sqrt(np.einsum("tc,tc->t", cr, cr))
     tr = C[:, 0, 0] + C[:, 1, 1]
     t = np.sqrt(tr + 2.0 * sd)
-    S = (C + sd[:, None, None] * np.eye(2)) / t[:, None, None]
-    R = np.einsum("tck,tkl->tcl", F, np.linalg.inv(S))
+    deg = polar_degenerate(F)
+    S = np.zeros_like(C)
+    ok = ~deg
+    S[ok] = (C[ok] + sd[ok, None, None] * np.eye(2)) / t[ok, None, None]
+    S[deg] = C[deg] / np.maximum(t[deg], 1e-300)[:, None, None]
+    R = np.zeros_like(F)
+    R[ok] = np.einsum("tck,tkl->tcl", F[ok], np.linalg.inv(S[ok]))
+    for i in np.nonzero(deg)[0]:
+        R[i] = _polar_collapsed(F[i])
     return R, S
+
+
+def polar_degenerate(F):
+    """Reading R1, degenerate case: det(F^T F) <= 1e-30 (tr F^T F)^2, i.e. the
+    smaller singular value of F is at most ~1e-15 of the larger one."""
+    cr = np.cross(F[:, :, 0], F[:, :, 1])
+    det = np.einsum("tc,tc->t", cr, cr)
+    tr = np.einsum("tck,tck->t", F, F)
+    return det <= 1e-30 * tr * tr
+
+
+def _polar_collapsed(F):
+    """A polar factor of a 3x2 F of rank <= 1 (reading R1, degenerate case), from
+    the singular vectors of F with the missing left vector chosen by a fixed rule:
+    v1 = the eigenvector of C = F^T F of its larger eigenvalue, v2 = v1 rotated
+    by +90 degrees; u1 = F v1 / |F v1|; u2 = normalize(u1 x e_a) with e_a the
+    coordinate axis of smallest |u1_a| (lowest index on ties); R = u1 v1^T + u2 v2^T.
+    F = 0 gives R = [e_x, e_y]."""
+    C = F.T @ F
+    tr = C[0, 0] + C[1, 1]
+    if tr == 0.0:
+        return np.array([[1.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+    d = 0.5 * (C[0, 0] - C[1, 1])
+    r = np.hypot(d, C[0, 1])
+    v1 = np.array([d + r, C[0, 1]]) if d >= 0.0 else np.array([C[0, 1], r - d])
+    v1 = v1 / np.linalg.norm(v1)
+    v2 = np.array([-v1[1], v1[0]])
+    w1 = F @ v1
+    u1 = w1 / np.linalg.norm(w1)
+    a = int(np.argmin(np.abs(u1)))
+    e = np.zeros(3)
+    e[a] = 1.0
+    u2 = np.cross(u1, e)
+    u2 = u2 / np.linalg.norm(u2)
+    return np.outer(u1, v1) + np.outer(u2, v2)
 
 
 def project_bending(q, s_b, q_rest):
@@ -297,7 +347,8 @@ def project_bending(q, s_b, q_rest):
 
 def polar_derivative(R, S, dF):
     """dR for F = R S perturbed by dF (3x2): dR = R Om + (I - R R^T) dF S^-1 with
-    Om = w [[0,-1],[1,0]], w = ((R^T dF)_21 - (R^T dF)_12) / tr S."""
+    Om = w [[0,-1],[1,0]], w = ((R^T dF)_21 - (R^T dF)_12) / tr S.  (Not defined
+    for a collapsed triangle; ``hessian_W`` takes dR = 0 there, reading R1.)"""
     RtdF = R.T @ dF
     w = (RtdF[1, 0] - RtdF[0, 1]) / np.trace(S)
     Om = np.array([[0.0, -w], [w, 0.0]])
@@ -477,6 +528,7 @@ def hessian_W(model: Model, x):
     rows, cols, vals = [], [], []
     T = len(model.tris)
     # stretch: vec(F) index (c, k) -> 3*k + c; A_t[(c,k), (a,c')] = G[a,k] delta_cc'
+    deg = polar_degenerate(F)
     for t in range(T):
         A = np.zeros((6, 9))
         for a in range(3):
@@ -484,7 +536,7 @@ def hessian_W(model: Model, x):
                 for cc in range(3):
                     A[3 * k + cc, 3 * a + cc] = model.G[t, a, k]
         Jp = np.zeros((6, 6))
-        for e in range(6):
+        for e in range(6 if not deg[t] else 0):   # collapsed: projection taken as locally constant (R1)
             dF = np.zeros((3, 2))
             dF[e % 3, e // 3] = 1.0
             dR = polar_derivative(R[t], S[t], dF)

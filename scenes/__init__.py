@@ -212,6 +212,31 @@ def small_scene(n: int = 4, seed: int = 0, contact: str = "sphere", pinned: bool
                  loss_weights(n * n, seed))
 
 
+def liftoff_scene(mu: float = 1.2, n: int = 4, n_steps: int = 3) -> Scene:
+    """A flat, unstretched cloth lying on the ground at rest, three of its nodes
+    moving straight up at 0.4 m/s, with a 1 cm detection margin so that they are
+    still in the contact set: their neighbours stick under gravity, they take off,
+    and (at this friction) no node slips."""
+    pos, tris = grid_mesh(n, side=0.3, height=0.0, x0=-0.15, z0=0.0)
+    v0 = np.zeros_like(pos)
+    v0[[n + 1, n + 2, 2 * n + 2]] = (0.0, 0.4, 0.0)
+    prm = Params(k_stretch=100.0, k_bend=5e-3, density=0.1, mu=mu, h=1.0 / 60.0, contact_margin=0.01)
+    return Scene("liftoff", n, pos, tris, np.zeros(0, np.int32), [Obstacle("plane")], prm, pos.copy(), v0,
+                 n_steps, loss_weights(n * n, 0))
+
+
+def collapsed_triangle_scene(n: int = 5, n_steps: int = 3) -> Scene:
+    """A small pinned cloth whose first triangle starts collapsed onto a line:
+    node (1, 1) is moved onto the segment between nodes (0, 0) and (1, 0)."""
+    pos, tris = grid_mesh(n, side=0.3, height=0.3, x0=-0.15, z0=0.0)
+    x0 = pos.copy()
+    x0[n + 1] = 0.5 * (pos[0] + pos[1])
+    pins = np.array([n - 1, n * n - 1], dtype=np.int32)
+    prm = Params(k_stretch=200.0, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0)
+    return Scene("collapsed", n, pos, tris, pins, [Obstacle("plane")], prm, x0, np.zeros_like(pos), n_steps,
+                 loss_weights(n * n, 1))
+
+
 def serve_request(seed: int, dof_lo: float = 1e3, dof_hi: float = 3e4, steps_lo: int = 25,
                   steps_hi: int = 150) -> Scene:
     """One request of the served workload: a square cloth of log-uniform DOF count

@@ -273,7 +273,208 @@ def test_adjoint_matches_central_differences(contact, seed):
 
 
 def test_mu_gradient_vanishes_without_slip():
-    sc = scenes.small_scene(4, seed=0, contact="none", n_steps=2)
-    M, xs, vs, recs = _run(sc, tol=1e-12)
+    """With contacts that stick or take off but never slip, the converged step does
+    not depend on mu (it only enters the slip branch and the stick test): the
+    adjoint's dL/dmu is exactly 0, and the central difference in mu is 0 up to
+    rounding (intermediate PD iterations may pass through a slip case, so the
+    iterates, though not the fixed point, see mu)."""
+    sc = scenes.liftoff_scene(mu=1.2)
+    M, xs, vs, recs = _run(sc, tol=1e-14)
+    cases = np.zeros(3, int)
+    for r in recs:
+        cases += np.bincount(r.cases, minlength=3)
+    assert cases[oc.STICK] > 0 and cases[oc.TAKEOFF] > 0 and cases[oc.SLIP] == 0
     _, _, dth = oc.rollout_gradient(M, recs, sc.loss_w)
     assert dth[2] == 0.0
+    assert abs(dth[0]) > 0.0 and abs(dth[1]) > 0.0
+    e = 1e-6 * sc.params.mu
+    lp = np.sum(sc.loss_w * _run(sc, tol=1e-14, mu=sc.params.mu + e)[1][-1])
+    lm = np.sum(sc.loss_w * _run(sc, tol=1e-14, mu=sc.params.mu - e)[1][-1])
+    assert abs(lp - lm) / (2 * e) <= 1e-8 * max(1.0, abs(lp))
+
+
+# --------------------------------------------------------------------- degenerate triangles (R1)
+
+def test_polar_of_collapsed_triangles():
+    """A 3x2 F of rank <= 1 is flagged degenerate; its polar factor still has
+    orthonormal columns and is a closest one: |F - R|_F^2 = sum_i (sigma_i - 1)^2
+    with the singular values of numpy's SVD (the minimum over all matrices with
+    orthonormal columns)."""
+    rng = np.random.default_rng(11)
+    Fs = [np.outer(rng.standard_normal(3), rng.standard_normal(2)) for _ in range(20)]
+    Fs.append(np.zeros((3, 2)))
+    Fs.append(np.array([[1.0, 2.0], [0.0, 0.0], [0.0, 0.0]]))
+    Fs.append(np.array([[0.3, 0.3], [-1.0, -1.0], [2.0, 2.0]]))
+    F = np.stack(Fs)
+    assert np.all(oc.polar_degenerate(F))
+    R, _ = oc.polar(F)
+    np.testing.assert_allclose(np.einsum("tck,tcl->tkl", R, R), np.broadcast_to(np.eye(2), (len(F), 2, 2)),
+                               atol=1e-14)
+    sig = np.linalg.svd(F, compute_uv=False)
+    np.testing.assert_allclose(np.sum((F - R) ** 2, axis=(1, 2)), np.sum((sig - 1.0) ** 2, axis=1), atol=1e-12)
+    # nearly collapsed but above the threshold: the closed form, equal to the SVD factor
+    F2 = np.stack([np.outer(rng.standard_normal(3), rng.standard_normal(2)) for _ in range(20)])
+    U, s, Vt = np.linalg.svd(F2, full_matrices=False)
+    F2 = np.einsum("tck,tk,tkl->tcl", U, np.stack([s[:, 0], 1e-9 * s[:, 0]], axis=1), Vt)
+    assert not np.any(oc.polar_degenerate(F2))
+    R2, _ = oc.polar(F2)
+    np.testing.assert_allclose(R2, U @ Vt, atol=1e-6)
+
+
+def test_step_with_a_collapsed_triangle():
+    """A cloth that starts with one triangle collapsed onto a line: the first local
+    step meets the degenerate case, the step stays finite, the surrogate g~ still
+    decreases after every local and global step (the collapsed projection is still
+    a closest point), and the triangle is no longer collapsed afterwards."""
+    sc = scenes.collapsed_triangle_scene()
+    M = oc.model_from_scene(sc)
+    assert oc.polar_degenerate(M.deformation_gradients(sc.x0))[0]
+    tr = []
+    x1, v1, _ = oc.step(M, sc.x0, sc.v0, n_iters=30, trace=tr)
+    assert np.all(np.isfinite(x1)) and np.all(np.isfinite(v1))
+    t = np.asarray(tr)
+    assert np.all(np.diff(t) <= 1e-14 * np.abs(t[:-1]))
+    assert not np.any(oc.polar_degenerate(M.deformation_gradients(x1)))
+
+
+# --------------------------------------------------------------------- rest operators and P
+
+def test_rest_deformation_gradient_is_a_rotation():
+    """F(x_rest) has orthonormal columns for every triangle (G = E D_m^-1 maps the
+    rest triangle to itself), and a uniform scaling by s has singular values (s, s)."""
+    pos, tris = scenes.grid_mesh(5, side=0.4)
+    rng = np.random.default_rng(3)
+    pos = pos + 0.02 * rng.standard_normal(pos.shape)          # a non-flat, irregular rest shape
+    G, area = oc.triangle_rest(pos, tris)
+    X = pos[tris]
+    F = np.einsum("tac,tak->tck", X, G)
+    np.testing.assert_allclose(np.einsum("tck,tcl->tkl", F, F), np.broadcast_to(np.eye(2), (len(tris), 2, 2)),
+                               atol=1e-12)
+    F2 = np.einsum("tac,tak->tck", 2.5 * X, G)
+    np.testing.assert_allclose(np.linalg.svd(F2, compute_uv=False), 2.5, rtol=1e-12)
+    e1, e2 = X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]
+    np.testing.assert_allclose(area, 0.5 * np.linalg.norm(np.cross(e1, e2), axis=1), rtol=1e-14)
+
+
+def test_P_is_the_hessian_of_the_quadratic_energy():
+    """P = M + h^2 sum_i w_i A_i^T A_i (Eq. pd_global) is the Hessian of
+    |x|_M^2/2 + h^2 sum_i w_i |A_i x|^2 / 2 per coordinate; central differences of
+    that quadratic (written here from the per-triangle edge vectors and the bending
+    rows) recover every entry of the scalar P_s."""
+    pos, tris = scenes.grid_mesh(4, side=0.3)
+    rng = np.random.default_rng(5)
+    pos = pos + 0.01 * rng.standard_normal(pos.shape)
+    M = _model(pos, tris, k_stretch=70.0, k_bend=3e-3, density=0.2)
+    h = M.h
+
+    def energy(u):                     # u: one coordinate of every node
+        e = 0.5 * np.sum(M.mass * u * u)
+        ut = u[M.tris]
+        F = np.einsum("ta,tak->tk", ut, M.G)
+        e += 0.5 * h * h * np.sum(M.w_t * np.sum(F * F, axis=1))
+        q = M.Lb @ u
+        e += 0.5 * h * h * np.sum(M.w_b * q * q)
+        return e
+
+    P = M.P.toarray()
+    eps = 1e-3
+    for i in range(M.m):
+        for j in range(M.m):
+            ei = np.zeros(M.m); ei[i] = eps
+            ej = np.zeros(M.m); ej[j] = eps
+            fd = (energy(ei + ej) - energy(ei - ej) - energy(ej - ei) + energy(-ei - ej)) / (4 * eps * eps)
+            assert abs(fd - P[i, j]) <= 1e-9 * abs(P).max()
+
+
+def test_compliance_is_the_row_sum_of_the_contact_block_of_h_P_inverse():
+    """c_j = h (P^-1 1_I)_j (reading R5): the banded solve against the explicit dense
+    inverse of P_ff (numpy inverse, i.e. unit-vector solves)."""
+    sc = scenes.hanging_cloth(n=8, n_steps=1)
+    M = oc.model_from_scene(sc)
+    nodes = M.free[[3, 4, 5, 17, 40, 41]]
+    ctr = oc.Contacts(nodes, np.zeros(len(nodes), int), np.zeros((len(nodes), 3)), np.zeros(len(nodes)))
+    c = M.compliance(ctr)
+    Pinv = np.linalg.inv(M.Pff.toarray())
+    pos = np.searchsorted(M.free, nodes)
+    expect = M.h * Pinv[np.ix_(pos, pos)].sum(axis=1)
+    np.testing.assert_allclose(c, expect, rtol=1e-12)
+    assert np.all(c > 0)
+
+
+# --------------------------------------------------------------------- curved obstacles (R4)
+
+def test_sphere_and_capsule_signed_distance():
+    """phi and its gradient against points placed at known distances: along random
+    directions from a sphere's centre; across a capsule's barrel (perpendicular to
+    the axis) and beyond its end caps; plus a brute-force distance to the segment
+    (dense sampling) for random points."""
+    rng = np.random.default_rng(8)
+    c = np.array([0.1, -0.2, 0.3])
+    sph = scenes.Obstacle("sphere", center=tuple(c), radius=0.4)
+    for _ in range(50):
+        u = rng.standard_normal(3); u /= np.linalg.norm(u)
+        d = rng.uniform(-0.35, 0.5)
+        ph, n = oc.signed_distance(sph, c + (0.4 + d) * u)
+        assert abs(ph - d) < 1e-14 and np.allclose(n, u, atol=1e-12)
+    a, b = np.array([-0.3, 0.1, 0.0]), np.array([0.5, 0.3, 0.2])
+    cap = scenes.Obstacle("capsule", a=tuple(a), b=tuple(b), radius=0.15)
+    e = (b - a) / np.linalg.norm(b - a)
+    for _ in range(50):
+        w = rng.standard_normal(3); w -= np.dot(w, e) * e; w /= np.linalg.norm(w)
+        t = rng.uniform(0.0, 1.0)
+        d = rng.uniform(-0.14, 0.3)
+        ph, n = oc.signed_distance(cap, a + t * (b - a) + (0.15 + d) * w)            # barrel
+        assert abs(ph - d) < 1e-13 and np.allclose(n, w, atol=1e-12)
+        u = rng.standard_normal(3); u /= np.linalg.norm(u)
+        end, sgn = (a, -1.0) if rng.uniform() < 0.5 else (b, 1.0)
+        if sgn * np.dot(u, e) < 0:
+            u -= 2 * np.dot(u, e) * e                                                # point into the cap's half-space
+        ph, n = oc.signed_distance(cap, end + (0.15 + d) * u)                        # end cap
+        assert abs(ph - d) < 1e-13 and np.allclose(n, u, atol=1e-12)
+    seg = a[None, :] + np.linspace(0.0, 1.0, 200001)[:, None] * (b - a)[None, :]
+    for _ in range(20):
+        x = a + rng.uniform(-0.5, 1.5) * (b - a) + 0.4 * rng.standard_normal(3)
+        brute = np.min(np.linalg.norm(seg - x, axis=1)) - 0.15
+        ph, _ = oc.signed_distance(cap, x)
+        assert abs(ph - brute) < 1e-11
+
+
+def test_obstacle_normal_jacobian_matches_central_differences():
+    rng = np.random.default_rng(9)
+    obs = [scenes.Obstacle("sphere", center=(0.0, 0.1, 0.2), radius=0.3),
+           scenes.Obstacle("capsule", a=(-0.3, 0.0, 0.0), b=(0.4, 0.1, 0.3), radius=0.1)]
+    for ob in obs:
+        for _ in range(30):
+            x = rng.uniform(-0.6, 0.6, 3)
+            J = oc.normal_jacobian(ob, x)
+            fd = np.zeros((3, 3))
+            for k in range(3):
+                d = np.zeros(3); d[k] = 1e-6
+                fd[:, k] = (oc.signed_distance(ob, x + d)[1] - oc.signed_distance(ob, x - d)[1]) / 2e-6
+            np.testing.assert_allclose(J, fd, atol=1e-6)
+            g = np.array([(oc.signed_distance(ob, x + 1e-6 * np.eye(3)[k])[0] -
+                           oc.signed_distance(ob, x - 1e-6 * np.eye(3)[k])[0]) / 2e-6 for k in range(3)])
+            np.testing.assert_allclose(oc.signed_distance(ob, x)[1], g, atol=1e-8)
+
+
+@pytest.mark.parametrize("contact,seed", [("sphere", 0), ("sphere", 5), ("capsule", 1), ("capsule", 4)])
+def test_curved_obstacles_are_not_penetrated(contact, seed):
+    """Every contact node ends its step on or outside the tangent plane at its
+    closest surface point (stick and slip put u_N = 0 with the bias phi(x_n)/h,
+    take-off u_N >= 0), so on a convex obstacle phi(x_{n+1}) >= 0 up to rounding
+    (reading R4); nodes outside the contact set may move in by at most about
+    h^2 |a| for this step's acceleration a."""
+    sc = scenes.small_scene(4, seed=seed, contact=contact, drop=True, n_steps=4)
+    M = oc.model_from_scene(sc)
+    xs, vs, recs = oc.rollout(M, sc.x0, sc.v0, sc.n_steps)
+    n_contacts = 0
+    for n, rec in enumerate(recs):
+        for a, j in enumerate(rec.contacts.nodes):
+            ph, _ = oc.signed_distance(M.obstacles[rec.contacts.obs[a]], rec.x_np1[j])
+            assert ph >= -1e-12
+            n_contacts += 1
+        for j in M.free:
+            ph = min(oc.signed_distance(ob, rec.x_np1[j])[0] for ob in M.obstacles)
+            acc = np.linalg.norm(vs[n + 1][j] - vs[n][j]) / M.h
+            assert ph >= -(M.h ** 2) * acc - 1e-12
+    assert n_contacts > 0
