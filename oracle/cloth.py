@@ -45,6 +45,9 @@ Readings of passages the paper leaves open (the CUDA path implements the same on
      of the contact block of h P^-1, a Gershgorin bound on the coupling).  The
      printed M-splitting (Eq. ly_et_al_govrningEq) diverges for the stiffness
      values used here; any positive compliance has the same fixed point.
+     Alternatives for ablation (params.contact_compliance): "diag_pinv"
+     c_j = h (P^-1)_jj, "diag_p" c_j = h / P_jj, and "mass": the splitting as
+     printed, M v^{k+1} = b - (P - M) v^k + h J^T r^{k+1} with c_j = h / m_j.
   R7 contact adjoint: the exact linearisation of the converged step, solved as
      one KKT system; stick nodes constrain z_j = 0, slip nodes constrain
      (n - mu t).z_j = 0 (oblique), and the slip friction direction adds
@@ -132,6 +135,9 @@ class Model:
         self.k_b = float(params.k_bend)
         self.g = np.asarray(params.gravity, dtype=np.float64)
         self.delta = float(params.contact_margin)
+        self.compliance_mode = getattr(params, "contact_compliance", "rowsum")
+        if self.compliance_mode not in ("rowsum", "diag_pinv", "diag_p", "mass"):
+            raise ValueError(self.compliance_mode)
 
         self.G, self.area = triangle_rest(self.rest, self.tris)
         self.Lb, self.abar = cotan_laplacian(self.rest, self.tris, self.area)
@@ -249,13 +255,25 @@ class Model:
                         np.array(normals).reshape(-1, 3), np.array(betas, dtype=np.float64))
 
     def compliance(self, contacts):
-        """c_j = h (P^-1 1_I)_j for the current contact set (R5)."""
+        """c_j = h (P^-1 1_I)_j for the current contact set (R5), or the
+        ablation choices h (P^-1)_jj, h / P_jj, h / m_j."""
         if len(contacts.nodes) == 0:
             return np.zeros(0)
         pos = np.searchsorted(self.free, contacts.nodes)
-        ind = np.zeros(len(self.free))
-        ind[pos] = 1.0
-        return self.h * self.solve_P(ind)[pos]
+        if self.compliance_mode == "rowsum":
+            ind = np.zeros(len(self.free))
+            ind[pos] = 1.0
+            return self.h * self.solve_P(ind)[pos]
+        if self.compliance_mode == "diag_pinv":
+            out = np.zeros(len(pos))
+            for a, p in enumerate(pos):
+                e = np.zeros(len(self.free))
+                e[p] = 1.0
+                out[a] = self.h * self.solve_P(e)[p]
+            return out
+        if self.compliance_mode == "diag_p":
+            return self.h / self.Pff.diagonal()[pos]
+        return self.h / self.mass[contacts.nodes]
 
 
 class Contacts:
@@ -472,17 +490,26 @@ def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace
         n_iters = model.params.n_pd_iters
     limit = n_iters if n_iters is not None else max_iters
     k = 0
+    mass_split = model.compliance_mode == "mass"
     while k < limit:
         x = x_n + h * v
-        R, pb, _, _, _ = model.project(x)                          # local step
+        R, pb, F_k, _, q_k = model.project(x)                      # local step
         if trace is not None:
             trace.append(model.g_tilde(x, y, R, pb))
-        bhat = Mdy + h * model.AtWp(R - F_n, pb - q_n)             # Eq. pd_global / pd_velocity
+        if mass_split:
+            # Eq. ly_et_al_govrningEq as printed: M v_half = b - (P - M) v^k + h J^T r,
+            # with b - (P - M) v^k = M (y - x_n)/h + h sum_i w_i A_i^T (p_i - A_i x^k)
+            bhat = Mdy + h * model.AtWp(R - F_k, pb - q_k)
+        else:
+            bhat = Mdy + h * model.AtWp(R - F_n, pb - q_n)         # Eq. pd_global / pd_velocity
         rhs = bhat.copy()
         if nc:
             rhs[contacts.nodes] += h * f                           # Eq. pd_velocity_with_contact
         v_half = np.zeros_like(v)
-        v_half[free] = model.solve_P(rhs[free])                    # global step
+        if mass_split:
+            v_half[free] = rhs[free] / model.mass[free][:, None]   # global step of the mass splitting
+        else:
+            v_half[free] = model.solve_P(rhs[free])                # global step
         if trace is not None:
             trace.append(model.g_tilde(x_n + h * v_half, y, R, pb))
         v_new = v_half

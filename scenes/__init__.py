@@ -46,6 +46,8 @@ class Params:
     gravity: tuple = GRAVITY
     n_pd_iters: int = 20
     contact_margin: float = 1e-6   # detection margin delta (m)
+    # compliance of the per-node contact solve: "rowsum", "diag_pinv", "diag_p" or "mass"
+    contact_compliance: str = "rowsum"
 
 
 @dataclasses.dataclass

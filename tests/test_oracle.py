@@ -478,3 +478,62 @@ def test_curved_obstacles_are_not_penetrated(contact, seed):
             acc = np.linalg.norm(vs[n + 1][j] - vs[n][j]) / M.h
             assert ph >= -(M.h ** 2) * acc - 1e-12
     assert n_contacts > 0
+
+
+# --------------------------------------------------------------------- contact compliance choices (R5)
+
+def _soft_contact_scene():
+    sc = scenes.small_scene(5, seed=3, contact="both", drop=True, n_steps=1)
+    return dataclasses.replace(sc, params=dataclasses.replace(sc.params, k_stretch=0.15, k_bend=1e-7))
+
+
+def test_compliance_choices_share_the_fixed_point():
+    """Every compliance choice of the per-node contact solve, the printed mass
+    splitting of Eq. ly_et_al_govrningEq included, converges to the same solution
+    of Eq. implicit_with_contact where it converges at all (a soft cloth, where
+    h^2 rho(M^-1 (P - M)) < 1)."""
+    sc = _soft_contact_scene()
+    M0 = oc.model_from_scene(sc)
+    A = M0.Pff.toarray()
+    m = M0.mass[M0.free]
+    assert np.max(np.abs(np.linalg.eigvals((A - np.diag(m)) / m[:, None]))) < 1.0
+    ref = None
+    for mode in ("rowsum", "diag_pinv", "diag_p", "mass"):
+        M = oc.model_from_scene(sc, contact_compliance=mode)
+        x1, v1, rec = oc.step(M, sc.x0, sc.v0, tol=1e-13, max_iters=20000)
+        assert rec.iters < 20000 and len(rec.contacts) > 0
+        _check_contact_law(M, rec, tol=1e-10)
+        if ref is None:
+            ref = v1
+        else:
+            np.testing.assert_allclose(v1, ref, rtol=0, atol=1e-11)
+
+
+def test_mass_splitting_diverges_at_cloth_stiffness():
+    """At the hanging cloth's stiffness h^2 rho(M^-1 (P - M)) is about 1.3e3, so the
+    printed splitting blows up within one step of 20 iterations (the reason the
+    default reading uses the prefactorised P)."""
+    sc = scenes.hanging_cloth(n_steps=1)
+    M = oc.model_from_scene(sc, contact_compliance="mass")
+    A = M.Pff.toarray()
+    m = M.mass[M.free]
+    assert np.max(np.abs(np.linalg.eigvals((A - np.diag(m)) / m[:, None]))) > 1e3
+    with np.errstate(all="ignore"):
+        _, v1, _ = oc.step(M, sc.x0, sc.v0, n_iters=20)
+    assert not np.all(np.abs(v1) < 1e20)
+
+
+def test_diagonal_compliances_match_the_dense_matrices():
+    """diag_pinv: c_j = h (P_ff^-1)_jj from unit-vector solves against numpy's dense
+    inverse; diag_p: h / (P_ff)_jj; mass: h / m_j."""
+    sc = scenes.hanging_cloth(n=7, n_steps=1)
+    nodes = np.array([3, 9, 10, 30, 44])
+    ctr = oc.Contacts(nodes, np.zeros(5, int), np.zeros((5, 3)), np.zeros(5))
+    M = oc.model_from_scene(sc, contact_compliance="diag_pinv")
+    pos = np.searchsorted(M.free, nodes)
+    dense = M.Pff.toarray()
+    np.testing.assert_allclose(M.compliance(ctr), M.h * np.diag(np.linalg.inv(dense))[pos], rtol=1e-12)
+    M = oc.model_from_scene(sc, contact_compliance="diag_p")
+    np.testing.assert_allclose(M.compliance(ctr), M.h / np.diag(dense)[pos], rtol=1e-14)
+    M = oc.model_from_scene(sc, contact_compliance="mass")
+    np.testing.assert_allclose(M.compliance(ctr), M.h / M.mass[nodes], rtol=1e-14)
