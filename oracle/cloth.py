@@ -330,8 +330,10 @@ def _polar_collapsed(F):
     the singular vectors of F with the missing left vector chosen by a fixed rule:
     v1 = the eigenvector of C = F^T F of its larger eigenvalue, v2 = v1 rotated
     by +90 degrees; u1 = F v1 / |F v1|; u2 = normalize(u1 x e_a) with e_a the
-    coordinate axis of smallest |u1_a| (lowest index on ties); R = u1 v1^T + u2 v2^T.
-    F = 0 gives R = [e_x, e_y]."""
+    first coordinate axis (x, y, z order) with |u1_a| <= 0.6 (one exists since
+    1/sqrt(3) < 0.6; the choice only changes where a component crosses 0.6, far
+    from the axis-aligned collapses whose other components are rounding noise);
+    R = u1 v1^T + u2 v2^T.  F = 0 gives R = [e_x, e_y]."""
     C = F.T @ F
     tr = C[0, 0] + C[1, 1]
     if tr == 0.0:
@@ -343,7 +345,7 @@ def _polar_collapsed(F):
     v2 = np.array([-v1[1], v1[0]])
     w1 = F @ v1
     u1 = w1 / np.linalg.norm(w1)
-    a = int(np.argmin(np.abs(u1)))
+    a = int(np.nonzero(np.abs(u1) <= 0.6)[0][0])
     e = np.zeros(3)
     e[a] = 1.0
     u2 = np.cross(u1, e)
@@ -596,8 +598,11 @@ def hessian_W(model: Model, x):
     return Hm, (R, pb, F, S, q)
 
 
-def adjoint_step(model: Model, rec: StepRecord, gx, gv):
+def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None):
     """Back-propagate (dL/dx_{n+1}, dL/dv_{n+1}) through one converged step.
+
+    ``hess``, if given, is ``hessian_W(model, rec.x_np1)`` computed beforehand
+    (e.g. for many steps in parallel); the result is the same.
 
     Returns (dL/dx_n, dL/dv_n, dL/d[k_stretch, k_bend, mu], z, eta).
 
@@ -616,7 +621,7 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv):
     gx = np.asarray(gx, dtype=np.float64)
     gv = np.asarray(gv, dtype=np.float64)
     g = gv + h * gx
-    Hw, (R, pb, F, S, q) = hessian_W(model, x1)
+    Hw, (R, pb, F, S, q) = hessian_W(model, x1) if hess is None else hess
     Mfull = sp.diags(np.repeat(model.mass, 3))
     fd = _dof(free)
     H = (Mfull + h * h * Hw)[fd][:, fd].tolil()
@@ -705,8 +710,9 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv):
     return dx_n, dv_n, np.array([dks, dkb, dmu]), z, eta
 
 
-def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dtraj_x=None):
-    """Reverse pass over a rollout: returns (dL/dx0, dL/dv0, dL/d[k_s, k_b, mu])."""
+def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dtraj_x=None, hessians=None):
+    """Reverse pass over a rollout: returns (dL/dx0, dL/dv0, dL/d[k_s, k_b, mu]).
+    ``hessians[n]``, if given, is hessian_W at records[n].x_np1."""
     gx = np.asarray(dL_dx_final, dtype=np.float64).copy()
     gv = np.zeros_like(gx) if dL_dv_final is None else np.asarray(dL_dv_final, dtype=np.float64).copy()
     dth = np.zeros(3)
@@ -714,7 +720,7 @@ def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dt
     for n in range(N - 1, -1, -1):
         if dL_dtraj_x is not None:
             gx = gx + dL_dtraj_x[n + 1]
-        gx, gv, d, _, _ = adjoint_step(model, records[n], gx, gv)
+        gx, gv, d, _, _ = adjoint_step(model, records[n], gx, gv, None if hessians is None else hessians[n])
         dth += d
     if dL_dtraj_x is not None:
         gx = gx + dL_dtraj_x[0]
