@@ -59,19 +59,18 @@ SINGLE_WORKLOAD = ("draped cloth 61x61 (3721 nodes, 7200 triangles), sphere r=0.
                    "125 steps at h=1/120 s, 20 PD iterations/step, forward + checkpointed adjoint (every 25 steps), "
                    "gradient w.r.t. x0, v0, k_stretch, k_bend, mu")
 
-# FP32 CUDA-core peak from unit counts and the maximum SM clock (GB300: 152 SMs,
-# 128 FP32 lanes per SM, FMA = 2 flops, 2070 MHz); FP64 nominal 1.25 TFLOP/s.
+# CUDA-core ALU peaks derived from unit counts and the maximum SM clock (GB300:
+# 152 SMs, 128 FP32 lanes per SM, FMA = 2 flops, 2070 MHz; FP64 at 1.25 TFLOP/s
+# nominal, i.e. 2 FP64 FMA per SM and clock).  The roofline fractions use the
+# FMA peaks measured by dc_fma_peak in the same run; these are reported beside them.
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-FP64_PEAK_TFLOPS = 1.25
+FP32_DERIVED_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+FP64_DERIVED_TFLOPS = 1.25
+HBM_FALLBACK_GBS = 6800.0
 
-# DRAM traffic per launch of the roofline kernel from the ncu capture summarised in
-# profiles/ (null when the kernel source changed since the capture).
-TRAFFIC = {"front": {"bytes": None, "source_sha": None}, "solve_fwd": {"bytes_per_nnz": None, "source_sha": None},
-           # k_ps_fwd_tree: DRAM bytes per algorithmic flop of one sweep (96-cloth capture,
-           # profiles/k_ps_fwd_tree_batched_96cloths.md), scaled by the sweep's flops
-           "ps_solve_fwd": {"bytes_per_flop": (143285504.0 + 12266240.0) / 62559690.0,
-                            "source_sha": "7d84422f04d8e204"}}
+# DRAM read + write bytes per launch measured by ncu on this workload (the
+# kernel-traffic profile; null once the kernel's source file has changed).
+TRAFFIC = {}
 
 
 def parse_args(argv=None):
@@ -88,6 +87,7 @@ def parse_args(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / single / served side runs")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--cpu-all-cores", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
 
@@ -215,15 +215,57 @@ def oracle_sample(workload: str):
     return 1.0 / ((t1 - t0) / 5 + (t2 - t1)), t2 - t0, sample
 
 
-def cpu_baseline_subprocess(workload: str):
-    """Run the oracle sample single-threaded in a child process."""
+def _oracle_job(job):
+    """One cloth of the sample on one core: model setup (untimed), then one forward
+    step and the adjoint step of that step, each timed."""
+    workload, seed = job
+    import scenes
+    from oracle import cloth as oc
+    sc = scenes.batch_instance(seed, n_steps=BATCH_STEPS) if workload == "batch" else scenes.draped_cloth()
+    M = oc.model_from_scene(sc)
+    t0 = time.perf_counter()
+    _, _, rec = oc.step(M, sc.x0, sc.v0)
+    t1 = time.perf_counter()
+    oc.adjoint_step(M, rec, sc.loss_w, sc.loss_w * 0.0)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1
+
+
+def oracle_sample_all_cores(workload: str):
+    """The oracle on every host core at once: worker processes (spawned, one BLAS
+    thread each) take the sampled cloths (batch: 32 of the 256, seeds 0, 8, ...;
+    single: 2 copies of the 61x61 cloth per worker) and time one forward and one
+    adjoint step each, concurrently.  Value = workers / mean (forward + adjoint)
+    seconds per cloth under that load."""
+    import multiprocessing
+    n = os.cpu_count() or 1
+    jobs = [(workload, s) for s in range(0, BATCH, 8)] if workload == "batch" else [(workload, 0)] * (2 * n)
+    ctx = multiprocessing.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(n) as pool:
+        res = pool.map(_oracle_job, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    per = statistics.mean(a + b for a, b in res)
+    workers = min(n, len(jobs))
+    sample = (f"oracle on {workers} host cores at once ({len(jobs)} cloths: "
+              + ("32 of the 256 batched cloths, seeds 0, 8, ..., 248" if workload == "batch" else
+                 "copies of the 61x61 draped cloth")
+              + "), one forward + one adjoint step each; value = workers / mean per-cloth (fwd + adj) seconds")
+    return workers / per, wall, sample, workers
+
+
+def cpu_baseline_subprocess(workload: str, all_cores: bool = False):
+    """Run the oracle sample in a child process: single-threaded, or on all host
+    cores with one single-threaded worker process per core."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
     env.pop("RANK", None)
     env.pop("WORLD_SIZE", None)
-    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload], env=env,
-                       capture_output=True, text=True, timeout=900)
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-sample", "--workload", workload]
+    if all_cores:
+        cmd.append("--cpu-all-cores")
+    r = subprocess.run(cmd, env=env, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": "failed: " + r.stderr[-300:]}
     return json.loads(r.stdout.strip().splitlines()[-1])
@@ -420,6 +462,119 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=8, seed0=10000
                         "from the first arrival to the last result"}
 
 
+def measured_peaks():
+    """HBM copy bandwidth from the generated MEASURED_PEAKS.json, and the FP64 /
+    FP32 FMA peaks measured now by dc_fma_peak."""
+    import paper_2106_05306_gb300 as dc
+    hbm, src = HBM_FALLBACK_GBS, "fallback 6.8 TB/s (MEASURED_PEAKS.json absent)"
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            hbm = float(json.load(open(path))["hbm_gbs"])
+            src = "measured (MEASURED_PEAKS.json: STREAM-style copy)"
+        except (ValueError, KeyError):
+            pass
+    return {"hbm_gbs": hbm, "hbm_source": src, "fp64_tflops": dc.fma_peak(64), "fp32_tflops": dc.fma_peak(32),
+            "fma_source": "measured by dc_fma_peak (independent FMA chains on every SM, best of 3)",
+            "fp64_derived_tflops": FP64_DERIVED_TFLOPS, "fp32_derived_tflops": FP32_DERIVED_TFLOPS}
+
+
+# Kernel classes of the per-kernel table: dc_set_kernel_timer class -> kernels
+KERNEL_CLASSES = {
+    "local": "k_local (stretch + bending projections and their rhs terms)",
+    "gather": "k_gather_rhs (per-node right-hand side gather)",
+    "solve_fwd": "k_ps_fwd_tree (forward supernodal sweep, FP64, 3 columns)",
+    "solve_bwd": "k_ps_bwd_tree (backward sweep + fused per-node Signorini-Coulomb solve)",
+    "front": "k_front_level (one level of the FP32 multifrontal LDL^T of the adjoint preconditioner)",
+    "msolve": "k_msolve_fwd_tree / k_msolve_bwd_tree (preconditioner solves)",
+    "krylov": "k_bmdot / k_breduce / k_bvupdate / k_bscale (GMRES vectors)",
+    "apply_h": "k_adj_elem + k_adj_gather (matrix-free adjoint operator)",
+    "assemble": "adjoint per-step setup and front assembly",
+}
+
+
+def kernel_model(cls, st, contacts_per_launch):
+    """Algorithmic bytes and FP flops of one launch (the unit of work of each class is
+    described in the design doc; bytes count FP64 = 8 B, indices = 4 B, no padding)."""
+    m, mf, T, nb = st["n_nodes"], st["n_free"], st["n_tris"], st["bend_nnz"]
+    if cls == "local":
+        return 92.0 * m + 100.0 * T + 12.0 * nb, 150.0 * T + 25.0 * m + 12.0 * nb, "fp64"
+    if cls == "gather":
+        return 96.0 * mf + 60.0 * T + 12.0 * nb + 24.0 * m, 12.0 * T + 6.0 * nb + 12.0 * mf, "fp64"
+    if cls in ("solve_fwd", "solve_bwd") and st["global_solver"] == 1:
+        e = st["psolve_flops"] / 6.0                     # panel entries read by one sweep
+        b, f = 8.0 * e + 48.0 * mf, st["psolve_flops"]
+        if cls == "solve_bwd":
+            b += 124.0 * contacts_per_launch
+            f += 60.0 * contacts_per_launch
+        return b, f, "fp64"
+    if cls == "front":
+        levels = max(st["front_levels"], 1)
+        return 8.0 * st["front_entries"] / levels, st["front_flops"] / levels, "fp32"
+    return None, None, None
+
+
+def kernel_table(wl, peaks, steps_per_pass=1):
+    """One extra (untimed-for-value) bench step per kernel class with that class's
+    CUDA-event timer on: time per bench step, launches, mean launch time, and for
+    the classes with an algorithmic count, achieved GB/s and TFLOP/s against the
+    measured HBM and FMA peaks."""
+    rows = {}
+    for cls in KERNEL_CLASSES:
+        st0 = wl.ctx.stats()
+        wl.ctx.set_kernel_timer(cls)
+        for _ in range(steps_per_pass):
+            wl.step()
+        st = wl.ctx.stats()
+        wl.ctx.set_kernel_timer("none")
+        n = max(st["timer_launches"], 1)
+        ms = st["timer_ms"] / steps_per_pass
+        row = {"kernels": KERNEL_CLASSES[cls], "ms_per_bench_step": ms,
+               "launches_per_bench_step": st["timer_launches"] / steps_per_pass,
+               "mean_launch_us": 1e3 * st["timer_ms"] / n}
+        nc = ((st["contacts_takeoff"] + st["contacts_stick"] + st["contacts_slip"]) -
+              (st0["contacts_takeoff"] + st0["contacts_stick"] + st0["contacts_slip"])) / max(
+            st["steps"] - st0["steps"], 1)
+        b, f, prec = kernel_model(cls, st, nc)
+        if b is not None:
+            sec = 1e-3 * st["timer_ms"] / n
+            alu_peak = peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
+            row.update({"algorithmic_bytes_per_launch": b, "algorithmic_flops_per_launch": f, "precision": prec,
+                        "achieved_gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / peaks["hbm_gbs"],
+                        "achieved_tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak})
+            row["bound"] = "alu" if row["alu_frac"] >= row["hbm_frac"] else "hbm"
+        rows[cls] = row
+    total = sum(r["ms_per_bench_step"] for r in rows.values())
+    for r in rows.values():
+        r["share_of_timed_kernels"] = r["ms_per_bench_step"] / total if total > 0 else None
+    return rows
+
+
+def roofline(table, peaks):
+    """Roofline object of the dominant kernel: the class with an algorithmic count
+    that takes the most time per bench step."""
+    counted = {k: r for k, r in table.items() if "achieved_tflops" in r}
+    cls = max(counted, key=lambda k: counted[k]["ms_per_bench_step"])
+    r = counted[cls]
+    alu = r["bound"] == "alu"
+    peak = (peaks["fp64_tflops"] if r["precision"] == "fp64" else peaks["fp32_tflops"]) if alu else peaks["hbm_gbs"]
+    achieved = r["achieved_tflops"] if alu else r["achieved_gbs"]
+    roof = {"kernel": r["kernels"], "class": cls, "bound": r["bound"], "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s" if alu else "GB/s", "frac": achieved / peak,
+            "peak_source": (peaks["fma_source"] + f" ({r['precision'].upper()})") if alu else peaks["hbm_source"],
+            "frac_of_derived_peak": (achieved / (peaks["fp64_derived_tflops"] if r["precision"] == "fp64" else
+                                                 peaks["fp32_derived_tflops"])) if alu else None,
+            "hbm_frac": r["hbm_frac"], "traffic": None, "mean_launch_us": r["mean_launch_us"],
+            "algorithmic_flops_per_launch": r["algorithmic_flops_per_launch"],
+            "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
+    tr = TRAFFIC.get(cls)
+    if tr and tr.get("source_sha") == kernel_sha(os.path.join(ROOT, "paper_2106_05306_gb300", "csrc",
+                                                              tr["source"])):
+        roof["traffic"] = tr["bytes_per_launch"]
+        roof["traffic_note"] = tr["note"]
+    return roof
+
+
 def run_ours(args):
     import torch
 
@@ -434,13 +589,11 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     wl = Workload(args.workload, args, dev)
-    roof_cls = args.roofline_kernel or ("solve_fwd" if args.workload == "batch" else "front")
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     for _ in range(max(args.warmup, 0)):
         wl.step()
     torch.cuda.synchronize()
     st0 = wl.ctx.stats()
-    wl.ctx.set_kernel_timer(roof_cls)
     clocks = ClockSampler(local)
     barrier(world)
     clocks.start()
@@ -457,7 +610,6 @@ def run_ours(args):
     barrier(world)
     clk = clocks.stop()
     st1 = wl.ctx.stats()
-    wl.ctx.set_kernel_timer("none")
     max_ms = aggregate(total_ms, world)
     value = world * args.steps * wl.steps_per_bench_step / (max_ms / 1e3)
 
@@ -476,7 +628,9 @@ def run_ours(args):
            "h2d_bytes_per_step": 3 * m * 3 * 8,
            "d2h_bytes_per_step": 4 * m * 3 * 8 + 3 * 8 * wl.cloths}
 
-    roof = roofline(roof_cls, st1)
+    peaks = measured_peaks()
+    table = kernel_table(wl, peaks)
+    roof = roofline(table, peaks)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -486,11 +640,15 @@ def run_ours(args):
         "gpu_launches": int(st1["kernel_launches"] - st0["kernel_launches"]),
         "library_launches_before_timed": int(st0["kernel_launches"]),
         "roofline": roof,
+        "kernels": table,
+        "peaks": peaks,
         "clocks": clk,
         "adjoint": {"gmres_iters_per_cloth_step": (st1["adj_iters"] - st0["adj_iters"]) / max(
             st1["adj_steps"] - st0["adj_steps"], 1),
             "lockstep_iters_per_step": (st1["adj_batch_iters"] - st0["adj_batch_iters"]) / max(
                 args.steps * wl.n_cloth, 1),
+            "fallback_cloth_steps": st1["adj_fallbacks"] - st0["adj_fallbacks"],
+            "fallback_iters": st1["adj_fallback_iters"] - st0["adj_fallback_iters"],
             "nonconverged_cloth_steps": st1["adj_nonconverged"] - st0["adj_nonconverged"]},
     }
     wl.ctx.close()
@@ -502,56 +660,12 @@ def run_ours(args):
         out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_subprocess(args.workload)
+        out["cpu_baseline_all_cores"] = cpu_baseline_subprocess(args.workload, all_cores=True)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-def roofline(cls, st):
-    """Roofline of the dominant kernel from the live CUDA-event timing of its launches."""
-    launches = st["timer_launches"]
-    kern_ms = st["timer_ms"] / max(launches, 1)
-    if cls == "front":
-        n_fact = launches / max(st["front_levels"], 1)
-        work = st["front_flops"] * n_fact / max(launches, 1)          # flops per launch (mean)
-        roof = {"kernel": "k_front_level (one level of the FP32 multifrontal LDL^T)", "bound": "alu",
-                "achieved": work / (kern_ms / 1e3) / 1e12, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz", "traffic": None}
-        tr = TRAFFIC["front"]
-        src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_frontal.cu")
-        if tr["source_sha"] == kernel_sha(src):
-            roof["traffic"] = tr["bytes"]
-    elif st.get("global_solver", 0) == 1:
-        work = st["psolve_flops"]                         # exact count of one sweep, 3 right-hand sides
-        name = "k_ps_fwd_tree" if cls == "solve_fwd" else "k_ps_bwd_tree"
-        roof = {"kernel": f"{name} (P^-1 sweep, supernodal substitution, FP64, 3 right-hand sides; one launch per "
-                          f"sweep, fronts of the {st['front_levels']}-level trees taken in dependency order)",
-                "bound": "alu", "achieved": work / (kern_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 table of the profiling recipe)",
-                "traffic": None, "algorithmic_flops_per_launch": work}
-        tr = TRAFFIC.get("ps_" + cls)
-        src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_kernels.cu")
-        if tr and tr["source_sha"] == kernel_sha(src):
-            roof["traffic"] = tr["bytes_per_flop"] * work
-            roof["traffic_note"] = ("DRAM read+write of one sweep measured by ncu on 96 cloths, scaled to this "
-                                    "sweep by its flops (profiles/k_ps_fwd_tree_batched_96cloths.md)")
-    else:
-        nnz = st["fwd_solve_nnz"] if cls == "solve_fwd" else st["bwd_solve_nnz"]
-        work = 6.0 * nnz                                  # 3 right-hand sides: one FMA each per nonzero
-        roof = {"kernel": f"k_{cls} (P^-1 sweep with the explicit inverse factor rows, FP64, 3 right-hand sides)",
-                "bound": "alu", "achieved": work / (kern_ms / 1e3) / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "FP64 nominal 1.25 TFLOP/s (GB300 table of the profiling recipe)",
-                "traffic": None, "algorithmic_flops_per_launch": work}
-        tr = TRAFFIC.get(cls)
-        src = os.path.join(ROOT, "paper_2106_05306_gb300", "csrc", "dc_kernels.cu")
-        if tr and tr["bytes_per_nnz"] and tr["source_sha"] == kernel_sha(src):
-            roof["traffic"] = tr["bytes_per_nnz"] * nnz
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["mean_launch_us"] = kern_ms * 1e3
-    roof["launches_timed"] = launches
-    return roof
 
 
 def workload_config(wl, world):
@@ -563,7 +677,8 @@ def workload_config(wl, world):
                 "nodes": int(wl.ctx.m), "triangles": int(sum(s.tris.shape[0] for s in wl.scs)),
                 "cloth_steps_per_bench_step": wl.steps_per_bench_step, "pd_iters": 20, "checkpoint_every": 1,
                 "global_solver": "supernodal substitution (1)",
-                "graphs": "captured per rollout; bypassed while the roofline kernel timer runs (timed region)",
+                "graphs": "rollout replayed as a captured CUDA graph in the timed region (the per-kernel timer "
+                          "passes that feed the roofline run afterwards, outside it)",
                 "autotuned": True, "parallelism": f"replicas x{world}",
                 "l2": "flushed (512 MB write) before every timed step; inputs also larger than L2"}
     return {"workload": SINGLE_WORKLOAD if wl.n_cloth == SINGLE_STEPS else
@@ -599,8 +714,11 @@ def run_reference(args):
 def main():
     args = parse_args()
     if args.cpu_sample:
-        v, secs, sample = oracle_sample(args.workload)
-        print(json.dumps({"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+        if args.cpu_all_cores:
+            v, secs, sample, cores = oracle_sample_all_cores(args.workload)
+        else:
+            (v, secs, sample), cores = oracle_sample(args.workload), 1
+        print(json.dumps({"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
                           "seconds": secs}))
         return
     if args.impl == "reference":

@@ -9,22 +9,24 @@
  * Conventions for every entry point
  *  - Functions return a dc_status (0 = DC_OK) and never throw.  dc_last_error()
  *    gives a message for the last failing call on a context.
- *  - Node arrays are FP64, node-major "[m][3]" (x0,y0,z0,x1,...), in the node
- *    numbering of the mesh passed to dc_create_mesh.
+ *  - Node arrays are FP64 in the node numbering of the mesh passed to
+ *    dc_create_mesh, node-major "[m][3]" (x0,y0,z0,x1,...) by default, or
+ *    component-major "[3][m]" (all x, then all y, then all z) after
+ *    dc_set_layout(ctx, DC_LAYOUT_COMPONENT_MAJOR).
  *  - Array arguments may be host or device pointers (CUDA unified addressing
  *    tells them apart).  Device pointers keep the call asynchronous on the
  *    context's stream; if any argument is host memory the call synchronises the
  *    stream before it returns.  The caller owns every argument array; the
  *    library owns the factor, work buffers and checkpoints.
  *  - All GPU work is enqueued on the CUDA stream given to dc_create_mesh.
- *    Errors found on the device (non-finite values) are reported by the next
- *    synchronising call (dc_sync, dc_get_stats, or any call with host buffers).
- *    A triangular-solve sweep over the elimination trees (the supernodal
- *    substitution of global_solver 1, the preconditioner solves of the adjoint)
- *    is one launch whose CTAs wait for one another's fronts; every such wait is
- *    bounded, and one that gives up sets a sticky device flag that dc_sync,
- *    dc_get_stats and dc_backward report as DC_ERR_CUDA (the context's results
- *    are invalid from then on).
+ *    Errors found on the device are reported by the next synchronising call
+ *    (dc_sync, dc_get_stats, dc_backward, or any call with host buffers): a
+ *    non-finite state at the end of a forward step as DC_ERR_NONFINITE (reported
+ *    once); and a triangular-solve sweep over the elimination trees (the
+ *    supernodal substitution of global_solver 1, the preconditioner solves of
+ *    the adjoint) is one launch whose CTAs wait for one another's fronts, every
+ *    such wait is bounded, and one that gives up sets a sticky device flag
+ *    reported as DC_ERR_TIMEOUT (the context's results are invalid from then on).
  *  - A context is not thread-safe.
  *  - Batches.  dc_create_batch packs several cloths (instances) of any sizes
  *    into one context; every call below then works on all of them at once,
@@ -51,9 +53,29 @@ enum {
     DC_ERR_NOT_SPD = 3,      /* the PD matrix factorisation met a pivot <= 0 */
     DC_ERR_OOM = 4,          /* device allocation failed */
     DC_ERR_NONFINITE = 5,    /* a NaN/Inf was produced on the device */
-    DC_ERR_NONCONVERGED = 6, /* the adjoint solve hit its iteration cap */
-    DC_ERR_STATE = 7         /* call out of order (e.g. dc_step before dc_set_params) */
+    DC_ERR_NONCONVERGED = 6, /* an adjoint step stopped above adj_tol (after its fallback) */
+    DC_ERR_STATE = 7,        /* call out of order (e.g. dc_step before dc_set_params) */
+    DC_ERR_TIMEOUT = 8       /* a bounded device-side wait gave up (see above) */
 };
+
+/* Compliance c_j of the per-node contact solve (Eq. ly_et_al_govrningEq: the
+ * Signorini-Coulomb law is solved per node against a diagonal approximation of
+ * the velocity response to its impulse, v = v_free + c_j r_j).
+ *   DC_COMPLIANCE_ROWSUM (default): c_j = h (P^-1 1_I)_j, the row sum of the
+ *       contact block of h P^-1 (one extra P^-1 solve per step).
+ *   DC_COMPLIANCE_DIAG_PINV: c_j = h (P^-1)_jj (selected inversion of the factor,
+ *       once per dc_set_params).
+ *   DC_COMPLIANCE_DIAG_P: c_j = h / P_jj.
+ *   DC_COMPLIANCE_MASS: the splitting as printed, M v^{k+1} = b - (P - M) v^k +
+ *       h J^T r^{k+1} with c_j = h / m_j: the global step is a per-node division
+ *       by the mass instead of P^-1.  It converges only while h^2 rho(M^-1 (P-M)) < 1,
+ *       i.e. at small stiffness.
+ * Every choice has the same fixed point (Eq. implicit_with_contact); they differ
+ * in how fast (and whether) the K PD iterations of a step approach it. */
+enum { DC_COMPLIANCE_ROWSUM = 0, DC_COMPLIANCE_DIAG_PINV = 1, DC_COMPLIANCE_DIAG_P = 2, DC_COMPLIANCE_MASS = 3 };
+
+/* Layout of node arrays at the boundary (dc_set_layout). */
+enum { DC_LAYOUT_NODE_MAJOR = 0, DC_LAYOUT_COMPONENT_MAJOR = 1 };
 
 enum { DC_PLANE = 0, DC_SPHERE = 1, DC_CAPSULE = 2 };
 #define DC_MAX_OBSTACLES 16
@@ -88,10 +110,16 @@ typedef struct dc_params {
     int32_t global_solver;   /* how P^-1 is applied (Eq. pd_global): 0 = rows of the
                                 explicit inverse factors L^-1, L^-T, two launches per
                                 application (default; best for one small cloth);
-                                1 = level-scheduled supernodal substitution with L,
-                                about 4x fewer flops, one launch per tree level
-                                (best for batches; needs adj_precond 0).  Equal
-                                results up to rounding. */
+                                1 = supernodal substitution with L, about 4x fewer
+                                flops, one launch per sweep with the fronts of the
+                                elimination trees taken in dependency order (best for
+                                batches; needs adj_precond 0).  Equal results up to
+                                rounding. */
+    int32_t contact_compliance; /* DC_COMPLIANCE_* (default ROWSUM)                  */
+    int32_t adj_fallback;    /* 1 (default): an adjoint step whose GMRES stops above
+                                adj_tol is solved again by the fallback (dc_backward);
+                                0: no fallback, such a step makes dc_backward return
+                                DC_ERR_NONCONVERGED                                  */
     int32_t reserved_;
     dc_obstacle obstacles[DC_MAX_OBSTACLES];
 } dc_params;
@@ -130,6 +158,16 @@ typedef struct dc_stats {
     int32_t global_solver;     /* dc_params.global_solver in use                      */
     int32_t reserved_;
     double psolve_flops;       /* FP64 flops of one supernodal substitution sweep (3 columns) */
+    int64_t adj_fallbacks;     /* adjoint steps of one instance re-solved by the fallback */
+    int64_t adj_fallback_iters;/* GMRES iterations the fallback solves took            */
+    int32_t layout;            /* DC_LAYOUT_* of the node arrays                       */
+    int32_t contact_compliance;/* DC_COMPLIANCE_* in use                               */
+    int64_t device_bytes;      /* device memory the context holds now                 */
+    int64_t device_bytes_peak; /* ... at most since its creation                      */
+    int32_t n_nodes;           /* nodes of all instances                              */
+    int32_t n_tris;            /* triangles of all instances                          */
+    int64_t bend_nnz;          /* entries of the bending stencil rows (all vertices)  */
+    int64_t front_entries;     /* FP32 entries stored for one multifrontal factorisation */
 } dc_stats;
 
 /* Kernel classes for dc_set_kernel_timer. */
@@ -196,6 +234,28 @@ dc_status dc_set_params(dc_ctx* ctx, const dc_params* params);
  * Each instance's P is assembled and factorised on its own (host threads). */
 dc_status dc_set_params_batch(dc_ctx* ctx, int32_t n_instances, const dc_params* params);
 
+/* Node-array layout of every later call on ctx: DC_LAYOUT_NODE_MAJOR ([m][3],
+ * the default) or DC_LAYOUT_COMPONENT_MAJOR ([3][m]: the x block, then y, then
+ * z; for a batch m is the total node count and each block is the concatenation
+ * of the instances' nodes).  It applies to the state and gradient arguments of
+ * dc_step, dc_rollout (traj_x: [(n_steps+1)][3][m]), dc_backward (dL_dtraj_x:
+ * [(n_steps+1)][3][m]), dc_global_solve and dc_global_solve_static; dc_create_mesh
+ * and dc_create_batch always take [n][3] rest positions.  The conversion is part
+ * of the kernels that move node arrays across the boundary (no extra copy).  No
+ * counterpart in the paper.  DC_ERR_INVALID for an unknown layout. */
+dc_status dc_set_layout(dc_ctx* ctx, int32_t layout);
+
+/* Device bytes a context of these cloths would hold at most through dc_rollout
+ * of n_steps steps and dc_backward, computed on the host without touching the
+ * device (the meshes are ordered and P factorised on host threads, as
+ * dc_create_batch and dc_set_params_batch would): for admission of work by HBM
+ * budget.  instances: n_instances cloths (as for dc_create_batch); params: one
+ * dc_params per instance.  *bytes receives the total.  DC_ERR_INVALID /
+ * DC_ERR_NOT_SPD as dc_create_batch / dc_set_params_batch would report.  No
+ * counterpart in the paper. */
+dc_status dc_batch_hbm_bytes(int32_t n_instances, const dc_instance* instances, const dc_params* params,
+                             int32_t n_steps, int64_t* bytes);
+
 /* Replay the forward steps of dc_rollout and of dc_backward's checkpoint
  * recomputation as captured CUDA graphs (enable = 1) or launch them one by one
  * (0, the default).  A graph is captured on first use for a given step count and
@@ -230,8 +290,14 @@ dc_status dc_rollout(dc_ctx* ctx, int32_t n_steps, const double* x0, const doubl
  *   dL_dtraj_x: [(n_steps+1)][m][3] per-step dL/dx_n or NULL.
  * Outputs dL_dx0, dL_dv0: [m][3]; dL_dparams: [n_instances][3] =
  * dL/d(k_stretch, k_bend, mu) of each instance.
- * DC_ERR_NONCONVERGED is reported (after all outputs are written) when an
- * adjoint step reached adj_max_iters above adj_tol. */
+ * Each step's adjoint system is solved by flexible GMRES with the per-step
+ * preconditioner (adj_precond).  With adj_fallback = 1, an instance whose GMRES
+ * stops above adj_tol (iteration cap, or a restart cycle that no longer halves
+ * its residual) is solved again, alone, from its last iterate, by GMRES with the
+ * other preconditioner's sweep added (the node-block inverse of H around a
+ * fresh single-precision factorisation) and with an FP64-refined restart; the
+ * count is in dc_stats.adj_fallbacks.  DC_ERR_NONCONVERGED is reported (after
+ * all outputs are written) when an adjoint step still ends above adj_tol. */
 dc_status dc_backward(dc_ctx* ctx, const double* dL_dx_final, const double* dL_dv_final,
                       const double* dL_dtraj_x, double* dL_dx0, double* dL_dv0,
                       double* dL_dparams);
@@ -252,14 +318,19 @@ dc_status dc_set_kernel_timer(dc_ctx* ctx, int32_t kernel_class);
  * caching allocator under a fixed budget, or a latency-bound loop that cannot
  * take the device-wide synchronisation cudaMalloc/cudaFree may cause.  No
  * counterpart in the paper.  It allocates nothing: rhs and out must be device
- * arrays [m][3] (host pointers are rejected with DC_ERR_INVALID), and its three
+ * arrays (host pointers are rejected with DC_ERR_INVALID), and its three
  * intermediate node vectors live in a fixed library array of 6 MiB per GPU,
  * held from library load until process exit, which serves meshes of at most
- * 65536 nodes (larger meshes: DC_ERR_INVALID).  The first call on a device looks
- * up that array's address (cudaGetSymbolAddress, device current); make it
- * before any stream capture.  Every call shares the array: calls that overlap on
- * the GPU (other streams or contexts on the same device) race and must be
- * serialised by the caller.  Asynchronous on the context's stream. */
+ * 65536 nodes (larger meshes: DC_ERR_INVALID).  The device that was current at
+ * dc_create_mesh must be current (DC_ERR_INVALID otherwise); the first call on
+ * a device looks up that array's address (cudaGetSymbolAddress); make it before
+ * any stream capture.  Every call shares the array: calls that overlap on the
+ * GPU (other streams or contexts on the same device) race and must be
+ * serialised by the caller.  With global_solver 1 the substitution also writes
+ * the context's own sweep vectors and dependency flags (allocated by
+ * dc_set_params), so calls on one context must also be serialised with its
+ * other calls (the context's stream does that).  Asynchronous on the context's
+ * stream. */
 dc_status dc_global_solve_static(dc_ctx* ctx, const double* rhs, double* out);
 
 /* Testing the bounded waits of the tree-scheduled sweeps (global_solver 1).
@@ -270,8 +341,18 @@ dc_status dc_global_solve_static(dc_ctx* ctx, const double* rhs, double* out);
  * call synchronises and returns DC_ERR_CUDA when the fault was raised (DC_OK if
  * no skipped item had a waiting parent).  The context's results are invalid
  * afterwards: destroy it.  DC_ERR_INVALID without global_solver 1 or with
- * skip_items outside [1, number of items). */
+ * skip_items outside [1, number of items).  Returns DC_ERR_TIMEOUT when the
+ * wait gave up. */
 dc_status dc_debug_sweep_wait_timeout(dc_ctx* ctx, int32_t skip_items);
+
+/* Measured fused-multiply-add throughput of the GPU's CUDA cores, in TFLOP/s
+ * (2 flops per FMA), for precision 64 (FP64) or 32 (FP32): a kernel of
+ * independent FMA chains on every SM, n_iter x 128 FMAs per chain and thread,
+ * best of three launches timed with CUDA events on the current device (legacy
+ * default stream, synchronous).  It changes no clock or power setting.  The
+ * denominator of the roofline fraction of the ALU-bound kernels.  No
+ * counterpart in the paper.  DC_ERR_INVALID for another precision or n_iter < 1. */
+dc_status dc_fma_peak(int32_t precision, int32_t n_iter, double* tflops);
 
 /* Counters and factor sizes (synchronises the stream). */
 dc_status dc_get_stats(dc_ctx* ctx, dc_stats* out);
@@ -359,7 +440,7 @@ void dc_server_destroy(dc_server* srv);
 /* Fill *p with the library defaults (k_stretch 1e3, k_bend 1e-3, density 0.1,
  * mu 0.3, h 1/120, g = (0,-9.8,0), delta 1e-6, K = 20, adjoint tol 1e-10,
  * 2000 iterations, restart 200, checkpoint every step, no obstacles,
- * multifrontal preconditioner). */
+ * multifrontal preconditioner, ROWSUM compliance, adjoint fallback on). */
 void dc_default_params(dc_params* p);
 
 #ifdef __cplusplus

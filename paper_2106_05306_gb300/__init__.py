@@ -23,16 +23,18 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (DC_CAPSULE, DC_MAX_OBSTACLES, DC_PLANE, DC_SPHERE, STATUS_NAMES, DCError, check, dc_instance,
-                   dc_params, dc_request, dc_result, dc_server_config, dc_server_stats, dc_stats, load)
+from ._lib import (COMPLIANCE, DC_CAPSULE, DC_MAX_OBSTACLES, DC_PLANE, DC_SPHERE, LAYOUTS, STATUS_NAMES, DCError,
+                   check, dc_instance, dc_params, dc_request, dc_result, dc_server_config, dc_server_stats, dc_stats,
+                   load)
 
-__all__ = ["Cloth", "ClothBatch", "Server", "rollout_fn", "DCError", "load"]
+__all__ = ["Cloth", "ClothBatch", "Server", "rollout_fn", "batch_hbm_bytes", "fma_peak", "DCError", "load"]
 
 _KIND = {"plane": DC_PLANE, "sphere": DC_SPHERE, "capsule": DC_CAPSULE}
 
 _PARAM_DEFAULTS = dict(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0, gravity=(0.0, -9.8, 0.0),
                        contact_margin=1e-6, n_pd_iters=20, obstacles=(), adj_tol=1e-10, adj_max_iters=2000,
-                       adj_restart=200, checkpoint_every=1, adj_precond=0, global_solver=0)
+                       adj_restart=200, checkpoint_every=1, adj_precond=0, global_solver=0,
+                       contact_compliance="rowsum", adj_fallback=1)
 
 
 def _torch():
@@ -82,6 +84,9 @@ def _make_params(lib, kw) -> dc_params:
     p.checkpoint_every = int(q["checkpoint_every"])
     p.adj_precond = int(q["adj_precond"])
     p.global_solver = int(q["global_solver"])
+    cm = q["contact_compliance"]
+    p.contact_compliance = COMPLIANCE[cm] if isinstance(cm, str) else int(cm)
+    p.adj_fallback = int(q["adj_fallback"])
     obstacles = list(q["obstacles"])
     if len(obstacles) > DC_MAX_OBSTACLES:
         raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
@@ -114,6 +119,7 @@ class _Context:
         self.node_offsets = offs
         self.m = int(offs[-1])
         self.params = None
+        self.layout = "node_major"
 
     # ------------------------------------------------------------------ helpers
     def _arr(self, a, name):
@@ -128,9 +134,12 @@ class _Context:
             raise ValueError(f"{name}: expected {self.m} x 3 values, got {tuple(a.shape)}")
         return a.contiguous()
 
+    def _node_shape(self):
+        return (3, self.m) if self.layout == "component_major" else (self.m, 3)
+
     def _like(self, a, shape=None):
         torch = _torch()
-        shape = (self.m, 3) if shape is None else shape
+        shape = self._node_shape() if shape is None else shape
         return torch.empty(shape, dtype=torch.float64, device=a.device,
                            pin_memory=(a.device.type == "cpu" and a.is_pinned()))
 
@@ -151,7 +160,7 @@ class _Context:
         x0 = self._arr(x0, "x0")
         v0 = self._arr(v0, "v0")
         xN, vN = self._like(x0), self._like(x0)
-        tr = self._like(x0, (n_steps + 1, self.m, 3)) if traj else None
+        tr = self._like(x0, (n_steps + 1,) + self._node_shape()) if traj else None
         check(self._lib.dc_rollout(self._ctx, int(n_steps), x0.data_ptr(), v0.data_ptr(), xN.data_ptr(),
                                    vN.data_ptr(), tr.data_ptr() if tr is not None else None), self._ctx)
         self.n_steps = int(n_steps)
@@ -181,6 +190,13 @@ class _Context:
         check(self._lib.dc_global_solve(self._ctx, rhs.data_ptr(), out.data_ptr()), self._ctx)
         return out
 
+    def set_layout(self, layout):
+        """Node arrays of later calls: "node_major" ((m, 3), the default) or
+        "component_major" ((3, m): all x, then all y, then all z)."""
+        check(self._lib.dc_set_layout(self._ctx, LAYOUTS[layout]), self._ctx)
+        self.layout = layout
+        return self
+
     def set_graphs(self, enable=True):
         """Replay the forward steps of rollouts as captured CUDA graphs (results unchanged)."""
         check(self._lib.dc_set_graphs(self._ctx, 1 if enable else 0), self._ctx)
@@ -194,7 +210,7 @@ class _Context:
     def stats(self):
         s = dc_stats()
         check(self._lib.dc_get_stats(self._ctx, ctypes.byref(s)), self._ctx)
-        return {k: getattr(s, k) for k, _ in s._fields_}
+        return {k: getattr(s, k) for k, _ in s._fields_ if k != "reserved_"}
 
     def set_kernel_timer(self, kernel_class):
         """Time every launch of one kernel class (name from _lib.KT_CLASSES) on the context's stream."""
@@ -386,6 +402,39 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def fma_peak(precision=64, n_iter=None):
+    """Measured FMA throughput of the current GPU's CUDA cores (TFLOP/s) in FP64 or FP32."""
+    lib = load()
+    if n_iter is None:
+        n_iter = 1000 if precision == 64 else 20000
+    out = ctypes.c_double()
+    check(lib.dc_fma_peak(int(precision), int(n_iter), ctypes.byref(out)), None)
+    return float(out.value)
+
+
+def batch_hbm_bytes(meshes, params, n_steps):
+    """Device bytes a ClothBatch of these meshes (list of (rest_pos, tris, pins)) with
+    these parameters (one dict per mesh, or one for all) would hold at most through
+    a rollout of n_steps steps and its backward; computed on the host."""
+    lib = load()
+    arrays = [_mesh_arrays(*mesh) for mesh in meshes]
+    inst = (dc_instance * len(arrays))()
+    for i, (rest, tri, pin) in enumerate(arrays):
+        inst[i].n_nodes = rest.shape[0]
+        inst[i].n_tris = tri.shape[0]
+        inst[i].n_pins = len(pin)
+        inst[i].rest_pos = rest.ctypes.data
+        inst[i].tris = tri.ctypes.data
+        inst[i].pins = pin.ctypes.data if len(pin) else None
+    if isinstance(params, dict):
+        params = [params] * len(arrays)
+    prm = (dc_params * len(arrays))(*[_make_params(lib, kw)[0] for kw in params])
+    out = ctypes.c_int64()
+    check(lib.dc_batch_hbm_bytes(len(arrays), ctypes.addressof(inst), ctypes.addressof(prm), int(n_steps),
+                                 ctypes.byref(out)), None)
+    return int(out.value)
 
 
 def _rollout_function():

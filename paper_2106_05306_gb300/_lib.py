@@ -9,7 +9,9 @@ LIB_PATH = os.path.join(HERE, "lib", "libdc.so")
 
 DC_OK = 0
 STATUS_NAMES = {0: "DC_OK", 1: "DC_ERR_INVALID", 2: "DC_ERR_CUDA", 3: "DC_ERR_NOT_SPD", 4: "DC_ERR_OOM",
-                5: "DC_ERR_NONFINITE", 6: "DC_ERR_NONCONVERGED", 7: "DC_ERR_STATE"}
+                5: "DC_ERR_NONFINITE", 6: "DC_ERR_NONCONVERGED", 7: "DC_ERR_STATE", 8: "DC_ERR_TIMEOUT"}
+COMPLIANCE = {"rowsum": 0, "diag_pinv": 1, "diag_p": 2, "mass": 3}
+LAYOUTS = {"node_major": 0, "component_major": 1}
 DC_PLANE, DC_SPHERE, DC_CAPSULE = 0, 1, 2
 DC_MAX_OBSTACLES = 16
 
@@ -25,7 +27,8 @@ class dc_params(ctypes.Structure):
                 ("n_pd_iters", ctypes.c_int32), ("adj_max_iters", ctypes.c_int32),
                 ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("n_obstacles", ctypes.c_int32), ("adj_precond", ctypes.c_int32),
-                ("global_solver", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("global_solver", ctypes.c_int32), ("contact_compliance", ctypes.c_int32),
+                ("adj_fallback", ctypes.c_int32), ("reserved_", ctypes.c_int32),
                 ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
 
 
@@ -43,7 +46,12 @@ class dc_stats(ctypes.Structure):
                 ("factorisations", ctypes.c_int64), ("n_instances", ctypes.c_int32), ("graphs", ctypes.c_int32),
                 ("graph_replays", ctypes.c_int64), ("block_local", ctypes.c_int32), ("block_gather", ctypes.c_int32),
                 ("block_node", ctypes.c_int32), ("block_elem", ctypes.c_int32), ("adj_batch_iters", ctypes.c_int64),
-                ("global_solver", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("psolve_flops", ctypes.c_double)]
+                ("global_solver", ctypes.c_int32), ("reserved_", ctypes.c_int32), ("psolve_flops", ctypes.c_double),
+                ("adj_fallbacks", ctypes.c_int64), ("adj_fallback_iters", ctypes.c_int64),
+                ("layout", ctypes.c_int32), ("contact_compliance", ctypes.c_int32),
+                ("device_bytes", ctypes.c_int64), ("device_bytes_peak", ctypes.c_int64),
+                ("n_nodes", ctypes.c_int32), ("n_tris", ctypes.c_int32), ("bend_nnz", ctypes.c_int64),
+                ("front_entries", ctypes.c_int64)]
 
 
 class dc_instance(ctypes.Structure):
@@ -93,6 +101,8 @@ SIGNATURES = {
     "dc_set_params": (ctypes.c_int32, [_P, ctypes.POINTER(dc_params)]),
     "dc_set_params_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "dc_set_graphs": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_set_layout": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_batch_hbm_bytes": (ctypes.c_int32, [ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "dc_autotune": (ctypes.c_int32, [_P]),
     "dc_step": (ctypes.c_int32, [_P, _P, _P, _P, _P]),
     "dc_rollout": (ctypes.c_int32, [_P, ctypes.c_int32, _P, _P, _P, _P, _P]),
@@ -101,6 +111,7 @@ SIGNATURES = {
     "dc_global_solve_static": (ctypes.c_int32, [_P, _P, _P]),
     "dc_debug_sweep_wait_timeout": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_stats)]),
+    "dc_fma_peak": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "dc_set_kernel_timer": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_sync": (ctypes.c_int32, [_P]),
     "dc_destroy": (None, [_P]),

@@ -17,6 +17,7 @@
 // for bending) and a fixed-order per-node gather.
 #include "dc_internal.h"
 #include "dc_adjoint.h"
+#include "dc_polar.cuh"
 
 namespace {
 
@@ -51,20 +52,11 @@ __global__ void k_adj_setup_tri(DevMesh dm, const d4* __restrict__ x1, d4* __res
         F[k] = e1[k] * g.x + e2[k] * g.z;
         F[3 + k] = e1[k] * g.y + e2[k] * g.w;
     }
-    double c00 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
-    double c01 = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
-    double c11 = F[3] * F[3] + F[4] * F[4] + F[5] * F[5];
-    double det = c00 * c11 - c01 * c01;
-    double is = rsqrt(det);
-    double s = det * is;
-    double it = rsqrt(c00 + c11 + 2.0 * s);
-    double k = is * it;
-    double s00 = (c11 + s) * k, s01 = -c01 * k, s11 = (c00 + s) * k;   // S^-1
-    double R[6];
-    for (int q = 0; q < 3; ++q) {
-        R[q] = s00 * F[q] + s01 * F[3 + q];
-        R[3 + q] = s01 * F[q] + s11 * F[3 + q];
-    }
+    // R, S^-1 and 1/tr S; a collapsed triangle gets S^-1 = 0 and 1/tr S = 0, so
+    // its polar derivative vanishes (reading R1)
+    double R[6], sinv[3], it;
+    dc_polar3x2(F, R, sinv, &it);
+    const double s00 = sinv[0], s01 = sinv[1], s11 = sinv[2];
     // per vertex v of the triangle: a_v = (g_v0 R1 - g_v1 R0) / tr S, and the
     // projector P = I - R0 R0^T - R1 R1^T (the front assembly reads them for
     // every pair of the triangle's vertices instead of forming them again)
@@ -145,7 +137,7 @@ __global__ void k_adj_setup_node(DevMesh dm, AdjDev ad, const d4* __restrict__ v
         // block = w (|g|^2 I - trS a a^T - gam (I - R0 R0^T - R1 R1^T))
         double d = w * (gg - gam);
         H[0] += d; H[3] += d; H[5] += d;
-        sym_add(H, -w / itr, av);
+        if (itr > 0.0) sym_add(H, -w / itr, av);   // no rotation term for a collapsed triangle
         sym_add(H, w * gam, R0);
         sym_add(H, w * gam, R1);
     }
@@ -649,12 +641,12 @@ __global__ void k_param_accumulate(const double* __restrict__ part, const int* _
 }
 
 __global__ void k_add_ext(d4* __restrict__ g, const double* __restrict__ ext, const int* __restrict__ int2ext,
-                          int m) {
+                          int m, int cs, long ns) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    int e = int2ext[i];
+    const long e = (long)int2ext[i] * cs;
     d4 a = ld(g + i);
-    st(g + i, a.x + ext[3 * e], a.y + ext[3 * e + 1], a.z + ext[3 * e + 2]);
+    st(g + i, a.x + ext[e], a.y + ext[e + ns], a.z + ext[e + 2 * ns]);
 }
 
 // rhs = Pi_B (gv + h gx) on free nodes
@@ -743,7 +735,8 @@ void adj_params(const DevMesh& dm, const AdjDev& ad, const Segs& sg, const d4* z
     dc_note_launch();
     k_param_accumulate<<<nblk(3L * sg.B, 128), 128, 0, s>>>(part, sg.pcptr, sg.B, acc);
 }
-void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s) {
+void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, int layout, cudaStream_t s) {
+    const bool cm = layout == DC_LAYOUT_COMPONENT_MAJOR;
     dc_note_launch();
-    k_add_ext<<<nblk(m, 256), 256, 0, s>>>(g, ext, int2ext, m);
+    k_add_ext<<<nblk(m, 256), 256, 0, s>>>(g, ext, int2ext, m, cm ? 1 : 3, cm ? (long)m : 1L);
 }

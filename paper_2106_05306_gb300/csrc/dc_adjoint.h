@@ -59,7 +59,8 @@ void adj_outputs(const DevMesh& dm, const AdjDev& ad, const DevParams& P, const 
 // acc[4 i + q] += dL/d(k_stretch, k_bend, mu)_q of instance i for this step
 void adj_params(const DevMesh& dm, const AdjDev& ad, const Segs& sg, const d4* z, const d4* x1, double* part,
                 double* acc, cudaStream_t s);
-void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, cudaStream_t s);
+// g += the caller-order array ext (layout DC_LAYOUT_*), permuted to internal order
+void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, int layout, cudaStream_t s);
 
 // Per-step multifrontal LDL^T preconditioner (dc_frontal.cu).
 size_t frontal_factor_smem(int max_f, int max_p);

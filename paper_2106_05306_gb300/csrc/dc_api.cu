@@ -26,6 +26,12 @@ dc_status create_common(dc_ctx* c) {
 
 dc_status finish_create(dc_ctx* c, dc_ctx** out, void* stream) {
     c->stream = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        g_create_err = "no usable CUDA device";
+        delete c;
+        return DC_ERR_CUDA;
+    }
     c->kt.stream = c->stream;
     dc_status s = create_common(c);
     if (s) {
@@ -50,6 +56,28 @@ dc_status apply_params(dc_ctx* c, std::vector<dc_params> q) {
 
 }  // namespace
 
+// Device-side error words, read after the stream's work so far: the sticky
+// fault word of the bounded waits (counters[3], DC_ERR_TIMEOUT: every result
+// computed since is invalid) and the non-finite forward state flag
+// (counters[4], DC_ERR_NONFINITE, cleared once reported).
+dc_status check_device_flags(dc_ctx* c) {
+    if (!c->counters) return DC_OK;
+    unsigned long long w[2] = {0, 0};
+    CK(cudaMemcpyAsync(w, c->counters + 3, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
+    CK(ctx_sync(c, c->stream));
+    if (w[0]) {
+        c->err = "tree-scheduled solve: a bounded dependency wait gave up; results since then are invalid";
+        return DC_ERR_TIMEOUT;
+    }
+    if (w[1]) {
+        CK(cudaMemsetAsync(c->counters + 4, 0, sizeof(unsigned long long), c->stream));
+        CK(ctx_sync(c, c->stream));
+        c->err = "a forward step produced a non-finite position or velocity";
+        return DC_ERR_NONFINITE;
+    }
+    return DC_OK;
+}
+
 extern "C" {
 
 void dc_default_params(dc_params* p) {
@@ -67,6 +95,58 @@ void dc_default_params(dc_params* p) {
     p->adj_restart = 200;
     p->checkpoint_every = 1;
     p->n_obstacles = 0;
+    p->contact_compliance = DC_COMPLIANCE_ROWSUM;
+    p->adj_fallback = 1;
+}
+
+dc_status dc_set_layout(dc_ctx* c, int32_t layout) {
+    if (!c) return DC_ERR_INVALID;
+    if (layout != DC_LAYOUT_NODE_MAJOR && layout != DC_LAYOUT_COMPONENT_MAJOR) {
+        c->err = "dc_set_layout: unknown layout";
+        return DC_ERR_INVALID;
+    }
+    c->layout = layout;
+    return DC_OK;
+}
+
+dc_status dc_batch_hbm_bytes(int32_t n, const dc_instance* in, const dc_params* params, int32_t n_steps,
+                             int64_t* bytes) {
+    if (n < 1 || !in || !params || !bytes || n_steps < 0) {
+        g_create_err = "dc_batch_hbm_bytes: null argument, no instances or negative step count";
+        return DC_ERR_INVALID;
+    }
+    for (int i = 0; i < n; ++i)
+        if (!in[i].rest_pos || !in[i].tris || in[i].n_pins < 0 || (in[i].n_pins > 0 && !in[i].pins) ||
+            in[i].n_nodes < 0) {
+            g_create_err = "dc_batch_hbm_bytes: null argument (instance " + std::to_string(i) + ")";
+            return DC_ERR_INVALID;
+        }
+    // the host half of dc_create_batch + dc_set_params_batch, no device work
+    dc_ctx* c = new dc_ctx();
+    c->ihm.resize(n);
+    std::vector<std::string> err(n);
+    dc_parallel_for(n, [&](int i) {
+        err[i] = dc_build_mesh(c->ihm[i], in[i].n_nodes, in[i].rest_pos, in[i].n_tris, in[i].tris, in[i].n_pins,
+                               in[i].pins);
+    });
+    for (int i = 0; i < n; ++i)
+        if (!err[i].empty()) {
+            g_create_err = "dc_batch_hbm_bytes: instance " + std::to_string(i) + ": " + err[i];
+            delete c;
+            return DC_ERR_INVALID;
+        }
+    MeshPrep mp;
+    prep_mesh_host(c, mp);
+    ParamPrep pp;
+    dc_status s = prep_params_host(c, std::vector<dc_params>(params, params + n), pp);
+    if (s) {
+        g_create_err = "dc_batch_hbm_bytes: " + c->err;
+        delete c;
+        return s;
+    }
+    *bytes = (int64_t)estimate_device_bytes(c, mp, pp, n_steps);
+    delete c;
+    return DC_OK;
 }
 
 dc_status dc_create_mesh(dc_ctx** out, int32_t n_nodes, const double* rest_pos, int32_t n_tris,
@@ -181,7 +261,7 @@ dc_status dc_step(dc_ctx* c, const double* x_n, const double* v_n, double* x_np1
     RET(store_vec(c, c->xb, x_np1, host_io));
     RET(store_vec(c, c->vb, v_np1, host_io));
     CK(cudaGetLastError());
-    if (host_io) CK(ctx_sync(c, c->stream));
+    if (host_io) RET(check_device_flags(c));
     return DC_OK;
 }
 
@@ -245,22 +325,7 @@ dc_status dc_rollout(dc_ctx* c, int32_t n_steps, const double* x0, const double*
     CK(cudaGetLastError());
     c->ck_n_steps = n_steps;
     c->ck_every = k;
-    if (host_io) CK(ctx_sync(c, c->stream));
-    return DC_OK;
-}
-
-// The tree-scheduled solves' sticky fault word (counters[3]) is set when a
-// dependency wait gave up; every result computed since is invalid.  Call with
-// the stream idle.
-static dc_status check_sweep_fault(dc_ctx* c) {
-    if (!c->counters) return DC_OK;
-    unsigned long long w = 0;
-    CK(cudaMemcpyAsync(&w, c->counters + 3, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
-    CK(ctx_sync(c, c->stream));
-    if (w) {
-        c->err = "tree-scheduled solve: a dependency wait timed out; results since then are invalid";
-        return DC_ERR_CUDA;
-    }
+    if (host_io) RET(check_device_flags(c));
     return DC_OK;
 }
 
@@ -336,13 +401,13 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
                 CK(cudaEventRecord(c->ev_fact[kn], c->stream2));
             }
             CK(cudaStreamWaitEvent(s, c->ev_fact[k2], 0));
-            if (traj) adj_add_ext(c->gx, traj + (size_t)(t + 1) * 3 * m, c->d_int2ext, m, s);
+            if (traj) adj_add_ext(c->gx, traj + (size_t)(t + 1) * 3 * m, c->d_int2ext, m, c->layout, s);
             st = adjoint_step(c, X(t), X(t + 1), V(t + 1), k2, noncv);
             if (st) break;
         }
     }
     if (st == DC_OK) {
-        if (traj) adj_add_ext(c->gx, traj, c->d_int2ext, m, s);
+        if (traj) adj_add_ext(c->gx, traj, c->d_int2ext, m, c->layout, s);
         RET(store_vec(c, c->gx, dL_dx0, host_io));
         RET(store_vec(c, c->gv, dL_dv0, host_io));
         // [B][4] accumulator -> [B][3] output
@@ -356,7 +421,7 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
     free_pool(c, tmp);
     CK(cudaGetLastError());
     if (st) return st;
-    RET(check_sweep_fault(c));
+    RET(check_device_flags(c));
     if (noncv) {
         c->err = "dc_backward: an adjoint step reached adj_max_iters above adj_tol";
         return DC_ERR_NONCONVERGED;
@@ -398,13 +463,13 @@ dc_status dc_debug_sweep_wait_timeout(dc_ctx* c, int32_t skip_items) {
     launch_solve_fwd_skip(c->dm, c->b, c->y, skip_items, c->stream);
     CK(ctx_sync(c, c->stream));
     CK(cudaGetLastError());
-    return check_sweep_fault(c);
+    return check_device_flags(c);
 }
 
 dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     if (!c || !o) return DC_ERR_INVALID;
     CK(ctx_sync(c, c->stream));
-    unsigned long long cnt[4] = {0, 0, 0, 0};
+    unsigned long long cnt[3] = {0, 0, 0};
     CK(cudaMemcpyAsync(cnt, c->counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
     CK(ctx_sync(c, c->stream));
     std::memset(o, 0, sizeof(*o));
@@ -442,11 +507,17 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     o->adj_batch_iters = c->adj_batch_iters;
     o->global_solver = c->dm.solver;
     o->psolve_flops = c->psolve_flops;
-    if (cnt[3]) {
-        c->err = "tree-scheduled solve: a dependency wait timed out; results since then are invalid";
-        return DC_ERR_CUDA;
-    }
-    return DC_OK;
+    o->adj_fallbacks = c->adj_fallbacks;
+    o->adj_fallback_iters = c->adj_fallback_iters;
+    o->layout = c->layout;
+    o->contact_compliance = c->prm.contact_compliance;
+    o->device_bytes = (int64_t)c->dev_bytes;
+    o->device_bytes_peak = (int64_t)c->dev_peak;
+    o->n_nodes = c->hm.m;
+    o->n_tris = c->hm.T;
+    o->bend_nnz = (int64_t)c->hm.bidx.size();
+    o->front_entries = (int64_t)c->fr.pool_size;
+    return check_device_flags(c);
 }
 
 dc_status dc_set_kernel_timer(dc_ctx* c, int32_t kernel_class) {
@@ -467,7 +538,7 @@ dc_status dc_sync(dc_ctx* c) {
     if (!c) return DC_ERR_INVALID;
     CK(ctx_sync(c, c->stream));
     CK(cudaGetLastError());
-    return check_sweep_fault(c);
+    return check_device_flags(c);
 }
 
 void dc_destroy(dc_ctx* c) {
@@ -509,6 +580,8 @@ const char* dc_last_error(dc_ctx* c) { return c ? c->err.c_str() : g_create_err.
 bool dc_ctx_ready(const dc_ctx* c) { return c->have_params; }
 const DevMesh& dc_ctx_mesh(const dc_ctx* c) { return c->dm; }
 const DevParams& dc_ctx_params(const dc_ctx* c) { return c->dp; }
+int dc_ctx_device(const dc_ctx* c) { return c->device; }
+int dc_ctx_layout(const dc_ctx* c) { return c->layout; }
 const int* dc_ctx_int2ext(const dc_ctx* c) { return c->d_int2ext; }
 cudaStream_t dc_ctx_stream(const dc_ctx* c) { return c->stream; }
 void dc_ctx_set_error(dc_ctx* c, const std::string& msg) { c->err = msg; }

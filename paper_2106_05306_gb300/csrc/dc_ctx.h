@@ -46,6 +46,8 @@ struct GState {
 
 struct dc_ctx {
     cudaStream_t stream = nullptr;
+    int device = 0;                // device current at creation
+    int layout = DC_LAYOUT_NODE_MAJOR;   // node arrays at the boundary (dc_set_layout)
     std::string err;
     KTimer kt;
     double front_flops = 0.0;
@@ -84,6 +86,8 @@ struct dc_ctx {
     StepRec scratch;
     double* stage = nullptr;       // [m][3] staging for host/device conversion
     double* stage2 = nullptr;
+    // [0..2] contact cases, [3] sticky fault word of the bounded waits,
+    // [4] non-finite forward state
     unsigned long long* counters = nullptr;
     // rollout checkpoints
     int ck_n_steps = -1, ck_every = 1, ck_cap = 0;
@@ -141,6 +145,7 @@ struct dc_ctx {
     double adj_last_res = 0.0;
     long long n_factorisations = 0;
     long long adj_batch_iters = 0;
+    long long adj_fallbacks = 0, adj_fallback_iters = 0;
 };
 
 #define CK(call)                                                                              \
@@ -245,6 +250,7 @@ struct ParamPrep {
     std::vector<int> optr, okind, long_rows, short_rows;
     std::vector<float> tau;
     HostPSolve ps;                 // global_solver 1
+    std::vector<double> ccon;      // [m_free] constant compliance (modes other than ROWSUM)
     double front_flops = 0.0;
     long long factor_nnz = 0;
 };
@@ -278,3 +284,6 @@ dc_status ensure_records(dc_ctx* c, int n_steps);
 void prepare_step(dc_ctx* c, const StepRec& r, const d4* x1, const d4* v1, int k, cudaStream_t s);
 dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv);
 dc_status autotune(dc_ctx* c);
+// Reads the device-side error words (bounded-wait timeout, non-finite state);
+// synchronises the context's stream.
+dc_status check_device_flags(dc_ctx* c);

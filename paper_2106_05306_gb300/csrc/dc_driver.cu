@@ -71,17 +71,17 @@ dc_status load_vec(dc_ctx* c, const double* ext, d4* out, bool& host_io) {
         CK(cudaMemcpyAsync(c->stage, ext, sizeof(double) * 3 * m, cudaMemcpyDefault, c->stream));
         src = c->stage;
     }
-    launch_permute_in(src, out, c->d_int2ext, m, c->stream);
+    launch_permute_in(src, out, c->d_int2ext, m, c->layout, c->stream);
     return DC_OK;
 }
 
 dc_status store_vec(dc_ctx* c, const d4* in, double* ext, bool& host_io) {
     const int m = c->hm.m;
     if (is_device_ptr(ext)) {
-        launch_permute_out(in, ext, c->d_int2ext, m, c->stream);
+        launch_permute_out(in, ext, c->d_int2ext, m, c->layout, c->stream);
     } else {
         host_io = true;
-        launch_permute_out(in, c->stage2, c->d_int2ext, m, c->stream);
+        launch_permute_out(in, c->stage2, c->d_int2ext, m, c->layout, c->stream);
         CK(cudaMemcpyAsync(ext, c->stage2, sizeof(double) * 3 * m, cudaMemcpyDefault, c->stream));
     }
     return DC_OK;
@@ -93,9 +93,14 @@ void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepR
     const DevParams& P = c->dp;
     launch_detect(dm, P, xin, vin, r.contact, r.nb, r.f, c->ind, s);
     cudaMemsetAsync(r.case_, 0, sizeof(int) * dm.m_free, s);
-    // compliance c_j = h (P^-1 1_I)_j of the step's contact set (reading R5)
-    launch_solve_fwd(dm, c->ind, c->y, s);
-    launch_solve_bwd(dm, P, c->y, nullptr, 2, nullptr, nullptr, nullptr, nullptr, nullptr, c->cc, s);
+    // compliance of the per-node contact solve (reading R5): c_j = h (P^-1 1_I)_j
+    // of the step's contact set, or a constant per node for the other choices
+    const double* cc = P.ccon;
+    if (P.compliance == DC_COMPLIANCE_ROWSUM) {
+        launch_solve_fwd(dm, c->ind, c->y, s);
+        launch_solve_bwd(dm, P, c->y, nullptr, 2, nullptr, nullptr, nullptr, nullptr, nullptr, c->cc, s);
+        cc = c->cc;
+    }
     cudaMemcpyAsync(c->v, vin, sizeof(d4) * dm.m, cudaMemcpyDeviceToDevice, s);
     KTimer& kt = c->kt;
     for (int k = 0; k < c->prm.n_pd_iters; ++k) {
@@ -105,14 +110,20 @@ void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepR
         kt.begin(DC_KT_GATHER);
         launch_gather_rhs(dm, P, vin, c->c1, c->c2, c->bu, r.f, c->b, s);
         kt.end(DC_KT_GATHER);
+        if (P.mass_split) {   // global step of the mass splitting (DC_COMPLIANCE_MASS)
+            kt.begin(DC_KT_SOLVE_BWD);
+            launch_mass_solve(dm, P, c->b, c->v, r.contact, r.nb, cc, r.f, r.case_, s);
+            kt.end(DC_KT_SOLVE_BWD);
+            continue;
+        }
         kt.begin(DC_KT_SOLVE_FWD);
         launch_solve_fwd(dm, c->b, c->y, s);
         kt.end(DC_KT_SOLVE_FWD);
         kt.begin(DC_KT_SOLVE_BWD);
-        launch_solve_bwd(dm, P, c->y, c->v, 1, r.contact, r.nb, c->cc, r.f, r.case_, nullptr, s);
+        launch_solve_bwd(dm, P, c->y, c->v, 1, r.contact, r.nb, cc, r.f, r.case_, nullptr, s);
         kt.end(DC_KT_SOLVE_BWD);
     }
-    launch_finalize(dm, P, xin, c->v, xout, s);
+    launch_finalize(dm, P, xin, c->v, xout, c->counters + 4, s);
     if (vout != c->v) cudaMemcpyAsync(vout, c->v, sizeof(d4) * dm.m, cudaMemcpyDeviceToDevice, s);
     if (count) launch_count_cases(r.contact, r.case_, dm.m_free, c->counters, s);
 }
@@ -333,6 +344,14 @@ void precond(dc_ctx* c, const AdjDev& ad, const d4* w, d4* out) {
     adj_dplus(dm, ad, c->x2, c->r2, out, s);
 }
 
+// The fallback's preconditioner: K w (the per-step one), then one sweep of the
+// constrained node-block inverse D+ of H on what K left, out = K w + D+ (w - Pi_B H K w).
+void precond_fallback(dc_ctx* c, const AdjDev& ad, const d4* w, d4* out) {
+    precond(c, ad, w, out);
+    adj_apply_H(c->dm, ad, 1, out, w, c->r2, c->stream);
+    adj_dplus(c->dm, ad, out, c->r2, out, c->stream);
+}
+
 // Compacted front and chunk lists of the instances with gs[i].act (batches only).
 dc_status build_active_lists(dc_ctx* c) {
     const int B = c->B, nl = c->nlev;
@@ -395,17 +414,28 @@ dc_status upload_scale(dc_ctx* c, const std::vector<double>& sc) {
 // rotations, convergence tests and restarts.  An instance that has converged
 // (or stagnated, or reached the cap) is frozen with zero Krylov vectors, so its
 // iterates are exactly those of a run on its own.  iters[i] and rel[i] receive
-// each instance's iteration count and final relative residual.
-dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
+// each instance's iteration count and final relative residual (to |rhs_i|).
+//
+// The fallback pass (fallback = true) runs only the instances with sel[i] set,
+// continuing from their current z (its first residual is rhs - Pi_B H z), as
+// GMRES(30) with the stronger preconditioner precond_fallback, an iteration
+// budget of max(adj_max_iters, 300), and a restart cycle counted as stagnated
+// only when it fails to cut the residual by 10% (the first pass stops at 50%,
+// which keeps lockstep batches short; the short restart makes a fallback that
+// cannot get further stop after 30 iterations).
+dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel, bool fallback = false,
+                const std::vector<char>* sel = nullptr) {
     cudaStream_t s = c->stream;
     const int m = c->hm.m, B = c->B;
     const long ldv = 4L * m;
-    const int mr = std::max(1, std::min(256, c->prm.adj_restart));
-    const int maxit = std::max(1, c->prm.adj_max_iters);
+    const int mr_cap = std::max(1, std::min(256, c->prm.adj_restart));
+    const int mr = fallback ? std::min(30, mr_cap) : mr_cap;
+    const int maxit = fallback ? std::max(c->prm.adj_max_iters, 300) : std::max(1, c->prm.adj_max_iters);
     const double tol = c->prm.adj_tol;
+    const double stagnate = fallback ? 0.9 : 0.5;
     double* zz = reinterpret_cast<double*>(c->z);
     double* rr = reinterpret_cast<double*>(c->r1);
-    CK(cudaMemsetAsync(c->z, 0, sizeof(d4) * m, s));
+    if (!fallback) CK(cudaMemsetAsync(c->z, 0, sizeof(d4) * m, s));
     std::vector<double> nrm;
     RET(bdot_host(c, reinterpret_cast<double*>(c->rhs), reinterpret_cast<double*>(c->rhs), nrm));
     std::vector<GState>& gs = c->gs;
@@ -417,7 +447,7 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
             c->err = "non-finite adjoint right-hand side (instance " + std::to_string(i) + ")";
             return DC_ERR_NONFINITE;
         }
-        gs[i].fin = !(gs[i].beta0 > 0.0);
+        gs[i].fin = !(gs[i].beta0 > 0.0) || (sel && !(*sel)[i]);
         any |= !gs[i].fin;
     }
     iters.assign(B, 0);
@@ -427,7 +457,13 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
     std::vector<std::vector<double>> Hc(B), cs(B), sn(B), gg(B);
     std::vector<char> done(B, 0);
     std::vector<double> sc(B, 0.0), yv;
-    CK(cudaMemcpyAsync(c->r1, c->rhs, sizeof(d4) * m, cudaMemcpyDeviceToDevice, s));
+    if (fallback) {   // residual of the current iterate
+        c->kt.begin(DC_KT_APPLYH);
+        adj_apply_H(c->dm, c->ad, 1, c->z, c->rhs, c->r1, s);
+        c->kt.end(DC_KT_APPLYH);
+    } else {
+        CK(cudaMemcpyAsync(c->r1, c->rhs, sizeof(d4) * m, cudaMemcpyDeviceToDevice, s));
+    }
     const bool debug = std::getenv("DC_DEBUG_GMRES") != nullptr;
     const long long lock0 = c->adj_batch_iters;
     for (int cycle = 0;; ++cycle) {
@@ -444,7 +480,7 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
                              beta / g.beta0);
             // converged, capped, or a restart that did not halve the true residual
             // (the rounding floor, about eps * cond(H), has been reached)
-            if (beta <= tol * g.beta0 || g.total >= maxit || (cycle > 0 && beta > 0.5 * g.prev)) {
+            if (beta <= tol * g.beta0 || g.total >= maxit || (cycle > 0 && beta > stagnate * g.prev)) {
                 g.fin = true;
                 continue;
             }
@@ -477,7 +513,10 @@ dc_status gmres(dc_ctx* c, std::vector<int>& iters, std::vector<double>& rel) {
         for (int j = 0; j < mr; ++j) {
             d4* vj = vcol(c->V, j, m);
             d4* zj = vcol(c->Zb, j, m);
-            precond(c, adm, vj, zj);
+            if (fallback)
+                precond_fallback(c, adm, vj, zj);
+            else
+                precond(c, adm, vj, zj);
             c->kt.begin(DC_KT_APPLYH);
             adj_apply_H(c->dm, adm, 0, zj, nullptr, c->wv, s);
             c->kt.end(DC_KT_APPLYH);
@@ -646,6 +685,25 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int
     std::vector<int> it;
     std::vector<double> rel;
     RET(gmres(c, it, rel));
+    if (c->prm.adj_fallback) {
+        // instances stopped above adj_tol: a second pass from their iterate
+        std::vector<char> sel(c->B, 0);
+        bool any = false;
+        for (int i = 0; i < c->B; ++i)
+            if (!(rel[i] <= c->prm.adj_tol * 1.0000001)) sel[i] = 1, any = true;
+        if (any) {
+            std::vector<int> it2;
+            std::vector<double> rel2;
+            RET(gmres(c, it2, rel2, true, &sel));
+            for (int i = 0; i < c->B; ++i)
+                if (sel[i]) {
+                    c->adj_fallbacks++;
+                    c->adj_fallback_iters += it2[i];
+                    it[i] += it2[i];
+                    rel[i] = rel2[i];
+                }
+        }
+    }
     for (int i = 0; i < c->B; ++i) {
         c->adj_steps++;
         c->adj_iters += it[i];
@@ -725,7 +783,7 @@ dc_status autotune(dc_ctx* c) {
     pick(&dm.bs_gather, [&]() { launch_gather_rhs(dm, P, c->va, c->c1, c->c2, c->bu, c->scratch.f, c->b, s); });
     pick(&dm.bs_node, [&]() {
         launch_detect(dm, P, c->xa, c->va, c->scratch.contact, c->scratch.nb, c->scratch.f, c->ind, s);
-        launch_finalize(dm, P, c->xa, c->v, c->xb, s);
+        launch_finalize(dm, P, c->xa, c->v, c->xb, c->counters + 4, s);
     });
     pick(&dm.bs_elem, [&]() { adj_apply_H(dm, ad, 0, c->v, nullptr, c->wv, s); });
     cudaEventDestroy(e0);

@@ -77,7 +77,7 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
             double w = h2 * dm.wt[t];
             double gg = ga0 * gb0 + ga1 * gb1;
             double gam = ga0 * gb0 * s00 + (ga0 * gb1 + ga1 * gb0) * s01 + ga1 * gb1 * s11;
-            double trS = 1.0 / itr;
+            double trS = itr > 0.0 ? 1.0 / itr : 0.0;   // 0 for a collapsed triangle (a_a = a_b = 0)
             // block = w ((g_a.g_b) I - trS a_a a_b^T - gam P)
             for (int r = 0; r < 3; ++r)
                 for (int c = 0; c < 3; ++c) {

@@ -72,7 +72,15 @@ struct HostFactor {
     std::vector<int> bptr, bidx;
     std::vector<double> bval;
     double max_diag = 0.0;             // largest diagonal entry of P_ff
+    std::vector<double> pdiag;         // diagonal of P_ff
 };
+
+// Diagonal of P_ff^-1 from the factor's CSC columns (rowidx / val still held):
+// the selected inverse Z = P^-1 on the pattern of L, computed column by column
+// from the last (Takahashi's recurrence for P = L L^T):
+//   Z_ij = -(1/L_jj) sum_{k in struct(j)} L_kj Z_ik   (i in struct(j))
+//   Z_jj = 1/L_jj^2 - (1/L_jj) sum_{k in struct(j)} L_kj Z_kj.
+void dc_inverse_diagonal(const HostFactor& hf, std::vector<double>& zdiag);
 
 // Assembles P_ff (free nodes, internal order) and factorises it.  Returns
 // DC_OK, DC_ERR_NOT_SPD or DC_ERR_INVALID with a message in err.
@@ -214,6 +222,9 @@ struct DevParams {
     double h;
     double g[3];
     double delta;
+    int compliance;                    // DC_COMPLIANCE_* of the context
+    int mass_split;                    // 1: the global step is the mass splitting (DC_COMPLIANCE_MASS)
+    const double* ccon;                // [m_free] constant compliance (every mode but ROWSUM)
     const int* node_inst;              // [m] instance of each internal node
     const double* node_mu;             // [m] friction coefficient of the node's instance
     const int* optr;                   // [n_inst + 1] obstacles of instance i: optr[i] .. optr[i+1]-1
@@ -245,8 +256,9 @@ void dc_merge_fronts(const std::vector<HostFronts>& F, std::vector<InstInfo>& I,
 // ---------------------------------------------------------------- kernel launchers
 // (all asynchronous on the given stream)
 
-void launch_permute_in(const double* ext, d4* out, const int* ext2int, int m, cudaStream_t s);
-void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, cudaStream_t s);
+// layout: DC_LAYOUT_NODE_MAJOR ([m][3]) or DC_LAYOUT_COMPONENT_MAJOR ([3][m]) of ext
+void launch_permute_in(const double* ext, d4* out, const int* ext2int, int m, int layout, cudaStream_t s);
+void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, int layout, cudaStream_t s);
 void launch_zero_pins(d4* v, int m_free, int m, cudaStream_t s);
 
 // contact detection + per-step constants (Sec. 3.2, reading R4)
@@ -275,8 +287,13 @@ void launch_solve_fwd_skip(const DevMesh& dm, const d4* b, d4* y, int skip, cuda
 // max_fs nodes: the CTAs of each kernel that fit on the device at once, and the
 // dynamic shared memory
 cudaError_t psolve_tree_grid(int max_fs, int* grid_f, int* grid_b, size_t* smem);
+// x_{n+1} = x_n + h v; sets *nonfinite when a state entry is not finite
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v,
-                     d4* x_np1, cudaStream_t s);
+                     d4* x_np1, unsigned long long* nonfinite, cudaStream_t s);
+// Global step of the mass splitting (DC_COMPLIANCE_MASS): v_half = M^-1 b per
+// free node, then the node's Signorini-Coulomb update as in launch_solve_bwd mode 1
+void launch_mass_solve(const DevMesh& dm, const DevParams& P, const d4* b, d4* v, const int* contact,
+                       const d4* normal_beta, const double* c, d4* f, int* case_, cudaStream_t s);
 void launch_count_cases(const int* contact, const int* case_, int m_free,
                         unsigned long long* counters, cudaStream_t s);
 

@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "dc_internal.h"
+#include "dc_polar.cuh"
 #include "dc_wait.cuh"
 
 namespace {
@@ -73,21 +74,23 @@ __device__ double sdf(const DevParams& P, int o, double x, double y, double z, d
     return d - r;
 }
 
+// Boundary arrays: component c of caller node e sits at ext[e * cs + c * ns]
+// with (cs, ns) = (3, 1) node-major ([m][3]) or (1, m) component-major ([3][m]).
 __global__ void k_permute_in(const double* __restrict__ ext, d4* __restrict__ out,
-                             const int* __restrict__ int2ext, int m) {
+                             const int* __restrict__ int2ext, int m, int cs, long ns) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    int e = int2ext[i];
-    st(out + i, ext[3 * e], ext[3 * e + 1], ext[3 * e + 2]);
+    const long e = (long)int2ext[i] * cs;
+    st(out + i, ext[e], ext[e + ns], ext[e + 2 * ns]);
 }
 
 __global__ void k_permute_out(const d4* __restrict__ in, double* __restrict__ ext,
-                              const int* __restrict__ int2ext, int m) {
+                              const int* __restrict__ int2ext, int m, int cs, long ns) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
-    int e = int2ext[i];
+    const long e = (long)int2ext[i] * cs;
     d4 a = ld(in + i);
-    ext[3 * e] = a.x; ext[3 * e + 1] = a.y; ext[3 * e + 2] = a.z;
+    ext[e] = a.x; ext[e + ns] = a.y; ext[e + 2 * ns] = a.z;
 }
 
 __global__ void k_zero_range(d4* v, int lo, int hi) {
@@ -123,22 +126,11 @@ __global__ void k_detect(DevMesh dm, DevParams P, const d4* __restrict__ x_n, co
     }
 }
 
-// Closed-form polar factor R of a 3x2 F (reading R1):
-// S = (C + s I)/t, C = F^T F, s = sqrt(det C), t = sqrt(tr C + 2 s), R = F S^-1
-// = F adj(C + s I) / (s t).
+// Polar factor R of a 3x2 F (reading R1): the closed form, or the fixed rule
+// for a triangle collapsed onto a line (dc_polar.cuh).
 __device__ __forceinline__ void polar3x2(const double F[6], double R[6]) {
-    double c00 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
-    double c01 = F[0] * F[3] + F[1] * F[4] + F[2] * F[5];
-    double c11 = F[3] * F[3] + F[4] * F[4] + F[5] * F[5];
-    double det = c00 * c11 - c01 * c01;
-    double is = rsqrt(det);
-    double s = det * is;
-    double it = rsqrt(c00 + c11 + 2.0 * s);
-    double k = is * it;
-    double a = (c11 + s) * k, b = -c01 * k, d = (c00 + s) * k;
-    // R[:,0] = a F0 + b F1 ; R[:,1] = b F0 + d F1
-    R[0] = a * F[0] + b * F[3]; R[1] = a * F[1] + b * F[4]; R[2] = a * F[2] + b * F[5];
-    R[3] = b * F[0] + d * F[3]; R[4] = b * F[1] + d * F[4]; R[5] = b * F[2] + d * F[5];
+    double sinv[3], itr;
+    dc_polar3x2(F, R, sinv, &itr);
 }
 
 // Local step.  Threads [0, T): triangles; [T, T + m): bending vertices.
@@ -165,9 +157,11 @@ __global__ void k_local(DevMesh dm, DevParams P, const d4* __restrict__ x_n, con
             F[3 + c] = Fn[3 + c] + h * (f1[c] * g.y + f2[c] * g.w);
         }
         polar3x2(F, R);
+        // p - A x_n (Eq. pd_velocity), or p - A x^k for the mass splitting
+        const double* Fr = P.mass_split ? F : Fn;
         double D[6];
 #pragma unroll
-        for (int k = 0; k < 6; ++k) D[k] = w * (R[k] - Fn[k]);
+        for (int k = 0; k < 6; ++k) D[k] = w * (R[k] - Fr[k]);
         st(c1 + id, D[0] * g.x + D[3] * g.y, D[1] * g.x + D[4] * g.y, D[2] * g.x + D[5] * g.y);
         st(c2 + id, D[0] * g.z + D[3] * g.w, D[1] * g.z + D[4] * g.w, D[2] * g.z + D[5] * g.w);
         return;
@@ -196,7 +190,8 @@ __global__ void k_local(DevMesh dm, DevParams P, const d4* __restrict__ x_n, con
         }
     }
     double w = dm.wb[b] * h;
-    st(bu + b, w * (p[0] - qn[0]), w * (p[1] - qn[1]), w * (p[2] - qn[2]));
+    const double* qr = P.mass_split ? q : qn;
+    st(bu + b, w * (p[0] - qr[0]), w * (p[1] - qr[1]), w * (p[2] - qr[2]));
 }
 
 __global__ void k_gather_rhs(DevMesh dm, DevParams P, const d4* __restrict__ v_n, const d4* __restrict__ c1,
@@ -807,11 +802,26 @@ __global__ void __launch_bounds__(256) k_ps_bwd_tree(PSolveDev ps, DevParams P, 
 }
 
 __global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4* __restrict__ v,
-                           d4* __restrict__ x1) {
+                           d4* __restrict__ x1, unsigned long long* __restrict__ nonfinite) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= m) return;
     d4 a = ld(x_n + i), b = ld(v + i);
-    st(x1 + i, a.x + h * b.x, a.y + h * b.y, a.z + h * b.z);
+    const double x = a.x + h * b.x, y = a.y + h * b.y, z = a.z + h * b.z;
+    st(x1 + i, x, y, z);
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(b.x) && isfinite(b.y) && isfinite(b.z)))
+        atomicExch(nonfinite, 1ull);
+}
+
+// Global step of the mass splitting (Eq. ly_et_al_govrningEq as printed):
+// v_half = M^-1 b per free node, then the node's contact update.
+__global__ void k_mass_solve(DevMesh dm, DevParams P, const d4* __restrict__ b, d4* __restrict__ v,
+                             const int* __restrict__ contact, const d4* __restrict__ nb,
+                             const double* __restrict__ cc, d4* __restrict__ f, int* __restrict__ case_) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= dm.m_free) return;
+    const d4 q = ld(b + i);
+    const double mi = dm.mass[i];
+    finish_row(P, i, q.x / mi, q.y / mi, q.z / mi, v, 1, contact, nb, cc, f, case_, nullptr);
 }
 
 __global__ void k_count_cases(const int* __restrict__ contact, const int* __restrict__ case_, int n,
@@ -825,13 +835,15 @@ inline int nblk(long n, int b) { return (int)((n + b - 1) / b); }
 
 }  // namespace
 
-void launch_permute_in(const double* ext, d4* out, const int* int2ext, int m, cudaStream_t s) {
+void launch_permute_in(const double* ext, d4* out, const int* int2ext, int m, int layout, cudaStream_t s) {
     dc_note_launch();
-    k_permute_in<<<nblk(m, 256), 256, 0, s>>>(ext, out, int2ext, m);
+    const bool cm = layout == DC_LAYOUT_COMPONENT_MAJOR;
+    k_permute_in<<<nblk(m, 256), 256, 0, s>>>(ext, out, int2ext, m, cm ? 1 : 3, cm ? (long)m : 1L);
 }
-void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, cudaStream_t s) {
+void launch_permute_out(const d4* in, double* ext, const int* int2ext, int m, int layout, cudaStream_t s) {
     dc_note_launch();
-    k_permute_out<<<nblk(m, 256), 256, 0, s>>>(in, ext, int2ext, m);
+    const bool cm = layout == DC_LAYOUT_COMPONENT_MAJOR;
+    k_permute_out<<<nblk(m, 256), 256, 0, s>>>(in, ext, int2ext, m, cm ? 1 : 3, cm ? (long)m : 1L);
 }
 void launch_zero_pins(d4* v, int m_free, int m, cudaStream_t s) {
     if (m > m_free) {
@@ -957,9 +969,14 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
                                                                 c_out);
 }
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* x_np1,
-                     cudaStream_t s) {
+                     unsigned long long* nonfinite, cudaStream_t s) {
     dc_note_launch();
-    k_finalize<<<nblk(dm.m, dm.bs_node), dm.bs_node, 0, s>>>(dm.m, P.h, x_n, v, x_np1);
+    k_finalize<<<nblk(dm.m, dm.bs_node), dm.bs_node, 0, s>>>(dm.m, P.h, x_n, v, x_np1, nonfinite);
+}
+void launch_mass_solve(const DevMesh& dm, const DevParams& P, const d4* b, d4* v, const int* contact, const d4* nb,
+                       const double* c, d4* f, int* case_, cudaStream_t s) {
+    dc_note_launch();
+    k_mass_solve<<<nblk(dm.m_free, dm.bs_node), dm.bs_node, 0, s>>>(dm, P, b, v, contact, nb, c, f, case_);
 }
 void launch_count_cases(const int* contact, const int* case_, int m_free, unsigned long long* counters,
                         cudaStream_t s) {

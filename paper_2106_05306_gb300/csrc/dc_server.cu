@@ -140,6 +140,7 @@ void prep_loop(dc_server* s) {
 dc_status run_request(dc_server* s, Request* r, int slot, std::string& err) {
     dc_ctx* c = r->c;
     c->stream = s->streams[slot];
+    c->device = s->cfg.device;
     c->kt.stream = c->stream;
     c->hpin = s->pinned[slot];
     c->hpin_cap = 1024;

@@ -302,7 +302,11 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
                     add(iu, iv, val);
             }
     }
-    for (int j = 0; j < n; ++j) hf.max_diag = std::max(hf.max_diag, col[j][j]);
+    hf.pdiag.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) {
+        hf.pdiag[j] = col[j][j];
+        hf.max_diag = std::max(hf.max_diag, col[j][j]);
+    }
     // ---- elimination tree (Liu's algorithm with path compression)
     std::vector<std::vector<int>> lower_rows(n);   // rows i > j of column j
     std::vector<std::vector<int>> upper_cols(n);   // for row i: columns j < i
@@ -423,4 +427,33 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
         hf.fptr.push_back((int)hf.fidx.size());
     }
     return DC_OK;
+}
+
+void dc_inverse_diagonal(const HostFactor& hf, std::vector<double>& zdiag) {
+    const int n = hf.n;
+    // Z on the pattern of L (same CSC positions); entries of column j depend only
+    // on columns to its right, whose patterns contain every pair (i, k) of struct(j)
+    std::vector<double> Z(hf.val.size(), 0.0);
+    auto at = [&](int i, int k) -> double {   // Z_ik with i, k in struct of a common column
+        if (i < k) std::swap(i, k);            // lower triangle: row i of column k
+        const int* lo = hf.rowidx.data() + hf.colptr[k];
+        const int* hi = hf.rowidx.data() + hf.colptr[k + 1];
+        const int* p = std::lower_bound(lo, hi, i);
+        return Z[p - hf.rowidx.data()];
+    };
+    for (int j = n - 1; j >= 0; --j) {
+        const int q0 = hf.colptr[j], q1 = hf.colptr[j + 1];
+        const double ljj = hf.val[q0];
+        for (int a = q0 + 1; a < q1; ++a) {
+            const int i = hf.rowidx[a];
+            double s = 0.0;
+            for (int b = q0 + 1; b < q1; ++b) s += hf.val[b] * at(i, hf.rowidx[b]);
+            Z[a] = -s / ljj;
+        }
+        double s = 0.0;
+        for (int b = q0 + 1; b < q1; ++b) s += hf.val[b] * Z[b];
+        Z[q0] = 1.0 / (ljj * ljj) - s / ljj;
+    }
+    zdiag.assign(n, 0.0);
+    for (int j = 0; j < n; ++j) zdiag[j] = Z[hf.colptr[j]];
 }

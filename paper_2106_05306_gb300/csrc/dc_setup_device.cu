@@ -34,7 +34,8 @@ std::string normalise_params(dc_params& q) {
     if (!finite_params(q) || !(q.h > 0) || q.k_stretch < 0 || q.k_bend < 0 || !(q.density > 0) || q.mu < 0 ||
         q.n_pd_iters < 0 || q.n_obstacles < 0 || q.n_obstacles > DC_MAX_OBSTACLES || q.checkpoint_every < 1 ||
         q.adj_max_iters < 1 || q.adj_restart < 1 || !(q.adj_tol > 0) || q.adj_precond < 0 || q.adj_precond > 1 ||
-        q.global_solver < 0 || q.global_solver > 1)
+        q.global_solver < 0 || q.global_solver > 1 || q.contact_compliance < DC_COMPLIANCE_ROWSUM ||
+        q.contact_compliance > DC_COMPLIANCE_MASS || q.adj_fallback < 0 || q.adj_fallback > 1)
         return "invalid or non-finite parameter";
     if (q.adj_precond == 1 && q.global_solver != 0)
         return "adj_precond 1 needs global_solver 0 (it projects with the explicit inverse rows)";
@@ -65,7 +66,8 @@ bool same_batch_fields(const dc_params& a, const dc_params& b) {
            a.gravity[2] == b.gravity[2] && a.contact_margin == b.contact_margin && a.adj_tol == b.adj_tol &&
            a.n_pd_iters == b.n_pd_iters && a.adj_max_iters == b.adj_max_iters && a.adj_restart == b.adj_restart &&
            a.checkpoint_every == b.checkpoint_every && a.adj_precond == b.adj_precond &&
-           a.global_solver == b.global_solver;
+           a.global_solver == b.global_solver && a.contact_compliance == b.contact_compliance &&
+           a.adj_fallback == b.adj_fallback;
 }
 
 template <class T>
@@ -214,7 +216,7 @@ dc_status upload_mesh(dc_ctx* c, MeshPrep& mp) {
     RET(dalloc(c, W, &c->cc, m));
     RET(dalloc(c, W, &c->stage, 3 * (size_t)m));
     RET(dalloc(c, W, &c->stage2, 3 * (size_t)m));
-    RET(dalloc(c, W, &c->counters, 4));
+    RET(dalloc(c, W, &c->counters, 8));
     RET(alloc_rec(c, W, c->scratch));
     if (!c->hpin) {
         if (cudaMallocHost(&c->hpin, 1024 * sizeof(double)) != cudaSuccess) {
@@ -248,6 +250,7 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
     std::vector<HostFactor> hf(B);
     std::vector<HostFronts> fr(B);
     std::vector<HostPSolve> psi(B);
+    std::vector<std::vector<double>> ccon(B);   // constant compliance per free node (not ROWSUM)
     std::vector<dc_status> st(B, DC_OK);
     std::vector<std::string> err(B);
     dc_parallel_for(B, [&](int i) {
@@ -255,6 +258,20 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
         std::vector<double> mass(h.m);
         for (int l = 0; l < h.m; ++l) mass[l] = q[i].density * h.abar[l];
         st[i] = dc_build_factor(h, q[i], mass, hf[i], err[i]);
+        if (st[i] == DC_OK && q[i].contact_compliance != DC_COMPLIANCE_ROWSUM) {
+            // c_j per free node (internal order), reading of Eq. ly_et_al_govrningEq
+            std::vector<double>& cv = ccon[i];
+            cv.assign(h.m_free, 0.0);
+            if (q[i].contact_compliance == DC_COMPLIANCE_DIAG_PINV) {
+                std::vector<double> zd;
+                dc_inverse_diagonal(hf[i], zd);
+                for (int l = 0; l < h.m_free; ++l) cv[l] = q[i].h * zd[l];
+            } else if (q[i].contact_compliance == DC_COMPLIANCE_DIAG_P) {
+                for (int l = 0; l < h.m_free; ++l) cv[l] = q[i].h / hf[i].pdiag[l];
+            } else {
+                for (int l = 0; l < h.m_free; ++l) cv[l] = q[i].h / mass[l];
+            }
+        }
         if (st[i] == DC_OK) {
             std::string fe = dc_build_fronts(h, hf[i], fr[i]);
             if (!fe.empty()) {
@@ -293,9 +310,12 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
     pp.okind.clear();
     pp.oprm.clear();
     pp.tau.assign(frm.S, 0.0f);
+    pp.ccon.assign(q[0].contact_compliance != DC_COMPLIANCE_ROWSUM ? MF : 0, 0.0);
     for (int i = 0; i < B; ++i) {
         const InstInfo& in = c->inst[i];
         const HostMesh& h = c->ihm[i];
+        if (!pp.ccon.empty())
+            for (int l = 0; l < in.mf; ++l) pp.ccon[in.map(l, MF)] = ccon[i][l];
         for (int l = 0; l < in.m; ++l) {
             const int g = in.map(l, MF);
             pp.mass[g] = q[i].density * h.abar[l];
@@ -335,7 +355,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     c->graph_epoch++;
     c->have_params = false;
     auto& P = c->factor_allocs;
-    double *d_mass, *d_wt, *d_wb, *d_fval, *d_kval, *d_mu, *d_oprm;
+    double *d_mass, *d_wt, *d_wb, *d_fval, *d_kval, *d_mu, *d_oprm, *d_ccon = nullptr;
     int *d_fptr, *d_fidx, *d_kptr, *d_kidx, *d_long, *d_short, *d_optr, *d_okind;
     dc_status s;
     if ((s = upload(c, P, &d_mass, pp.mass)) || (s = upload(c, P, &d_wt, pp.wt)) || (s = upload(c, P, &d_wb, pp.wb)) ||
@@ -344,7 +364,8 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         (s = upload(c, P, &d_kidx, hfm.bidx)) || (s = upload(c, P, &d_kval, hfm.bval)) ||
         (s = upload(c, P, &d_long, pp.long_rows)) || (s = upload(c, P, &d_short, pp.short_rows)) ||
         (s = upload(c, P, &d_mu, pp.node_mu)) || (s = upload(c, P, &d_optr, pp.optr)) ||
-        (s = upload(c, P, &d_okind, pp.okind)) || (s = upload(c, P, &d_oprm, pp.oprm)))
+        (s = upload(c, P, &d_okind, pp.okind)) || (s = upload(c, P, &d_oprm, pp.oprm)) ||
+        (!pp.ccon.empty() && (s = upload(c, P, &d_ccon, pp.ccon))))
         return s;
     DevMesh& dm = c->dm;
     dm.n_long = (int)pp.long_rows.size();
@@ -364,6 +385,9 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     dp.h = pp.q[0].h;
     for (int k = 0; k < 3; ++k) dp.g[k] = pp.q[0].gravity[k];
     dp.delta = pp.q[0].contact_margin;
+    dp.compliance = pp.q[0].contact_compliance;
+    dp.mass_split = dp.compliance == DC_COMPLIANCE_MASS ? 1 : 0;
+    dp.ccon = d_ccon;
     dp.node_mu = d_mu;
     dp.optr = d_optr;
     dp.okind = d_okind;
@@ -630,7 +654,7 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     add(vbytes(mp.chunks)); add(vbytes(mp.pchunks));
     // forward work
     for (int i = 0; i < 9; ++i) add(m * d4b);
-    add(T * d4b); add(T * d4b); add(m * 8); add(m * 24); add(m * 24); add(32);
+    add(T * d4b); add(T * d4b); add(m * 8); add(m * 24); add(m * 24); add(64);
     add(MF * 4); add(MF * 4); add(MF * d4b); add(MF * d4b);
     // factor and tables
     const HostFactor& f = pp.hfm;
@@ -638,6 +662,7 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     add(vbytes(f.fval)); add(vbytes(f.bptr)); add(vbytes(f.bidx)); add(vbytes(f.bval)); add(vbytes(pp.long_rows));
     add(vbytes(pp.short_rows)); add(vbytes(pp.node_mu)); add(vbytes(pp.optr)); add(vbytes(pp.okind));
     add(vbytes(pp.oprm));
+    if (!pp.ccon.empty()) add(vbytes(pp.ccon));
     // fronts (numeric storage twice: two slots)
     const HostFronts& r = pp.frm;
     add(vbytes(r.begin)); add(vbytes(r.f)); add(vbytes(r.p)); add(vbytes(r.off)); add(vbytes(r.acc_off));

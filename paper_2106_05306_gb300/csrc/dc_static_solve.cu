@@ -20,7 +20,15 @@
 // it: each call rewrites every entry it reads (the permuted input, the forward
 // result, and the pinned-node rows of the solution, which are zeroed) before
 // reading it.  Calls whose execution overlaps on the GPU (different streams or
-// contexts on the same device) race on the array; serialise them.
+// contexts on the same device) race on the array; serialise them.  With
+// global_solver 1 the supernodal sweeps also write the context's own update
+// and solution vectors and dependency flags (allocated once by dc_set_params),
+// so calls on one context must also be serialised with its other calls, which
+// its stream does.
+//
+// The scratch address is looked up for the device the context was created on,
+// which must be the current device (a kernel on one device must not be handed
+// another device's array).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -51,6 +59,8 @@ bool device_accessible(const void* p) {
 
 // Accessors of the context (defined in dc_api.cu).
 bool dc_ctx_ready(const dc_ctx* c);
+int dc_ctx_device(const dc_ctx* c);
+int dc_ctx_layout(const dc_ctx* c);
 const DevMesh& dc_ctx_mesh(const dc_ctx* c);
 const DevParams& dc_ctx_params(const dc_ctx* c);
 const int* dc_ctx_int2ext(const dc_ctx* c);
@@ -76,8 +86,14 @@ extern "C" dc_status dc_global_solve_static(dc_ctx* c, const double* rhs, double
     }
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= DC_STATIC_MAX_DEVICES) {
+        cudaGetLastError();
         dc_ctx_set_error(c, "dc_global_solve_static: no usable current device");
         return DC_ERR_CUDA;
+    }
+    if (dev != dc_ctx_device(c)) {
+        dc_ctx_set_error(c, "dc_global_solve_static: device " + std::to_string(dc_ctx_device(c)) +
+                                " (the context's) must be current, not device " + std::to_string(dev));
+        return DC_ERR_INVALID;
     }
     d4* scratch = nullptr;
     {
@@ -86,6 +102,7 @@ extern "C" dc_status dc_global_solve_static(dc_ctx* c, const double* rhs, double
             void* p = nullptr;
             cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
             if (e != cudaSuccess) {
+                cudaGetLastError();   // do not leave the error for a later call to report
                 dc_ctx_set_error(c, std::string("dc_global_solve_static: cudaGetSymbolAddress: ") +
                                         cudaGetErrorString(e));
                 return DC_ERR_CUDA;
@@ -99,11 +116,11 @@ extern "C" dc_status dc_global_solve_static(dc_ctx* c, const double* rhs, double
     d4* v = scratch + 2 * DC_STATIC_MAX_NODES;
     cudaStream_t s = dc_ctx_stream(c);
     const int* int2ext = dc_ctx_int2ext(c);
-    launch_permute_in(rhs, b, int2ext, dm.m, s);
+    launch_permute_in(rhs, b, int2ext, dm.m, dc_ctx_layout(c), s);
     launch_solve_fwd(dm, b, y, s);
     launch_zero_pins(v, dm.m_free, dm.m, s);
     launch_solve_bwd(dm, dc_ctx_params(c), y, v, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, s);
-    launch_permute_out(v, out, int2ext, dm.m, s);
+    launch_permute_out(v, out, int2ext, dm.m, dc_ctx_layout(c), s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         dc_ctx_set_error(c, std::string("dc_global_solve_static: ") + cudaGetErrorString(e));

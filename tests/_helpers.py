@@ -17,7 +17,8 @@ def make_cloth(sc, device="cuda", **over):
     cloth = dc.Cloth(sc.rest_pos, sc.tris, sc.pins, device=device)
     cloth.set_params(k_stretch=p.k_stretch, k_bend=p.k_bend, density=p.density, mu=p.mu, h=p.h,
                      gravity=p.gravity, contact_margin=p.contact_margin, n_pd_iters=p.n_pd_iters,
-                     obstacles=extra.pop("obstacles", sc.obstacles), **extra)
+                     contact_compliance=p.contact_compliance, obstacles=extra.pop("obstacles", sc.obstacles),
+                     **extra)
     return cloth
 
 
@@ -48,7 +49,8 @@ def params_kw(sc, **over):
     """The set_params keyword arguments of a scene (with overrides)."""
     p = dataclasses.replace(sc.params, **{k: v for k, v in over.items() if hasattr(sc.params, k)})
     kw = dict(k_stretch=p.k_stretch, k_bend=p.k_bend, density=p.density, mu=p.mu, h=p.h, gravity=p.gravity,
-              contact_margin=p.contact_margin, n_pd_iters=p.n_pd_iters, obstacles=sc.obstacles)
+              contact_margin=p.contact_margin, n_pd_iters=p.n_pd_iters, contact_compliance=p.contact_compliance,
+              obstacles=sc.obstacles)
     kw.update({k: v for k, v in over.items() if not hasattr(sc.params, k)})
     return kw
 

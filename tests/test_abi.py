@@ -47,9 +47,10 @@ def test_struct_layouts_match_header(lib):
 #include <stddef.h>
 #include "dc.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu\n", sizeof(dc_params), sizeof(dc_obstacle), sizeof(dc_stats),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(dc_params), sizeof(dc_obstacle), sizeof(dc_stats),
          offsetof(dc_params, n_pd_iters), offsetof(dc_params, obstacles), offsetof(dc_stats, factor_nnz),
-         offsetof(dc_stats, n_free));
+         offsetof(dc_stats, n_free), offsetof(dc_params, contact_compliance), offsetof(dc_params, adj_fallback),
+         offsetof(dc_stats, adj_fallbacks), offsetof(dc_stats, device_bytes_peak));
   return 0;
 }
 """
@@ -61,7 +62,8 @@ int main(void) {
         got = [int(v) for v in subprocess.check_output([exe]).split()]
     P, O, S = _lib.dc_params, _lib.dc_obstacle, _lib.dc_stats
     want = [ctypes.sizeof(P), ctypes.sizeof(O), ctypes.sizeof(S), P.n_pd_iters.offset, P.obstacles.offset,
-            S.factor_nnz.offset, S.n_free.offset]
+            S.factor_nnz.offset, S.n_free.offset, P.contact_compliance.offset, P.adj_fallback.offset,
+            S.adj_fallbacks.offset, S.device_bytes_peak.offset]
     assert got == want
 
 
@@ -84,3 +86,23 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cpp", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in txt.replace("no CPU fallback", ""), f
+
+
+def test_batch_hbm_bytes_runs_on_the_host(lib):
+    """dc_batch_hbm_bytes orders, factorises and sizes on the host only (no device
+    call), so it runs here: the footprint grows with the step count (one recorded
+    state per step) and with the cloths, and invalid input is rejected."""
+    import numpy as np
+    import paper_2106_05306_gb300 as dc
+    import scenes
+    a, b = scenes.batch_instance(0), scenes.batch_instance(1)
+    mesh = lambda s: (s.rest_pos, s.tris, s.pins)
+    kw = dict(k_stretch=a.params.k_stretch, checkpoint_every=1)
+    one = dc.batch_hbm_bytes([mesh(a)], kw, 10)
+    assert one > 0
+    assert dc.batch_hbm_bytes([mesh(a)], kw, 20) > one
+    two = dc.batch_hbm_bytes([mesh(a), mesh(b)], kw, 10)
+    assert two > one
+    for bad in ([(a.rest_pos, np.array([[0, 1, 10 ** 6]]), [])], [mesh(a), mesh(b)]):
+        with pytest.raises(dc.DCError):
+            dc.batch_hbm_bytes(bad, [dict(kw), dict(kw, h=2e-2)] if len(bad) == 2 else kw, 10)

@@ -51,6 +51,17 @@ def test_backward_parity_hanging_cloth_16x16(precond):
         assert st["adj_max_iters_seen"] <= 40
 
 
+def test_backward_parity_through_a_collapsed_triangle():
+    """With no PD iteration the step ends where it started, so the adjoint is
+    linearised at a state with a triangle collapsed onto a line: both sides take
+    its projection as locally constant (reading R1, dR = 0)."""
+    sc = scenes.collapsed_triangle_scene(n_steps=1)
+    M = oracle_model(sc)
+    assert oc.polar_degenerate(M.deformation_gradients(sc.x0))[0]
+    got, want, st, recs = _grad_parity(sc, 1, n_pd_iters=0)
+    assert np.all(np.isfinite(got[0])) and np.all(np.isfinite(got[2]))
+
+
 def test_backward_with_per_step_loss_and_checkpoint_invariance():
     import torch
     sc = scenes.small_scene(5, seed=1, contact="both", drop=True, n_steps=6)

@@ -76,6 +76,16 @@ def test_step_parity_draped_61x61_sampled():
     assert n_cases.sum() > 0
 
 
+def test_step_parity_collapsed_triangle():
+    """A triangle collapsed onto a line at x_n: the first local step takes reading
+    R1's degenerate rule on both sides (the kernel's closed form would divide by
+    det F^T F = 0)."""
+    sc = scenes.collapsed_triangle_scene()
+    M = oracle_model(sc)
+    assert oc.polar_degenerate(M.deformation_gradients(sc.x0))[0]
+    _per_step_parity(sc, 3)
+
+
 @pytest.mark.parametrize("n", [2, 3, 7])
 def test_ragged_and_tiny_grids(n):
     sc = scenes.small_scene(n, seed=n, contact="both", drop=True, pinned=(n > 2))

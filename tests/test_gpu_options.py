@@ -1,0 +1,169 @@
+"""GPU tests of the boundary's options and error paths: the contact-compliance
+choices (parity with the oracle, the printed mass splitting's divergence), the
+component-major node layout, host-injected non-finite input, the adjoint
+fallback and DC_ERR_NONCONVERGED, DC_ERR_NOT_SPD, and dc_batch_hbm_bytes against
+the device memory a context actually held.  Every failure here is made on the
+host (a parameter, an input array); none faults the GPU."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import scenes
+from oracle import cloth as oc
+from tests._helpers import GRAD_TOL, STATE_TOL, cuda, make_batch, make_cloth, oracle_model, rel_inf, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+def _soft(sc, ks=0.15):
+    return dataclasses.replace(sc, params=dataclasses.replace(sc.params, k_stretch=ks, k_bend=1e-7))
+
+
+@pytest.mark.parametrize("mode,soft", [("diag_pinv", False), ("diag_p", False), ("diag_pinv", True),
+                                       ("diag_p", True), ("mass", True), ("rowsum", True)])
+def test_compliance_choices_match_the_oracle(mode, soft):
+    """Each step from the oracle's state, K = 20 iterations, both sides with the
+    same compliance choice (reading R5 and its ablations)."""
+    sc = scenes.small_scene(5, seed=3, contact="both", drop=True, n_steps=3)
+    if soft:
+        sc = _soft(sc)
+    for solver in (0, 1):
+        cloth = make_cloth(sc, contact_compliance=mode, global_solver=solver)
+        M = oracle_model(sc, contact_compliance=mode)
+        xs, vs, recs = oc.rollout(M, sc.x0, sc.v0, sc.n_steps)
+        assert sum(len(r.contacts) for r in recs) > 0
+        for n in range(sc.n_steps):
+            x1, v1 = cloth.step(cuda(xs[n]), cuda(vs[n]))
+            assert rel_inf(x1.cpu().numpy(), xs[n + 1]) <= STATE_TOL
+            assert rel_inf(v1.cpu().numpy(), vs[n + 1]) <= STATE_TOL, (mode, solver, n)
+        assert cloth.stats()["contact_compliance"] == oc_mode_code(mode)
+        cloth.close()
+
+
+def oc_mode_code(mode):
+    return {"rowsum": 0, "diag_pinv": 1, "diag_p": 2, "mass": 3}[mode]
+
+
+def test_mass_splitting_diverges_at_cloth_stiffness():
+    """The printed splitting at the hanging cloth's stiffness: the states blow up
+    and the forward step reports DC_ERR_NONFINITE once they overflow."""
+    import paper_2106_05306_gb300 as dc
+    sc = scenes.hanging_cloth()
+    cloth = make_cloth(sc, contact_compliance="mass")
+    x, v = sc.x0.copy(), sc.v0.copy()
+    x1, v1 = cloth.step(x, v)                     # host arrays: synchronous, flags checked
+    assert np.max(np.abs(v1.numpy())) > 1e20
+    with pytest.raises(dc.DCError, match="DC_ERR_NONFINITE"):
+        for _ in range(20):
+            x, v = cloth.step(x, v)
+            x, v = x.numpy(), v.numpy()
+    cloth.close()
+
+
+def test_component_major_layout_gives_the_same_numbers():
+    """A batch with [3][m] node arrays: rollout (with trajectory), backward (with a
+    per-step loss) and the global solve are the transposes of the [m][3] results,
+    bit for bit (the layout only changes the boundary permutation)."""
+    import torch
+    scs = [scenes.small_scene(5, seed=3, contact="both", drop=True, n_steps=4),
+           scenes.small_scene(4, seed=1, contact="sphere", drop=True, n_steps=4)]
+    n = 4
+    res = {}
+    for layout in ("node_major", "component_major"):
+        b = make_batch(scs, checkpoint_every=2)
+        b.set_layout(layout)
+        cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
+        x0, v0, xi = cat("x0"), cat("v0"), cat("loss_w")
+        rng = np.random.default_rng(3)
+        gT = 0.1 * rng.standard_normal((n + 1, b.m, 3))
+        if layout == "component_major":
+            x0, v0, xi = x0.T.copy(), v0.T.copy(), xi.T.copy()
+            gT = gT.transpose(0, 2, 1).copy()
+        xN, vN, tr = b.rollout(cuda(x0), cuda(v0), n, traj=True)
+        dx0, dv0, dth = b.backward(cuda(xi), None, cuda(gT))
+        sol = b.global_solve(cuda(x0))
+        out = [xN, vN, dx0, dv0, sol]
+        if layout == "component_major":
+            out = [a.t() for a in out]
+            tr = tr.transpose(1, 2)
+        res[layout] = [a.cpu() for a in out] + [tr.cpu(), dth.cpu()]
+        b.close()
+    for a, c in zip(res["node_major"], res["component_major"]):
+        assert torch.equal(a.contiguous(), c.contiguous())
+
+
+def test_nan_input_is_reported_once():
+    import paper_2106_05306_gb300 as dc
+    sc = scenes.small_scene(4, seed=2, contact="plane", drop=True)
+    cloth = make_cloth(sc)
+    x = sc.x0.copy()
+    x[5, 1] = np.nan
+    with pytest.raises(dc.DCError, match="DC_ERR_NONFINITE"):
+        cloth.step(x, sc.v0)                      # host arrays: the call synchronises and reports
+    x1, v1 = cloth.step(sc.x0, sc.v0)             # reported once; a finite step is fine again
+    assert np.all(np.isfinite(x1.numpy()))
+    xd = cuda(x)
+    cloth.rollout(xd, cuda(sc.v0), 2)             # device arrays: asynchronous, reported at the next sync
+    with pytest.raises(dc.DCError, match="DC_ERR_NONFINITE"):
+        cloth.sync()
+    cloth.close()
+
+
+def test_adjoint_fallback_and_nonconverged():
+    """adj_max_iters = 1 stops every adjoint step far above adj_tol.  With the
+    fallback off, dc_backward reports DC_ERR_NONCONVERGED (after writing its
+    outputs); with it on, the fallback pass finishes each step and the gradient
+    matches the oracle's direct adjoint."""
+    import paper_2106_05306_gb300 as dc
+    sc = scenes.small_scene(5, seed=3, contact="both", drop=True, n_steps=3)
+    M = oracle_model(sc)
+    xs, vs, recs = oc.rollout(M, sc.x0, sc.v0, sc.n_steps)
+    want = oc.rollout_gradient(M, recs, sc.loss_w)
+    off = make_cloth(sc, adj_max_iters=1, adj_fallback=0)
+    off.rollout(cuda(sc.x0), cuda(sc.v0), sc.n_steps)
+    with pytest.raises(dc.DCError, match="DC_ERR_NONCONVERGED"):
+        off.backward(cuda(sc.loss_w))
+    st = off.stats()
+    assert st["adj_nonconverged"] == sc.n_steps and st["adj_fallbacks"] == 0
+    off.close()
+    for solver in (0, 1):
+        on = make_cloth(sc, adj_max_iters=1, adj_fallback=1, global_solver=solver)
+        on.rollout(cuda(sc.x0), cuda(sc.v0), sc.n_steps)
+        dx0, dv0, dth = on.backward(cuda(sc.loss_w))
+        st = on.stats()
+        assert st["adj_fallbacks"] == sc.n_steps and st["adj_nonconverged"] == 0
+        assert rel_l2(dx0.cpu().numpy(), want[0]) <= GRAD_TOL
+        assert rel_l2(dv0.cpu().numpy(), want[1]) <= GRAD_TOL
+        assert rel_l2(dth.cpu().numpy(), want[2]) <= GRAD_TOL
+        on.close()
+
+
+def test_underflowing_mass_is_not_spd():
+    """A density so small that the lumped masses underflow to 0, with no stiffness:
+    P = M has a zero pivot, which the factorisation reports."""
+    import paper_2106_05306_gb300 as dc
+    sc = scenes.small_scene(4, seed=1)
+    cloth = dc.Cloth(sc.rest_pos, sc.tris, sc.pins)
+    with pytest.raises(dc.DCError, match="DC_ERR_NOT_SPD"):
+        cloth.set_params(density=5e-324, k_stretch=0.0, k_bend=0.0)
+    cloth.set_params()                            # the context is still usable
+    cloth.close()
+
+
+def test_batch_hbm_bytes_bounds_the_memory_held():
+    """dc_batch_hbm_bytes is an upper bound of what the context holds through the
+    rollout and backward it was asked about, and not far above it."""
+    import paper_2106_05306_gb300 as dc
+    scs = [scenes.batch_instance(s, n_steps=6) for s in (3, 4, 5)]
+    kw = [dict(k_stretch=s.params.k_stretch, k_bend=s.params.k_bend, mu=s.params.mu, obstacles=s.obstacles,
+               checkpoint_every=2, global_solver=1) for s in scs]
+    est = dc.batch_hbm_bytes([(s.rest_pos, s.tris, s.pins) for s in scs], kw, 6)
+    b = dc.ClothBatch([(s.rest_pos, s.tris, s.pins) for s in scs])
+    b.set_params(kw)
+    cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
+    b.rollout(cuda(cat("x0")), cuda(cat("v0")), 6)
+    b.backward(cuda(cat("loss_w")), allow_nonconverged=True)
+    peak = b.stats()["device_bytes_peak"]
+    b.close()
+    assert peak <= est <= 1.5 * peak, (peak, est)
