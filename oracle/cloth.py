@@ -379,8 +379,92 @@ def polar_derivative(R, S, dF):
 # Obstacles (R4)
 # ----------------------------------------------------------------------------
 
+def _closest_on_triangle(x, P):
+    """Closest point of triangle P (3 x 3, rows = vertices) to x, and its feature:
+    ("face",), ("edge", i, j) or ("vertex", i) with local vertex indices.  The
+    projection onto the triangle's plane is kept if its barycentric coordinates
+    are all >= 0; otherwise the closest point is the nearest of the three edge
+    segments' closest points (first edge on ties)."""
+    A, B, C = P
+    nrm = np.cross(B - A, C - A)
+    nrm = nrm / np.linalg.norm(nrm)
+    p = x - np.dot(x - A, nrm) * nrm
+    v0, v1, v2 = B - A, C - A, p - A
+    d00, d01, d11 = np.dot(v0, v0), np.dot(v0, v1), np.dot(v1, v1)
+    d20, d21 = np.dot(v2, v0), np.dot(v2, v1)
+    den = d00 * d11 - d01 * d01
+    bv = (d11 * d20 - d01 * d21) / den
+    bw = (d00 * d21 - d01 * d20) / den
+    if bv >= 0.0 and bw >= 0.0 and 1.0 - bv - bw >= 0.0:
+        return p, ("face",)
+    best = None
+    for i, j in ((0, 1), (1, 2), (2, 0)):
+        Q0, Q1 = P[i], P[j]
+        t = np.clip(np.dot(x - Q0, Q1 - Q0) / np.dot(Q1 - Q0, Q1 - Q0), 0.0, 1.0)
+        c = Q0 + t * (Q1 - Q0)
+        d = np.linalg.norm(x - c)
+        feat = ("vertex", i) if t == 0.0 else (("vertex", j) if t == 1.0 else ("edge", i, j))
+        if best is None or d < best[0]:
+            best = (d, c, feat)
+    return best[1], best[2]
+
+
+def _mesh_closest(ob, x):
+    """Closest point of a closed triangle mesh to x: (point, distance, feature in
+    mesh vertex indices, face index); the lowest face index wins ties."""
+    V = np.asarray(ob.vertices, dtype=np.float64)
+    F = np.asarray(ob.triangles, dtype=np.int64)
+    best = None
+    for f in range(len(F)):
+        c, feat = _closest_on_triangle(x, V[F[f]])
+        d = np.linalg.norm(x - c)
+        if best is None or d < best[1]:
+            if feat[0] == "edge":
+                feat = ("edge", int(F[f][feat[1]]), int(F[f][feat[2]]))
+            elif feat[0] == "vertex":
+                feat = ("vertex", int(F[f][feat[1]]))
+            best = (c, d, feat, f)
+    return best
+
+
+def _mesh_pseudo_normal(ob, feat, face):
+    """Angle-weighted pseudo-normal of a mesh feature (its sign test tells inside
+    from outside): the face normal; the sum of the two incident face normals for
+    an edge; the sum of incident face normals weighted by their angle at a vertex."""
+    V = np.asarray(ob.vertices, dtype=np.float64)
+    F = np.asarray(ob.triangles, dtype=np.int64)
+
+    def fn(f):
+        a, b, c = V[F[f]]
+        n = np.cross(b - a, c - a)
+        return n / np.linalg.norm(n)
+    if feat[0] == "face":
+        return fn(face)
+    if feat[0] == "edge":
+        i, j = feat[1], feat[2]
+        fs = [f for f in range(len(F)) if i in F[f] and j in F[f]]
+        return sum(fn(f) for f in fs)
+    i = feat[1]
+    out = np.zeros(3)
+    for f in range(len(F)):
+        if i in F[f]:
+            k = list(F[f]).index(i)
+            p, q = V[F[f][(k + 1) % 3]] - V[i], V[F[f][(k + 2) % 3]] - V[i]
+            ang = np.arccos(np.clip(np.dot(p, q) / (np.linalg.norm(p) * np.linalg.norm(q)), -1.0, 1.0))
+            out += ang * fn(f)
+    return out
+
+
 def signed_distance(ob, x):
-    """(phi, grad phi) of an analytic obstacle at point x."""
+    """(phi, grad phi) of an obstacle at point x."""
+    if ob.kind == "mesh":
+        # |x - c| to the closest point c, signed by the pseudo-normal of c's feature;
+        # grad phi = s (x - c)/|x - c|
+        c, d, feat, face = _mesh_closest(ob, x)
+        s = 1.0 if np.dot(x - c, _mesh_pseudo_normal(ob, feat, face)) >= 0.0 else -1.0
+        if d == 0.0:
+            return 0.0, _mesh_pseudo_normal(ob, ("face",), face)
+        return float(s * d), s * (x - c) / d
     if ob.kind == "plane":
         n = np.asarray(ob.normal, dtype=np.float64)
         return float(np.dot(n, x) - ob.offset), n.copy()
@@ -400,9 +484,24 @@ def signed_distance(ob, x):
 
 
 def normal_jacobian(ob, x):
-    """d n / d x for the obstacle normal taken at x (3x3); zero for planes."""
+    """d n / d x for the obstacle normal taken at x (3x3); zero for planes and in
+    the face region of a mesh; s (I - u u^T - e e^T)/r on a mesh edge (e its unit
+    direction), s (I - u u^T)/r at a mesh vertex, u = (x - c)/r, r = |x - c|."""
     if ob.kind == "plane":
         return np.zeros((3, 3))
+    if ob.kind == "mesh":
+        c, r, feat, face = _mesh_closest(ob, x)
+        if feat[0] == "face" or r == 0.0:
+            return np.zeros((3, 3))
+        s = 1.0 if np.dot(x - c, _mesh_pseudo_normal(ob, feat, face)) >= 0.0 else -1.0
+        u = (x - c) / r
+        J = np.eye(3) - np.outer(u, u)
+        if feat[0] == "edge":
+            V = np.asarray(ob.vertices, dtype=np.float64)
+            e = V[feat[2]] - V[feat[1]]
+            e = e / np.linalg.norm(e)
+            J = J - np.outer(e, e)
+        return s * J / r
     if ob.kind == "sphere":
         d = x - np.asarray(ob.center, dtype=np.float64)
         r = np.linalg.norm(d)

@@ -13,7 +13,8 @@ Geometry conventions (the paper fixes none of them):
     (x0 + i*a, height, z0 + j*a) with a = side/(n-1).
   * Each grid quad (i, j)-(i+1, j+1) is split along that diagonal into the
     triangles (v00, v10, v11) and (v00, v11, v01).
-  * Obstacles are analytic: planes {x : n.x = d}, spheres and capsules.
+  * Obstacles are analytic (planes {x : n.x = d}, spheres and capsules) or
+    closed triangle meshes with outward (counter-clockwise) orientation.
 """
 from __future__ import annotations
 
@@ -27,13 +28,49 @@ GRAVITY = (0.0, -9.8, 0.0)
 
 @dataclasses.dataclass
 class Obstacle:
-    kind: str                      # "plane" | "sphere" | "capsule"
+    kind: str                      # "plane" | "sphere" | "capsule" | "mesh"
     normal: tuple = (0.0, 1.0, 0.0)  # plane: unit normal
     offset: float = 0.0            # plane: n.x = offset
     center: tuple = (0.0, 0.0, 0.0)  # sphere centre
     radius: float = 0.0            # sphere / capsule radius
     a: tuple = (0.0, 0.0, 0.0)     # capsule segment end points
     b: tuple = (0.0, 0.0, 0.0)
+    vertices: Optional[np.ndarray] = None   # mesh: (V, 3) positions
+    triangles: Optional[np.ndarray] = None  # mesh: (F, 3) int32, counter-clockwise seen from outside
+
+
+def icosphere(center=(0.0, 0.0, 0.0), radius: float = 1.0, subdivisions: int = 1):
+    """A closed triangle mesh of a sphere: the icosahedron, each face split into 4
+    subdivisions times, vertices pushed onto the sphere.  Outward orientation."""
+    t = (1.0 + 5.0 ** 0.5) / 2.0
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    verts = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    faces = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2),
+             (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5),
+             (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdivisions):
+        mid = {}
+
+        def midpoint(i, j):
+            key = (min(i, j), max(i, j))
+            if key not in mid:
+                p = verts[i] + verts[j]
+                verts.append(p / np.linalg.norm(p))
+                mid[key] = len(verts) - 1
+            return mid[key]
+        nf = []
+        for a, b, c in faces:
+            ab, bc, ca = midpoint(a, b), midpoint(b, c), midpoint(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.asarray(center, dtype=np.float64) + radius * np.stack(verts)
+    return V, np.asarray(faces, dtype=np.int32)
+
+
+def mesh_sphere(center, radius, subdivisions=1) -> Obstacle:
+    V, F = icosphere(center, radius, subdivisions)
+    return Obstacle("mesh", vertices=V, triangles=F)
 
 
 @dataclasses.dataclass
@@ -181,6 +218,35 @@ def inclined_plane(theta: float, mu: float, n: int = 4, side: float = 0.3) -> Sc
     prm = Params(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=mu, h=1.0 / 100.0)
     return Scene("slope", n, pos, tris, np.zeros(0, np.int32), obst, prm, pos.copy(),
                  np.zeros_like(pos), 10)
+
+
+def sliding_breathing_scene(n: int = 8, n_steps: int = 24) -> Scene:
+    """A cloth on a plane tilted 0.15 rad past the friction angle of mu = 0.5,
+    started with a uniform in-plane expansion velocity (0.5 s^-1 about its centre):
+    it slides down (rate set by mu) while it breathes (frequency set by
+    k_stretch).  Both motions are smooth, so a handful of PD iterations per step
+    reach the step's fixed point (the system-identification scene)."""
+    sc = inclined_plane(float(np.arctan(0.5) + 0.15), 0.5, n=n, side=0.4)
+    nrm = np.asarray(sc.obstacles[0].normal)
+    c = sc.x0.mean(axis=0)
+    v0 = 0.5 * (sc.x0 - c)
+    v0 -= np.outer(v0 @ nrm, nrm)
+    return dataclasses.replace(sc, name="sliding_breathing", v0=v0, n_steps=n_steps,
+                               loss_w=loss_weights(n * n, 2))
+
+
+def sphere_drop(offset: float = 0.0, mesh_subdivisions: int = -1, n: int = 5, n_steps: int = 8) -> Scene:
+    """A small cloth (side 0.2 m, 5x5) falling at 0.5 m/s onto a sphere of radius
+    0.3 m centred at the origin, shifted by `offset` along x: the analytic sphere,
+    or (mesh_subdivisions >= 0) an icosphere of that many subdivisions with its
+    vertices on the sphere (the scene of the continuity study)."""
+    pos, tris = grid_mesh(n, side=0.2, height=0.32, x0=-0.1 + offset, z0=-0.1)
+    ob = (Obstacle("sphere", center=(0.0, 0.0, 0.0), radius=0.3) if mesh_subdivisions < 0
+          else mesh_sphere((0.0, 0.0, 0.0), 0.3, mesh_subdivisions))
+    prm = Params(k_stretch=100.0, k_bend=1e-3, density=0.1, mu=0.2, h=1.0 / 100.0)
+    v0 = np.tile([0.0, -0.5, 0.0], (n * n, 1))
+    return Scene(f"sphere_drop_{offset:.4f}_{mesh_subdivisions}", n, pos, tris, np.zeros(0, np.int32), [ob], prm,
+                 pos.copy(), v0, n_steps, loss_weights(n * n, 3))
 
 
 def small_scene(n: int = 4, seed: int = 0, contact: str = "sphere", pinned: bool = True,

@@ -537,3 +537,115 @@ def test_diagonal_compliances_match_the_dense_matrices():
     np.testing.assert_allclose(M.compliance(ctr), M.h / np.diag(dense)[pos], rtol=1e-14)
     M = oc.model_from_scene(sc, contact_compliance="mass")
     np.testing.assert_allclose(M.compliance(ctr), M.h / M.mass[nodes], rtol=1e-14)
+
+
+# --------------------------------------------------------------------- triangle-mesh obstacles
+
+def _ray_inside(V, F, x, d=np.array([0.5377, 0.8310, -0.1424])):
+    """Inside test by ray parity (Moller-Trumbore crossings of a fixed ray)."""
+    n = 0
+    for a, b, c in F:
+        e1, e2 = V[b] - V[a], V[c] - V[a]
+        p = np.cross(d, e2)
+        det = np.dot(e1, p)
+        if abs(det) < 1e-14:
+            continue
+        t0 = x - V[a]
+        u = np.dot(t0, p) / det
+        q = np.cross(t0, e1)
+        v = np.dot(d, q) / det
+        t = np.dot(e2, q) / det
+        n += (u >= 0) and (v >= 0) and (u + v <= 1) and (t > 0)
+    return n % 2 == 1
+
+
+def test_mesh_signed_distance_against_sampling_and_ray_parity():
+    """|phi| equals the distance to a dense sampling of the mesh surface (to the
+    sampling's resolution), and its sign agrees with a ray-crossing inside test."""
+    ob = scenes.mesh_sphere((0.1, -0.2, 0.3), 0.4, 1)
+    V, F = np.asarray(ob.vertices), np.asarray(ob.triangles)
+    k = 40
+    bary = np.array([(i / k, j / k) for i in range(k + 1) for j in range(k + 1 - i)])
+    pts = np.concatenate([V[a] + bary[:, :1] * (V[b] - V[a]) + bary[:, 1:] * (V[c] - V[a]) for a, b, c in F])
+    spacing = max(np.linalg.norm(V[a] - V[b]) for a, b, _ in F) / k
+    rng = np.random.default_rng(12)
+    n_in = 0
+    for _ in range(60):
+        x = np.array([0.1, -0.2, 0.3]) + rng.uniform(-0.6, 0.6, 3)
+        ph, n = oc.signed_distance(ob, x)
+        brute = np.min(np.linalg.norm(pts - x, axis=1))
+        assert brute - spacing <= abs(ph) <= brute + 1e-12
+        inside = _ray_inside(V, F, x)
+        n_in += inside
+        assert (ph < 0) == inside
+        assert abs(np.linalg.norm(n) - 1.0) < 1e-12
+    assert 5 < n_in < 55
+
+
+def test_mesh_normal_and_jacobian_match_differences():
+    """grad phi and d n/d x by central differences, away from region boundaries
+    (points are kept only where the closest feature is the same at +-1e-6)."""
+    ob = scenes.mesh_sphere((0.0, 0.0, 0.0), 0.5, 1)
+    rng = np.random.default_rng(13)
+    kinds = set()
+    tested = 0
+    while tested < 40:
+        x = rng.uniform(-0.8, 0.8, 3)
+        _, _, feat, _ = oc._mesh_closest(ob, x)
+        same = all(oc._mesh_closest(ob, x + s * 1e-6 * np.eye(3)[q])[2] == feat for q in range(3) for s in (-1, 1))
+        if not same:
+            continue
+        kinds.add(feat[0])
+        tested += 1
+        ph, n = oc.signed_distance(ob, x)
+        g = np.array([(oc.signed_distance(ob, x + 1e-6 * np.eye(3)[q])[0] -
+                       oc.signed_distance(ob, x - 1e-6 * np.eye(3)[q])[0]) / 2e-6 for q in range(3)])
+        np.testing.assert_allclose(n, g, atol=1e-8)
+        J = oc.normal_jacobian(ob, x)
+        fd = np.stack([(oc.signed_distance(ob, x + 1e-6 * np.eye(3)[q])[1] -
+                        oc.signed_distance(ob, x - 1e-6 * np.eye(3)[q])[1]) / 2e-6 for q in range(3)], axis=1)
+        np.testing.assert_allclose(J, fd, atol=1e-6)
+    assert kinds == {"face", "edge", "vertex"}
+
+
+def test_fine_mesh_sphere_approaches_the_analytic_sphere():
+    """A subdivided icosphere's phi is within its sagitta of the analytic sphere's
+    (vertices lie on the sphere, faces at most r (1 - cos(theta/2)) inside it, theta
+    the largest edge angle)."""
+    c, r = np.array([0.0, 0.1, 0.0]), 0.3
+    sph = scenes.Obstacle("sphere", center=tuple(c), radius=r)
+    for sub in (1, 2):
+        ob = scenes.mesh_sphere(tuple(c), r, sub)
+        V, F = np.asarray(ob.vertices), np.asarray(ob.triangles)
+        ang = max(np.arccos(np.clip(np.dot(V[a] - c, V[b] - c) / r ** 2, -1, 1)) for a, b, _ in F)
+        sag = r * (1 - np.cos(ang / 2)) * 1.2
+        rng = np.random.default_rng(sub)
+        for _ in range(20):
+            u = rng.standard_normal(3)
+            u /= np.linalg.norm(u)
+            x = c + rng.uniform(0.2, 0.6) * u
+            dm, _ = oc.signed_distance(ob, x)
+            ds, _ = oc.signed_distance(sph, x)
+            assert -1e-12 <= dm - ds <= sag
+
+
+def test_continuity_study_analytic_vs_triangulated_sphere():
+    """Sec. "Continuity and Smoothness": sweep where a cloth lands on a sphere; the
+    gradient of its final mean x w.r.t. the landing offset changes by small steps
+    over the analytic sphere and by large jumps over a coarse triangulation of it
+    (normals jump across edges, curvature concentrates at edges and vertices)."""
+    offsets = np.linspace(0.0, 0.12, 13)
+
+    def sweep(sub):
+        g = []
+        for d in offsets:
+            sc = scenes.sphere_drop(float(d), mesh_subdivisions=sub)
+            M = oc.model_from_scene(sc)
+            _, _, recs = oc.rollout(M, sc.x0, sc.v0, sc.n_steps)
+            w = np.zeros((sc.m, 3))
+            w[:, 0] = 1.0 / sc.m
+            gx, _, _ = oc.rollout_gradient(M, recs, w)
+            g.append(gx[:, 0].sum())
+        return np.abs(np.diff(np.array(g)))
+    js, jm = sweep(-1), sweep(1)
+    assert np.median(jm) > 10.0 * np.median(js)
