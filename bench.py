@@ -495,7 +495,7 @@ KERNEL_CLASSES = {
 
 def kernel_model(cls, st, contacts_per_launch):
     """Algorithmic bytes and FP flops of one launch (the unit of work of each class is
-    described in the design doc; bytes count FP64 = 8 B, indices = 4 B, no padding)."""
+    listed with the kernel table; bytes count FP64 = 8 B, indices = 4 B, no padding)."""
     m, mf, T, nb = st["n_nodes"], st["n_free"], st["n_tris"], st["bend_nnz"]
     if cls == "local":
         return 92.0 * m + 100.0 * T + 12.0 * nb, 150.0 * T + 25.0 * m + 12.0 * nb, "fp64"

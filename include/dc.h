@@ -77,13 +77,15 @@ enum { DC_COMPLIANCE_ROWSUM = 0, DC_COMPLIANCE_DIAG_PINV = 1, DC_COMPLIANCE_DIAG
 /* Layout of node arrays at the boundary (dc_set_layout). */
 enum { DC_LAYOUT_NODE_MAJOR = 0, DC_LAYOUT_COMPONENT_MAJOR = 1 };
 
-enum { DC_PLANE = 0, DC_SPHERE = 1, DC_CAPSULE = 2 };
+enum { DC_PLANE = 0, DC_SPHERE = 1, DC_CAPSULE = 2, DC_MESH = 3 };
 #define DC_MAX_OBSTACLES 16
 
-/* Analytic obstacle (reading of Sec. 3.2 "Extensions": static, possibly curved).
+/* Static obstacle (reading of Sec. 3.2 "Extensions": any obstacle with a signed
+ * distance; analytic or triangulated, Sec. "Continuity and Smoothness").
  *   DC_PLANE:   p[0..2] = unit normal n, p[3] = d        (surface n.x = d)
  *   DC_SPHERE:  p[0..2] = centre, p[3] = radius
- *   DC_CAPSULE: p[0..2] = a, p[3..5] = b, p[6] = radius  (segment a-b) */
+ *   DC_CAPSULE: p[0..2] = a, p[3..5] = b, p[6] = radius  (segment a-b)
+ *   DC_MESH:    p[0] = a mesh id from dc_add_obstacle_mesh on the same context */
 typedef struct dc_obstacle {
     int32_t kind;
     int32_t pad_;
@@ -116,10 +118,10 @@ typedef struct dc_params {
                                 batches; needs adj_precond 0).  Equal results up to
                                 rounding. */
     int32_t contact_compliance; /* DC_COMPLIANCE_* (default ROWSUM)                  */
-    int32_t adj_fallback;    /* 1 (default): an adjoint step whose GMRES stops above
-                                adj_tol is solved again by the fallback (dc_backward);
-                                0: no fallback, such a step makes dc_backward return
-                                DC_ERR_NONCONVERGED                                  */
+    int32_t adj_fallback;    /* 1 (default): an adjoint step whose GMRES reaches
+                                adj_max_iters, or stops more than 100 x adj_tol above
+                                it, is solved again by the fallback (dc_backward);
+                                0: no fallback                                       */
     int32_t reserved_;
     dc_obstacle obstacles[DC_MAX_OBSTACLES];
 } dc_params;
@@ -234,6 +236,20 @@ dc_status dc_set_params(dc_ctx* ctx, const dc_params* params);
  * Each instance's P is assembled and factorised on its own (host threads). */
 dc_status dc_set_params_batch(dc_ctx* ctx, int32_t n_instances, const dc_params* params);
 
+/* Register a closed triangle mesh as an obstacle shape of ctx and return its id
+ * in *mesh_id, for DC_MESH obstacles of later dc_set_params calls.  verts:
+ * [n_verts][3] (host); tris: [n_tris][3] vertex indices (host), counter-clockwise
+ * seen from outside; every edge must be shared by exactly two triangles with
+ * opposite directions (closed and consistently oriented) and no triangle may be
+ * degenerate (DC_ERR_INVALID otherwise).  Its signed distance is |x - c| to the
+ * closest surface point c, signed by the angle-weighted pseudo-normal of c's
+ * face, edge or vertex, and is computed on the GPU by a closest-triangle query
+ * over all its triangles (meant for obstacles of up to a few thousand
+ * triangles).  Its normal jumps across edges: the paper's discontinuity of
+ * triangulated obstacles (Sec. "Continuity and Smoothness"). */
+dc_status dc_add_obstacle_mesh(dc_ctx* ctx, int32_t n_verts, const double* verts, int32_t n_tris,
+                               const int32_t* tris, int32_t* mesh_id);
+
 /* Node-array layout of every later call on ctx: DC_LAYOUT_NODE_MAJOR ([m][3],
  * the default) or DC_LAYOUT_COMPONENT_MAJOR ([3][m]: the x block, then y, then
  * z; for a batch m is the total node count and each block is the concatenation
@@ -291,13 +307,16 @@ dc_status dc_rollout(dc_ctx* ctx, int32_t n_steps, const double* x0, const doubl
  * Outputs dL_dx0, dL_dv0: [m][3]; dL_dparams: [n_instances][3] =
  * dL/d(k_stretch, k_bend, mu) of each instance.
  * Each step's adjoint system is solved by flexible GMRES with the per-step
- * preconditioner (adj_precond).  With adj_fallback = 1, an instance whose GMRES
- * stops above adj_tol (iteration cap, or a restart cycle that no longer halves
- * its residual) is solved again, alone, from its last iterate, by GMRES with the
- * other preconditioner's sweep added (the node-block inverse of H around a
- * fresh single-precision factorisation) and with an FP64-refined restart; the
- * count is in dc_stats.adj_fallbacks.  DC_ERR_NONCONVERGED is reported (after
- * all outputs are written) when an adjoint step still ends above adj_tol. */
+ * preconditioner (adj_precond); an instance stops at a relative residual of
+ * adj_tol, at adj_max_iters, or when a restart cycle no longer halves its
+ * residual (the rounding floor of the FP64 operator, about eps cond(H)).  With
+ * adj_fallback = 1, an instance that reached adj_max_iters or stopped more than
+ * 100 x adj_tol above the tolerance is solved again from its iterate, by
+ * GMRES(30) with a stronger preconditioner (the per-step one followed by a
+ * sweep of the constrained node-block inverse of H) and a looser stagnation
+ * test; the count is in dc_stats.adj_fallbacks.  DC_ERR_NONCONVERGED is
+ * reported (after all outputs are written) when an adjoint step still ends
+ * above adj_tol. */
 dc_status dc_backward(dc_ctx* ctx, const double* dL_dx_final, const double* dL_dv_final,
                       const double* dL_dtraj_x, double* dL_dx0, double* dL_dv0,
                       double* dL_dparams);

@@ -697,11 +697,14 @@ def hessian_W(model: Model, x):
     return Hm, (R, pb, F, S, q)
 
 
-def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None):
+def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None, permc_spec=None):
     """Back-propagate (dL/dx_{n+1}, dL/dv_{n+1}) through one converged step.
 
     ``hess``, if given, is ``hessian_W(model, rec.x_np1)`` computed beforehand
-    (e.g. for many steps in parallel); the result is the same.
+    (e.g. for many steps in parallel); the result is the same.  ``permc_spec``
+    picks the column ordering of the sparse LU (scipy's default if None); two
+    orderings give the same solution up to rounding, and their difference shows
+    how much rounding the KKT system amplifies.
 
     Returns (dL/dx_n, dL/dv_n, dL/d[k_stretch, k_bend, mu], z, eta).
 
@@ -763,7 +766,7 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None):
             Cm[base + e, col] = cv[e]
     K = sp.bmat([[H, Bm.tocsr()], [Cm.tocsr().T, None]], format="csc")
     rhs = np.concatenate([g[free].reshape(-1), np.zeros(nk)])
-    sol = spla.spsolve(K, rhs) if nk or nf3 else rhs
+    sol = spla.spsolve(K, rhs, permc_spec=permc_spec) if nk or nf3 else rhs
     sol = np.atleast_1d(sol)
     z = np.zeros((m, 3))
     z[free] = sol[:nf3].reshape(-1, 3)
@@ -809,9 +812,11 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None):
     return dx_n, dv_n, np.array([dks, dkb, dmu]), z, eta
 
 
-def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dtraj_x=None, hessians=None):
+def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dtraj_x=None, hessians=None,
+                     permc_spec=None):
     """Reverse pass over a rollout: returns (dL/dx0, dL/dv0, dL/d[k_s, k_b, mu]).
-    ``hessians[n]``, if given, is hessian_W at records[n].x_np1."""
+    ``hessians[n]``, if given, is hessian_W at records[n].x_np1; ``permc_spec`` as
+    for adjoint_step."""
     gx = np.asarray(dL_dx_final, dtype=np.float64).copy()
     gv = np.zeros_like(gx) if dL_dv_final is None else np.asarray(dL_dv_final, dtype=np.float64).copy()
     dth = np.zeros(3)
@@ -819,7 +824,8 @@ def rollout_gradient(model: Model, records, dL_dx_final, dL_dv_final=None, dL_dt
     for n in range(N - 1, -1, -1):
         if dL_dtraj_x is not None:
             gx = gx + dL_dtraj_x[n + 1]
-        gx, gv, d, _, _ = adjoint_step(model, records[n], gx, gv, None if hessians is None else hessians[n])
+        gx, gv, d, _, _ = adjoint_step(model, records[n], gx, gv, None if hessians is None else hessians[n],
+                                       permc_spec)
         dth += d
     if dL_dtraj_x is not None:
         gx = gx + dL_dtraj_x[0]

@@ -23,13 +23,13 @@ import ctypes
 
 import numpy as np
 
-from ._lib import (COMPLIANCE, DC_CAPSULE, DC_MAX_OBSTACLES, DC_PLANE, DC_SPHERE, LAYOUTS, STATUS_NAMES, DCError,
+from ._lib import (COMPLIANCE, DC_CAPSULE, DC_MAX_OBSTACLES, DC_MESH, DC_PLANE, DC_SPHERE, LAYOUTS, STATUS_NAMES, DCError,
                    check, dc_instance, dc_params, dc_request, dc_result, dc_server_config, dc_server_stats, dc_stats,
                    load)
 
 __all__ = ["Cloth", "ClothBatch", "Server", "rollout_fn", "batch_hbm_bytes", "fma_peak", "DCError", "load"]
 
-_KIND = {"plane": DC_PLANE, "sphere": DC_SPHERE, "capsule": DC_CAPSULE}
+_KIND = {"plane": DC_PLANE, "sphere": DC_SPHERE, "capsule": DC_CAPSULE, "mesh": DC_MESH}
 
 _PARAM_DEFAULTS = dict(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0, gravity=(0.0, -9.8, 0.0),
                        contact_margin=1e-6, n_pd_iters=20, obstacles=(), adj_tol=1e-10, adj_max_iters=2000,
@@ -42,7 +42,7 @@ def _torch():
     return torch
 
 
-def _obstacle_struct(ob, out):
+def _obstacle_struct(ob, out, mesh_ids=None):
     if isinstance(ob, dict):
         get = ob.get
     else:
@@ -51,7 +51,11 @@ def _obstacle_struct(ob, out):
     kind = get("kind")
     out.kind = _KIND[kind] if isinstance(kind, str) else int(kind)
     p = [0.0] * 7
-    if out.kind == DC_PLANE:
+    if out.kind == DC_MESH:
+        if mesh_ids is None or id(ob) not in mesh_ids:
+            raise ValueError("a mesh obstacle must be registered with the context (set_params does this)")
+        p[0] = float(mesh_ids[id(ob)])
+    elif out.kind == DC_PLANE:
         p[0:3] = list(get("normal"))
         p[3] = float(get("offset", 0.0))
     elif out.kind == DC_SPHERE:
@@ -65,7 +69,7 @@ def _obstacle_struct(ob, out):
         out.p[i] = float(p[i])
 
 
-def _make_params(lib, kw) -> dc_params:
+def _make_params(lib, kw, mesh_ids=None) -> dc_params:
     unknown = set(kw) - set(_PARAM_DEFAULTS)
     if unknown:
         raise TypeError(f"unknown parameter(s): {sorted(unknown)}")
@@ -92,7 +96,7 @@ def _make_params(lib, kw) -> dc_params:
         raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
     p.n_obstacles = len(obstacles)
     for i, ob in enumerate(obstacles):
-        _obstacle_struct(ob, p.obstacles[i])
+        _obstacle_struct(ob, p.obstacles[i], mesh_ids)
     q["obstacles"] = obstacles
     q["gravity"] = tuple(q["gravity"])
     return p, q
@@ -190,6 +194,27 @@ class _Context:
         check(self._lib.dc_global_solve(self._ctx, rhs.data_ptr(), out.data_ptr()), self._ctx)
         return out
 
+    def _register_meshes(self, obstacles):
+        """Registers the mesh obstacles of a parameter set with the context (once per
+        obstacle object) and returns {id(obstacle): mesh id}."""
+        if not hasattr(self, "_meshes"):
+            self._meshes = {}          # id(obstacle) -> (obstacle, mesh id); keeps the objects alive
+        for ob in obstacles:
+            kind = ob.get("kind") if isinstance(ob, dict) else getattr(ob, "kind", None)
+            if kind != "mesh" and kind != DC_MESH:
+                continue
+            if id(ob) in self._meshes:
+                continue
+            V = ob["vertices"] if isinstance(ob, dict) else ob.vertices
+            F = ob["triangles"] if isinstance(ob, dict) else ob.triangles
+            V = np.ascontiguousarray(np.asarray(V, dtype=np.float64).reshape(-1, 3))
+            F = np.ascontiguousarray(np.asarray(F, dtype=np.int32).reshape(-1, 3))
+            mid = ctypes.c_int32()
+            check(self._lib.dc_add_obstacle_mesh(self._ctx, V.shape[0], V.ctypes.data, F.shape[0], F.ctypes.data,
+                                                 ctypes.byref(mid)), self._ctx)
+            self._meshes[id(ob)] = (ob, mid.value)
+        return {k: v[1] for k, v in self._meshes.items()}
+
     def set_layout(self, layout):
         """Node arrays of later calls: "node_major" ((m, 3), the default) or
         "component_major" ((3, m): all x, then all y, then all z)."""
@@ -256,7 +281,7 @@ class Cloth(_Context):
         self.allow_nonconverged = False
 
     def set_params(self, **kw):
-        p, q = _make_params(self._lib, kw)
+        p, q = _make_params(self._lib, kw, self._register_meshes(kw.get("obstacles", ())))
         check(self._lib.dc_set_params(self._ctx, ctypes.byref(p)), self._ctx)
         self.params = q
         self._theta = (float(q["k_stretch"]), float(q["k_bend"]), float(q["mu"]))
@@ -308,7 +333,7 @@ class ClothBatch(_Context):
         if isinstance(params, dict):
             params = [params] * self.n_instances
         params = list(params)
-        built = [_make_params(self._lib, kw) for kw in params]
+        built = [_make_params(self._lib, kw, self._register_meshes(kw.get("obstacles", ()))) for kw in params]
         arr = (dc_params * len(built))(*[b[0] for b in built])
         check(self._lib.dc_set_params_batch(self._ctx, len(built), ctypes.addressof(arr)), self._ctx)
         self.params = [b[1] for b in built]

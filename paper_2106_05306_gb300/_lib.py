@@ -12,7 +12,7 @@ STATUS_NAMES = {0: "DC_OK", 1: "DC_ERR_INVALID", 2: "DC_ERR_CUDA", 3: "DC_ERR_NO
                 5: "DC_ERR_NONFINITE", 6: "DC_ERR_NONCONVERGED", 7: "DC_ERR_STATE", 8: "DC_ERR_TIMEOUT"}
 COMPLIANCE = {"rowsum": 0, "diag_pinv": 1, "diag_p": 2, "mass": 3}
 LAYOUTS = {"node_major": 0, "component_major": 1}
-DC_PLANE, DC_SPHERE, DC_CAPSULE = 0, 1, 2
+DC_PLANE, DC_SPHERE, DC_CAPSULE, DC_MESH = 0, 1, 2, 3
 DC_MAX_OBSTACLES = 16
 
 
@@ -102,6 +102,8 @@ SIGNATURES = {
     "dc_set_params_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "dc_set_graphs": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_set_layout": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_add_obstacle_mesh": (ctypes.c_int32, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P,
+                                              ctypes.POINTER(ctypes.c_int32)]),
     "dc_batch_hbm_bytes": (ctypes.c_int32, [ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
     "dc_autotune": (ctypes.c_int32, [_P]),
     "dc_step": (ctypes.c_int32, [_P, _P, _P, _P, _P]),

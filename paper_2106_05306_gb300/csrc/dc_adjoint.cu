@@ -17,6 +17,7 @@
 // for bending) and a fixed-order per-node gather.
 #include "dc_internal.h"
 #include "dc_adjoint.h"
+#include "dc_obstacle.cuh"
 #include "dc_polar.cuh"
 
 namespace {
@@ -455,6 +456,11 @@ __device__ void normal_jacobian(const DevParams& P, int o, const double x[3], do
     int kind = P.okind[o];
     if (kind == DC_PLANE) return;
     const double* p = P.oprm + 8 * o;
+    if (kind == DC_MESH) {
+        double nn[3];
+        dc_mesh_sdf(P.mesh, (int)p[0], (int)p[1], x, nn, Dn);
+        return;
+    }
     double c[3];
     double e[3] = {0, 0, 0};
     bool axis = false;

@@ -64,8 +64,18 @@ void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, int layout
 
 // Per-step multifrontal LDL^T preconditioner (dc_frontal.cu).
 size_t frontal_factor_smem(int max_f, int max_p);
+// a factorisation CTA with its panel scratch in global memory: shared bytes, and
+// global floats per CTA
+size_t frontal_factor_smem_small();
+long frontal_factor_gscr(int max_f, int max_p);
 size_t frontal_solve_smem(int max_f);
-cudaError_t frontal_configure(int max_f, int max_p);
+// Raises the shared-memory limits of the factorisation kernel (to factor_bytes)
+// and of the solve kernels (fronts of up to max_f unknowns).
+cudaError_t frontal_configure(size_t factor_bytes, int max_f);
+// Fronts per level that exceed the shared memory of one CTA: the global scratch
+// (floats) their level launch needs, the largest over the levels (0 if none),
+// and the largest shared-memory size of the other levels.
+void frontal_plan(const HostFronts& fr, size_t smem_limit, long* gscr_floats, size_t* factor_bytes);
 // Launch shape of the tree-scheduled solves for fronts of at most max_f
 // unknowns: the CTAs of each kernel that fit on the device at once, and the
 // dynamic shared memory.

@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "dc_ctx.h"
+#include "dc_obstacle.cuh"
 
 namespace {
 
@@ -97,6 +98,90 @@ void dc_default_params(dc_params* p) {
     p->n_obstacles = 0;
     p->contact_compliance = DC_COMPLIANCE_ROWSUM;
     p->adj_fallback = 1;
+}
+
+dc_status dc_add_obstacle_mesh(dc_ctx* c, int32_t nv, const double* verts, int32_t nt, const int32_t* tris,
+                               int32_t* mesh_id) {
+    if (!c) return DC_ERR_INVALID;
+    if (nv < 3 || nt < 4 || !verts || !tris || !mesh_id) {
+        c->err = "dc_add_obstacle_mesh: a closed mesh needs at least 4 triangles and 3 vertices";
+        return DC_ERR_INVALID;
+    }
+    for (long k = 0; k < 3L * nv; ++k)
+        if (!std::isfinite(verts[k])) {
+            c->err = "dc_add_obstacle_mesh: non-finite vertex";
+            return DC_ERR_INVALID;
+        }
+    // closed and consistently oriented: every directed edge once, with its reverse once
+    std::vector<std::pair<long long, int>> dir;
+    dir.reserve(3 * (size_t)nt);
+    for (int t = 0; t < nt; ++t)
+        for (int k = 0; k < 3; ++k) {
+            const int i = tris[3 * t + k], j = tris[3 * t + (k + 1) % 3];
+            if (i < 0 || i >= nv || j < 0 || j >= nv || i == j) {
+                c->err = "dc_add_obstacle_mesh: bad vertex index in triangle " + std::to_string(t);
+                return DC_ERR_INVALID;
+            }
+            dir.push_back({(long long)i * nv + j, t});
+        }
+    std::sort(dir.begin(), dir.end());
+    for (size_t q = 0; q < dir.size(); ++q) {
+        const long long e = dir[q].first, rev = (e % nv) * nv + e / nv;
+        const bool dup = (q > 0 && dir[q - 1].first == e) || (q + 1 < dir.size() && dir[q + 1].first == e);
+        const auto it = std::lower_bound(dir.begin(), dir.end(), std::make_pair(rev, -1));
+        if (dup || it == dir.end() || it->first != rev) {
+            c->err = "dc_add_obstacle_mesh: the mesh is not closed and consistently oriented";
+            return DC_ERR_INVALID;
+        }
+    }
+    auto V = [&](int i, int k) { return verts[3 * (long)i + k]; };
+    std::vector<double> fn(3 * (size_t)nt), vn(3 * (size_t)nv, 0.0);
+    for (int t = 0; t < nt; ++t) {
+        const int a = tris[3 * t], b = tris[3 * t + 1], cc = tris[3 * t + 2];
+        double u[3], w[3];
+        for (int k = 0; k < 3; ++k) { u[k] = V(b, k) - V(a, k); w[k] = V(cc, k) - V(a, k); }
+        double n[3] = {u[1] * w[2] - u[2] * w[1], u[2] * w[0] - u[0] * w[2], u[0] * w[1] - u[1] * w[0]};
+        const double nn = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(nn > 0.0)) {
+            c->err = "dc_add_obstacle_mesh: degenerate triangle " + std::to_string(t);
+            return DC_ERR_INVALID;
+        }
+        for (int k = 0; k < 3; ++k) fn[3 * t + k] = n[k] / nn;
+        // angle-weighted vertex pseudo-normals
+        const int idx[3] = {a, b, cc};
+        for (int q = 0; q < 3; ++q) {
+            const int i = idx[q], j = idx[(q + 1) % 3], l = idx[(q + 2) % 3];
+            double p1[3], p2[3];
+            for (int k = 0; k < 3; ++k) { p1[k] = V(j, k) - V(i, k); p2[k] = V(l, k) - V(i, k); }
+            const double cs = (p1[0] * p2[0] + p1[1] * p2[1] + p1[2] * p2[2]) /
+                              (std::sqrt(p1[0] * p1[0] + p1[1] * p1[1] + p1[2] * p1[2]) *
+                               std::sqrt(p2[0] * p2[0] + p2[1] * p2[1] + p2[2] * p2[2]));
+            const double ang = std::acos(std::max(-1.0, std::min(1.0, cs)));
+            for (int k = 0; k < 3; ++k) vn[3 * (size_t)i + k] += ang * fn[3 * t + k];
+        }
+    }
+    // the triangle on the other side of each directed edge
+    auto other = [&](int i, int j) {
+        const auto it = std::lower_bound(dir.begin(), dir.end(), std::make_pair((long long)j * nv + i, -1));
+        return it->second;
+    };
+    const int t0 = (int)(c->mesh_rec.size() / DC_MESH_REC);
+    for (int t = 0; t < nt; ++t) {
+        const int idx[3] = {tris[3 * t], tris[3 * t + 1], tris[3 * t + 2]};
+        for (int q = 0; q < 3; ++q) c->mesh_rec.push_back(d4{V(idx[q], 0), V(idx[q], 1), V(idx[q], 2), 0.0});
+        c->mesh_rec.push_back(d4{fn[3 * t], fn[3 * t + 1], fn[3 * t + 2], 0.0});
+        for (int q = 0; q < 3; ++q) {   // edges AB, BC, CA
+            const int u = other(idx[q], idx[(q + 1) % 3]);
+            c->mesh_rec.push_back(d4{fn[3 * t] + fn[3 * u], fn[3 * t + 1] + fn[3 * u + 1],
+                                     fn[3 * t + 2] + fn[3 * u + 2], 0.0});
+        }
+        for (int q = 0; q < 3; ++q)
+            c->mesh_rec.push_back(d4{vn[3 * (size_t)idx[q]], vn[3 * (size_t)idx[q] + 1], vn[3 * (size_t)idx[q] + 2], 0.0});
+    }
+    c->mesh_t0.push_back(t0);
+    c->mesh_nt.push_back(nt);
+    *mesh_id = (int32_t)c->mesh_t0.size() - 1;
+    return DC_OK;
 }
 
 dc_status dc_set_layout(dc_ctx* c, int32_t layout) {

@@ -146,6 +146,10 @@ struct dc_ctx {
     long long n_factorisations = 0;
     long long adj_batch_iters = 0;
     long long adj_fallbacks = 0, adj_fallback_iters = 0;
+    // obstacle meshes (dc_add_obstacle_mesh): triangle records, and per mesh its
+    // first record and triangle count
+    std::vector<d4> mesh_rec;      // DC_MESH_REC records per triangle (dc_obstacle.cuh)
+    std::vector<int> mesh_t0, mesh_nt;
 };
 
 #define CK(call)                                                                              \

@@ -686,11 +686,17 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int
     std::vector<double> rel;
     RET(gmres(c, it, rel));
     if (c->prm.adj_fallback) {
-        // instances stopped above adj_tol: a second pass from their iterate
+        // instances that hit the iteration cap, or stopped more than 100 x adj_tol
+        // above it: a second pass from their iterate.  A restart cycle that fails
+        // to halve the residual close to adj_tol has met the rounding floor of the
+        // FP64 operator (about eps cond(H)), which no preconditioner moves; those
+        // steps are accepted and counted as non-converged.
         std::vector<char> sel(c->B, 0);
         bool any = false;
+        const int maxit = std::max(1, c->prm.adj_max_iters);
         for (int i = 0; i < c->B; ++i)
-            if (!(rel[i] <= c->prm.adj_tol * 1.0000001)) sel[i] = 1, any = true;
+            if (!(rel[i] <= c->prm.adj_tol * 1.0000001) && (it[i] >= maxit || !(rel[i] <= 100.0 * c->prm.adj_tol)))
+                sel[i] = 1, any = true;
         if (any) {
             std::vector<int> it2;
             std::vector<double> rel2;

@@ -146,7 +146,13 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
 // solves its rows below the block against that inverse, in place; the trailing
 // matrix is updated with TM x TM register tiles whose operands come from the
 // transposed rows (128-bit shared-memory loads).
-__global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin, int mf) {
+// Levels whose fronts are too large for one CTA's shared memory pass gscr: then
+// the transposed rows and the scratch of the pivot-block inverse live in gscr
+// (gsz floats per CTA, 16-byte aligned, read through L1/L2) and shared memory
+// holds only the diagonal block, its inverse and the pivots.  The arithmetic and
+// its order are the same either way.
+__global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin, int mf, float* __restrict__ gscr,
+                                                     long gsz) {
     extern __shared__ __align__(16) float sm[];
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
@@ -156,7 +162,9 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
     float* Db = sm;                                  // [PB][LDS] diagonal block, row-major
     float* Xs = Db + PB * LDS;                       // [PB][LDS] diagonal-block inverse
     float* Dd = Xs + PB * LDS;                       // [PB] pivots of the panel
-    float* Lt = sm + (2 * PB * LDS + PB + 3) / 4 * 4;   // [PB][ldt] rows below the block, 16-byte aligned
+    float* const scr = gscr ? gscr + (long)blockIdx.x * gsz : sm;
+    // [PB][ldt] rows below the block, 16-byte aligned
+    float* Lt = gscr ? scr : sm + (2 * PB * LDS + PB + 3) / 4 * 4;
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
         const int c = fd.child[q];
         const float* Fc = fd.pool + fd.off[c];
@@ -335,7 +343,7 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
         const int i0 = I * PB, ib = min(PB, p - i0);
         const float* Bi = binv + (long)I * PB * PB;
         const int lr = i0 + 1;                         // odd row stride: no bank conflicts
-        float* Lrow = sm;                              // [PB][lr]: L[i0 + r][k], k < i0
+        float* Lrow = scr;                             // [PB][lr]: L[i0 + r][k], k < i0
         float* Xc = Lrow + (long)PB * lr;              // [PB][lr]: X[k][32J + c], k < i0
         float* T = Xc + (long)PB * lr;                 // [PB][PB] partial sums of one J
         for (long e = tid; e < (long)ib * i0; e += nt) {
@@ -677,15 +685,42 @@ size_t frontal_factor_smem(int max_f, int max_p) {
     return (panel > inverse ? panel : inverse) * sizeof(float) + 64;
 }
 
+// The same CTA with its panel and inverse scratch in global memory: the shared
+// part, and the global floats per CTA (a multiple of 4).
+size_t frontal_factor_smem_small() { return ((2 * (size_t)PB * LDS + PB + 3) / 4 * 4) * sizeof(float) + 64; }
+long frontal_factor_gscr(int max_f, int max_p) {
+    const long ldt = ((long)max_f + 7) / 8 * 8;
+    const long panel = (long)PB * ldt, inverse = 2L * PB * (max_p + 1) + (long)PB * PB;
+    return ((panel > inverse ? panel : inverse) + 3) / 4 * 4;
+}
+
 size_t frontal_solve_smem(int max_f) { return (2 * (size_t)max_f + GV_ROWS * GV_MAXG) * sizeof(float) + 64; }
 
 // The dynamic shared-memory limit of the front kernels is a per-function
 // attribute shared by every context of the process, so it only ever grows.
-cudaError_t frontal_configure(int max_f, int max_p) {
+void frontal_plan(const HostFronts& fr, size_t smem_limit, long* gscr_floats, size_t* factor_bytes) {
+    const int nl = (int)fr.lvl_ptr.size() - 1;
+    *gscr_floats = 0;
+    *factor_bytes = frontal_factor_smem_small();
+    for (int l = 0; l < nl; ++l) {
+        int mf = 0, mp = 0;
+        for (int q = fr.lvl_ptr[l]; q < fr.lvl_ptr[l + 1]; ++q) {
+            mf = std::max(mf, fr.f[fr.lvl_sn[q]]);
+            mp = std::max(mp, fr.p[fr.lvl_sn[q]]);
+        }
+        const size_t need = frontal_factor_smem(mf, mp);
+        if (need <= smem_limit)
+            *factor_bytes = std::max(*factor_bytes, need);
+        else
+            *gscr_floats = std::max(*gscr_floats, (long)(fr.lvl_ptr[l + 1] - fr.lvl_ptr[l]) * frontal_factor_gscr(mf, mp));
+    }
+}
+
+cudaError_t frontal_configure(size_t fb, int max_f) {
     static std::mutex mu;
     static size_t factor_bytes = 48 * 1024, solve_bytes = 48 * 1024;
     std::lock_guard<std::mutex> lock(mu);
-    const size_t fb = frontal_factor_smem(max_f, max_p), sb = frontal_solve_smem(max_f);
+    const size_t sb = frontal_solve_smem(max_f);
     if (fb > factor_bytes) {
         cudaError_t e = cudaFuncSetAttribute(k_front_level, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fb);
         if (e != cudaSuccess) return e;
@@ -728,6 +763,7 @@ static int factor_threads(int mf, int mp, int cnt, int sms) {
     if (mf <= 96) return 128;
     if (mf <= 192) return 256;
     if (cnt >= 4 * sms && 2 * frontal_factor_smem(mf, mp) <= 227 * 1024) return 256;
+    // (levels on the global-scratch path keep FT2 threads)
     return FT2;
 }
 static int solve_threads(int mf) { return mf <= 64 ? 128 : (mf <= 128 ? 256 : (mf <= 256 ? 512 : FT)); }
@@ -749,8 +785,13 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
             dc_note_launch();
             if (kt) kt->begin(DC_KT_FRONT);
             const int mp = lvl_maxp[l];
-            k_front_level<<<cnt, factor_threads(mf, mp, cnt, sms), frontal_factor_smem(mf, mp), s>>>(fd, lvl_ptr[l],
-                                                                                                  mf);
+            if (frontal_factor_smem(mf, mp) <= fd.smem_limit) {
+                k_front_level<<<cnt, factor_threads(mf, mp, cnt, sms), frontal_factor_smem(mf, mp), s>>>(
+                    fd, lvl_ptr[l], mf, nullptr, 0L);
+            } else {   // fronts too large for shared memory: panel scratch in fd.gscr
+                k_front_level<<<cnt, FT2, frontal_factor_smem_small(), s>>>(fd, lvl_ptr[l], mf, fd.gscr,
+                                                                          frontal_factor_gscr(mf, mp));
+            }
             if (kt) kt->end(DC_KT_FRONT);
         }
     }

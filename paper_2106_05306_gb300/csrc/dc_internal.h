@@ -228,8 +228,10 @@ struct DevParams {
     const int* node_inst;              // [m] instance of each internal node
     const double* node_mu;             // [m] friction coefficient of the node's instance
     const int* optr;                   // [n_inst + 1] obstacles of instance i: optr[i] .. optr[i+1]-1
-    const int* okind;                  // [n_obst] DC_PLANE / DC_SPHERE / DC_CAPSULE
-    const double* oprm;                // [n_obst][8] obstacle parameters (normalised plane)
+    const int* okind;                  // [n_obst] DC_PLANE / DC_SPHERE / DC_CAPSULE / DC_MESH
+    const double* oprm;                // [n_obst][8] obstacle parameters (normalised plane; for a
+                                       // mesh: first triangle record, triangle count)
+    const d4* mesh;                    // triangle records of the context's meshes (dc_obstacle.cuh)
 };
 
 // Instance layout inside a context.  Internal node order is: the free nodes of
@@ -346,4 +348,8 @@ struct FrontDev {
     unsigned long long* fault;         // sticky: set when a dependency wait gave up
     int tree_grid_f, tree_grid_b;      // host: CTAs of a tree-scheduled launch
     size_t tree_smem;                  // host: its dynamic shared memory
+    // factorisation levels whose CTAs need more than smem_limit bytes of shared
+    // memory keep their panel scratch in gscr instead (per CTA, per slot)
+    size_t smem_limit;                 // host
+    float* gscr;
 };

@@ -16,6 +16,7 @@
 #include <mutex>
 
 #include "dc_internal.h"
+#include "dc_obstacle.cuh"
 #include "dc_polar.cuh"
 #include "dc_wait.cuh"
 
@@ -54,6 +55,10 @@ __device__ __forceinline__ void st(d4* p, double x, double y, double z, double w
 __device__ double sdf(const DevParams& P, int o, double x, double y, double z, double* n) {
     const double* q = P.oprm + 8 * o;
     const int kind = P.okind[o];
+    if (kind == DC_MESH) {
+        const double xx[3] = {x, y, z};
+        return dc_mesh_sdf(P.mesh, (int)q[0], (int)q[1], xx, n, nullptr);
+    }
     if (kind == DC_PLANE) {
         if (n) { n[0] = q[0]; n[1] = q[1]; n[2] = q[2]; }
         return q[0] * x + q[1] * y + q[2] * z - q[3];

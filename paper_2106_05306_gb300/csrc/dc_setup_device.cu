@@ -53,6 +53,8 @@ std::string normalise_params(dc_params& q) {
         } else if (ob.kind == DC_CAPSULE) {
             double L = std::fabs(ob.p[3] - ob.p[0]) + std::fabs(ob.p[4] - ob.p[1]) + std::fabs(ob.p[5] - ob.p[2]);
             if (!(ob.p[6] > 0) || !(L > 0)) return "bad capsule";
+        } else if (ob.kind == DC_MESH) {
+            if (!(ob.p[0] >= 0) || ob.p[0] != std::floor(ob.p[0])) return "bad obstacle mesh id";
         } else {
             return "unknown obstacle kind";
         }
@@ -324,8 +326,19 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
         }
         for (int t = 0; t < in.T; ++t) pp.wt[in.to + t] = q[i].k_stretch * h.area[t];
         for (int o = 0; o < q[i].n_obstacles; ++o) {
-            pp.okind.push_back(q[i].obstacles[o].kind);
-            for (int k = 0; k < 8; ++k) pp.oprm.push_back(k < 7 ? q[i].obstacles[o].p[k] : 0.0);
+            const dc_obstacle& ob = q[i].obstacles[o];
+            pp.okind.push_back(ob.kind);
+            if (ob.kind == DC_MESH) {
+                const int id = (int)ob.p[0];
+                if (id >= (int)c->mesh_t0.size()) {
+                    c->err = "dc_set_params: obstacle mesh " + std::to_string(id) + " was not registered";
+                    return DC_ERR_INVALID;
+                }
+                for (int k = 0; k < 8; ++k)
+                    pp.oprm.push_back(k == 0 ? (double)c->mesh_t0[id] : (k == 1 ? (double)c->mesh_nt[id] : 0.0));
+            } else {
+                for (int k = 0; k < 8; ++k) pp.oprm.push_back(k < 7 ? ob.p[k] : 0.0);
+            }
         }
         pp.optr[i + 1] = (int)pp.okind.size();
         const int S_i = (i + 1 < B ? c->inst[i + 1].so : frm.S) - in.so;
@@ -356,6 +369,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     c->have_params = false;
     auto& P = c->factor_allocs;
     double *d_mass, *d_wt, *d_wb, *d_fval, *d_kval, *d_mu, *d_oprm, *d_ccon = nullptr;
+    d4* d_mesh = nullptr;
     int *d_fptr, *d_fidx, *d_kptr, *d_kidx, *d_long, *d_short, *d_optr, *d_okind;
     dc_status s;
     if ((s = upload(c, P, &d_mass, pp.mass)) || (s = upload(c, P, &d_wt, pp.wt)) || (s = upload(c, P, &d_wb, pp.wb)) ||
@@ -365,7 +379,8 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         (s = upload(c, P, &d_long, pp.long_rows)) || (s = upload(c, P, &d_short, pp.short_rows)) ||
         (s = upload(c, P, &d_mu, pp.node_mu)) || (s = upload(c, P, &d_optr, pp.optr)) ||
         (s = upload(c, P, &d_okind, pp.okind)) || (s = upload(c, P, &d_oprm, pp.oprm)) ||
-        (!pp.ccon.empty() && (s = upload(c, P, &d_ccon, pp.ccon))))
+        (!pp.ccon.empty() && (s = upload(c, P, &d_ccon, pp.ccon))) ||
+        (!c->mesh_rec.empty() && (s = upload(c, P, &d_mesh, c->mesh_rec))))
         return s;
     DevMesh& dm = c->dm;
     dm.n_long = (int)pp.long_rows.size();
@@ -388,6 +403,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     dp.compliance = pp.q[0].contact_compliance;
     dp.mass_split = dp.compliance == DC_COMPLIANCE_MASS ? 1 : 0;
     dp.ccon = d_ccon;
+    dp.mesh = d_mesh;
     dp.node_mu = d_mu;
     dp.optr = d_optr;
     dp.okind = d_okind;
@@ -396,17 +412,21 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
     int dev = 0, smem_optin = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    int max_p = 0;
-    for (int q = 0; q < frm.S; ++q) max_p = std::max(max_p, frm.p[q]);
-    if (frontal_factor_smem(frm.max_f, max_p) > (size_t)smem_optin) {
+    // levels whose fronts do not fit one CTA's shared memory factorise with a
+    // global scratch instead (the top fronts of large meshes)
+    long gscr_floats = 0;
+    size_t factor_bytes = 0;
+    frontal_plan(frm, (size_t)smem_optin, &gscr_floats, &factor_bytes);
+    if (frontal_solve_smem(frm.max_f) > (size_t)smem_optin) {
         c->err = "dc_set_params: the largest front (" + std::to_string(frm.max_f) +
-                 " unknowns) exceeds the shared memory of one CTA";
+                 " unknowns) exceeds the shared memory of one solve CTA";
         return DC_ERR_INVALID;
     }
-    CK(frontal_configure(frm.max_f, max_p));
+    CK(frontal_configure(factor_bytes, frm.max_f));
     free_pool(c, c->front_allocs);
     auto& F = c->front_allocs;
     FrontDev fd{};
+    fd.smem_limit = (size_t)smem_optin;
     fd.S = frm.S;
     fd.NP = (int)frm.pr_i.size();
     fd.max_f = frm.max_f;
@@ -494,6 +514,11 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         (s = dalloc(c, F, &c->fds[1].binv, (size_t)frm.binv_size)) ||
         (s = dalloc(c, F, &c->fds[1].linv, (size_t)frm.linv_size)))
         return s;
+    for (int k = 0; k < 2; ++k) {
+        c->fds[k].gscr = nullptr;
+        if (gscr_floats > 0 && (s = dalloc(c, F, &c->fds[k].gscr, (size_t)gscr_floats, false))) return s;
+    }
+    c->fdv = c->fds[0];
     // supernodal substitution of P (global_solver 1) on the same partition
     dm.solver = pp.q[0].global_solver;
     if (dm.solver == 1) {
@@ -670,10 +695,20 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     add(vbytes(r.child)); add(vbytes(r.cmap)); add(vbytes(r.lvl_sn)); add(vbytes(r.pr_i)); add(vbytes(r.pr_j));
     add(vbytes(r.pr_dst)); add(vbytes(r.pr_ld)); add(vbytes(r.pr_cptr)); add(vbytes(r.pr_code));
     add(vbytes(r.pr_coef)); add(vbytes(pp.tau)); add(vbytes(pp.tau));
+    long gscr_floats = 0;
+    size_t factor_bytes = 0;
+    int dev = 0, optin = 227 * 1024;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) {
+        cudaGetLastError();
+        optin = 227 * 1024;   // host-only estimate without a device: the GB300 limit
+    }
+    frontal_plan(r, (size_t)optin, &gscr_floats, &factor_bytes);
     for (int s = 0; s < 2; ++s) {
         add(4 * (size_t)r.pool_size);
         add(4 * (size_t)r.binv_size);
         add(4 * (size_t)r.linv_size);
+        if (gscr_floats > 0) add(4 * (size_t)gscr_floats);
     }
     add(4 * (size_t)r.acc_size); add(12 * MF); add(12 * MF); add(12 * MF);
     add(4 * (size_t)r.S); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));   // tree order, parents, tickets/flags

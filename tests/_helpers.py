@@ -62,3 +62,91 @@ def make_batch(scs, device="cuda", **over):
     batch = dc.ClothBatch([(s.rest_pos, s.tris, s.pins) for s in scs], device=device)
     batch.set_params([params_kw(s, **over) for s in scs])
     return batch
+
+
+# ---------------------------------------------------------------- oracle in worker processes
+# The large parity tests run the oracle along the GPU's own trajectory: every
+# step is recomputed from the GPU's (x_n, v_n), so the comparison isolates one
+# step (or one adjoint solve) at a time, and the independent steps and Hessian
+# assemblies run in a pool of spawned processes (the adjoint solves themselves
+# stay sequential, per cloth).
+
+_MODELS = {}
+
+
+def _scene(spec):
+    import scenes
+    kind, arg, over = spec
+    if kind == "batch":
+        sc = scenes.batch_instance(arg)
+    elif kind == "capsules":
+        sc = scenes.capsule_field(seed=arg)
+    else:
+        sc = scenes.draped_cloth()
+    return sc, over
+
+
+def _model(spec):
+    if spec not in _MODELS:
+        from oracle import cloth as oc
+        sc, over = _scene(spec)
+        _MODELS[spec] = oc.model_from_scene(sc, **dict(over))
+    return _MODELS[spec]
+
+
+def _job_step(job):
+    from oracle import cloth as oc
+    spec, x, v = job
+    return oc.step(_model(spec), x, v)
+
+
+def _job_hessian(job):
+    from oracle import cloth as oc
+    spec, x1 = job
+    return oc.hessian_W(_model(spec), x1)
+
+
+def _job_gradient(job):
+    from oracle import cloth as oc
+    spec, recs, hs, gx, permc = job
+    return oc.rollout_gradient(_model(spec), recs, gx, hessians=hs, permc_spec=permc)
+
+
+def oracle_along(specs, trajs, v0s, h, losses, pool, gradient=True, second_ordering=False):
+    """For each cloth i (oracle scene spec, GPU positions trajs[i] = x_0..x_N,
+    initial velocity v0s[i]): the oracle's step from every GPU state (velocities
+    recovered as (x_{n+1} - x_n)/h), and the oracle's direct adjoint of sum(xi * x_N)
+    along those steps (gradient=False: steps only).  Returns (records, gradients);
+    with second_ordering, gradients[i] is a pair: the adjoint with the sparse LU's
+    default column ordering and with another one (their difference is the
+    rounding the oracle's own KKT solves amplify)."""
+    jobs, index = [], []
+    for i, (spec, tr) in enumerate(zip(specs, trajs)):
+        v = np.asarray(v0s[i], dtype=np.float64)
+        for n in range(len(tr) - 1):
+            jobs.append((spec, tr[n], v))
+            index.append(i)
+            v = (tr[n + 1] - tr[n]) / h
+    out = pool.map(_job_step, jobs, chunksize=1)
+    recs = [[] for _ in specs]
+    for i, (_, _, rec) in zip(index, out):
+        recs[i].append(rec)
+    if not gradient:
+        return recs, None
+    hs = pool.map(_job_hessian, [(specs[i], r.x_np1) for i in range(len(specs)) for r in recs[i]], chunksize=1)
+    hper, k = [], 0
+    for i in range(len(specs)):
+        hper.append(hs[k:k + len(recs[i])])
+        k += len(recs[i])
+    orders = [None, "MMD_AT_PLUS_A"] if second_ordering else [None]
+    jobs = [(specs[i], recs[i], hper[i], losses[i], o) for i in range(len(specs)) for o in orders]
+    out = pool.map(_job_gradient, jobs, chunksize=1)
+    grads = [tuple(out[len(orders) * i:len(orders) * (i + 1)]) if second_ordering else out[i]
+             for i in range(len(specs))]
+    return recs, grads
+
+
+def spawn_pool():
+    import multiprocessing
+    import os
+    return multiprocessing.get_context("spawn").Pool(os.cpu_count() or 1)
