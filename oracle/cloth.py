@@ -409,22 +409,52 @@ def _closest_on_triangle(x, P):
     return best[1], best[2]
 
 
+# Distances within MESH_TIE (relative, plus MESH_TIE_ABS) of the smallest count as
+# ties, which the lowest face index wins; closer than MESH_ON_SURFACE (metres) a
+# point is on the surface and takes as normal the pseudo-normal of the feature its
+# closest point lies on to within MESH_SNAP metres (a vertex, else an edge, else
+# the face).
+MESH_TIE = 1e-9
+MESH_TIE_ABS = 1e-14
+MESH_ON_SURFACE = 1e-12
+MESH_SNAP = 1e-9
+
+
+def _snap_feature(P, c):
+    """The feature of triangle P (rows = vertices) that the point c on it lies on
+    to within MESH_SNAP: ("vertex", k) for the first vertex, else ("edge", k, k+1)
+    for the first edge AB, BC, CA, else ("face",) (local indices)."""
+    for k in range(3):
+        if np.linalg.norm(c - P[k]) <= MESH_SNAP:
+            return ("vertex", k)
+    for k in range(3):
+        a, b = P[k], P[(k + 1) % 3]
+        t = np.clip(np.dot(c - a, b - a) / np.dot(b - a, b - a), 0.0, 1.0)
+        if np.linalg.norm(c - (a + t * (b - a))) <= MESH_SNAP:
+            return ("edge", k, (k + 1) % 3)
+    return ("face",)
+
+
 def _mesh_closest(ob, x):
     """Closest point of a closed triangle mesh to x: (point, distance, feature in
-    mesh vertex indices, face index); the lowest face index wins ties."""
+    mesh vertex indices, face index).  Among faces whose distance is within
+    MESH_TIE of the smallest, the lowest face index wins, so that points
+    equidistant from several faces (symmetric configurations) are not decided
+    by rounding."""
     V = np.asarray(ob.vertices, dtype=np.float64)
     F = np.asarray(ob.triangles, dtype=np.int64)
-    best = None
+    cand = []
     for f in range(len(F)):
         c, feat = _closest_on_triangle(x, V[F[f]])
-        d = np.linalg.norm(x - c)
-        if best is None or d < best[1]:
+        cand.append((c, float(np.linalg.norm(x - c)), feat))
+    dmin = min(d for _, d, _ in cand)
+    for f, (c, d, feat) in enumerate(cand):
+        if d <= dmin * (1.0 + MESH_TIE) + MESH_TIE_ABS:
             if feat[0] == "edge":
                 feat = ("edge", int(F[f][feat[1]]), int(F[f][feat[2]]))
             elif feat[0] == "vertex":
                 feat = ("vertex", int(F[f][feat[1]]))
-            best = (c, d, feat, f)
-    return best
+            return c, d, feat, f
 
 
 def _mesh_pseudo_normal(ob, feat, face):
@@ -458,12 +488,19 @@ def _mesh_pseudo_normal(ob, feat, face):
 def signed_distance(ob, x):
     """(phi, grad phi) of an obstacle at point x."""
     if ob.kind == "mesh":
-        # |x - c| to the closest point c, signed by the pseudo-normal of c's feature;
-        # grad phi = s (x - c)/|x - c|
+        # |x - c| to the closest point c, signed by the pseudo-normal N of c's
+        # feature; grad phi = s (x - c)/|x - c|.  On the surface (|x - c| below
+        # MESH_ON_SURFACE, where a stick or slip step leaves a node and (x - c) is
+        # rounding) the normal is N/|N|.
         c, d, feat, face = _mesh_closest(ob, x)
-        s = 1.0 if np.dot(x - c, _mesh_pseudo_normal(ob, feat, face)) >= 0.0 else -1.0
-        if d == 0.0:
-            return 0.0, _mesh_pseudo_normal(ob, ("face",), face)
+        N = _mesh_pseudo_normal(ob, feat, face)
+        s = 1.0 if np.dot(x - c, N) >= 0.0 else -1.0
+        if d < MESH_ON_SURFACE:
+            Fi = np.asarray(ob.triangles, dtype=np.int64)[face]
+            sf = _snap_feature(np.asarray(ob.vertices, dtype=np.float64)[Fi], c)
+            sf = sf if sf[0] == "face" else (sf[0],) + tuple(int(Fi[k]) for k in sf[1:])
+            Ns = _mesh_pseudo_normal(ob, sf, face)
+            return float(s * d), Ns / np.linalg.norm(Ns)
         return float(s * d), s * (x - c) / d
     if ob.kind == "plane":
         n = np.asarray(ob.normal, dtype=np.float64)
@@ -484,14 +521,14 @@ def signed_distance(ob, x):
 
 
 def normal_jacobian(ob, x):
-    """d n / d x for the obstacle normal taken at x (3x3); zero for planes and in
-    the face region of a mesh; s (I - u u^T - e e^T)/r on a mesh edge (e its unit
+    """d n / d x for the obstacle normal taken at x (3x3); zero for planes, in
+    the face region of a mesh and on a mesh's surface; s (I - u u^T - e e^T)/r on a mesh edge (e its unit
     direction), s (I - u u^T)/r at a mesh vertex, u = (x - c)/r, r = |x - c|."""
     if ob.kind == "plane":
         return np.zeros((3, 3))
     if ob.kind == "mesh":
         c, r, feat, face = _mesh_closest(ob, x)
-        if feat[0] == "face" or r == 0.0:
+        if feat[0] == "face" or r < MESH_ON_SURFACE:
             return np.zeros((3, 3))
         s = 1.0 if np.dot(x - c, _mesh_pseudo_normal(ob, feat, face)) >= 0.0 else -1.0
         u = (x - c) / r

@@ -608,6 +608,35 @@ def test_mesh_normal_and_jacobian_match_differences():
     assert kinds == {"face", "edge", "vertex"}
 
 
+def test_mesh_normal_on_the_surface_and_exact_ties():
+    """The readings for points on a mesh's surface and for exact distance ties, on
+    the regular icosahedron (circumradius 0.5), whose symmetry fixes the answers:
+    on the surface (|x - c| below 1e-12 m: a vertex, an edge midpoint, a face
+    centre, each also displaced by 1e-14 m) the normal is the feature's
+    pseudo-normal, which the 5-fold, 2-fold and 3-fold symmetry makes radial; at
+    the centre all 20 faces tie at the inradius R sqrt((5 + 2 sqrt 5)/15), and the
+    lowest face index wins (also 1e-13 m off centre, inside the tie band)."""
+    R = 0.5
+    ob = scenes.mesh_sphere((0.0, 0.0, 0.0), R, 0)
+    V, F = np.asarray(ob.vertices), np.asarray(ob.triangles)
+    rng = np.random.default_rng(3)
+    pts = [V[0], V[7], 0.5 * (V[F[3][0]] + V[F[3][1]]), 0.5 * (V[1] + V[8]), V[F[5]].mean(axis=0)]
+    for p in pts:
+        for x in (p, p + 1e-14 * rng.standard_normal(3)):
+            ph, n = oc.signed_distance(ob, x)
+            assert abs(ph) < 1e-13
+            np.testing.assert_allclose(n, p / np.linalg.norm(p), atol=1e-12)
+            assert np.all(oc.normal_jacobian(ob, x) == 0.0)
+    a, b, c = V[F[0]]
+    n0 = np.cross(b - a, c - a)
+    n0 /= np.linalg.norm(n0)
+    for x in (np.zeros(3), 1e-13 * rng.standard_normal(3)):
+        ph, n = oc.signed_distance(ob, x)
+        assert abs(ph + R * np.sqrt((5 + 2 * np.sqrt(5)) / 15)) < 1e-12
+        np.testing.assert_allclose(n, n0, atol=1e-11)
+        assert oc._mesh_closest(ob, x)[3] == 0
+
+
 def test_fine_mesh_sphere_approaches_the_analytic_sphere():
     """A subdivided icosphere's phi is within its sagitta of the analytic sphere's
     (vertices lie on the sphere, faces at most r (1 - cos(theta/2)) inside it, theta
@@ -631,9 +660,11 @@ def test_fine_mesh_sphere_approaches_the_analytic_sphere():
 
 def test_continuity_study_analytic_vs_triangulated_sphere():
     """Sec. "Continuity and Smoothness": sweep where a cloth lands on a sphere; the
-    gradient of its final mean x w.r.t. the landing offset changes by small steps
-    over the analytic sphere and by large jumps over a coarse triangulation of it
-    (normals jump across edges, curvature concentrates at edges and vertices)."""
+    gradient of its final mean x w.r.t. the landing offset varies little over the
+    analytic sphere and by large jumps over a coarse triangulation of it (normals
+    jump across edges, curvature concentrates at edges and vertices): the total
+    variation of the gradient over the sweep is ten times larger (both sweeps also
+    jump where contacts begin at another step)."""
     offsets = np.linspace(0.0, 0.12, 13)
 
     def sweep(sub):
@@ -648,4 +679,4 @@ def test_continuity_study_analytic_vs_triangulated_sphere():
             g.append(gx[:, 0].sum())
         return np.abs(np.diff(np.array(g)))
     js, jm = sweep(-1), sweep(1)
-    assert np.median(jm) > 10.0 * np.median(js)
+    assert jm.sum() > 10.0 * js.sum()
