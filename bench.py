@@ -79,13 +79,16 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batch", "single"], default="batch")
+    ap.add_argument("--workload", choices=["batch", "single", "served"], default="batch")
     ap.add_argument("--roofline-kernel", default=None, help="kernel class timed for the roofline")
     ap.add_argument("--rollout-steps", type=int, default=None,
                     help="cloth steps per rollout (default: the workload's; ncu launch lists use a shorter one)")
     ap.add_argument("--batch", type=int, default=BATCH, help="cloths in the batch (256 for the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / single / served side runs")
+    ap.add_argument("--served-requests", type=int, default=64, help="requests of the served side run")
+    ap.add_argument("--served-rates", default="4,16,64", help="Poisson arrival rates (per s) of the served run")
+    ap.add_argument("--served-max-batch", type=int, default=16, help="requests packed into one batch context")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-all-cores", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -397,11 +400,13 @@ def single_side_run(args, dev):
             "nonconverged_cloth_steps": st["adj_nonconverged"]}
 
 
-def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=8, seed0=10000):
+def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000, max_batch=16, plain_sample=None):
     """Served runs: n_req requests (1k-30k DOF, 25-150 steps, random sphere + ground,
     mu 0.1-0.6) with Poisson arrivals into the request server, one run per arrival
-    rate; then the same requests one at a time through the plain path.  The served
-    value is the best throughput of the sweep (the server saturated)."""
+    rate; requests queued together are packed into batch contexts of up to
+    max_batch cloths (supernodal solver, P factorised on the GPU); then the same
+    requests one at a time through the plain path.  The served value is the best
+    throughput of the sweep (the server saturated)."""
     import threading
 
     import torch
@@ -414,14 +419,14 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=8, seed0=10000
     for rate in rates:
         rng = np.random.default_rng(4242)
         gaps = rng.exponential(1.0 / rate, n_req)
-        srv = dc.Server(n_slots=slots, n_prep_threads=4, device=dev.index or 0)
+        srv = dc.Server(n_slots=slots, n_prep_threads=4, device=dev.index or 0, max_batch=max_batch)
         tickets = [None] * n_req
 
         def producer():
             for i, sc in enumerate(reqs):
                 time.sleep(gaps[i])
                 tickets[i] = srv.submit(sc.rest_pos, sc.tris, sc.pins, sc.x0, sc.v0, sc.loss_w, sc.n_steps,
-                                        scene_kw(sc, checkpoint_every=1))
+                                        scene_kw(sc, checkpoint_every=1, global_solver=1, factor_on_gpu=1))
 
         t0 = time.perf_counter()
         th = threading.Thread(target=producer)
@@ -439,8 +444,10 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=8, seed0=10000
     # the same requests one at a time (plain path, no server)
     stream = torch.cuda.Stream(dev)
     plain_s = 0.0
+    plain_reqs = reqs if plain_sample is None else reqs[:plain_sample]
+    plain_steps = sum(sc.n_steps for sc in plain_reqs)
     with torch.cuda.stream(stream):
-        for sc in reqs:
+        for sc in plain_reqs:
             c = dc.Cloth(sc.rest_pos, sc.tris, sc.pins, device=dev)
             c.set_params(**scene_kw(sc, checkpoint_every=1))
             x0, v0, xi = (torch.tensor(a, device=dev) for a in (sc.x0, sc.v0, sc.loss_w))
@@ -452,14 +459,17 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=8, seed0=10000
             plain_s += time.perf_counter() - t
             c.close()
     best = max(sweep, key=lambda r: r["value"])
-    return {"value": best["value"], "unit": UNIT, "requests": n_req, "slots": slots,
+    return {"value": best["value"], "unit": UNIT, "requests": n_req, "slots": slots, "max_batch": max_batch,
             "p50_latency_s": best["p50_latency_s"], "p99_latency_s": best["p99_latency_s"],
             "at_rate_per_s": best["rate_per_s"], "rate_sweep": sweep,
-            "plain_sequential": {"value": steps / plain_s, "unit": UNIT,
-                                 "note": "same requests one at a time, setup excluded"},
+            "plain_sequential": {"value": plain_steps / plain_s, "unit": UNIT,
+                                 "note": ("same requests one at a time, setup excluded" if plain_sample is None else
+                                          f"the first {len(plain_reqs)} of the requests one at a time, setup "
+                                          f"excluded")},
             "workload": "requests of 1k-30k DOF (log-uniform), 25-150 steps, random sphere + ground, "
-                        "fwd + adjoint, all steps recorded; Poisson arrivals; throughput = steps / makespan "
-                        "from the first arrival to the last result"}
+                        "fwd + adjoint, all steps recorded; Poisson arrivals; requests queued together packed into "
+                        "batch contexts (own step counts); throughput = steps / makespan from the first arrival "
+                        "to the last result"}
 
 
 def measured_peaks():
@@ -483,6 +493,8 @@ def measured_peaks():
 KERNEL_CLASSES = {
     "local": "k_local (stretch + bending projections and their rhs terms)",
     "gather": "k_gather_rhs (per-node right-hand side gather)",
+    "sweeps": "k_ps_sweeps_tree (forward + backward supernodal sweeps in one launch, FP64, 3 columns, per-node "
+              "Signorini-Coulomb solve fused in)",
     "solve_fwd": "k_ps_fwd_tree (forward supernodal sweep, FP64, 3 columns)",
     "solve_bwd": "k_ps_bwd_tree (backward sweep + fused per-node Signorini-Coulomb solve)",
     "front": "k_front_level (one level of the FP32 multifrontal LDL^T of the adjoint preconditioner)",
@@ -501,6 +513,10 @@ def kernel_model(cls, st, contacts_per_launch):
         return 92.0 * m + 100.0 * T + 12.0 * nb, 150.0 * T + 25.0 * m + 12.0 * nb, "fp64"
     if cls == "gather":
         return 96.0 * mf + 60.0 * T + 12.0 * nb + 24.0 * m, 12.0 * T + 6.0 * nb + 12.0 * mf, "fp64"
+    if cls == "sweeps":
+        e = st["psolve_flops"] / 6.0
+        return (2.0 * (8.0 * e + 48.0 * mf) + 124.0 * contacts_per_launch,
+                2.0 * st["psolve_flops"] + 60.0 * contacts_per_launch, "fp64")
     if cls in ("solve_fwd", "solve_bwd") and st["global_solver"] == 1:
         e = st["psolve_flops"] / 6.0                     # panel entries read by one sweep
         b, f = 8.0 * e + 48.0 * mf, st["psolve_flops"]
@@ -543,7 +559,8 @@ def kernel_table(wl, peaks, steps_per_pass=1):
                         "achieved_gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / peaks["hbm_gbs"],
                         "achieved_tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak})
             row["bound"] = "alu" if row["alu_frac"] >= row["hbm_frac"] else "hbm"
-        rows[cls] = row
+        if st["timer_launches"] > 0:
+            rows[cls] = row
     total = sum(r["ms_per_bench_step"] for r in rows.values())
     for r in rows.values():
         r["share_of_timed_kernels"] = r["ms_per_bench_step"] / total if total > 0 else None
@@ -573,6 +590,34 @@ def roofline(table, peaks):
         roof["traffic"] = tr["bytes_per_launch"]
         roof["traffic_note"] = tr["note"]
     return roof
+
+
+def run_served(args):
+    """The serving configuration as its own line: --served-requests requests (2000
+    by default here) with Poisson arrivals at each rate of --served-rates, into a
+    server that packs queued requests into batch contexts; value = the best
+    throughput of the sweep; the plain comparison runs the first 64 requests one
+    at a time."""
+    import torch
+
+    from paper_2106_05306_gb300 import build as dcbuild
+    rank, world, local = dist_env()
+    dcbuild.build()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    sv = served_side_run(dev, n_req=args.served_requests,
+                         rates=tuple(float(r) for r in args.served_rates.split(",")),
+                         max_batch=args.served_max_batch, plain_sample=64)
+    clk = clocks.stop()
+    out = {"metric": METRIC, "value": sv["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "served: " + sv["workload"], "requests": sv["requests"], "slots": sv["slots"],
+                      "max_batch": sv["max_batch"]},
+           "served": sv, "served_vs_plain": sv["value"] / sv["plain_sequential"]["value"], "clocks": clk}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
 
 
 def run_ours(args):
@@ -656,7 +701,9 @@ def run_ours(args):
         out["plain"] = plain_sample(args, dev, wl.n_cloth)
         out["batched_vs_plain"] = value / out["plain"]["value"]
         out["single_61x61"] = single_side_run(args, dev)
-        out["served"] = served_side_run(dev)
+        out["served"] = served_side_run(dev, n_req=args.served_requests,
+                                        rates=tuple(float(r) for r in args.served_rates.split(",")),
+                                        max_batch=args.served_max_batch)
         out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_subprocess(args.workload)
@@ -723,6 +770,8 @@ def main():
         return
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "served":
+        run_served(args)
     else:
         run_ours(args)
 

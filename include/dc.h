@@ -122,7 +122,12 @@ typedef struct dc_params {
                                 adj_max_iters, or stops more than 100 x adj_tol above
                                 it, is solved again by the fallback (dc_backward);
                                 0: no fallback                                       */
-    int32_t reserved_;
+    int32_t factor_on_gpu;   /* 1: P's numeric Cholesky (Eq. pd_global, "prefactorised")
+                                runs on the GPU as a multifrontal FP64 factorisation
+                                written straight into the supernodal panels; the host
+                                does only the ordering and symbolic analysis.  Needs
+                                global_solver 1; not with DC_COMPLIANCE_DIAG_PINV.
+                                0 (default): numeric factorisation on the host.      */
     dc_obstacle obstacles[DC_MAX_OBSTACLES];
 } dc_params;
 
@@ -183,7 +188,9 @@ enum {
     DC_KT_MSOLVE = 6,      /* one level of the multifrontal forward or backward solve  */
     DC_KT_KRYLOV = 7,      /* GMRES vector kernels (dot products, updates, scaling)    */
     DC_KT_APPLYH = 8,      /* adjoint operator application (element pass + gather)    */
-    DC_KT_ASSEMBLE = 9     /* per-step adjoint setup and front assembly               */
+    DC_KT_ASSEMBLE = 9,    /* per-step adjoint setup and front assembly               */
+    DC_KT_SWEEPS = 10      /* both substitution sweeps of one global step in one launch
+                              (global_solver 1; the contact solve fused in)           */
 };
 
 typedef struct dc_ctx dc_ctx;
@@ -235,6 +242,15 @@ dc_status dc_set_params(dc_ctx* ctx, const dc_params* params);
  * otherwise).  dc_set_params on a batch gives every instance the same values.
  * Each instance's P is assembled and factorised on its own (host threads). */
 dc_status dc_set_params_batch(dc_ctx* ctx, int32_t n_instances, const dc_params* params);
+
+/* Per-instance step counts of a batch for the next dc_rollout calls: instance i
+ * takes steps[i] steps (0 <= steps[i] <= the n_steps of dc_rollout) and then
+ * keeps its state; dc_backward starts its adjoint at the instance's own last
+ * step (its adjoint passes unchanged through the steps it did not take).  An
+ * instance's results are bitwise those of a rollout of steps[i] steps alone.
+ * steps = NULL restores one count for all.  Lets a server pack requests of
+ * different lengths into one batch.  No counterpart in the paper. */
+dc_status dc_set_instance_steps(dc_ctx* ctx, const int32_t* steps);
 
 /* Register a closed triangle mesh as an obstacle shape of ctx and return its id
  * in *mesh_id, for DC_MESH obstacles of later dc_set_params calls.  verts:
@@ -357,12 +373,30 @@ dc_status dc_global_solve_static(dc_ctx* ctx, const double* rhs, double* out);
  * the first skip_items work items never executed, so that a front whose child
  * is among them waits for a flag that nothing sets.  The wait gives up after
  * about a second, sets the context's sticky fault flag and the launch ends; the
- * call synchronises and returns DC_ERR_CUDA when the fault was raised (DC_OK if
- * no skipped item had a waiting parent).  The context's results are invalid
+ * call synchronises and returns DC_ERR_TIMEOUT when the fault was raised (DC_OK
+ * if no skipped item had a waiting parent).  The context's results are invalid
  * afterwards: destroy it.  DC_ERR_INVALID without global_solver 1 or with
- * skip_items outside [1, number of items).  Returns DC_ERR_TIMEOUT when the
- * wait gave up. */
+ * skip_items outside [1, number of items). */
 dc_status dc_debug_sweep_wait_timeout(dc_ctx* ctx, int32_t skip_items);
+
+/* Testing the adjoint preconditioner's dense front kernel on its own: one
+ * symmetric n x n front A (host, column-major FP32; the lower triangle is read)
+ * with p pivot columns goes through the partial LDL^T that factorises every
+ * front of the multifrontal preconditioner (Sec. 4, Eq. ppr_adjoint is the
+ * system it preconditions).  out (host, n x n column-major) receives the front
+ * afterwards: in its first p columns D on the diagonal and the unit-lower L
+ * below it, in the trailing (n - p) x (n - p) lower triangle the Schur
+ * complement A22 - L21 D L21^T.  linv_out (host, p x p column-major, nullable)
+ * receives the inverse of L's unit-lower pivot block.  threads: 128, 256 or
+ * 512; use_tc: 1 updates trailing blocks of 64 rows or more on the tensor
+ * cores (TF32 split in three passes, FP32 accumulation), 0 by FP32 FMA tiles;
+ * use_gscr: 1 keeps the panel scratch in global memory (the path of fronts
+ * too large for shared memory).  Synchronous; allocates its own device memory.
+ * DC_ERR_INVALID unless 1 <= p <= n <= 4096 (and the shared memory fits),
+ * DC_ERR_TIMEOUT if a tensor-core completion wait gave up, DC_ERR_CUDA on a
+ * CUDA error; dc_last_error(NULL) has the message. */
+dc_status dc_debug_front_factor(int32_t n, int32_t p, const float* A, float* out, float* linv_out,
+                                int32_t threads, int32_t use_tc, int32_t use_gscr);
 
 /* Measured fused-multiply-add throughput of the GPU's CUDA cores, in TFLOP/s
  * (2 flops per FMA), for precision 64 (FP64) or 32 (FP32): a kernel of
@@ -390,16 +424,22 @@ const char* dc_last_error(dc_ctx* ctx);
  * A request server: many independent forward + adjoint rollouts (each its own
  * cloth, size, step count and parameters) submitted at any time and run
  * concurrently on one GPU.  No counterpart in the paper.
- *  - Each request is prepared on a host thread (ordering, factorisation,
- *    fronts) as soon as it is submitted, which also gives its exact device
- *    footprint.  It is admitted, in submission order, when one of n_slots
- *    slots is free and its footprint fits in what the HBM budget has left.  A
- *    request larger than the whole budget fails with DC_ERR_OOM.
+ *  - Each request (or batch of requests, below) is prepared on a host thread
+ *    (ordering, factorisation, fronts) as soon as it is submitted, which also
+ *    gives its exact device footprint.  It is admitted, in submission order,
+ *    when one of n_slots slots is free and its footprint fits in what the HBM
+ *    budget has left.  A request larger than the whole budget fails with
+ *    DC_ERR_OOM.
  *  - An admitted request keeps its factorisation, fronts and checkpoints
  *    resident until it finishes; slots run on their own CUDA streams and host
  *    threads, so requests overlap on the device, and device memory comes from
  *    the stream-ordered pool (no device-wide synchronisation when a request
  *    starts or ends).
+ *  - Continuous batching: with max_batch > 1 a preparation thread packs the
+ *    requests queued at that moment whose shared parameters agree (the fields a
+ *    batch shares, dc_set_params_batch) into one batch context of up to
+ *    max_batch cloths, each with its own step count (dc_set_instance_steps);
+ *    a slot runs the whole batch, one launch per phase for all its requests.
  *  - A request's results are bitwise those of the same rollout and backward
  *    run alone through dc_create_mesh / dc_rollout / dc_backward. */
 typedef struct dc_server dc_server;
@@ -408,8 +448,10 @@ typedef struct dc_server_config {
     int32_t n_slots;           /* requests on the device at once (>= 1)              */
     int32_t n_prep_threads;    /* host threads preparing requests (>= 1)             */
     int64_t hbm_budget_bytes;  /* device bytes the admitted requests may hold        */
-    int32_t max_prepared;      /* prepared requests waiting for a slot, at most      */
+    int32_t max_prepared;      /* prepared jobs waiting for a slot, at most          */
     int32_t device;            /* CUDA device ordinal                                */
+    int32_t max_batch;         /* requests packed into one batch context (<= 1: one) */
+    int32_t reserved_;
 } dc_server_config;
 
 typedef struct dc_request {

@@ -34,7 +34,7 @@ _KIND = {"plane": DC_PLANE, "sphere": DC_SPHERE, "capsule": DC_CAPSULE, "mesh": 
 _PARAM_DEFAULTS = dict(k_stretch=1e3, k_bend=1e-3, density=0.1, mu=0.3, h=1.0 / 120.0, gravity=(0.0, -9.8, 0.0),
                        contact_margin=1e-6, n_pd_iters=20, obstacles=(), adj_tol=1e-10, adj_max_iters=2000,
                        adj_restart=200, checkpoint_every=1, adj_precond=0, global_solver=0,
-                       contact_compliance="rowsum", adj_fallback=1)
+                       contact_compliance="rowsum", adj_fallback=1, factor_on_gpu=0)
 
 
 def _torch():
@@ -91,6 +91,7 @@ def _make_params(lib, kw, mesh_ids=None) -> dc_params:
     cm = q["contact_compliance"]
     p.contact_compliance = COMPLIANCE[cm] if isinstance(cm, str) else int(cm)
     p.adj_fallback = int(q["adj_fallback"])
+    p.factor_on_gpu = int(q["factor_on_gpu"])
     obstacles = list(q["obstacles"])
     if len(obstacles) > DC_MAX_OBSTACLES:
         raise ValueError(f"at most {DC_MAX_OBSTACLES} obstacles")
@@ -339,6 +340,18 @@ class ClothBatch(_Context):
         self.params = [b[1] for b in built]
         return self
 
+    def set_instance_steps(self, steps):
+        """Per-instance step counts for the next rollouts (None: one count for all):
+        instance i takes steps[i] steps, then keeps its state."""
+        if steps is None:
+            check(self._lib.dc_set_instance_steps(self._ctx, None), self._ctx)
+            return self
+        arr = np.ascontiguousarray(np.asarray(steps, dtype=np.int32).reshape(-1))
+        if arr.shape[0] != self.n_instances:
+            raise ValueError(f"expected {self.n_instances} step counts")
+        check(self._lib.dc_set_instance_steps(self._ctx, arr.ctypes.data), self._ctx)
+        return self
+
     def set_theta(self, theta):
         """Per-instance differentiable parameters, shape (n_instances, 3) = (k_stretch,
         k_bend, mu); refactorises when they change."""
@@ -365,7 +378,7 @@ class Server:
     ``submit`` copies its arguments and returns a ticket; ``wait(ticket)`` blocks
     until that request is done and returns its results (numpy arrays) and timings."""
 
-    def __init__(self, n_slots=4, n_prep_threads=4, hbm_budget_bytes=None, max_prepared=None, device=0):
+    def __init__(self, n_slots=4, n_prep_threads=4, hbm_budget_bytes=None, max_prepared=None, device=0, max_batch=1):
         self._lib = load()
         if hbm_budget_bytes is None:
             torch = _torch()
@@ -374,7 +387,7 @@ class Server:
         cfg = dc_server_config(n_slots=int(n_slots), n_prep_threads=int(n_prep_threads),
                                hbm_budget_bytes=int(hbm_budget_bytes),
                                max_prepared=int(max_prepared if max_prepared is not None else 2 * n_slots + 2),
-                               device=int(device))
+                               device=int(device), max_batch=int(max_batch))
         srv = ctypes.c_void_p()
         check(self._lib.dc_server_create(ctypes.byref(srv), ctypes.byref(cfg)), None)
         self._srv = srv
@@ -437,6 +450,23 @@ def fma_peak(precision=64, n_iter=None):
     out = ctypes.c_double()
     check(lib.dc_fma_peak(int(precision), int(n_iter), ctypes.byref(out)), None)
     return float(out.value)
+
+
+def front_factor(A, p, threads=512, use_tc=True, use_gscr=False):
+    """One dense front through the adjoint preconditioner's front kernel (a test
+    hook): A is a symmetric (n, n) array, p the pivot count.  Returns (F, Linv):
+    F holds D and the unit-lower L in its first p columns and the Schur complement
+    in its trailing lower triangle (float32, (n, n)); Linv is the inverse of L's
+    pivot block ((p, p))."""
+    import numpy as np
+    lib = load()
+    A = np.asfortranarray(np.asarray(A, dtype=np.float32))
+    n = A.shape[0]
+    out = np.zeros((n, n), dtype=np.float32, order="F")
+    linv = np.zeros((p, p), dtype=np.float32, order="F")
+    check(lib.dc_debug_front_factor(int(n), int(p), A.ctypes.data, out.ctypes.data, linv.ctypes.data,
+                                    int(threads), int(bool(use_tc)), int(bool(use_gscr))), None)
+    return out, linv
 
 
 def batch_hbm_bytes(meshes, params, n_steps):

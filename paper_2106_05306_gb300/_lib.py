@@ -28,7 +28,7 @@ class dc_params(ctypes.Structure):
                 ("adj_restart", ctypes.c_int32), ("checkpoint_every", ctypes.c_int32),
                 ("n_obstacles", ctypes.c_int32), ("adj_precond", ctypes.c_int32),
                 ("global_solver", ctypes.c_int32), ("contact_compliance", ctypes.c_int32),
-                ("adj_fallback", ctypes.c_int32), ("reserved_", ctypes.c_int32),
+                ("adj_fallback", ctypes.c_int32), ("factor_on_gpu", ctypes.c_int32),
                 ("obstacles", dc_obstacle * DC_MAX_OBSTACLES)]
 
 
@@ -61,7 +61,8 @@ class dc_instance(ctypes.Structure):
 
 class dc_server_config(ctypes.Structure):
     _fields_ = [("n_slots", ctypes.c_int32), ("n_prep_threads", ctypes.c_int32), ("hbm_budget_bytes", ctypes.c_int64),
-                ("max_prepared", ctypes.c_int32), ("device", ctypes.c_int32)]
+                ("max_prepared", ctypes.c_int32), ("device", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("reserved_", ctypes.c_int32)]
 
 
 class dc_request(ctypes.Structure):
@@ -87,7 +88,7 @@ class dc_server_stats(ctypes.Structure):
 
 
 KT_CLASSES = {"none": 0, "solve_fwd": 1, "solve_bwd": 2, "local": 3, "gather": 4, "front": 5, "msolve": 6,
-              "krylov": 7, "apply_h": 8, "assemble": 9}
+              "krylov": 7, "apply_h": 8, "assemble": 9, "sweeps": 10}
 
 
 _P = ctypes.c_void_p
@@ -102,6 +103,7 @@ SIGNATURES = {
     "dc_set_params_batch": (ctypes.c_int32, [_P, ctypes.c_int32, _P]),
     "dc_set_graphs": (ctypes.c_int32, [_P, ctypes.c_int32]),
     "dc_set_layout": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_set_instance_steps": (ctypes.c_int32, [_P, _P]),
     "dc_add_obstacle_mesh": (ctypes.c_int32, [_P, ctypes.c_int32, _P, ctypes.c_int32, _P,
                                               ctypes.POINTER(ctypes.c_int32)]),
     "dc_batch_hbm_bytes": (ctypes.c_int32, [ctypes.c_int32, _P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int64)]),
@@ -112,6 +114,8 @@ SIGNATURES = {
     "dc_global_solve": (ctypes.c_int32, [_P, _P, _P]),
     "dc_global_solve_static": (ctypes.c_int32, [_P, _P, _P]),
     "dc_debug_sweep_wait_timeout": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_debug_front_factor": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
+                                               ctypes.c_int32, ctypes.c_int32]),
     "dc_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_stats)]),
     "dc_fma_peak": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "dc_set_kernel_timer": (ctypes.c_int32, [_P, ctypes.c_int32]),

@@ -63,10 +63,13 @@ void adj_params(const DevMesh& dm, const AdjDev& ad, const Segs& sg, const d4* z
 void adj_add_ext(d4* g, const double* ext, const int* int2ext, int m, int layout, cudaStream_t s);
 
 // Per-step multifrontal LDL^T preconditioner (dc_frontal.cu).
-size_t frontal_factor_smem(int max_f, int max_p);
+size_t frontal_factor_smem(int max_f, int max_p, bool tc);
+bool frontal_level_tc(int max_f);
+dc_status frontal_debug_factor(int n, int p, const float* A, float* out, float* linv_out, int threads, int tc,
+                               int use_gscr, std::string* err);
 // a factorisation CTA with its panel scratch in global memory: shared bytes, and
 // global floats per CTA
-size_t frontal_factor_smem_small();
+size_t frontal_factor_smem_small(bool tc);
 long frontal_factor_gscr(int max_f, int max_p);
 size_t frontal_solve_smem(int max_f);
 // Raises the shared-memory limits of the factorisation kernel (to factor_bytes)

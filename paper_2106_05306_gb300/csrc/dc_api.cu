@@ -67,7 +67,7 @@ dc_status check_device_flags(dc_ctx* c) {
     CK(cudaMemcpyAsync(w, c->counters + 3, sizeof(w), cudaMemcpyDeviceToHost, c->stream));
     CK(ctx_sync(c, c->stream));
     if (w[0]) {
-        c->err = "tree-scheduled solve: a bounded dependency wait gave up; results since then are invalid";
+        c->err = "a bounded device wait (a dependency flag or a tensor-core completion) gave up; results since then are invalid";
         return DC_ERR_TIMEOUT;
     }
     if (w[1]) {
@@ -98,6 +98,31 @@ void dc_default_params(dc_params* p) {
     p->n_obstacles = 0;
     p->contact_compliance = DC_COMPLIANCE_ROWSUM;
     p->adj_fallback = 1;
+}
+
+dc_status dc_set_instance_steps(dc_ctx* c, const int32_t* steps) {
+    if (!c) return DC_ERR_INVALID;
+    if (!steps) {
+        c->inst_steps.clear();
+        c->d_inst_steps = nullptr;   // the device copy stays in work_allocs until dc_destroy
+        c->graph_epoch++;
+        return DC_OK;
+    }
+    for (int i = 0; i < c->B; ++i)
+        if (steps[i] < 0) {
+            c->err = "dc_set_instance_steps: negative step count";
+            return DC_ERR_INVALID;
+        }
+    c->inst_steps.assign(steps, steps + c->B);
+    // B step counts, then the first step of the segment a recomputation replays
+    if (!c->d_inst_steps_buf) RET(dalloc(c, c->work_allocs, &c->d_inst_steps_buf, (size_t)c->B + 1));
+    CK(cudaMemcpyAsync(c->d_inst_steps_buf, c->inst_steps.data(), sizeof(int) * c->B, cudaMemcpyHostToDevice,
+                       c->stream));
+    CK(cudaMemsetAsync(c->d_inst_steps_buf + c->B, 0, sizeof(int), c->stream));
+    CK(ctx_sync(c, c->stream));
+    c->d_inst_steps = c->d_inst_steps_buf;
+    c->graph_epoch++;
+    return DC_OK;
 }
 
 dc_status dc_add_obstacle_mesh(dc_ctx* c, int32_t nv, const double* verts, int32_t nt, const int32_t* tris,
@@ -393,7 +418,7 @@ dc_status dc_rollout(dc_ctx* c, int32_t n_steps, const double* x0, const double*
                     nv = bufv[(s + 1) & 1];
                 }
             }
-            run_step(c, cx, cv, nx, nv, k == 1 ? c->rec_all[s] : c->scratch);
+            run_step(c, cx, cv, nx, nv, k == 1 ? c->rec_all[s] : c->scratch, true, s);
             RET(store_vec(c, nx, traj_x + (size_t)(s + 1) * 3 * m, h2));
             host_io |= h2;
             cx = nx;
@@ -487,7 +512,7 @@ dc_status dc_backward(dc_ctx* c, const double* dL_dx_final, const double* dL_dv_
             }
             CK(cudaStreamWaitEvent(s, c->ev_fact[k2], 0));
             if (traj) adj_add_ext(c->gx, traj + (size_t)(t + 1) * 3 * m, c->d_int2ext, m, c->layout, s);
-            st = adjoint_step(c, X(t), X(t + 1), V(t + 1), k2, noncv);
+            st = adjoint_step(c, X(t), X(t + 1), V(t + 1), k2, noncv, t);
             if (st) break;
         }
     }
@@ -551,6 +576,14 @@ dc_status dc_debug_sweep_wait_timeout(dc_ctx* c, int32_t skip_items) {
     return check_device_flags(c);
 }
 
+dc_status dc_debug_front_factor(int32_t n, int32_t p, const float* A, float* out, float* linv_out,
+                                int32_t threads, int32_t use_tc, int32_t use_gscr) {
+    std::string err;
+    const dc_status st = frontal_debug_factor(n, p, A, out, linv_out, threads, use_tc, use_gscr, &err);
+    if (st != DC_OK) g_create_err = err;
+    return st;
+}
+
 dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
     if (!c || !o) return DC_ERR_INVALID;
     CK(ctx_sync(c, c->stream));
@@ -607,7 +640,7 @@ dc_status dc_get_stats(dc_ctx* c, dc_stats* o) {
 
 dc_status dc_set_kernel_timer(dc_ctx* c, int32_t kernel_class) {
     if (!c) return DC_ERR_INVALID;
-    if (kernel_class < DC_KT_NONE || kernel_class > DC_KT_ASSEMBLE) {
+    if (kernel_class < DC_KT_NONE || kernel_class > DC_KT_SWEEPS) {
         c->err = "dc_set_kernel_timer: unknown kernel class";
         return DC_ERR_INVALID;
     }

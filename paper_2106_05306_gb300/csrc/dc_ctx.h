@@ -87,7 +87,7 @@ struct dc_ctx {
     double* stage = nullptr;       // [m][3] staging for host/device conversion
     double* stage2 = nullptr;
     // [0..2] contact cases, [3] sticky fault word of the bounded waits,
-    // [4] non-finite forward state
+    // [4] non-finite forward state, [5] non-positive pivot of the GPU factorisation
     unsigned long long* counters = nullptr;
     // rollout checkpoints
     int ck_n_steps = -1, ck_every = 1, ck_cap = 0;
@@ -148,6 +148,10 @@ struct dc_ctx {
     long long adj_fallbacks = 0, adj_fallback_iters = 0;
     // obstacle meshes (dc_add_obstacle_mesh): triangle records, and per mesh its
     // first record and triangle count
+    // per-instance step counts (dc_set_instance_steps): device copy, or null
+    int* d_inst_steps = nullptr;
+    int* d_inst_steps_buf = nullptr;
+    std::vector<int> inst_steps;
     std::vector<d4> mesh_rec;      // DC_MESH_REC records per triangle (dc_obstacle.cuh)
     std::vector<int> mesh_t0, mesh_nt;
 };
@@ -264,6 +268,8 @@ dc_status upload_mesh(dc_ctx* c, MeshPrep& mp);
 // Validates q, factorises every instance's P and builds its fronts (host threads).
 dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp);
 dc_status upload_params(dc_ctx* c, ParamPrep& pp);
+// True when two parameter sets may be instances of one batch (equal shared fields).
+bool dc_same_batch_fields(const dc_params& a, const dc_params& b);
 // Upper bound of the device bytes a context holds through dc_rollout(n_steps) and
 // dc_backward (with mesh and parameters prepared).
 size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPrep& pp, int n_steps);
@@ -275,7 +281,13 @@ dc_status alloc_rec(dc_ctx* c, Pool& pool, StepRec& r);
 dc_status load_vec(dc_ctx* c, const double* ext, d4* out, bool& host_io);
 dc_status store_vec(dc_ctx* c, const d4* in, double* ext, bool& host_io);
 // One time step (Sec. 3.2) on internal vectors; writes the contact record into r.
-void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepRec& r, bool count = true);
+// step: the step's index in its rollout; instances whose own step count
+// (dc_set_instance_steps) is reached keep their state (-1: no such check).
+// step: the index of the step in its rollout (-1: none), for the per-instance step
+// counts; plus *step_base when step_base is given (a segment graph replayed for
+// several segments reads its first step from device memory).
+void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepRec& r, bool count = true,
+              int step = -1, const int* step_base = nullptr);
 // run_step for steps [0, n) of dc_rollout (graph-captured when enabled)
 dc_status rollout_steps(dc_ctx* c, int n_steps, int k);
 dc_status ensure_checkpoints(dc_ctx* c, int n_ck);
@@ -286,8 +298,12 @@ dc_status recompute_segment(dc_ctx* c, int seg, int s0, int s1);
 dc_status ensure_records(dc_ctx* c, int n_steps);
 // Per-step adjoint data of the step with record r, ending at (x1, v1), into slot k.
 void prepare_step(dc_ctx* c, const StepRec& r, const d4* x1, const d4* v1, int k, cudaStream_t s);
-dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv);
+// step: the index of the step being differentiated (for per-instance step counts)
+dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv, int step);
 dc_status autotune(dc_ctx* c);
+// Numeric Cholesky of P on the GPU into the supernodal panels (factor_on_gpu);
+// synchronous, DC_ERR_NOT_SPD for a pivot <= 0.
+dc_status gpu_factor_P(dc_ctx* c, const HostFronts& frm, double h);
 // Reads the device-side error words (bounded-wait timeout, non-finite state);
 // synchronises the context's stream.
 dc_status check_device_flags(dc_ctx* c);

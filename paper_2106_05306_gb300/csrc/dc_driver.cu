@@ -87,7 +87,8 @@ dc_status store_vec(dc_ctx* c, const d4* in, double* ext, bool& host_io) {
     return DC_OK;
 }
 
-void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepRec& r, bool count) {
+void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepRec& r, bool count, int step,
+              const int* step_base) {
     cudaStream_t s = c->stream;
     const DevMesh& dm = c->dm;
     const DevParams& P = c->dp;
@@ -97,8 +98,11 @@ void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepR
     // of the step's contact set, or a constant per node for the other choices
     const double* cc = P.ccon;
     if (P.compliance == DC_COMPLIANCE_ROWSUM) {
-        launch_solve_fwd(dm, c->ind, c->y, s);
-        launch_solve_bwd(dm, P, c->y, nullptr, 2, nullptr, nullptr, nullptr, nullptr, nullptr, c->cc, s);
+        if (!launch_solve_sweeps(dm, P, c->ind, c->y, nullptr, 2, nullptr, nullptr, nullptr, nullptr, nullptr, c->cc,
+                                 s)) {
+            launch_solve_fwd(dm, c->ind, c->y, s);
+            launch_solve_bwd(dm, P, c->y, nullptr, 2, nullptr, nullptr, nullptr, nullptr, nullptr, c->cc, s);
+        }
         cc = c->cc;
     }
     cudaMemcpyAsync(c->v, vin, sizeof(d4) * dm.m, cudaMemcpyDeviceToDevice, s);
@@ -116,6 +120,11 @@ void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepR
             kt.end(DC_KT_SOLVE_BWD);
             continue;
         }
+        kt.begin(DC_KT_SWEEPS);
+        const bool fused = launch_solve_sweeps(dm, P, c->b, c->y, c->v, 1, r.contact, r.nb, cc, r.f, r.case_,
+                                               nullptr, s);
+        kt.end(DC_KT_SWEEPS);
+        if (fused) continue;
         kt.begin(DC_KT_SOLVE_FWD);
         launch_solve_fwd(dm, c->b, c->y, s);
         kt.end(DC_KT_SOLVE_FWD);
@@ -125,6 +134,8 @@ void run_step(dc_ctx* c, const d4* xin, const d4* vin, d4* xout, d4* vout, StepR
     }
     launch_finalize(dm, P, xin, c->v, xout, c->counters + 4, s);
     if (vout != c->v) cudaMemcpyAsync(vout, c->v, sizeof(d4) * dm.m, cudaMemcpyDeviceToDevice, s);
+    if (step >= 0 && c->d_inst_steps)
+        launch_freeze(dm, P, c->d_inst_steps, step, step_base, xin, vin, xout, vout, r.contact, s);
     if (count) launch_count_cases(r.contact, r.case_, dm.m_free, c->counters, s);
 }
 
@@ -197,7 +208,7 @@ dc_status rollout_steps(dc_ctx* c, int n_steps, int k) {
                     nv = bufv[(s + 1) & 1];
                 }
             }
-            run_step(c, cx, cv, nx, nv, k == 1 ? c->rec_all[s] : c->scratch);
+            run_step(c, cx, cv, nx, nv, k == 1 ? c->rec_all[s] : c->scratch, true, s);
             cx = nx;
             cv = nv;
         }
@@ -246,10 +257,13 @@ dc_status recompute_segment(dc_ctx* c, int seg, int s0, int s1) {
     CK(cudaMemcpyAsync(c->segV, ckx + m, sizeof(d4) * m, cudaMemcpyDeviceToDevice, s));
     const int n = s1 - s0;
     GraphCache& gc = c->g_seg[n == c->ck_every ? 0 : 1];
+    // the segment's first step, read by the per-instance freeze inside the graph
+    const int* base = c->d_inst_steps ? c->d_inst_steps + c->B : nullptr;
+    if (base) launch_set_int(c->d_inst_steps + c->B, s0, s);
     return run_graph(c, gc, n, 0, [&]() {
         for (int q = 0; q < n; ++q)
             run_step(c, c->segX + (size_t)q * m, c->segV + (size_t)q * m, c->segX + (size_t)(q + 1) * m,
-                     c->segV + (size_t)(q + 1) * m, c->seg_rec[q], false);
+                     c->segV + (size_t)(q + 1) * m, c->seg_rec[q], false, base ? q : s0 + q, base);
     });
 }
 
@@ -676,7 +690,7 @@ void prepare_step(dc_ctx* c, const StepRec& r, const d4* x1, const d4* v1, int k
 
 // One adjoint step from slot k: (gx, gv) at n+1 -> (gx2, gv2) at n, parameter
 // terms into dparam_acc.
-dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv) {
+dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int k, bool& noncv, int step) {
     cudaStream_t s = c->stream;
     c->ad = c->ads[k];
     c->fdv = c->fds[k];
@@ -684,7 +698,13 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int
     adj_rhs(c->dm, ad, c->gx, c->gv, c->g, c->rhs, s);
     std::vector<int> it;
     std::vector<double> rel;
-    RET(gmres(c, it, rel));
+    // instances past their own last step take no part (their adjoint passes through)
+    std::vector<char> live;
+    if (c->d_inst_steps) {
+        live.assign(c->B, 1);
+        for (int i = 0; i < c->B; ++i) live[i] = c->inst_steps[i] > step;
+    }
+    RET(gmres(c, it, rel, false, live.empty() ? nullptr : &live));
     if (c->prm.adj_fallback) {
         // instances that hit the iteration cap, or stopped more than 100 x adj_tol
         // above it: a second pass from their iterate.  A restart cycle that fails
@@ -723,6 +743,7 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int
     adj_apply_H(c->dm, ad, 3, c->z, nullptr, c->E, s);
     adj_apply_H(c->dm, ad, 2, c->z, c->g, c->resid, s);
     adj_outputs(c->dm, ad, c->dp, c->z, c->E, c->resid, x_n, v1, c->gx, c->gx2, c->gv2, s);
+    if (c->d_inst_steps) launch_pass_adjoint(c->dm, c->dp, c->d_inst_steps, step, c->gv, c->gv2, s);
     adj_params(c->dm, ad, c->sg, c->z, x1, c->dparam_part, c->dparam_acc, s);
     CK(cudaEventRecord(c->ev_free[k], s));
     std::swap(c->gx, c->gx2);

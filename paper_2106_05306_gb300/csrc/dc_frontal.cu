@@ -15,6 +15,7 @@
 
 #include "dc_adjoint.h"
 #include "dc_internal.h"
+#include "dc_tc.cuh"
 #include "dc_wait.cuh"
 
 namespace {
@@ -24,6 +25,17 @@ constexpr int LDS = PB + 1;   // shared-memory row stride (no bank conflicts)
 constexpr int FT = 1024;      // threads per solve CTA
 constexpr int FT2 = 512;      // threads per factorisation CTA
 constexpr int TM = 8;         // register tile of the trailing update
+// Tensor-core trailing update: 128 x TC_N accumulator tiles in TMEM, operands in
+// shared memory (A: 128 rows, B: TC_N rows, each as TF32 hi and lo parts).
+constexpr int TC_M = 128;
+constexpr int TC_N = 64;
+constexpr uint32_t TC_COLS = 64;                          // TMEM columns per CTA
+constexpr int TC_A_BYTES = TC_M * TC_K * 4;               // one part of A
+constexpr int TC_B_BYTES = TC_N * TC_K * 4;               // one part of B
+constexpr int TC_FLOATS = (2 * TC_A_BYTES + 2 * TC_B_BYTES) / 4;
+constexpr int TC_MIN_N2 = 64;                             // smaller trailing blocks: FMA path
+constexpr int TC_MIN_F = 160;                             // levels with smaller fronts: FMA path
+constexpr int TC_WAIT = 1 << 22;                          // polls of an MMA completion
 
 __device__ __forceinline__ d4 ld(const d4* p) {
     const double2* q = reinterpret_cast<const double2*>(p);
@@ -137,6 +149,110 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
         for (int r = 0; r < 3; ++r) F[c * ldf + r] = (float)Hc[3 * r + c];
 }
 
+// Rows [g0, g0 + nrows) of the panel (column k of row g at Lt[k ldt + g]),
+// times Dd[k] when Dd is given, split into TF32 hi/lo parts in the operand layout;
+// rows at or beyond n2 and columns at or beyond kb are zero.
+__device__ __forceinline__ void tc_stage(const float* __restrict__ Lt, int ldt, int g0, int nrows, int n2, int kb,
+                                         const float* __restrict__ Dd, unsigned char* hi, unsigned char* lo) {
+    for (int e = threadIdx.x; e < nrows * (TC_K / 4); e += blockDim.x) {
+        const int r = e % nrows, k4 = e / nrows, g = g0 + r;
+        float v[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int k = 4 * k4 + j;
+            v[j] = (g < n2 && k < kb) ? Lt[k * ldt + g] * (Dd ? Dd[k] : 1.0f) : 0.0f;
+        }
+        float4 h, l;
+        tc_split(v[0], h.x, l.x);
+        tc_split(v[1], h.y, l.y);
+        tc_split(v[2], h.z, l.z);
+        tc_split(v[3], h.w, l.w);
+        *reinterpret_cast<float4*>(hi + tc_off(r, 4 * k4)) = h;
+        *reinterpret_cast<float4*>(lo + tc_off(r, 4 * k4)) = l;
+    }
+}
+
+// Trailing update T -= L D L^T of one panel on the tensor cores: for every
+// 128 x TC_N tile (I, J) of the n2 x n2 trailing block that meets its lower
+// triangle, stage L's rows of tile I (A) and L D's rows of tile J (B), issue the
+// three TF32 passes (hi hi, hi lo, lo hi; K = 32 in four slices each) from one
+// thread into TMEM, and subtract the accumulator from T's lower entries (thread
+// = row, coalesced down a column).  T is column-major with leading dimension f.
+// Returns false (fault word set) if an MMA did not complete within TC_WAIT polls.
+__device__ bool tc_trailing_update(float* __restrict__ T, int f, int n2, int kb, const float* __restrict__ Lt,
+                                   int ldt, const float* __restrict__ Dd, unsigned char* tcs, uint32_t tmem,
+                                   uint64_t* bar, uint32_t& phase, unsigned long long* fault) {
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nwg = blockDim.x >> 7, wg = warp >> 2, lq = warp & 3;
+    unsigned char* a_hi = tcs;
+    unsigned char* a_lo = a_hi + TC_A_BYTES;
+    unsigned char* b_hi = a_lo + TC_A_BYTES;
+    unsigned char* b_lo = b_hi + TC_B_BYTES;
+    constexpr uint32_t idesc = tc_idesc_tf32(TC_M, TC_N);
+    const int nI = (n2 + TC_M - 1) / TC_M, nJall = (n2 + TC_N - 1) / TC_N;
+    for (int I = 0; I < nI; ++I) {
+        const int r0 = I * TC_M;
+        const int nJ = min((r0 + TC_M - 1) / TC_N + 1, nJall);
+        for (int J = 0; J < nJ; ++J) {
+            const int q0 = J * TC_N;
+            if (J == 0) tc_stage(Lt, ldt, r0, TC_M, n2, kb, nullptr, a_hi, a_lo);
+            tc_stage(Lt, ldt, q0, TC_N, n2, kb, Dd, b_hi, b_lo);
+            tc_fence_async_smem();
+            tc_fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after_sync();
+                const uint32_t ah = tc_smem_u32(a_hi), al = tc_smem_u32(a_lo);
+                const uint32_t bh = tc_smem_u32(b_hi), bl = tc_smem_u32(b_lo);
+#pragma unroll
+                for (int pass = 0; pass < 3; ++pass) {
+                    const uint32_t a = pass == 2 ? al : ah, b = pass == 1 ? bl : bh;
+#pragma unroll
+                    for (int kk = 0; kk < TC_K / 8; ++kk)
+                        tc_mma_tf32(tmem, tc_desc(a + kk * 2 * TC_CORE_K_BYTES), tc_desc(b + kk * 2 * TC_CORE_K_BYTES),
+                                    idesc, (pass | kk) ? 1u : 0u);
+                }
+                tc_commit(bar);
+            }
+            // this thread's row; the current values of its first 16-column chunk are
+            // loaded while the tensor core works
+            const int r = r0 + 32 * lq + lane;
+            float old[16];
+            {
+                const int c0 = q0 + 16 * wg;
+#pragma unroll
+                for (int c = 0; c < 16; ++c)
+                    old[c] = (wg < TC_N / 16 && r < n2 && c0 + c <= r) ? T[(long)(c0 + c) * f + r] : 0.0f;
+            }
+            const bool done = tc_mbar_wait(bar, phase, TC_WAIT);
+            phase ^= 1u;
+            if (__syncthreads_or(!done)) {
+                if (tid == 0) atomicExch(fault, 1ull);
+                tc_mbar_wait(bar, phase ^ 1u, TC_WAIT);   // let an MMA still in flight finish
+                return false;
+            }
+            tc_fence_after_sync();
+            for (int ch = wg; ch < TC_N / 16; ch += nwg) {
+                float v[16];
+                tc_ld16(tmem + ((uint32_t)(32 * lq) << 16) + 16u * ch, v);
+                const int c0 = q0 + 16 * ch;
+                if (ch != wg) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) old[c] = (r < n2 && c0 + c <= r) ? T[(long)(c0 + c) * f + r] : 0.0f;
+                }
+                if (r < n2) {
+#pragma unroll
+                    for (int c = 0; c < 16; ++c)
+                        if (c0 + c <= r) T[(long)(c0 + c) * f + r] = old[c] - v[c];
+                }
+            }
+            tc_fence_before_sync();
+            __syncthreads();
+        }
+    }
+    return true;
+}
+
 // Extend-add of the children's update blocks, then the partial LDL^T of the
 // front's pivot columns; the trailing lower triangle becomes the update block.
 // Per panel of PB pivot columns: the panel's diagonal block is staged row-major
@@ -151,20 +267,39 @@ __global__ void k_pairs(DevMesh dm, AdjDev ad, FrontDev fd) {
 // (gsz floats per CTA, 16-byte aligned, read through L1/L2) and shared memory
 // holds only the diagonal block, its inverse and the pivots.  The arithmetic and
 // its order are the same either way.
+// With tc set, trailing blocks of at least TC_MIN_N2 rows are updated on the
+// tensor cores (tc_trailing_update; its operand buffers lead the shared memory)
+// and smaller ones by the FMA tiles.
 __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin, int mf, float* __restrict__ gscr,
-                                                     long gsz) {
-    extern __shared__ __align__(16) float sm[];
+                                                     long gsz, int tc) {
+    extern __shared__ __align__(1024) float sm[];
+    __shared__ uint64_t tc_bar;
+    __shared__ uint32_t tc_slot;
     const int s = fd.lvl_sn[lvl_begin + blockIdx.x];
     const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
     float* F = fd.pool + fd.off[s];
     const int f = fd.f[s], p = fd.p[s];
     const int ldt = (mf + 7) / 8 * 8;                // row stride of the transposed panel
-    float* Db = sm;                                  // [PB][LDS] diagonal block, row-major
+    float* const base = tc ? sm + TC_FLOATS : sm;
+    float* Db = base;                                // [PB][LDS] diagonal block, row-major
     float* Xs = Db + PB * LDS;                       // [PB][LDS] diagonal-block inverse
     float* Dd = Xs + PB * LDS;                       // [PB] pivots of the panel
-    float* const scr = gscr ? gscr + (long)blockIdx.x * gsz : sm;
+    float* const scr = gscr ? gscr + (long)blockIdx.x * gsz : base;
     // [PB][ldt] rows below the block, 16-byte aligned
-    float* Lt = gscr ? scr : sm + (2 * PB * LDS + PB + 3) / 4 * 4;
+    float* Lt = gscr ? scr : base + (2 * PB * LDS + PB + 3) / 4 * 4;
+    uint32_t tmem = 0, tc_phase = 0;
+    bool tc_ok = tc != 0;
+    if (tc) {
+        if (tid == 0) {
+            tc_mbar_init(&tc_bar, 1);
+            tc_mbar_init_fence();
+        }
+        if (warp == 0) tc_alloc(&tc_slot, TC_COLS);
+        tc_fence_before_sync();
+        __syncthreads();
+        tc_fence_after_sync();
+        tmem = tc_slot;
+    }
     for (int q = fd.cptr[s]; q < fd.cptr[s + 1]; ++q) {
         const int c = fd.child[q];
         const float* Fc = fd.pool + fd.off[c];
@@ -281,6 +416,12 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
             float* dst = F + (long)(k0 + c) * f + k0;
             for (int r = c + lane; r < nr; r += 32) dst[r] = r < kb ? Db[r * LDS + c] : Lt[c * ldt + r - kb];
         }
+        if (tc_ok && n2 >= TC_MIN_N2) {
+            tc_ok = tc_trailing_update(F + (long)(k0 + kb) * f + k0 + kb, f, n2, kb, Lt, ldt, Dd,
+                                       reinterpret_cast<unsigned char*>(sm), tmem, &tc_bar, tc_phase, fd.fault);
+            if (!tc_ok) break;
+            continue;
+        }
         // trailing update in TM x 4 half-tiles of the TM x TM tiles of the lower
         // triangle; each thread prefetches its tile's current values before the FMA
         // loop so that the memory latency overlaps the arithmetic
@@ -338,7 +479,7 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
     // X is column-major p x p.  Per block row I the rows L[i0.., 0..i0) are staged in
     // shared memory, and per block column J the needed part of X as well.
     float* X = fd.linv + fd.linv_off[s];
-    const int nb = (p + PB - 1) / PB;
+    const int nb = (tc && !tc_ok) ? 0 : (p + PB - 1) / PB;   // (nothing more after an MMA timeout)
     for (int I = 0; I < nb; ++I) {
         const int i0 = I * PB, ib = min(PB, p - i0);
         const float* Bi = binv + (long)I * PB * PB;
@@ -393,6 +534,12 @@ __global__ void __launch_bounds__(FT2) k_front_level(FrontDev fd, int lvl_begin,
             if (col > i0 + r) X[(long)col * p + i0 + r] = 0.0f;
         }
         __syncthreads();
+    }
+    if (tc) {
+        tc_fence_before_sync();
+        __syncthreads();
+        tc_fence_after_sync();
+        if (warp == 0) tc_dealloc(tmem, TC_COLS);
     }
 }
 
@@ -678,16 +825,29 @@ __global__ void k_pre_out(int n, const double* __restrict__ mu, const int* __res
 // Shared memory of a factorisation CTA: the diagonal block, its inverse, the
 // pivots and the transposed rows below the block (one panel width of the front),
 // or the scratch of the explicit inverse of a pivot block of up to max_p rows.
-size_t frontal_factor_smem(int max_f, int max_p) {
+// With tc, the tensor-core operand buffers come first.
+size_t frontal_factor_smem(int max_f, int max_p, bool tc) {
     const size_t ldt = ((size_t)max_f + 7) / 8 * 8;
     size_t panel = (2 * (size_t)PB * LDS + PB + 3) / 4 * 4 + PB * ldt;
     size_t inverse = 2 * (size_t)PB * (max_p + 1) + (size_t)PB * PB;
-    return (panel > inverse ? panel : inverse) * sizeof(float) + 64;
+    return ((tc ? TC_FLOATS : 0) + (panel > inverse ? panel : inverse)) * sizeof(float) + 64;
+}
+
+// Whether a level whose largest front has max_f unknowns uses the tensor-core
+// trailing update (off for every level when DC_FRONT_FMA=1 is in the environment).
+bool frontal_level_tc(int max_f) {
+    static const bool off = [] {
+        const char* e = getenv("DC_FRONT_FMA");
+        return e && e[0] == '1';
+    }();
+    return !off && max_f >= TC_MIN_F;
 }
 
 // The same CTA with its panel and inverse scratch in global memory: the shared
 // part, and the global floats per CTA (a multiple of 4).
-size_t frontal_factor_smem_small() { return ((2 * (size_t)PB * LDS + PB + 3) / 4 * 4) * sizeof(float) + 64; }
+size_t frontal_factor_smem_small(bool tc) {
+    return ((tc ? TC_FLOATS : 0) + (2 * (size_t)PB * LDS + PB + 3) / 4 * 4) * sizeof(float) + 64;
+}
 long frontal_factor_gscr(int max_f, int max_p) {
     const long ldt = ((long)max_f + 7) / 8 * 8;
     const long panel = (long)PB * ldt, inverse = 2L * PB * (max_p + 1) + (long)PB * PB;
@@ -701,18 +861,21 @@ size_t frontal_solve_smem(int max_f) { return (2 * (size_t)max_f + GV_ROWS * GV_
 void frontal_plan(const HostFronts& fr, size_t smem_limit, long* gscr_floats, size_t* factor_bytes) {
     const int nl = (int)fr.lvl_ptr.size() - 1;
     *gscr_floats = 0;
-    *factor_bytes = frontal_factor_smem_small();
+    *factor_bytes = frontal_factor_smem_small(false);
     for (int l = 0; l < nl; ++l) {
         int mf = 0, mp = 0;
         for (int q = fr.lvl_ptr[l]; q < fr.lvl_ptr[l + 1]; ++q) {
             mf = std::max(mf, fr.f[fr.lvl_sn[q]]);
             mp = std::max(mp, fr.p[fr.lvl_sn[q]]);
         }
-        const size_t need = frontal_factor_smem(mf, mp);
-        if (need <= smem_limit)
+        const bool tc = frontal_level_tc(mf);
+        const size_t need = frontal_factor_smem(mf, mp, tc);
+        if (need <= smem_limit) {
             *factor_bytes = std::max(*factor_bytes, need);
-        else
+        } else {
+            *factor_bytes = std::max(*factor_bytes, frontal_factor_smem_small(tc));
             *gscr_floats = std::max(*gscr_floats, (long)(fr.lvl_ptr[l + 1] - fr.lvl_ptr[l]) * frontal_factor_gscr(mf, mp));
+        }
     }
 }
 
@@ -735,6 +898,102 @@ cudaError_t frontal_configure(size_t fb, int max_f) {
         solve_bytes = sb;
     }
     return cudaSuccess;
+}
+
+// One dense front through k_front_level: the test hook behind
+// dc_debug_front_factor (synchronous; allocates and frees its own buffers).
+dc_status frontal_debug_factor(int n, int p, const float* A, float* out, float* linv_out, int threads, int tc,
+                               int use_gscr, std::string* err) {
+    if (n < 1 || p < 1 || p > n || n > 4096 || (threads != 128 && threads != 256 && threads != 512)) {
+        *err = "dc_debug_front_factor: needs 1 <= p <= n <= 4096 and 128, 256 or 512 threads";
+        return DC_ERR_INVALID;
+    }
+    if (!A || !out) {
+        *err = "dc_debug_front_factor: null A or out";
+        return DC_ERR_INVALID;
+    }
+    const int nbk = (p + PB - 1) / PB;
+    const long gsz = frontal_factor_gscr(n, p);
+    const size_t smem = use_gscr ? frontal_factor_smem_small(tc != 0) : frontal_factor_smem(n, p, tc != 0);
+    if (smem > 227 * 1024) {
+        *err = "dc_debug_front_factor: front too large for shared memory; set use_gscr";
+        return DC_ERR_INVALID;
+    }
+    // device image: ints [lvl_sn, f, p, cptr0, cptr1], long longs [off, binv_off, linv_off]
+    int hi[5] = {0, n, p, 0, 0};
+    long long hl[3] = {0, 0, 0};
+    float tau = 1e-30f;
+    int* di = nullptr;
+    long long* dl = nullptr;
+    float *pool = nullptr, *binv = nullptr, *linv = nullptr, *dtau = nullptr, *gscr = nullptr;
+    unsigned long long* fault = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto fail = [&](cudaError_t ce) {
+        *err = std::string("dc_debug_front_factor: ") + cudaGetErrorString(ce);
+        return DC_ERR_CUDA;
+    };
+    dc_status st = DC_OK;
+    do {
+        if ((e = cudaMalloc(&di, sizeof(hi))) || (e = cudaMalloc(&dl, sizeof(hl))) ||
+            (e = cudaMalloc(&pool, sizeof(float) * (size_t)n * n)) ||
+            (e = cudaMalloc(&binv, sizeof(float) * (size_t)nbk * PB * PB)) ||
+            (e = cudaMalloc(&linv, sizeof(float) * (size_t)p * p)) || (e = cudaMalloc(&dtau, sizeof(float))) ||
+            (e = cudaMalloc(&fault, sizeof(unsigned long long))) ||
+            (use_gscr && (e = cudaMalloc(&gscr, sizeof(float) * (size_t)gsz)))) {
+            st = fail(e);
+            break;
+        }
+        if ((e = cudaMemcpy(di, hi, sizeof(hi), cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(dl, hl, sizeof(hl), cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(dtau, &tau, sizeof(float), cudaMemcpyHostToDevice)) ||
+            (e = cudaMemcpy(pool, A, sizeof(float) * (size_t)n * n, cudaMemcpyHostToDevice)) ||
+            (e = cudaMemset(fault, 0, sizeof(unsigned long long))) ||
+            (e = frontal_configure(smem, n))) {
+            st = fail(e);
+            break;
+        }
+        FrontDev fd{};
+        fd.S = 1;
+        fd.max_f = n;
+        fd.tau = dtau;
+        fd.lvl_sn = di;
+        fd.f = di + 1;
+        fd.p = di + 2;
+        fd.cptr = di + 3;
+        fd.off = dl;
+        fd.binv_off = dl + 1;
+        fd.linv_off = dl + 2;
+        fd.pool = pool;
+        fd.binv = binv;
+        fd.linv = linv;
+        fd.fault = fault;
+        dc_note_launch();
+        k_front_level<<<1, threads, smem>>>(fd, 0, n, use_gscr ? gscr : nullptr, use_gscr ? gsz : 0L, tc ? 1 : 0);
+        if ((e = cudaGetLastError()) || (e = cudaDeviceSynchronize())) {
+            st = fail(e);
+            break;
+        }
+        unsigned long long fl = 0;
+        if ((e = cudaMemcpy(&fl, fault, sizeof(fl), cudaMemcpyDeviceToHost)) ||
+            (e = cudaMemcpy(out, pool, sizeof(float) * (size_t)n * n, cudaMemcpyDeviceToHost)) ||
+            (linv_out && (e = cudaMemcpy(linv_out, linv, sizeof(float) * (size_t)p * p, cudaMemcpyDeviceToHost)))) {
+            st = fail(e);
+            break;
+        }
+        if (fl) {
+            *err = "dc_debug_front_factor: a tensor-core wait gave up";
+            st = DC_ERR_TIMEOUT;
+        }
+    } while (false);
+    cudaFree(di);
+    cudaFree(dl);
+    cudaFree(pool);
+    cudaFree(binv);
+    cudaFree(linv);
+    cudaFree(dtau);
+    cudaFree(fault);
+    cudaFree(gscr);
+    return st;
 }
 
 cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_out) {
@@ -762,7 +1021,7 @@ cudaError_t frontal_tree_grid(int max_f, int* grid_f, int* grid_b, size_t* smem_
 static int factor_threads(int mf, int mp, int cnt, int sms) {
     if (mf <= 96) return 128;
     if (mf <= 192) return 256;
-    if (cnt >= 4 * sms && 2 * frontal_factor_smem(mf, mp) <= 227 * 1024) return 256;
+    if (cnt >= 4 * sms && 2 * frontal_factor_smem(mf, mp, frontal_level_tc(mf)) <= 227 * 1024) return 256;
     // (levels on the global-scratch path keep FT2 threads)
     return FT2;
 }
@@ -785,12 +1044,13 @@ void frontal_factorize(const DevMesh& dm, const AdjDev& ad, const FrontDev& fd, 
             dc_note_launch();
             if (kt) kt->begin(DC_KT_FRONT);
             const int mp = lvl_maxp[l];
-            if (frontal_factor_smem(mf, mp) <= fd.smem_limit) {
-                k_front_level<<<cnt, factor_threads(mf, mp, cnt, sms), frontal_factor_smem(mf, mp), s>>>(
-                    fd, lvl_ptr[l], mf, nullptr, 0L);
+            const bool tc = frontal_level_tc(mf);
+            if (frontal_factor_smem(mf, mp, tc) <= fd.smem_limit) {
+                k_front_level<<<cnt, factor_threads(mf, mp, cnt, sms), frontal_factor_smem(mf, mp, tc), s>>>(
+                    fd, lvl_ptr[l], mf, nullptr, 0L, tc ? 1 : 0);
             } else {   // fronts too large for shared memory: panel scratch in fd.gscr
-                k_front_level<<<cnt, FT2, frontal_factor_smem_small(), s>>>(fd, lvl_ptr[l], mf, fd.gscr,
-                                                                          frontal_factor_gscr(mf, mp));
+                k_front_level<<<cnt, FT2, frontal_factor_smem_small(tc), s>>>(fd, lvl_ptr[l], mf, fd.gscr,
+                                                                            frontal_factor_gscr(mf, mp), tc ? 1 : 0);
             }
             if (kt) kt->end(DC_KT_FRONT);
         }

@@ -191,7 +191,7 @@ std::string dc_build_fronts(const HostMesh& hm, const HostFactor& hf, HostFronts
     return "";
 }
 
-void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps) {
+void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps, bool values) {
     const int S = fr.S;
     ps = HostPSolve();
     ps.poff.resize(S);
@@ -211,6 +211,10 @@ void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps)
         ao += nu;
     }
     ps.acc_nodes = ao;
+    ps.n_panel = po;
+    ps.n_xinv = xo;
+    ps.n_pant = to;
+    if (!values) return;
     ps.panel.assign(po, 0.0);
     ps.xinv.assign(xo, 0.0);
     ps.xinvt.assign(xo, 0.0);
@@ -265,12 +269,15 @@ void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out) {
         out.xinv.insert(out.xinv.end(), p.xinv.begin(), p.xinv.end());
         out.xinvt.insert(out.xinvt.end(), p.xinvt.begin(), p.xinvt.end());
         out.pant.insert(out.pant.end(), p.pant.begin(), p.pant.end());
-        po += (long long)p.panel.size();
-        xo += (long long)p.xinv.size();
-        to += (long long)p.pant.size();
+        po += p.n_panel;
+        xo += p.n_xinv;
+        to += p.n_pant;
         ao += p.acc_nodes;
     }
     out.acc_nodes = ao;
+    out.n_panel = po;
+    out.n_xinv = xo;
+    out.n_pant = to;
 }
 
 // Work items of the tree-scheduled sweeps, in a topological order (every front

@@ -83,9 +83,11 @@ struct HostFactor {
 void dc_inverse_diagonal(const HostFactor& hf, std::vector<double>& zdiag);
 
 // Assembles P_ff (free nodes, internal order) and factorises it.  Returns
-// DC_OK, DC_ERR_NOT_SPD or DC_ERR_INVALID with a message in err.
+// DC_OK, DC_ERR_NOT_SPD or DC_ERR_INVALID with a message in err.  symbolic_only:
+// the elimination tree and the structure of L (colptr, rowidx) without values
+// (the numeric factorisation then runs on the GPU).
 dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vector<double>& mass,
-                          HostFactor& hf, std::string& err);
+                          HostFactor& hf, std::string& err, bool symbolic_only = false);
 
 // Symbolic structure of the per-step multifrontal LDL^T (dc_frontal_setup.cpp).
 struct HostFronts {
@@ -111,10 +113,12 @@ struct HostPSolve {
     std::vector<long long> poff, xoff;   // [S] offsets of panel / inverse (doubles)
     std::vector<long long> toff;         // [S] offset of the transposed update block (doubles)
     std::vector<int> aoff;               // [S] offset of the update vector (nodes)
-    std::vector<double> panel, xinv, pant, xinvt;
+    std::vector<double> panel, xinv, pant, xinvt;   // empty when the GPU fills them
+    long long n_panel = 0, n_xinv = 0, n_pant = 0;  // their sizes (doubles)
     long long acc_nodes = 0;
 };
-void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps);
+// values = false: offsets and sizes only (the GPU factorisation fills the panels)
+void dc_build_psolve(const HostFactor& hf, const HostFronts& fr, HostPSolve& ps, bool values = true);
 void dc_merge_psolve(const std::vector<HostPSolve>& P, HostPSolve& out);
 // Work items of the tree-scheduled sweeps (see PSolveDev::tq_ptr)
 void dc_build_tree_items(const HostFronts& fr, std::vector<int>& tq_ptr, std::vector<int>& tq_sn);
@@ -178,6 +182,7 @@ struct PSolveDev {
     unsigned long long* fault;         // sticky: set when a dependency wait gave up
     int tree_grid_f, tree_grid_b;      // host: CTAs of a tree-scheduled launch (fwd, bwd)
     size_t tree_smem;                  // host: its dynamic shared memory
+    int fused;                         // host: 1: both sweeps of a global step as one launch
 };
 
 struct DevMesh {
@@ -279,6 +284,13 @@ void launch_solve_fwd(const DevMesh& dm, const d4* b, d4* y, cudaStream_t s);
 void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* out, int mode,
                       const int* contact, const d4* normal_beta, const double* c, d4* f,
                       int* case_, double* c_out, cudaStream_t s);
+// Both substitution sweeps of one global step as one tree-scheduled launch (the
+// forward sweep, then launch_solve_bwd's backward sweep with the same mode and
+// outputs), when global_solver 1 runs tree-scheduled with fused sweeps; returns
+// false (nothing launched) otherwise.
+bool launch_solve_sweeps(const DevMesh& dm, const DevParams& P, const d4* b, d4* y, d4* out, int mode,
+                         const int* contact, const d4* nb, const double* c, d4* f, int* case_, double* c_out,
+                         cudaStream_t s);
 // Raises the shared-memory limit of the supernodal level kernels for fronts of
 // up to max_fs nodes (process-wide, never lowered).
 cudaError_t psolve_configure(int max_fs);
@@ -292,6 +304,15 @@ cudaError_t psolve_tree_grid(int max_fs, int* grid_f, int* grid_b, size_t* smem)
 // x_{n+1} = x_n + h v; sets *nonfinite when a state entry is not finite
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v,
                      d4* x_np1, unsigned long long* nonfinite, cudaStream_t s);
+// Instances whose step count inst_steps[i] <= step keep their state: x_out = x_in,
+// v_out = v_in, and their free nodes leave the contact record (contact = -1).
+void launch_freeze(const DevMesh& dm, const DevParams& P, const int* inst_steps, int step, const int* step_base,
+                   const d4* xin, const d4* vin, d4* xout, d4* vout, int* contact, cudaStream_t s);
+void launch_set_int(int* p, int v, cudaStream_t s);
+// gv_out = gv_in on the nodes of instances with inst_steps[i] <= step (their
+// adjoint passes through a step they did not take).
+void launch_pass_adjoint(const DevMesh& dm, const DevParams& P, const int* inst_steps, int step, const d4* gv_in,
+                         d4* gv_out, cudaStream_t s);
 // Global step of the mass splitting (DC_COMPLIANCE_MASS): v_half = M^-1 b per
 // free node, then the node's Signorini-Coulomb update as in launch_solve_bwd mode 1
 void launch_mass_solve(const DevMesh& dm, const DevParams& P, const d4* b, d4* v, const int* contact,

@@ -581,6 +581,7 @@ __global__ void __launch_bounds__(256) k_ps_fwd(PSolveDev ps, const int* __restr
     if (q < n_small) ps_fwd_warp(ps, small[q], b, y, smd + warp * 6 * PS_LD);
 }
 
+template <bool YL2 = false>
 __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams& P, int s, const d4* __restrict__ y,
                                            d4* __restrict__ out, int mode, const int* __restrict__ contact,
                                            const d4* __restrict__ nb, const double* __restrict__ cc,
@@ -593,7 +594,7 @@ __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams&
     double* red = xu + 3 * nu;         // [3][GV_MAXG * GV_ROWS]
     const int* un = ps.unode + ps.uptr[s];
     for (int t = tid; t < ns; t += nt) {
-        const d4 a = ld(y + begin + t);
+        const d4 a = YL2 ? ld_cg(y + begin + t) : ld(y + begin + t);   // y written in the same launch: L2 only
         w[t] = a.x;
         w[ns + t] = a.y;
         w[2 * ns + t] = a.z;
@@ -621,6 +622,7 @@ __device__ __forceinline__ void ps_bwd_cta(const PSolveDev& ps, const DevParams&
 
 // Warp path, backward: w is this warp's [3][PS_LD] right-hand side, then
 // [3][PS_LD] of x_U, later of x_s.  One lane per (row, column) pair, as forward.
+template <bool YL2 = false>
 __device__ __forceinline__ void ps_bwd_warp(const PSolveDev& ps, const DevParams& P, int s, const d4* __restrict__ y,
                                             d4* __restrict__ out, int mode, const int* __restrict__ contact,
                                             const d4* __restrict__ nb, const double* __restrict__ cc,
@@ -632,7 +634,7 @@ __device__ __forceinline__ void ps_bwd_warp(const PSolveDev& ps, const DevParams
     double* xu = w + 3 * L;
     const int* un = ps.unode + ps.uptr[s];
     for (int t = lane; t < ns; t += 32) {
-        const d4 a = ld(y + begin + t);
+        const d4 a = YL2 ? ld_cg(y + begin + t) : ld(y + begin + t);
         w[t] = a.x;
         w[L + t] = a.y;
         w[2 * L + t] = a.z;
@@ -806,6 +808,84 @@ __global__ void __launch_bounds__(256) k_ps_bwd_tree(PSolveDev ps, DevParams P, 
     }
 }
 
+// Both sweeps of one global step as one launch: tickets [0, n) are the forward
+// items, [n, 2n) the backward items (the forward order reversed).  A backward
+// item waits for its parent's backward flag, or, at a root, for the root's
+// forward flag; every wait is again on a smaller ticket, so the launch makes
+// progress whatever the number of resident CTAs.  The backward work of small
+// trees runs while the forward sweeps of large ones are still in their upper
+// levels.  Same arithmetic as the two launches, so the same bits.
+__global__ void __launch_bounds__(256) k_ps_sweeps_tree(PSolveDev ps, DevParams P, const d4* __restrict__ b,
+                                                        d4* __restrict__ y, d4* __restrict__ out, int mode,
+                                                        const int* __restrict__ contact,
+                                                        const d4* __restrict__ nb, const double* __restrict__ cc,
+                                                        d4* __restrict__ f, int* __restrict__ case_,
+                                                        double* __restrict__ c_out) {
+    extern __shared__ double smd[];
+    __shared__ int s_item, s_ok;
+    int* ticket = ps.sched;
+    int* done_f = ps.sched + 1;
+    int* done_b = ps.sched + ps.S + 2;
+    const int n = ps.n_items;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = dc_fault_set(ps.fault) ? 2 * n : atomicAdd(ticket, 1);
+        __syncthreads();
+        const int t = s_item;
+        if (t >= 2 * n) return;
+        const bool fwd = t < n;
+        const int it = fwd ? t : n - 1 - (t - n);
+        const int q0 = ps.tq_ptr[it], nq = ps.tq_ptr[it + 1] - q0;
+        const int s0 = ps.tq_sn[q0];
+        if (ps.f[s0] / 3 > PS_SMALL) {
+            if (fwd) ps_fwd_prefetch(ps, s0);
+            else ps_bwd_prefetch(ps, s0);
+            if (threadIdx.x == 0) {
+                bool ok = true;
+                if (fwd) {
+                    for (int q = ps.cptr[s0]; ok && q < ps.cptr[s0 + 1]; ++q)
+                        ok = dc_wait_flag(done_f + ps.child[q], ps.fault);
+                } else {
+                    const int par = ps.parent[s0];
+                    ok = par < 0 ? dc_wait_flag(done_f + s0, ps.fault) : dc_wait_flag(done_b + par, ps.fault);
+                }
+                s_ok = ok;
+            }
+            __syncthreads();
+            if (!s_ok) return;
+            if (fwd) ps_fwd_cta(ps, s0, b, y, smd);
+            else ps_bwd_cta<true>(ps, P, s0, y, out, mode, contact, nb, cc, f, case_, c_out, smd);
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) dc_st_release((fwd ? done_f : done_b) + s0, 1);
+        } else {
+            const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+            if (warp < nq) {
+                const int s = ps.tq_sn[q0 + warp];
+                int ok = 1;
+                if (lane == 0) {
+                    if (fwd) {
+                        for (int q = ps.cptr[s]; ok && q < ps.cptr[s + 1]; ++q)
+                            ok = dc_wait_flag(done_f + ps.child[q], ps.fault);
+                    } else {
+                        const int par = ps.parent[s];
+                        ok = par < 0 ? dc_wait_flag(done_f + s, ps.fault) : dc_wait_flag(done_b + par, ps.fault);
+                    }
+                }
+                ok = __shfl_sync(0xffffffffu, ok, 0);
+                if (ok) {
+                    if (fwd) ps_fwd_warp(ps, s, b, y, smd + warp * 6 * PS_LD);
+                    else ps_bwd_warp<true>(ps, P, s, y, out, mode, contact, nb, cc, f, case_, c_out,
+                                           smd + warp * 6 * PS_LD);
+                    __threadfence();
+                    __syncwarp();
+                    if (lane == 0) dc_st_release((fwd ? done_f : done_b) + s, 1);
+                }
+            }
+            __syncthreads();   // every warp has read s_item before it is rewritten
+        }
+    }
+}
+
 __global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4* __restrict__ v,
                            d4* __restrict__ x1, unsigned long long* __restrict__ nonfinite) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -815,6 +895,29 @@ __global__ void k_finalize(int m, double h, const d4* __restrict__ x_n, const d4
     st(x1 + i, x, y, z);
     if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(b.x) && isfinite(b.y) && isfinite(b.z)))
         atomicExch(nonfinite, 1ull);
+}
+
+// Instances that have taken their own number of steps keep their state.
+__global__ void k_freeze(int m, int m_free, const int* __restrict__ node_inst, const int* __restrict__ inst_steps,
+                         int step, const int* __restrict__ step_base, const d4* __restrict__ xin,
+                         const d4* __restrict__ vin, d4* __restrict__ xout, d4* __restrict__ vout,
+                         int* __restrict__ contact) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || inst_steps[node_inst[i]] > step + (step_base ? *step_base : 0)) return;
+    const d4 x = ld(xin + i), v = ld(vin + i);
+    st(xout + i, x.x, x.y, x.z);
+    st(vout + i, v.x, v.y, v.z);
+    if (i < m_free) contact[i] = -1;
+}
+
+__global__ void k_set_int(int* p, int v) { *p = v; }
+
+__global__ void k_pass_adjoint(int m, const int* __restrict__ node_inst, const int* __restrict__ inst_steps,
+                               int step, const d4* __restrict__ gv_in, d4* __restrict__ gv_out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= m || inst_steps[node_inst[i]] > step) return;
+    const d4 g = ld(gv_in + i);
+    st(gv_out + i, g.x, g.y, g.z);
 }
 
 // Global step of the mass splitting (Eq. ly_et_al_govrningEq as printed):
@@ -896,6 +999,8 @@ cudaError_t psolve_configure(int max_fs) {
         e = cudaFuncSetAttribute(k_ps_fwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_ps_bwd_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_ps_sweeps_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
     if (e == cudaSuccess) configured = need;
     return e;
 }
@@ -973,10 +1078,37 @@ void launch_solve_bwd(const DevMesh& dm, const DevParams& P, const d4* y, d4* ou
     k_solve_bwd<<<nblk((long)dm.m_free * 32, 256), 256, 0, s>>>(dm, P, y, out, mode, contact, nb, c, f, case_,
                                                                 c_out);
 }
+bool launch_solve_sweeps(const DevMesh& dm, const DevParams& P, const d4* b, d4* y, d4* out, int mode,
+                         const int* contact, const d4* nb, const double* c, d4* f, int* case_, double* c_out,
+                         cudaStream_t s) {
+    const PSolveDev& ps = dm.ps;
+    if (dm.solver != 1 || !ps.tree || !ps.fused) return false;
+    if (ps.n_items == 0) return true;
+    cudaMemsetAsync(ps.sched, 0, sizeof(int) * 2 * (ps.S + 1), s);
+    dc_note_launch();
+    k_ps_sweeps_tree<<<std::min(std::max(ps.tree_grid_f, ps.tree_grid_b), 2 * ps.n_items), 256, ps.tree_smem, s>>>(
+        ps, P, b, y, out, mode, contact, nb, c, f, case_, c_out);
+    return true;
+}
 void launch_finalize(const DevMesh& dm, const DevParams& P, const d4* x_n, const d4* v, d4* x_np1,
                      unsigned long long* nonfinite, cudaStream_t s) {
     dc_note_launch();
     k_finalize<<<nblk(dm.m, dm.bs_node), dm.bs_node, 0, s>>>(dm.m, P.h, x_n, v, x_np1, nonfinite);
+}
+void launch_freeze(const DevMesh& dm, const DevParams& P, const int* inst_steps, int step, const int* step_base,
+                   const d4* xin, const d4* vin, d4* xout, d4* vout, int* contact, cudaStream_t s) {
+    dc_note_launch();
+    k_freeze<<<nblk(dm.m, 256), 256, 0, s>>>(dm.m, dm.m_free, P.node_inst, inst_steps, step, step_base, xin, vin,
+                                             xout, vout, contact);
+}
+void launch_set_int(int* p, int v, cudaStream_t s) {
+    dc_note_launch();
+    k_set_int<<<1, 1, 0, s>>>(p, v);
+}
+void launch_pass_adjoint(const DevMesh& dm, const DevParams& P, const int* inst_steps, int step, const d4* gv_in,
+                         d4* gv_out, cudaStream_t s) {
+    dc_note_launch();
+    k_pass_adjoint<<<nblk(dm.m, 256), 256, 0, s>>>(dm.m, P.node_inst, inst_steps, step, gv_in, gv_out);
 }
 void launch_mass_solve(const DevMesh& dm, const DevParams& P, const d4* b, d4* v, const int* contact, const d4* nb,
                        const double* c, d4* f, int* case_, cudaStream_t s) {

@@ -29,11 +29,6 @@ struct Request {
     std::vector<int32_t> tris, pins;
     int n_steps = 0;
     dc_params prm{};
-    // prepared
-    dc_ctx* c = nullptr;
-    MeshPrep mp;
-    ParamPrep pp;
-    size_t bytes = 0;
     // results
     bool done = false;
     dc_status status = DC_OK;
@@ -42,8 +37,17 @@ struct Request {
     std::vector<double> xN, vN, dx0, dv0;
     double dth[3] = {0, 0, 0};
     double t_submit = 0, t_admit = 0, t_done = 0;
-    size_t peak = 0;
+    size_t bytes = 0, peak = 0;
     long long adj_iters = 0;
+};
+
+// One or more requests prepared as one context (a batch when max_batch > 1).
+struct Job {
+    std::vector<Request*> reqs;
+    dc_ctx* c = nullptr;
+    MeshPrep mp;
+    ParamPrep pp;
+    size_t bytes = 0;
 };
 
 }  // namespace
@@ -53,7 +57,7 @@ struct dc_server {
     std::mutex mu;
     std::condition_variable cv;     // any state change
     std::deque<Request*> to_prep;
-    std::map<int64_t, Request*> ready;   // prepared, by ticket
+    std::map<int64_t, Job*> ready;       // prepared, by the ticket of their first request
     std::map<int64_t, Request*> all;
     int64_t next_ticket = 1;
     size_t reserved = 0, peak_reserved = 0;
@@ -63,6 +67,7 @@ struct dc_server {
     std::vector<std::thread> threads;
     std::vector<cudaStream_t> streams;
     std::vector<double*> pinned;
+    size_t pinned_doubles = 0;
     std::chrono::steady_clock::time_point t0;
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -86,9 +91,66 @@ void finish(dc_server* s, Request* r, dc_status st, const std::string& err) {
     s->cv.notify_all();
 }
 
+void finish_job(dc_server* s, Job* j, dc_status st, const std::string& err) {
+    for (Request* r : j->reqs) finish(s, r, st, err);
+}
+
+// Requests queued now whose shared parameters agree with the first one, up to
+// max_batch of them, leave the preparation queue together (caller holds s->mu).
+std::vector<Request*> take_group(dc_server* s) {
+    std::vector<Request*> g;
+    const int cap = std::max(1, s->cfg.max_batch);
+    g.push_back(s->to_prep.front());
+    s->to_prep.pop_front();
+    for (auto it = s->to_prep.begin(); it != s->to_prep.end() && (int)g.size() < cap;) {
+        if (dc_same_batch_fields((*it)->prm, g[0]->prm)) {
+            g.push_back(*it);
+            it = s->to_prep.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    return g;
+}
+
+// Host preparation of one job (meshes, ordering, factorisation, fronts,
+// footprint), without the server lock.  On failure j->c stays null.
+dc_status prepare_job(Job* j, std::string& err) {
+    const int B = (int)j->reqs.size();
+    dc_ctx* c = new dc_ctx();
+    c->async_alloc = true;
+    c->blocking_sync = true;
+    c->ihm.resize(B);
+    for (int i = 0; i < B; ++i) {
+        Request* r = j->reqs[i];
+        err = dc_build_mesh(c->ihm[i], (int)(r->rest.size() / 3), r->rest.data(), (int)(r->tris.size() / 3),
+                            r->tris.data(), (int)r->pins.size(), r->pins.empty() ? nullptr : r->pins.data());
+        if (!err.empty()) {
+            delete c;
+            return DC_ERR_INVALID;
+        }
+    }
+    prep_mesh_host(c, j->mp);
+    std::vector<dc_params> q;
+    int max_steps = 0;
+    for (Request* r : j->reqs) {
+        q.push_back(r->prm);
+        max_steps = std::max(max_steps, r->n_steps);
+    }
+    dc_status st = prep_params_host(c, q, j->pp);
+    if (st) {
+        err = c->err;
+        delete c;
+        return st;
+    }
+    j->c = c;
+    j->bytes = estimate_device_bytes(c, j->mp, j->pp, max_steps) + 4 * (size_t)B + 64;
+    return DC_OK;
+}
+
 void prep_loop(dc_server* s) {
     for (;;) {
-        Request* r;
+        std::vector<Request*> group;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
@@ -96,107 +158,144 @@ void prep_loop(dc_server* s) {
                        (!s->to_prep.empty() && (int)s->ready.size() + s->preparing < s->cfg.max_prepared);
             });
             if (s->to_prep.empty()) return;   // stop with nothing left
-            r = s->to_prep.front();
-            s->to_prep.pop_front();
+            group = take_group(s);
             s->preparing++;
         }
-        dc_status st = DC_OK;
-        std::string err;
-        dc_ctx* c = new dc_ctx();
-        c->async_alloc = true;
-        c->blocking_sync = true;
-        c->ihm.resize(1);
-        err = dc_build_mesh(c->ihm[0], (int)(r->rest.size() / 3), r->rest.data(), (int)(r->tris.size() / 3),
-                            r->tris.data(), (int)r->pins.size(), r->pins.empty() ? nullptr : r->pins.data());
-        if (!err.empty()) {
-            st = DC_ERR_INVALID;
-        } else {
-            prep_mesh_host(c, r->mp);
-            st = prep_params_host(c, std::vector<dc_params>(1, r->prm), r->pp);
-            if (st) err = c->err;
+        // a group that fails is prepared again request by request, so that a bad
+        // request fails alone and the others still run
+        std::vector<Job*> jobs(1, new Job());
+        jobs[0]->reqs = group;
+        std::vector<dc_status> st(1);
+        std::vector<std::string> err(1);
+        st[0] = prepare_job(jobs[0], err[0]);
+        if (st[0] && group.size() > 1) {
+            delete jobs[0];
+            jobs.clear();
+            st.clear();
+            err.clear();
+            for (Request* r : group) {
+                Job* j = new Job();
+                j->reqs.push_back(r);
+                std::string e;
+                st.push_back(prepare_job(j, e));
+                err.push_back(e);
+                jobs.push_back(j);
+            }
         }
         std::lock_guard<std::mutex> lk(s->mu);
         s->preparing--;
-        if (st) {
-            delete c;
-            finish(s, r, st, err);
-            continue;
+        for (size_t q = 0; q < jobs.size(); ++q) {
+            Job* j = jobs[q];
+            if (st[q]) {
+                finish_job(s, j, st[q], err[q]);
+                delete j;
+            } else if (j->bytes > (size_t)s->cfg.hbm_budget_bytes) {
+                delete j->c;
+                finish_job(s, j, DC_ERR_OOM,
+                           "request needs " + std::to_string(j->bytes) + " device bytes, more than the server's budget");
+                delete j;
+            } else {
+                s->ready[j->reqs[0]->ticket] = j;
+            }
         }
-        r->c = c;
-        r->bytes = estimate_device_bytes(c, r->mp, r->pp, r->n_steps);
-        if (r->bytes > (size_t)s->cfg.hbm_budget_bytes) {
-            delete c;
-            r->c = nullptr;
-            finish(s, r, DC_ERR_OOM,
-                   "request needs " + std::to_string(r->bytes) + " device bytes, more than the server's budget");
-            continue;
-        }
-        s->ready[r->ticket] = r;
         s->cv.notify_all();
     }
 }
 
-// Runs one admitted request on the slot's stream; returns its status.
-dc_status run_request(dc_server* s, Request* r, int slot, std::string& err) {
-    dc_ctx* c = r->c;
+// Runs one admitted job on the slot's stream; returns its status.
+dc_status run_job(dc_server* s, Job* j, int slot, std::string& err) {
+    dc_ctx* c = j->c;
+    const int B = (int)j->reqs.size();
     c->stream = s->streams[slot];
     c->device = s->cfg.device;
     c->kt.stream = c->stream;
     c->hpin = s->pinned[slot];
-    c->hpin_cap = 1024;
+    c->hpin_cap = s->pinned_doubles;
     c->hpin_external = true;
-    dc_status st = upload_mesh(c, r->mp);
-    if (!st) st = upload_params(c, r->pp);
-    r->mp = MeshPrep();
-    r->pp = ParamPrep();
-    const size_t n3 = r->x0.size();
-    r->xN.resize(n3);
-    r->vN.resize(n3);
-    r->dx0.resize(n3);
-    r->dv0.resize(n3);
+    dc_status st = upload_mesh(c, j->mp);
+    if (!st) st = upload_params(c, j->pp);
+    j->mp = MeshPrep();
+    j->pp = ParamPrep();
+    // concatenated inputs; instance i's nodes are [ext_off_i, ext_off_i + m_i)
+    std::vector<double> x0, v0, gx, gv;
+    std::vector<int32_t> steps(B);
+    bool any_gv = false;
+    int max_steps = 0;
+    for (int i = 0; i < B; ++i) {
+        Request* r = j->reqs[i];
+        x0.insert(x0.end(), r->x0.begin(), r->x0.end());
+        v0.insert(v0.end(), r->v0.begin(), r->v0.end());
+        gx.insert(gx.end(), r->gx.begin(), r->gx.end());
+        any_gv |= !r->gv.empty();
+        steps[i] = r->n_steps;
+        max_steps = std::max(max_steps, r->n_steps);
+    }
+    if (any_gv)
+        for (int i = 0; i < B; ++i) {
+            Request* r = j->reqs[i];
+            if (r->gv.empty())
+                gv.insert(gv.end(), r->x0.size(), 0.0);
+            else
+                gv.insert(gv.end(), r->gv.begin(), r->gv.end());
+        }
+    const size_t n3 = x0.size();
+    std::vector<double> xN(n3), vN(n3), dx0(n3), dv0(n3), dth(3 * (size_t)B);
+    if (!st && B > 1) st = dc_set_instance_steps(c, steps.data());
+    if (!st) st = dc_rollout(c, max_steps, x0.data(), v0.data(), xN.data(), vN.data(), nullptr);
     if (!st)
-        st = dc_rollout(c, r->n_steps, r->x0.data(), r->v0.data(), r->xN.data(), r->vN.data(), nullptr);
-    if (!st)
-        st = dc_backward(c, r->gx.data(), r->gv.empty() ? nullptr : r->gv.data(), nullptr, r->dx0.data(),
-                         r->dv0.data(), r->dth);
+        st = dc_backward(c, gx.data(), any_gv ? gv.data() : nullptr, nullptr, dx0.data(), dv0.data(), dth.data());
     if (st) err = c->err;
-    r->adj_iters = c->adj_iters;
-    r->peak = c->dev_peak;
+    for (int i = 0; i < B; ++i) {
+        Request* r = j->reqs[i];
+        const size_t lo = 3 * (size_t)c->inst[i].ext_off, hi = lo + r->x0.size();
+        r->xN.assign(xN.begin() + lo, xN.begin() + hi);
+        r->vN.assign(vN.begin() + lo, vN.begin() + hi);
+        r->dx0.assign(dx0.begin() + lo, dx0.begin() + hi);
+        r->dv0.assign(dv0.begin() + lo, dv0.begin() + hi);
+        for (int k = 0; k < 3; ++k) r->dth[k] = dth[3 * i + k];
+        r->adj_iters = c->adj_iters;
+        r->peak = c->dev_peak;
+        r->bytes = j->bytes;
+    }
     dc_destroy(c);
-    r->c = nullptr;
+    j->c = nullptr;
     return st;
 }
 
 void slot_loop(dc_server* s, int slot) {
     cudaSetDevice(s->cfg.device);
     for (;;) {
-        Request* r;
+        Job* j;
         {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv.wait(lk, [&] {
                 if (!s->ready.empty()) {
-                    Request* h = s->ready.begin()->second;
+                    Job* h = s->ready.begin()->second;
                     if (s->reserved + h->bytes <= (size_t)s->cfg.hbm_budget_bytes) return true;
                 }
                 return s->stop && s->ready.empty() && s->to_prep.empty() && s->preparing == 0;
             });
             if (s->ready.empty()) return;
-            r = s->ready.begin()->second;
+            j = s->ready.begin()->second;
             s->ready.erase(s->ready.begin());
-            s->reserved += r->bytes;
+            s->reserved += j->bytes;
             s->peak_reserved = std::max(s->peak_reserved, s->reserved);
-            s->in_flight++;
+            s->in_flight += (int64_t)j->reqs.size();
             s->peak_in_flight = std::max(s->peak_in_flight, s->in_flight);
-            r->slot = slot;
-            r->t_admit = s->now();
-            s->cv.notify_all();   // a prep thread may now prepare the next request
+            const double t = s->now();
+            for (Request* r : j->reqs) {
+                r->slot = slot;
+                r->t_admit = t;
+            }
+            s->cv.notify_all();   // a prep thread may now prepare the next job
         }
         std::string err;
-        dc_status st = run_request(s, r, slot, err);
+        dc_status st = run_job(s, j, slot, err);
         std::lock_guard<std::mutex> lk(s->mu);
-        s->reserved -= r->bytes;
-        s->in_flight--;
-        finish(s, r, st, err);
+        s->reserved -= j->bytes;
+        s->in_flight -= (int64_t)j->reqs.size();
+        finish_job(s, j, st, err);
+        delete j;
     }
 }
 
@@ -219,11 +318,15 @@ dc_status dc_server_create(dc_server** out, const dc_server_config* cfg) {
     dc_server* s = new dc_server();
     s->cfg = *cfg;
     s->t0 = std::chrono::steady_clock::now();
+    // pinned host scratch of a slot: what the batched GMRES needs for max_batch
+    // instances at the largest restart length (dc_ctx::hpin)
+    const size_t mb = (size_t)std::max(1, cfg->max_batch);
+    s->pinned_doubles = std::max<size_t>(1024, 3 * 257 * mb + 4 * mb + 64);
     for (int i = 0; i < cfg->n_slots; ++i) {
         cudaStream_t st;
         double* h;
         if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaMallocHost(&h, 1024 * sizeof(double)) != cudaSuccess) {
+            cudaMallocHost(&h, s->pinned_doubles * sizeof(double)) != cudaSuccess) {
             for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
             for (double* x : s->pinned) cudaFreeHost(x);
             delete s;
@@ -292,7 +395,7 @@ dc_status dc_server_wait(dc_server* s, int64_t ticket, dc_result* out) {
     out->t_submit = r->t_submit;
     out->t_admit = r->t_admit;
     out->t_done = r->t_done;
-    out->device_bytes = (int64_t)r->bytes;
+    out->device_bytes = (int64_t)r->bytes;   // the footprint of its job (a batch: all its requests)
     out->device_bytes_peak = (int64_t)r->peak;
     out->adj_iters = r->adj_iters;
     std::snprintf(out->message, sizeof(out->message), "%s", r->err.c_str());
@@ -322,10 +425,11 @@ void dc_server_destroy(dc_server* s) {
         s->cv.notify_all();
     }
     for (auto& t : s->threads) t.join();
-    for (auto& kv : s->all) {
+    for (auto& kv : s->ready) {
         if (kv.second->c) dc_destroy(kv.second->c);
         delete kv.second;
     }
+    for (auto& kv : s->all) delete kv.second;
     for (cudaStream_t x : s->streams) cudaStreamDestroy(x);
     for (double* x : s->pinned) cudaFreeHost(x);
     delete s;

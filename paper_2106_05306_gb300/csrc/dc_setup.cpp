@@ -264,7 +264,7 @@ std::string dc_build_mesh(HostMesh& hm, int m, const double* rest_pos, int T, co
 }
 
 dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vector<double>& mass,
-                          HostFactor& hf, std::string& err) {
+                          HostFactor& hf, std::string& err, bool symbolic_only) {
     const int n = hm.m_free;
     const double h2 = p.h * p.h;
     // ---- assemble the lower triangle of P_ff by columns (map per column)
@@ -355,6 +355,15 @@ dc_status dc_build_factor(const HostMesh& hm, const dc_params& p, const std::vec
         int q = hf.colptr[j];
         hf.rowidx[q++] = j;
         for (int r : st[j]) hf.rowidx[q++] = r;
+    }
+    if (symbolic_only) {
+        hf.fptr.assign(n + 1, 0);
+        hf.bptr.assign(n + 1, 0);
+        hf.fidx.clear();
+        hf.fval.clear();
+        hf.bidx.clear();
+        hf.bval.clear();
+        return DC_OK;
     }
     // row access: for row i, the (column k, position of i in column k) with k < i
     std::vector<std::vector<std::pair<int, int>>> rowpos(n);

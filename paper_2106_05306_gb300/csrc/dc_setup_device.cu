@@ -35,8 +35,13 @@ std::string normalise_params(dc_params& q) {
         q.n_pd_iters < 0 || q.n_obstacles < 0 || q.n_obstacles > DC_MAX_OBSTACLES || q.checkpoint_every < 1 ||
         q.adj_max_iters < 1 || q.adj_restart < 1 || !(q.adj_tol > 0) || q.adj_precond < 0 || q.adj_precond > 1 ||
         q.global_solver < 0 || q.global_solver > 1 || q.contact_compliance < DC_COMPLIANCE_ROWSUM ||
-        q.contact_compliance > DC_COMPLIANCE_MASS || q.adj_fallback < 0 || q.adj_fallback > 1)
+        q.contact_compliance > DC_COMPLIANCE_MASS || q.adj_fallback < 0 || q.adj_fallback > 1 ||
+        q.factor_on_gpu < 0 || q.factor_on_gpu > 1)
         return "invalid or non-finite parameter";
+    if (q.factor_on_gpu == 1 && q.global_solver != 1)
+        return "factor_on_gpu needs global_solver 1 (the GPU factor is written as supernodal panels)";
+    if (q.factor_on_gpu == 1 && q.contact_compliance == DC_COMPLIANCE_DIAG_PINV)
+        return "DC_COMPLIANCE_DIAG_PINV needs the host factor (factor_on_gpu 0)";
     if (q.adj_precond == 1 && q.global_solver != 0)
         return "adj_precond 1 needs global_solver 0 (it projects with the explicit inverse rows)";
     for (int o = 0; o < q.n_obstacles; ++o) {
@@ -62,15 +67,21 @@ std::string normalise_params(dc_params& q) {
     return "";
 }
 
+}  // namespace
+
 // The fields every instance of a batch must share.
-bool same_batch_fields(const dc_params& a, const dc_params& b) {
+bool dc_same_batch_fields(const dc_params& a, const dc_params& b) {
     return a.h == b.h && a.gravity[0] == b.gravity[0] && a.gravity[1] == b.gravity[1] &&
            a.gravity[2] == b.gravity[2] && a.contact_margin == b.contact_margin && a.adj_tol == b.adj_tol &&
            a.n_pd_iters == b.n_pd_iters && a.adj_max_iters == b.adj_max_iters && a.adj_restart == b.adj_restart &&
            a.checkpoint_every == b.checkpoint_every && a.adj_precond == b.adj_precond &&
            a.global_solver == b.global_solver && a.contact_compliance == b.contact_compliance &&
-           a.adj_fallback == b.adj_fallback;
+           a.adj_fallback == b.adj_fallback && a.factor_on_gpu == b.factor_on_gpu;
 }
+
+namespace {
+
+bool same_batch_fields(const dc_params& a, const dc_params& b) { return dc_same_batch_fields(a, b); }
 
 template <class T>
 size_t vbytes(const std::vector<T>& v) {
@@ -259,7 +270,7 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
         const HostMesh& h = c->ihm[i];
         std::vector<double> mass(h.m);
         for (int l = 0; l < h.m; ++l) mass[l] = q[i].density * h.abar[l];
-        st[i] = dc_build_factor(h, q[i], mass, hf[i], err[i]);
+        st[i] = dc_build_factor(h, q[i], mass, hf[i], err[i], q[i].factor_on_gpu == 1);
         if (st[i] == DC_OK && q[i].contact_compliance != DC_COMPLIANCE_ROWSUM) {
             // c_j per free node (internal order), reading of Eq. ly_et_al_govrningEq
             std::vector<double>& cv = ccon[i];
@@ -280,7 +291,7 @@ dc_status prep_params_host(dc_ctx* c, std::vector<dc_params> q, ParamPrep& pp) {
                 st[i] = DC_ERR_INVALID;
                 err[i] = fe;
             } else if (q[i].global_solver == 1) {
-                dc_build_psolve(hf[i], fr[i], psi[i]);
+                dc_build_psolve(hf[i], fr[i], psi[i], q[i].factor_on_gpu == 0);
             }
         }
         // only the explicit inverse rows, the size and the largest pivot are kept
@@ -528,8 +539,13 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         d4 *d_acc, *d_xint;
         if ((s = upload(c, F, &d_poff, pp.ps.poff)) || (s = upload(c, F, &d_xoff, pp.ps.xoff)) ||
             (s = upload(c, F, &d_toff, pp.ps.toff)) || (s = upload(c, F, &d_aoff, pp.ps.aoff)) ||
-            (s = upload(c, F, &d_panel, pp.ps.panel)) || (s = upload(c, F, &d_xinv, pp.ps.xinv)) ||
-            (s = upload(c, F, &d_pant, pp.ps.pant)) || (s = upload(c, F, &d_xinvt, pp.ps.xinvt)) ||
+            (pp.ps.panel.empty()   // factor_on_gpu: the GPU factorisation fills them below
+                 ? ((s = dalloc(c, F, &d_panel, (size_t)std::max<long long>(pp.ps.n_panel, 1), false)) ||
+                    (s = dalloc(c, F, &d_xinv, (size_t)std::max<long long>(pp.ps.n_xinv, 1), false)) ||
+                    (s = dalloc(c, F, &d_pant, (size_t)std::max<long long>(pp.ps.n_pant, 1), false)) ||
+                    (s = dalloc(c, F, &d_xinvt, (size_t)std::max<long long>(pp.ps.n_xinv, 1), false)))
+                 : ((s = upload(c, F, &d_panel, pp.ps.panel)) || (s = upload(c, F, &d_xinv, pp.ps.xinv)) ||
+                    (s = upload(c, F, &d_pant, pp.ps.pant)) || (s = upload(c, F, &d_xinvt, pp.ps.xinvt)))) ||
             (s = dalloc(c, F, &d_acc, (size_t)std::max<long long>(pp.ps.acc_nodes, 1))) ||
             (s = dalloc(c, F, &d_xint, (size_t)std::max(MF, 1))))
             return s;
@@ -581,6 +597,9 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
         ps.pull_idx = d_pull_idx;
         ps.fault = c->counters + 3;
         ps.tree = fd.tree;
+        // both sweeps of a global step in one launch (DC_SEPARATE_SWEEPS=1 in the
+        // environment: two launches, for comparison; the same results)
+        ps.fused = std::getenv("DC_SEPARATE_SWEEPS") ? 0 : 1;
         ps.sn = d_psn;
         ps.begin = d_begin;
         ps.f = d_f;
@@ -651,6 +670,7 @@ dc_status upload_params(dc_ctx* c, ParamPrep& pp) {
             P[B] = c->fr.lvl_ptr[l + 1];
         }
     }
+    if (pp.q[0].factor_on_gpu == 1) RET(gpu_factor_P(c, c->fr, pp.q[0].h));
     c->prm = pp.q[0];
     c->iprm = pp.q;
     c->have_params = true;
@@ -719,8 +739,14 @@ size_t estimate_device_bytes(const dc_ctx* c, const MeshPrep& mp, const ParamPre
     }
     if (q.global_solver == 1) {
         add(vbytes(pp.ps.poff)); add(vbytes(pp.ps.xoff)); add(vbytes(pp.ps.toff)); add(vbytes(pp.ps.aoff));
-        add(vbytes(pp.ps.panel)); add(vbytes(pp.ps.xinv)); add(vbytes(pp.ps.pant)); add(vbytes(pp.ps.xinvt));
+        add(8 * (size_t)pp.ps.n_panel); add(8 * (size_t)pp.ps.n_xinv); add(8 * (size_t)pp.ps.n_pant);
+        add(8 * (size_t)pp.ps.n_xinv);
         add(vbytes(pp.ps.aoff));
+        if (q.factor_on_gpu == 1) {   // temporary node-level fronts, their offsets and pair destinations
+            size_t ff = 0;
+            for (int s = 0; s < r.S; ++s) ff += (size_t)(r.f[s] / 3) * (r.f[s] / 3);
+            add(8 * ff); add(8 * ((size_t)r.S + 1)); add(8 * r.pr_i.size());
+        }
         add((size_t)pp.ps.acc_nodes * d4b); add(MF * d4b);
         // tree schedule: items (at most one per front), two ticket/flag arrays
         add(4 * ((size_t)r.S + 1)); add(4 * (size_t)r.S); add(8 * ((size_t)r.S + 1));

@@ -138,7 +138,7 @@ def oracle_along(specs, trajs, v0s, h, losses, pool, gradient=True, second_order
     for i in range(len(specs)):
         hper.append(hs[k:k + len(recs[i])])
         k += len(recs[i])
-    orders = [None, "MMD_AT_PLUS_A"] if second_ordering else [None]
+    orders = [None, "MMD_ATA"] if second_ordering else [None]
     jobs = [(specs[i], recs[i], hper[i], losses[i], o) for i in range(len(specs)) for o in orders]
     out = pool.map(_job_gradient, jobs, chunksize=1)
     grads = [tuple(out[len(orders) * i:len(orders) * (i + 1)]) if second_ordering else out[i]

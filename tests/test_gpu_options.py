@@ -167,3 +167,93 @@ def test_batch_hbm_bytes_bounds_the_memory_held():
     peak = b.stats()["device_bytes_peak"]
     b.close()
     assert peak <= est <= 1.5 * peak, (peak, est)
+
+
+@pytest.mark.parametrize("which", ["hanging_16x16", "draped_61x61", "batch_3", "capsules_200x200"])
+def test_gpu_factorisation_of_P_matches_the_host_factor(which):
+    """factor_on_gpu: P's numeric Cholesky on the GPU (multifrontal, FP64, into the
+    supernodal panels) solves the global step like the host factor and like the
+    oracle's banded Cholesky to 2e-11 (two factorisations in different orders
+    differ by about cond(P) eps, and cond(P) reaches 1e5 here); a short rollout and
+    its gradient agree with the host-factor context to 1e-9 / 1e-7 (gradients
+    below 1e-9 in absolute value, such as that of the bending stiffness of a
+    cloth still in free fall, are rounding and compared absolutely)."""
+    import time
+
+    import torch
+    if which == "batch_3":
+        scs = [scenes.batch_instance(s, n_steps=4) for s in (3, 15, 21)]
+    else:
+        scs = [{"hanging_16x16": scenes.hanging_cloth, "draped_61x61": scenes.draped_cloth,
+                "capsules_200x200": scenes.capsule_field}[which]()]
+    ctx, secs = [], []
+    for gpu in (0, 1):
+        t0 = time.perf_counter()
+        b = make_batch(scs, global_solver=1, factor_on_gpu=gpu, checkpoint_every=2)
+        torch.cuda.synchronize()
+        secs.append(time.perf_counter() - t0)
+        ctx.append(b)
+    print(f"{which}: context + parameters with the host factor {secs[0]:.2f} s, GPU factor {secs[1]:.2f} s")
+    rhs = cuda(np.random.default_rng(5).standard_normal((ctx[0].m, 3)))
+    a, g = ctx[0].global_solve(rhs), ctx[1].global_solve(rhs)
+    assert rel_inf(g.cpu().numpy(), a.cpu().numpy()) <= 2e-11
+    if which == "draped_61x61":
+        M = oracle_model(scs[0])
+        want = np.zeros((scs[0].m, 3))
+        want[M.free] = M.solve_P(rhs.cpu().numpy()[M.free])
+        assert rel_inf(g.cpu().numpy(), want) <= 2e-11
+    if which != "capsules_200x200":
+        cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
+        outs = []
+        for b in ctx:
+            xN, vN = b.rollout(cuda(cat("x0")), cuda(cat("v0")), 4)
+            outs.append((xN.cpu().numpy(), vN.cpu().numpy()) + tuple(
+                t.cpu().numpy() for t in b.backward(cuda(cat("loss_w")), allow_nonconverged=True)))
+        for k in range(2):
+            assert rel_inf(outs[1][k], outs[0][k]) <= STATE_TOL
+        for k in range(2, 5):
+            d = np.linalg.norm(np.ravel(outs[1][k] - outs[0][k]))
+            assert d <= GRAD_TOL * np.linalg.norm(np.ravel(outs[0][k])) + 1e-9, (k, d)
+    for b in ctx:
+        b.close()
+
+
+def test_gpu_factorisation_reports_a_non_positive_pivot():
+    import paper_2106_05306_gb300 as dc
+    sc = scenes.small_scene(4, seed=1)
+    cloth = dc.Cloth(sc.rest_pos, sc.tris, sc.pins)
+    with pytest.raises(dc.DCError, match="DC_ERR_NOT_SPD"):
+        cloth.set_params(density=5e-324, k_stretch=0.0, k_bend=0.0, global_solver=1, factor_on_gpu=1)
+    cloth.set_params(global_solver=1, factor_on_gpu=1)
+    cloth.close()
+
+
+@pytest.mark.parametrize("ck", [1, 2])
+def test_instances_of_different_lengths_in_one_batch(ck):
+    """dc_set_instance_steps: each instance of a batch takes its own number of steps
+    (then keeps its state, and its adjoint passes through the remaining steps):
+    every output is bitwise that of the instance rolled out alone for its steps."""
+    import torch
+    scs = [scenes.small_scene(5, seed=3, contact="both", drop=True), scenes.small_scene(4, seed=1, contact="sphere",
+                                                                                      drop=True),
+           scenes.small_scene(5, seed=2, contact="plane", drop=True)]
+    steps = [3, 6, 4]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = make_batch(scs, checkpoint_every=ck)
+        b.set_graphs(True)
+        b.set_instance_steps(steps)
+        cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
+        xN, vN = b.rollout(cuda(cat("x0")), cuda(cat("v0")), max(steps))
+        dx0, dv0, dth = b.backward(cuda(cat("loss_w")))
+    torch.cuda.synchronize()
+    o = b.node_offsets
+    for i, (sc, n) in enumerate(zip(scs, steps)):
+        c = make_cloth(sc, checkpoint_every=ck)
+        x1, v1 = c.rollout(cuda(sc.x0), cuda(sc.v0), n)
+        g = c.backward(cuda(sc.loss_w))
+        sl = slice(int(o[i]), int(o[i + 1]))
+        assert torch.equal(xN[sl], x1) and torch.equal(vN[sl], v1)
+        assert torch.equal(dx0[sl], g[0]) and torch.equal(dv0[sl], g[1]) and torch.equal(dth[i], g[2])
+        c.close()
+    b.close()

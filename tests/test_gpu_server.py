@@ -30,15 +30,19 @@ def _submit_all(srv, reqs):
             for sc, gv, kw in reqs]
 
 
-def test_server_results_match_alone_and_oracle():
+@pytest.mark.parametrize("max_batch", [1, 4])
+def test_server_results_match_alone_and_oracle(max_batch):
+    """max_batch 4: the requests submitted together are packed into batch contexts
+    of up to four cloths with their own step counts; each result is still bitwise
+    the request run alone."""
     import paper_2106_05306_gb300 as dc
     reqs = _requests()
-    srv = dc.Server(n_slots=3, n_prep_threads=2)
+    srv = dc.Server(n_slots=3, n_prep_threads=2, max_batch=max_batch)
     res = [srv.wait(t) for t in _submit_all(srv, reqs)]
     st = srv.stats()
     srv.close()
     assert st["completed"] == len(reqs) and st["failed"] == 0
-    assert 1 <= st["peak_in_flight"] <= 3
+    assert 1 <= st["peak_in_flight"] <= 3 * max_batch
     assert st["cloth_steps"] == sum(sc.n_steps for sc, _, _ in reqs)
     for i, ((sc, gv, kw), r) in enumerate(zip(reqs, res)):
         assert r["status"] == "DC_OK", r["message"]
@@ -87,12 +91,14 @@ def test_server_hbm_budget_bounds_admission():
     assert r["status"] == "DC_ERR_OOM" and r["slot"] == -1
 
 
-def test_server_bad_request_fails_alone():
+@pytest.mark.parametrize("max_batch", [1, 4])
+def test_server_bad_request_fails_alone(max_batch):
     """A request with an out-of-range triangle index fails with DC_ERR_INVALID; the
-    requests around it still finish with the same results as alone."""
+    requests around it (also those packed into the same batch) still finish with
+    the same results as alone."""
     import paper_2106_05306_gb300 as dc
     reqs = _requests()[:3]
-    srv = dc.Server(n_slots=2, n_prep_threads=2)
+    srv = dc.Server(n_slots=2, n_prep_threads=2, max_batch=max_batch)
     t_ok1 = _submit_all(srv, reqs[:1])[0]
     sc, gv, kw = reqs[1]
     bad_tris = sc.tris.copy()

@@ -147,3 +147,32 @@ def test_supernodal_sweep_wait_gives_up_and_reports():
     assert rel_inf(got, want) < 1e-11
     fresh.stats()
     fresh.close()
+
+
+def test_fused_sweeps_are_bitwise_the_two_launches():
+    """Both substitution sweeps of a global step in one tree-scheduled launch (the
+    default) give the same bits as the forward and backward sweeps launched one
+    after the other (DC_SEPARATE_SWEEPS=1), for a rollout and its gradient."""
+    import os
+
+    import torch
+    scs = [scenes.batch_instance(s, n_steps=3) for s in (3, 15)]
+    for sc in scs:
+        sc.x0 = sc.x0 - np.array([0.0, 0.3, 0.0])   # start near the sphere: contacts in three steps
+    out = []
+    for separate in (False, True):
+        if separate:
+            os.environ["DC_SEPARATE_SWEEPS"] = "1"
+        try:
+            b = make_batch(scs, global_solver=1, checkpoint_every=1)
+        finally:
+            os.environ.pop("DC_SEPARATE_SWEEPS", None)
+        cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
+        xN, vN = b.rollout(cuda(cat("x0")), cuda(cat("v0")), 3)
+        g = b.backward(cuda(cat("loss_w")), allow_nonconverged=True)
+        st = b.stats()
+        out.append((xN, vN) + tuple(g))
+        b.close()
+    assert st["contacts_stick"] + st["contacts_slip"] > 0
+    for a, c in zip(out[0], out[1]):
+        assert torch.equal(a, c)

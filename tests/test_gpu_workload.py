@@ -10,9 +10,9 @@
 
 The oracle recomputes every step from the GPU's own state (one step at a time,
 in a pool of processes) and solves the direct adjoint along those steps, so each
-comparison is on identical inputs: states to 1e-9 per step, gradients to 1e-7
-with the GPU adjoint solved to a relative residual of 1e-12 (the parity reading of
-the adjoint tolerance; the benchmark runs at 1e-10).
+comparison is on identical inputs: states to 1e-9 per step; gradients to 1e-7,
+or to the oracle's own rounding spread scaled to the GPU adjoint's backward error
+(a relative residual of 1e-12; the benchmark runs at 1e-10), whichever is larger.
 """
 import numpy as np
 import pytest
@@ -32,19 +32,27 @@ def pool():
     p.join()
 
 
+ADJ_TOL = 1e-12          # the GPU adjoint's relative residual in these tests
+EPS = 2.0 ** -52
+
+
 def _check_grad(got, pair, label=""):
-    """GPU gradient against the oracle's: within GRAD_TOL relative, or within ten
-    times the oracle's own spread between two sparse-LU orderings (what rounding
-    the ill-conditioned adjoint systems amplify; the arithmetic leaves nothing
-    tighter to demand of either side)."""
+    """GPU gradient against the oracle's: within GRAD_TOL relative, or within the
+    oracle's own spread between two sparse-LU orderings scaled from the direct
+    solve's backward error (eps) to the GPU's (ADJ_TOL).  The spread is what the
+    ill-conditioned adjoint systems make of a backward error of eps; to first
+    order the forward error grows linearly with the backward error, and the GPU's
+    Krylov solve stops at a relative residual of ADJ_TOL, not at eps (reading
+    R10).  dL/dtheta sums per-step terms that cancel by two to three orders of
+    magnitude, so it shows this first."""
     want, want2 = pair
     for k, name in enumerate(("dL/dx0", "dL/dv0", "dL/dtheta")):
         err = np.linalg.norm(np.ravel(got[k]) - np.ravel(want[k]))
         spread = np.linalg.norm(np.ravel(want2[k]) - np.ravel(want[k]))
         ref = np.linalg.norm(np.ravel(want[k]))
         print(f"{label} {name}: |GPU - oracle| / |oracle| = {err / ref:.2e}, oracle ordering spread "
-              f"{spread / ref:.2e}")
-        assert err <= max(GRAD_TOL * ref, 10.0 * spread), (name, err / ref, spread / ref)
+              f"{spread / ref:.2e}, scaled to the GPU's residual {spread * ADJ_TOL / EPS / ref:.2e}")
+        assert err <= max(GRAD_TOL * ref, spread * ADJ_TOL / EPS), (name, err / ref, spread / ref)
 
 
 def test_batched_workload_solver1_parity(pool):
@@ -55,7 +63,7 @@ def test_batched_workload_solver1_parity(pool):
     import torch
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):       # the context's stream: capturable, unlike the legacy default one
-        b = make_batch(scs, checkpoint_every=1, global_solver=1, adj_tol=1e-12)
+        b = make_batch(scs, checkpoint_every=1, global_solver=1, adj_tol=ADJ_TOL)
         b.autotune()
         b.set_graphs(True)
     cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
@@ -100,7 +108,7 @@ def test_draped_61x61_checkpointed_gradient_parity(pool):
     import paper_2106_05306_gb300 as dc
     sc = scenes.draped_cloth()
     p = sc.params
-    cloth = make_cloth(sc, checkpoint_every=25, adj_tol=1e-12)
+    cloth = make_cloth(sc, checkpoint_every=25, adj_tol=ADJ_TOL)
     cloth.allow_nonconverged = True   # steps ended at their rounding floor are still compared below
     x0 = cuda(sc.x0).requires_grad_(True)
     v0 = cuda(sc.v0).requires_grad_(True)
@@ -133,7 +141,7 @@ def test_large_capsule_field_200x200(pool):
     import torch
     sc = scenes.capsule_field()
     h = sc.params.h
-    cloth = make_cloth(sc, checkpoint_every=10, global_solver=1, adj_tol=1e-12)
+    cloth = make_cloth(sc, checkpoint_every=10, global_solver=1, adj_tol=ADJ_TOL)
     n0, n1 = 46, 5                 # the highest capsule is reached at about step 43
     _, _, tr = cloth.rollout(cuda(sc.x0), cuda(sc.v0), n0, traj=True)
     tr = tr.cpu().numpy()
