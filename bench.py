@@ -86,8 +86,11 @@ def parse_args(argv=None):
     ap.add_argument("--batch", type=int, default=BATCH, help="cloths in the batch (256 for the workload)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain / single / served side runs")
-    ap.add_argument("--served-requests", type=int, default=64, help="requests of the served side run")
-    ap.add_argument("--served-rates", default="4,16,64", help="Poisson arrival rates (per s) of the served run")
+    ap.add_argument("--served-requests", type=int, default=None,
+                    help="requests of the served run (64 as a side run, 2000 for --workload served)")
+    ap.add_argument("--served-rates", default=None,
+                    help="Poisson arrival rates (per s) of the served run (side run: 4,16,64; --workload served: "
+                         "0.5, 1 and 2 times the capacity measured by a first run with every request at once)")
     ap.add_argument("--served-max-batch", type=int, default=16, help="requests packed into one batch context")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-all-cores", action="store_true", help=argparse.SUPPRESS)
@@ -400,13 +403,16 @@ def single_side_run(args, dev):
             "nonconverged_cloth_steps": st["adj_nonconverged"]}
 
 
-def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000, max_batch=16, plain_sample=None):
+def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000, max_batch=16, plain_sample=None,
+                    relative=False):
     """Served runs: n_req requests (1k-30k DOF, 25-150 steps, random sphere + ground,
     mu 0.1-0.6) with Poisson arrivals into the request server, one run per arrival
     rate; requests queued together are packed into batch contexts of up to
     max_batch cloths (supernodal solver, P factorised on the GPU); then the same
-    requests one at a time through the plain path.  The served value is the best
-    throughput of the sweep (the server saturated)."""
+    requests one at a time through the plain path.  With relative, a first run
+    submits every request at once and measures the service capacity (requests/s),
+    and rates are multiples of it.  The served value is the best throughput of
+    the sweep (the server saturated)."""
     import threading
 
     import torch
@@ -416,9 +422,15 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000
     reqs = [scenes.serve_request(seed0 + i) for i in range(n_req)]
     steps = sum(sc.n_steps for sc in reqs)
     sweep = []
-    for rate in rates:
+    runs = ([None] + list(rates)) if relative else list(rates)
+    capacity = None
+    for rate in runs:
         rng = np.random.default_rng(4242)
-        gaps = rng.exponential(1.0 / rate, n_req)
+        if rate is None:
+            gaps = np.zeros(n_req)
+        else:
+            rate = rate * capacity if relative else rate
+            gaps = rng.exponential(1.0 / rate, n_req)
         srv = dc.Server(n_slots=slots, n_prep_threads=4, device=dev.index or 0, max_batch=max_batch)
         tickets = [None] * n_req
 
@@ -438,7 +450,10 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000
         srv.close()
         lat = sorted(r["t_done"] - r["t_submit"] for r in res)
         ok = sum(r["status"] in ("DC_OK", "DC_ERR_NONCONVERGED") for r in res)
-        sweep.append({"rate_per_s": rate, "value": steps / makespan, "completed": ok,
+        if rate is None:
+            capacity = n_req / makespan
+        sweep.append({"rate_per_s": rate if rate is not None else "all at once", "value": steps / makespan,
+                      "completed": ok,
                       "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "peak_in_flight": st["peak_in_flight"], "peak_reserved_gb": st["peak_bytes_reserved"] / 1e9})
     # the same requests one at a time (plain path, no server)
@@ -460,6 +475,7 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000
             c.close()
     best = max(sweep, key=lambda r: r["value"])
     return {"value": best["value"], "unit": UNIT, "requests": n_req, "slots": slots, "max_batch": max_batch,
+            "capacity_requests_per_s": capacity,
             "p50_latency_s": best["p50_latency_s"], "p99_latency_s": best["p99_latency_s"],
             "at_rate_per_s": best["rate_per_s"], "rate_sweep": sweep,
             "plain_sequential": {"value": plain_steps / plain_s, "unit": UNIT,
@@ -543,7 +559,9 @@ def kernel_table(wl, peaks, steps_per_pass=1):
             wl.step()
         st = wl.ctx.stats()
         wl.ctx.set_kernel_timer("none")
-        n = max(st["timer_launches"], 1)
+        if st["timer_launches"] == 0 or not st["timer_ms"] > 0.0:
+            continue   # no kernel of this class runs on this path (e.g. the separate sweeps when fused)
+        n = st["timer_launches"]
         ms = st["timer_ms"] / steps_per_pass
         row = {"kernels": KERNEL_CLASSES[cls], "ms_per_bench_step": ms,
                "launches_per_bench_step": st["timer_launches"] / steps_per_pass,
@@ -559,8 +577,7 @@ def kernel_table(wl, peaks, steps_per_pass=1):
                         "achieved_gbs": b / sec / 1e9, "hbm_frac": b / sec / 1e9 / peaks["hbm_gbs"],
                         "achieved_tflops": f / sec / 1e12, "alu_frac": f / sec / 1e12 / alu_peak})
             row["bound"] = "alu" if row["alu_frac"] >= row["hbm_frac"] else "hbm"
-        if st["timer_launches"] > 0:
-            rows[cls] = row
+        rows[cls] = row
     total = sum(r["ms_per_bench_step"] for r in rows.values())
     for r in rows.values():
         r["share_of_timed_kernels"] = r["ms_per_bench_step"] / total if total > 0 else None
@@ -607,9 +624,9 @@ def run_served(args):
     torch.cuda.set_device(dev)
     clocks = ClockSampler(local)
     clocks.start()
-    sv = served_side_run(dev, n_req=args.served_requests,
-                         rates=tuple(float(r) for r in args.served_rates.split(",")),
-                         max_batch=args.served_max_batch, plain_sample=64)
+    sv = served_side_run(dev, n_req=args.served_requests or 2000,
+                         rates=tuple(float(r) for r in (args.served_rates or "0.5,1,2").split(",")),
+                         max_batch=args.served_max_batch, plain_sample=64, relative=args.served_rates is None)
     clk = clocks.stop()
     out = {"metric": METRIC, "value": sv["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -701,8 +718,8 @@ def run_ours(args):
         out["plain"] = plain_sample(args, dev, wl.n_cloth)
         out["batched_vs_plain"] = value / out["plain"]["value"]
         out["single_61x61"] = single_side_run(args, dev)
-        out["served"] = served_side_run(dev, n_req=args.served_requests,
-                                        rates=tuple(float(r) for r in args.served_rates.split(",")),
+        out["served"] = served_side_run(dev, n_req=args.served_requests or 64,
+                                        rates=tuple(float(r) for r in (args.served_rates or "4,16,64").split(",")),
                                         max_batch=args.served_max_batch)
         out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
