@@ -70,7 +70,21 @@ HBM_FALLBACK_GBS = 6800.0
 
 # DRAM read + write bytes per launch measured by ncu on this workload (the
 # kernel-traffic profile; null once the kernel's source file has changed).
-TRAFFIC = {}
+# DRAM read + write per full-size launch from one ncu capture of the 256-cloth batch
+# (profiles/kernel_traffic_batched_256cloths.md), valid while the kernel's source
+# file is the one measured (its hash).
+TRAFFIC = {
+    "front": {"source": "dc_frontal.cu", "source_sha": "89a6c5a5ab4cb2f3", "bytes_per_launch": 945.14e6,
+              "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the 9 levels of one "
+                      "factorisation, 256 cloths (profiles/kernel_traffic_batched_256cloths.md)"},
+    "sweeps": {"source": "dc_kernels.cu", "source_sha": "232ea24582784521", "bytes_per_launch": 747.46e6,
+               "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, 256 cloths "
+                       "(profiles/kernel_traffic_batched_256cloths.md)"},
+    "local": {"source": "dc_kernels.cu", "source_sha": "232ea24582784521", "bytes_per_launch": 182.29e6,
+              "note": "ncu, 256 cloths (profiles/kernel_traffic_batched_256cloths.md)"},
+    "gather": {"source": "dc_kernels.cu", "source_sha": "232ea24582784521", "bytes_per_launch": 149.42e6,
+               "note": "ncu, 256 cloths (profiles/kernel_traffic_batched_256cloths.md)"},
+}
 
 
 def parse_args(argv=None):
@@ -91,7 +105,8 @@ def parse_args(argv=None):
     ap.add_argument("--served-rates", default=None,
                     help="Poisson arrival rates (per s) of the served run (side run: 4,16,64; --workload served: "
                          "0.5, 1 and 2 times the capacity measured by a first run with every request at once)")
-    ap.add_argument("--served-max-batch", type=int, default=16, help="requests packed into one batch context")
+    ap.add_argument("--served-max-batch", type=int, default=None,
+                    help="requests packed into one batch context (side run 16, --workload served 64)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-all-cores", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -452,8 +467,11 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000
         ok = sum(r["status"] in ("DC_OK", "DC_ERR_NONCONVERGED") for r in res)
         if rate is None:
             capacity = n_req / makespan
+        statuses = {}
+        for r in res:
+            statuses[r["status"]] = statuses.get(r["status"], 0) + 1
         sweep.append({"rate_per_s": rate if rate is not None else "all at once", "value": steps / makespan,
-                      "completed": ok,
+                      "completed": ok, "statuses": statuses, "batch_retries": st["batch_retries"],
                       "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "peak_in_flight": st["peak_in_flight"], "peak_reserved_gb": st["peak_bytes_reserved"] / 1e9})
     # the same requests one at a time (plain path, no server)
@@ -626,7 +644,8 @@ def run_served(args):
     clocks.start()
     sv = served_side_run(dev, n_req=args.served_requests or 2000,
                          rates=tuple(float(r) for r in (args.served_rates or "0.5,1,2").split(",")),
-                         max_batch=args.served_max_batch, plain_sample=64, relative=args.served_rates is None)
+                         max_batch=args.served_max_batch or 64, plain_sample=64,
+                         relative=args.served_rates is None)
     clk = clocks.stop()
     out = {"metric": METRIC, "value": sv["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -720,7 +739,7 @@ def run_ours(args):
         out["single_61x61"] = single_side_run(args, dev)
         out["served"] = served_side_run(dev, n_req=args.served_requests or 64,
                                         rates=tuple(float(r) for r in (args.served_rates or "4,16,64").split(",")),
-                                        max_batch=args.served_max_batch)
+                                        max_batch=args.served_max_batch or 16)
         out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_subprocess(args.workload)

@@ -486,6 +486,9 @@ typedef struct dc_server_stats {
     int64_t in_flight, peak_in_flight;
     int64_t bytes_reserved, peak_bytes_reserved;
     int64_t cloth_steps;         /* forward steps of the completed requests             */
+    int64_t batch_retries;       /* batches that failed and whose requests were run
+                                    again one per context (a request that fails alone
+                                    no longer takes its batch-mates with it)         */
 } dc_server_stats;
 
 /* Start a server (threads and streams) on cfg->device. */

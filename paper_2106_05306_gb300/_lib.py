@@ -84,7 +84,7 @@ class dc_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("failed", ctypes.c_int64),
                 ("in_flight", ctypes.c_int64), ("peak_in_flight", ctypes.c_int64),
                 ("bytes_reserved", ctypes.c_int64), ("peak_bytes_reserved", ctypes.c_int64),
-                ("cloth_steps", ctypes.c_int64)]
+                ("cloth_steps", ctypes.c_int64), ("batch_retries", ctypes.c_int64)]
 
 
 KT_CLASSES = {"none": 0, "solve_fwd": 1, "solve_bwd": 2, "local": 3, "gather": 4, "front": 5, "msolve": 6,

@@ -29,6 +29,7 @@ struct Request {
     std::vector<int32_t> tris, pins;
     int n_steps = 0;
     dc_params prm{};
+    bool solo = false;   // runs in a context of its own (after its batch failed)
     // results
     bool done = false;
     dc_status status = DC_OK;
@@ -62,6 +63,7 @@ struct dc_server {
     int64_t next_ticket = 1;
     size_t reserved = 0, peak_reserved = 0;
     int64_t in_flight = 0, peak_in_flight = 0, submitted = 0, completed = 0, failed = 0, steps = 0;
+    int64_t batch_retries = 0;   // batches whose requests were run again one by one
     int preparing = 0;
     bool stop = false;
     std::vector<std::thread> threads;
@@ -95,21 +97,33 @@ void finish_job(dc_server* s, Job* j, dc_status st, const std::string& err) {
     for (Request* r : j->reqs) finish(s, r, st, err);
 }
 
-// Requests queued now whose shared parameters agree with the first one, up to
-// max_batch of them, leave the preparation queue together (caller holds s->mu).
+// The oldest queued request and up to max_batch - 1 others whose shared
+// parameters agree with it leave the preparation queue together (caller holds
+// s->mu).  A batch runs as many steps as its longest request, so among the
+// compatible requests those with the step counts closest to the first one's are
+// taken (the older one on ties).  Solo requests go alone.
 std::vector<Request*> take_group(dc_server* s) {
     std::vector<Request*> g;
     const int cap = std::max(1, s->cfg.max_batch);
     g.push_back(s->to_prep.front());
     s->to_prep.pop_front();
-    for (auto it = s->to_prep.begin(); it != s->to_prep.end() && (int)g.size() < cap;) {
-        if (dc_same_batch_fields((*it)->prm, g[0]->prm)) {
-            g.push_back(*it);
-            it = s->to_prep.erase(it);
-        } else {
-            ++it;
-        }
+    if (g[0]->solo || cap == 1) return g;
+    std::vector<std::pair<long long, size_t>> cand;   // (|step difference|, queue position)
+    for (size_t q = 0; q < s->to_prep.size(); ++q) {
+        const Request* r = s->to_prep[q];
+        if (!r->solo && dc_same_batch_fields(r->prm, g[0]->prm))
+            cand.push_back({std::llabs((long long)r->n_steps - g[0]->n_steps), q});
     }
+    const size_t take = std::min(cand.size(), (size_t)cap - 1);
+    std::partial_sort(cand.begin(), cand.begin() + take, cand.end());
+    std::vector<size_t> pos;
+    for (size_t k = 0; k < take; ++k) pos.push_back(cand[k].second);
+    std::sort(pos.begin(), pos.end());
+    for (size_t k = pos.size(); k-- > 0;) {
+        g.push_back(s->to_prep[pos[k]]);
+        s->to_prep.erase(s->to_prep.begin() + (long)pos[k]);
+    }
+    std::sort(g.begin() + 1, g.end(), [](const Request* a, const Request* b) { return a->ticket < b->ticket; });
     return g;
 }
 
@@ -294,7 +308,18 @@ void slot_loop(dc_server* s, int slot) {
         std::lock_guard<std::mutex> lk(s->mu);
         s->reserved -= j->bytes;
         s->in_flight -= (int64_t)j->reqs.size();
-        finish_job(s, j, st, err);
+        if (st != DC_OK && st != DC_ERR_NONCONVERGED && j->reqs.size() > 1) {
+            // one request can fail a whole batch (a non-finite state, say): run
+            // each of them again in a context of its own, ahead of the queue
+            for (size_t q = j->reqs.size(); q-- > 0;) {
+                j->reqs[q]->solo = true;
+                s->to_prep.push_front(j->reqs[q]);
+            }
+            s->batch_retries++;
+            s->cv.notify_all();
+        } else {
+            finish_job(s, j, st, err);
+        }
         delete j;
     }
 }
@@ -414,6 +439,7 @@ dc_status dc_server_get_stats(dc_server* s, dc_server_stats* o) {
     o->bytes_reserved = (int64_t)s->reserved;
     o->peak_bytes_reserved = (int64_t)s->peak_reserved;
     o->cloth_steps = s->steps;
+    o->batch_retries = s->batch_retries;
     return DC_OK;
 }
 

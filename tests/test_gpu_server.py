@@ -117,3 +117,34 @@ def test_server_bad_request_fails_alone(max_batch):
         dx0, _, _ = cl.backward(cuda(sc.loss_w), cuda(gv))
         cl.close()
         assert np.array_equal(r["x_final"], xN.cpu().numpy()) and np.array_equal(r["dL_dx0"], dx0.cpu().numpy())
+
+
+def test_failing_request_does_not_fail_its_batch():
+    """A request whose x0 holds a NaN fails its whole batch context (the forward's
+    non-finite flag is per context); the server then runs that batch's requests
+    again one per context, so only the bad request fails and the others are
+    bitwise their alone results."""
+    import paper_2106_05306_gb300 as dc
+    reqs = _requests()[:4]
+    bad_sc, bad_gv, bad_kw = reqs[0]
+    x0_bad = bad_sc.x0.copy()
+    x0_bad[1, 0] = np.nan
+    srv = dc.Server(n_slots=1, n_prep_threads=1, max_batch=8)
+    tickets = _submit_all(srv, reqs)
+    t_bad = srv.submit(bad_sc.rest_pos, bad_sc.tris, bad_sc.pins, x0_bad, bad_sc.v0, bad_sc.loss_w, bad_sc.n_steps,
+                       bad_kw, dL_dv=bad_gv)
+    res = [srv.wait(t) for t in tickets]
+    r_bad = srv.wait(t_bad)
+    st = srv.stats()
+    srv.close()
+    assert r_bad["status"] == "DC_ERR_NONFINITE", r_bad["status"]
+    assert st["batch_retries"] >= 1 and st["completed"] == len(reqs) and st["failed"] == 1
+    for i, ((sc, gv, kw), r) in enumerate(zip(reqs, res)):
+        assert r["status"] == "DC_OK", (i, r["status"], r["message"])
+        cl = make_cloth(sc, checkpoint_every=2)
+        xN, vN = cl.rollout(cuda(sc.x0), cuda(sc.v0), sc.n_steps)
+        dx0, dv0, dth = cl.backward(cuda(sc.loss_w), cuda(gv))
+        cl.close()
+        assert np.array_equal(r["x_final"], xN.cpu().numpy()), i
+        assert np.array_equal(r["dL_dx0"], dx0.cpu().numpy()), i
+        assert np.array_equal(r["dL_dparams"], dth.cpu().numpy()), i
