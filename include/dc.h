@@ -337,6 +337,13 @@ dc_status dc_backward(dc_ctx* ctx, const double* dL_dx_final, const double* dL_d
                       const double* dL_dtraj_x, double* dL_dx0, double* dL_dv0,
                       double* dL_dparams);
 
+/* Per instance of a batch (host array of n_instances entries): the adjoint steps
+ * since creation that stopped above adj_tol (the count dc_stats.adj_nonconverged
+ * sums), so that a caller can tell which instances a DC_ERR_NONCONVERGED from
+ * dc_backward concerns.  The counts are host bookkeeping that dc_backward
+ * updates; the call does no device work.  DC_ERR_INVALID on a null argument. */
+dc_status dc_get_instance_nonconverged(dc_ctx* ctx, int64_t* counts);
+
 /* Apply P_ff^-1 (the prefactorised global-step matrix restricted to free
  * nodes, Eq. pd_global) to three right-hand-side columns: out = P^-1 rhs.
  * rhs, out: [m][3]; entries of pinned nodes are ignored on input and set to 0. */

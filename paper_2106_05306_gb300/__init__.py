@@ -328,6 +328,14 @@ class ClothBatch(_Context):
                                         ctypes.c_void_p(stream)), None)
         self._init_common(ctx, device)
 
+    def instance_nonconverged(self):
+        """Per instance: adjoint steps since creation that stopped above adj_tol
+        (which instances a non-converged backward concerns)."""
+        import numpy as np
+        out = np.zeros(self.n_instances, dtype=np.int64)
+        check(self._lib.dc_get_instance_nonconverged(self._ctx, out.ctypes.data), self._ctx)
+        return out
+
     def set_params(self, params):
         """params: one dict for every instance, or a list of n_instances dicts.  Only
         k_stretch, k_bend, density, mu and obstacles may differ between instances."""

@@ -114,6 +114,7 @@ SIGNATURES = {
     "dc_global_solve": (ctypes.c_int32, [_P, _P, _P]),
     "dc_global_solve_static": (ctypes.c_int32, [_P, _P, _P]),
     "dc_debug_sweep_wait_timeout": (ctypes.c_int32, [_P, ctypes.c_int32]),
+    "dc_get_instance_nonconverged": (ctypes.c_int32, [_P, _P]),
     "dc_debug_front_factor": (ctypes.c_int32, [ctypes.c_int32, ctypes.c_int32, _P, _P, _P, ctypes.c_int32,
                                                ctypes.c_int32, ctypes.c_int32]),
     "dc_get_stats": (ctypes.c_int32, [_P, ctypes.POINTER(dc_stats)]),

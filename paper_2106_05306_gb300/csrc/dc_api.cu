@@ -576,6 +576,12 @@ dc_status dc_debug_sweep_wait_timeout(dc_ctx* c, int32_t skip_items) {
     return check_device_flags(c);
 }
 
+dc_status dc_get_instance_nonconverged(dc_ctx* c, int64_t* counts) {
+    if (!c || !counts) return DC_ERR_INVALID;
+    for (int i = 0; i < c->B; ++i) counts[i] = i < (int)c->inst_noncv.size() ? (int64_t)c->inst_noncv[i] : 0;
+    return DC_OK;
+}
+
 dc_status dc_debug_front_factor(int32_t n, int32_t p, const float* A, float* out, float* linv_out,
                                 int32_t threads, int32_t use_tc, int32_t use_gscr) {
     std::string err;

@@ -142,6 +142,7 @@ struct dc_ctx {
     GraphCache g_roll, g_seg[2];
     // stats
     long long steps = 0, adj_steps = 0, adj_iters = 0, adj_max_seen = 0, adj_noncv = 0;
+    std::vector<long long> inst_noncv;   // per instance: adjoint steps stopped above adj_tol
     double adj_last_res = 0.0;
     long long n_factorisations = 0;
     long long adj_batch_iters = 0;

@@ -730,12 +730,14 @@ dc_status adjoint_step(dc_ctx* c, const d4* x_n, const d4* x1, const d4* v1, int
                 }
         }
     }
+    if ((int)c->inst_noncv.size() != c->B) c->inst_noncv.assign(c->B, 0);
     for (int i = 0; i < c->B; ++i) {
         c->adj_steps++;
         c->adj_iters += it[i];
         c->adj_max_seen = std::max<long long>(c->adj_max_seen, it[i]);
         if (!(rel[i] <= c->prm.adj_tol * 1.0000001)) {
             c->adj_noncv++;
+            c->inst_noncv[i]++;
             noncv = true;
         }
     }

@@ -216,8 +216,10 @@ void prep_loop(dc_server* s) {
     }
 }
 
-// Runs one admitted job on the slot's stream; returns its status.
-dc_status run_job(dc_server* s, Job* j, int slot, std::string& err) {
+// Runs one admitted job on the slot's stream; returns the context's status, and
+// in inst[i] that of request i (a non-converged adjoint concerns only the
+// instances whose steps stopped above adj_tol).
+dc_status run_job(dc_server* s, Job* j, int slot, std::string& err, std::vector<dc_status>& inst) {
     dc_ctx* c = j->c;
     const int B = (int)j->reqs.size();
     c->stream = s->streams[slot];
@@ -259,6 +261,10 @@ dc_status run_job(dc_server* s, Job* j, int slot, std::string& err) {
     if (!st)
         st = dc_backward(c, gx.data(), any_gv ? gv.data() : nullptr, nullptr, dx0.data(), dv0.data(), dth.data());
     if (st) err = c->err;
+    inst.assign(B, st);
+    if (st == DC_ERR_NONCONVERGED)
+        for (int i = 0; i < B; ++i)
+            inst[i] = (i < (int)c->inst_noncv.size() && c->inst_noncv[i] > 0) ? DC_ERR_NONCONVERGED : DC_OK;
     for (int i = 0; i < B; ++i) {
         Request* r = j->reqs[i];
         const size_t lo = 3 * (size_t)c->inst[i].ext_off, hi = lo + r->x0.size();
@@ -304,7 +310,8 @@ void slot_loop(dc_server* s, int slot) {
             s->cv.notify_all();   // a prep thread may now prepare the next job
         }
         std::string err;
-        dc_status st = run_job(s, j, slot, err);
+        std::vector<dc_status> inst;
+        dc_status st = run_job(s, j, slot, err, inst);
         std::lock_guard<std::mutex> lk(s->mu);
         s->reserved -= j->bytes;
         s->in_flight -= (int64_t)j->reqs.size();
@@ -318,7 +325,8 @@ void slot_loop(dc_server* s, int slot) {
             s->batch_retries++;
             s->cv.notify_all();
         } else {
-            finish_job(s, j, st, err);
+            for (size_t q = 0; q < j->reqs.size(); ++q)
+                finish(s, j->reqs[q], inst[q], inst[q] == DC_OK ? std::string() : err);
         }
         delete j;
     }

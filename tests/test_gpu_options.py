@@ -139,6 +139,26 @@ def test_adjoint_fallback_and_nonconverged():
         on.close()
 
 
+def test_nonconverged_counts_per_instance():
+    """dc_get_instance_nonconverged: with adj_max_iters = 1 and the fallback off,
+    every adjoint step an instance takes stops above adj_tol, and the steps past
+    an instance's own count (its adjoint passes through) are not counted."""
+    import paper_2106_05306_gb300 as dc
+    scs = [scenes.small_scene(5, seed=3, contact="both", drop=True), scenes.small_scene(4, seed=1, contact="sphere",
+                                                                                        drop=True),
+           scenes.small_scene(5, seed=2, contact="plane", drop=True)]
+    steps = [3, 1, 2]
+    b = make_batch(scs, adj_max_iters=1, adj_fallback=0)
+    b.set_instance_steps(steps)
+    cat = lambda k: np.concatenate([getattr(s, k) for s in scs])
+    b.rollout(cuda(cat("x0")), cuda(cat("v0")), max(steps))
+    with pytest.raises(dc.DCError, match="DC_ERR_NONCONVERGED"):
+        b.backward(cuda(cat("loss_w")))
+    assert list(b.instance_nonconverged()) == steps
+    assert b.stats()["adj_nonconverged"] == sum(steps)
+    b.close()
+
+
 def test_underflowing_mass_is_not_spd():
     """A density so small that the lumped masses underflow to 0, with no stiffness:
     P = M has a zero pivot, which the factorisation reports."""
