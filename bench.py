@@ -470,8 +470,10 @@ def served_side_run(dev, n_req=32, rates=(4.0, 16.0, 64.0), slots=4, seed0=10000
         statuses = {}
         for r in res:
             statuses[r["status"]] = statuses.get(r["status"], 0) + 1
+        failed = [i for i, r in enumerate(res) if r["status"] not in ("DC_OK", "DC_ERR_NONCONVERGED")]
         sweep.append({"rate_per_s": rate if rate is not None else "all at once", "value": steps / makespan,
                       "completed": ok, "statuses": statuses, "batch_retries": st["batch_retries"],
+                      "failed_request_seeds": [seed0 + i for i in failed][:50],
                       "p50_latency_s": float(np.percentile(lat, 50)), "p99_latency_s": float(np.percentile(lat, 99)),
                       "peak_in_flight": st["peak_in_flight"], "peak_reserved_gb": st["peak_bytes_reserved"] / 1e9})
     # the same requests one at a time (plain path, no server)

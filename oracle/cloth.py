@@ -52,6 +52,27 @@ Readings of passages the paper leaves open (the CUDA path implements the same on
      one KKT system; stick nodes constrain z_j = 0, slip nodes constrain
      (n - mu t).z_j = 0 (oblique), and the slip friction direction adds
      h mu f_N b b^T / |u_T| to the matrix (the paper's -Delta R).
+  R13 node-node self-collision (the J_n paragraph after Eq.
+     implicit_with_contact; off unless params.self_thickness > 0): a pair of
+     nodes (i, j), i < j, at least one free, sharing no triangle, is in contact
+     when their predicted positions are within self_thickness + delta.  Its
+     row of J_n acts on the relative velocity v_i - v_j with the normal
+     n = (x_i - x_j)/|x_i - x_j| at x_n and the bias beta = (|x_i - x_j| -
+     self_thickness)/h, so that an active pair ends at least self_thickness
+     apart; the impulse acts as +r on i and -r on j.  As R5's row sum, its
+     compliance is the Gershgorin bound of the pairs' coupling,
+     c_k = sum_l |h (e_i - e_j)^T P^-1 (e_p - e_q)| over the step's pairs
+     l = (p, q) (pinned nodes contribute nothing), which keeps the Jacobi
+     iteration over pairs that share nodes from overshooting.  Within an
+     iteration the pairs are solved from the global step's v_half, Jacobi-style
+     beside the obstacle contacts; node i moves by w_i (r_new - r_old) and node
+     j by -w_j (r_new - r_old), w_i and w_j proportional to h (P^-1_ii - P^-1_ij)
+     and h (P^-1_jj - P^-1_ij) with w_i + w_j = c_k.
+     At a fixed point the write-backs vanish and the step satisfies
+     Eq. implicit_with_contact with the pair rows exactly.  The adjoint adds
+     the pair rows to the KKT system (stick: z_i - z_j = 0; slip:
+     (n - mu t).(z_i - z_j) = 0) with the friction term on the relative
+     velocity, and the derivatives of n and beta with respect to x_i and x_j.
 """
 from __future__ import annotations
 
@@ -135,6 +156,7 @@ class Model:
         self.k_b = float(params.k_bend)
         self.g = np.asarray(params.gravity, dtype=np.float64)
         self.delta = float(params.contact_margin)
+        self.self_thickness = float(getattr(params, "self_thickness", 0.0))
         self.compliance_mode = getattr(params, "contact_compliance", "rowsum")
         if self.compliance_mode not in ("rowsum", "diag_pinv", "diag_p", "mass"):
             raise ValueError(self.compliance_mode)
@@ -254,6 +276,63 @@ class Model:
         return Contacts(np.array(nodes, dtype=np.int64), np.array(obs, dtype=np.int64),
                         np.array(normals).reshape(-1, 3), np.array(betas, dtype=np.float64))
 
+    def detect_self(self, x_n, v_n):
+        """Self-contact pairs (R13) from the predicted positions x_n + h v_n."""
+        from scipy.spatial import cKDTree
+        d_s = self.self_thickness
+        xp = x_n + self.h * v_n
+        if not hasattr(self, "_adjacent"):
+            adj = set()
+            for t in self.tris:
+                for a in range(3):
+                    for b in range(3):
+                        if t[a] < t[b]:
+                            adj.add((int(t[a]), int(t[b])))
+            self._adjacent = adj
+        pairs = sorted(cKDTree(xp).query_pairs(d_s + self.delta + 1e-12))
+        ii, jj = [], []
+        for a, b in pairs:
+            i, j = (a, b) if a < b else (b, a)
+            if (i, j) in self._adjacent or (self.is_pin[i] and self.is_pin[j]):
+                continue
+            if np.linalg.norm(xp[i] - xp[j]) <= d_s + self.delta:
+                ii.append(i)
+                jj.append(j)
+        ii = np.array(ii, dtype=np.int64)
+        jj = np.array(jj, dtype=np.int64)
+        d = x_n[ii] - x_n[jj]
+        dist = np.linalg.norm(d, axis=1)
+        normals = d / dist[:, None] if len(ii) else np.zeros((0, 3))
+        wi, wj = self._pair_weights(ii, jj)
+        return SelfContacts(ii, jj, normals.reshape(-1, 3), dist, (dist - d_s) / self.h, wi, wj)
+
+    def _pair_weights(self, ii, jj):
+        """Write-back weights of the pairs (R13): w_i : w_j = h (P^-1_ii - P^-1_ij) :
+        h (P^-1_jj - P^-1_ij), scaled so that w_i + w_j is the pair's compliance
+        c_k = sum_l |h (e_i - e_j)^T P^-1 (e_p - e_q)| (free nodes only: a pinned
+        node has no row of P and its entries are 0)."""
+        nf = len(self.free)
+        pos = -np.ones(self.m, dtype=np.int64)
+        pos[self.free] = np.arange(nf)
+        npr = len(ii)
+        D = np.zeros((nf, npr))                       # columns e_i - e_j (free rows)
+        for a, (i, j) in enumerate(zip(ii, jj)):
+            if pos[i] >= 0:
+                D[pos[i], a] = 1.0
+            if pos[j] >= 0:
+                D[pos[j], a] = -1.0
+        PD = self.solve_P(D) if npr else D            # P^-1 (e_i - e_j)
+        W = self.h * (D.T @ PD)                       # pair coupling h (e_k)^T P^-1 (e_l)
+        c = np.abs(W).sum(axis=1)
+        wi, wj = np.zeros(npr), np.zeros(npr)
+        for a, (i, j) in enumerate(zip(ii, jj)):
+            # h P^-1 (e_i - e_j) restricted to rows i and -j
+            ai = self.h * PD[pos[i], a] if pos[i] >= 0 else 0.0
+            aj = -self.h * PD[pos[j], a] if pos[j] >= 0 else 0.0
+            wi[a] = c[a] * ai / (ai + aj)
+            wj[a] = c[a] * aj / (ai + aj)
+        return wi, wj
+
     def compliance(self, contacts):
         """c_j = h (P^-1 1_I)_j for the current contact set (R5), or the
         ablation choices h (P^-1)_jj, h / P_jj, h / m_j."""
@@ -282,6 +361,19 @@ class Contacts:
 
     def __len__(self):
         return len(self.nodes)
+
+
+class SelfContacts:
+    """Node-node contact pairs (R13): nodes i < j, normal n from j to i at x_n,
+    distance d = |x_i - x_j| at x_n, bias beta = (d - thickness)/h, and the
+    write-back weights w_i, w_j with compliance c = w_i + w_j."""
+
+    def __init__(self, i, j, normals, dist, betas, wi, wj):
+        self.i, self.j, self.normals, self.dist, self.betas, self.wi, self.wj = i, j, normals, dist, betas, wi, wj
+        self.c = wi + wj
+
+    def __len__(self):
+        return len(self.i)
 
 
 # ----------------------------------------------------------------------------
@@ -592,9 +684,15 @@ def signorini_coulomb(vt, n, beta, mu, c):
 class StepRecord:
     """What the adjoint needs from a converged forward step."""
 
-    def __init__(self, x_n, v_n, x_np1, v_np1, contacts, forces, cases, c, iters):
+    def __init__(self, x_n, v_n, x_np1, v_np1, contacts, forces, cases, c, iters, pairs=None, pair_forces=None,
+                 pair_cases=None):
         self.x_n, self.v_n, self.x_np1, self.v_np1 = x_n, v_n, x_np1, v_np1
         self.contacts, self.forces, self.cases, self.c, self.iters = contacts, forces, cases, c, iters
+        # self-contact pairs (R13): SelfContacts, their impulses r (on node i) and cases
+        self.pairs = pairs if pairs is not None else SelfContacts(*([np.zeros(0, np.int64)] * 2),
+                                                                  np.zeros((0, 3)), *([np.zeros(0)] * 4))
+        self.pair_forces = pair_forces if pair_forces is not None else np.zeros((0, 3))
+        self.pair_cases = pair_cases if pair_cases is not None else np.zeros(0, dtype=np.int64)
 
 
 def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace=None):
@@ -623,6 +721,10 @@ def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace
     nc = len(contacts)
     f = np.zeros((nc, 3))
     cases = np.zeros(nc, dtype=np.int64)
+    pairs = model.detect_self(x_n, v_n) if model.self_thickness > 0.0 else None   # R13
+    npr = len(pairs) if pairs is not None else 0
+    fp = np.zeros((npr, 3))
+    pcases = np.zeros(npr, dtype=np.int64)
     v = v_n.copy()
     if n_iters is None and tol is None:
         n_iters = model.params.n_pd_iters
@@ -643,6 +745,9 @@ def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace
         rhs = bhat.copy()
         if nc:
             rhs[contacts.nodes] += h * f                           # Eq. pd_velocity_with_contact
+        if npr:                                                    # pair rows: +r on i, -r on j
+            np.add.at(rhs, pairs.i, h * fp)
+            np.add.at(rhs, pairs.j, -h * fp)
         v_half = np.zeros_like(v)
         if mass_split:
             v_half[free] = rhs[free] / model.mass[free][:, None]   # global step of the mass splitting
@@ -652,18 +757,28 @@ def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace
             trace.append(model.g_tilde(x_n + h * v_half, y, R, pb))
         v_new = v_half
         f_new = np.zeros_like(f)
+        if npr:
+            v_new = v_half.copy()
         for a in range(nc):                                        # per-node contact solve
             j = contacts.nodes[a]
             vt = v_half[j] - c[a] * f[a]
             f_new[a], v_new[j], cases[a] = signorini_coulomb(
                 vt, contacts.normals[a], contacts.betas[a], model.mu, c[a])
+        fp_new = np.zeros_like(fp)
+        for a in range(npr):                                       # pair solves from v_half (R13)
+            i, j = pairs.i[a], pairs.j[a]
+            ut = v_half[i] - v_half[j] - pairs.c[a] * fp[a]
+            fp_new[a], _, pcases[a] = signorini_coulomb(ut, pairs.normals[a], pairs.betas[a], model.mu, pairs.c[a])
+            dr = fp_new[a] - fp[a]
+            v_new[i] += pairs.wi[a] * dr
+            v_new[j] -= pairs.wj[a] * dr
         dv = np.max(np.abs(v_new - v)) if v.size else 0.0
-        v, f = v_new, f_new
+        v, f, fp = v_new, f_new, fp_new
         k += 1
         if tol is not None and dv <= tol * max(np.max(np.abs(v)), 1e-3):
             break
     x_np1 = x_n + h * v
-    return x_np1, v, StepRecord(x_n, v_n, x_np1, v, contacts, f, cases, c, k)
+    return x_np1, v, StepRecord(x_n, v_n, x_np1, v, contacts, f, cases, c, k, pairs, fp, pcases)
 
 
 def rollout(model: Model, x0, v0, n_steps, n_iters=None, tol=None):
@@ -777,8 +892,8 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None, permc_spec=No
             for e in range(3):
                 col = np.zeros(3)
                 col[e] = 1.0
-                Bcols.append((base, col))
-                Ccols.append((base, col))
+                Bcols.append([(base, col)])
+                Ccols.append([(base, col)])
         elif rec.cases[a] == SLIP:
             uT = v1[j] - np.dot(nrm, v1[j]) * nrm
             nt = np.linalg.norm(uT)
@@ -789,18 +904,52 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None, permc_spec=No
             for r_ in range(3):
                 for c_ in range(3):
                     H[base + r_, base + c_] += blk[r_, c_]
-            Bcols.append((base, nrm.copy()))
-            Ccols.append((base, nrm - mu * th))
+            Bcols.append([(base, nrm.copy())])
+            Ccols.append([(base, nrm - mu * th)])
             tdirs[a] = (th, nt, fN)
+    # self-contact pairs (R13): rows on the relative velocity, +1 block at i, -1 at j
+    prs = rec.pairs
+    pdirs = {}
+    for a in range(len(prs)):
+        i, j = prs.i[a], prs.j[a]
+        nrm = prs.normals[a]
+        ends = [(3 * pos_of[i], 1.0)] if pos_of[i] >= 0 else []
+        if pos_of[j] >= 0:
+            ends.append((3 * pos_of[j], -1.0))
+        if rec.pair_cases[a] == STICK:
+            for e in range(3):
+                col = np.zeros(3)
+                col[e] = 1.0
+                Bcols.append([(b, sg * col) for b, sg in ends])
+                Ccols.append([(b, sg * col) for b, sg in ends])
+        elif rec.pair_cases[a] == SLIP:
+            u = v1[i] - v1[j]
+            uT = u - np.dot(nrm, u) * nrm
+            nt = np.linalg.norm(uT)
+            th = uT / nt
+            bh = np.cross(nrm, th)
+            fN = float(np.dot(rec.pair_forces[a], nrm))
+            blk = h * mu * fN / nt * np.outer(bh, bh)
+            for b1, s1 in ends:
+                for b2, s2 in ends:
+                    for r_ in range(3):
+                        for c_ in range(3):
+                            H[b1 + r_, b2 + c_] += s1 * s2 * blk[r_, c_]
+            Bcols.append([(b, sg * nrm) for b, sg in ends])
+            Ccols.append([(b, sg * (nrm - mu * th)) for b, sg in ends])
+            pdirs[a] = (th, nt, fN)
     H = H.tocsr()
     nf3 = 3 * len(free)
     nk = len(Bcols)
     Bm = sp.lil_matrix((nf3, nk))
     Cm = sp.lil_matrix((nf3, nk))
-    for col, ((base, bv), (_, cv)) in enumerate(zip(Bcols, Ccols)):
-        for e in range(3):
-            Bm[base + e, col] = bv[e]
-            Cm[base + e, col] = cv[e]
+    for col, (bblocks, cblocks) in enumerate(zip(Bcols, Ccols)):
+        for base, bv in bblocks:
+            for e in range(3):
+                Bm[base + e, col] += bv[e]
+        for base, cv in cblocks:
+            for e in range(3):
+                Cm[base + e, col] += cv[e]
     K = sp.bmat([[H, Bm.tocsr()], [Cm.tocsr().T, None]], format="csc")
     rhs = np.concatenate([g[free].reshape(-1), np.zeros(nk)])
     sol = spla.spsolve(K, rhs, permc_spec=permc_spec) if nk or nf3 else rhs
@@ -846,6 +995,37 @@ def adjoint_step(model: Model, rec: StepRecord, gx, gv, hess=None, permc_spec=No
             dx_n[j] += h * fN * (Dn - mu * Dt).T @ z[j]
             # G_j = n.v_j + beta: dG/dx_n = Dn^T v_j + n / h
             dx_n[j] -= (Dn.T @ vj + nrm / h) * psi
+    # self-contact pairs (R13): n = (x_i - x_j)/d and beta = (d - thickness)/h depend on
+    # x_i (derivatives Dn = (I - n n^T)/d and n/h) and on x_j (their negatives)
+    for a in range(len(prs)):
+        i, j = prs.i[a], prs.j[a]
+        nrm = prs.normals[a]
+        Dn = (np.eye(3) - np.outer(nrm, nrm)) / prs.dist[a]
+        beta = prs.betas[a]
+        if rec.pair_cases[a] == STICK:
+            psi = eta[col:col + 3]
+            col += 3
+            # G = v_i - v_j + beta n:  dG/dx_i = beta Dn + n n^T / h = -dG/dx_j
+            gi = beta * Dn.T @ psi + nrm * np.dot(nrm, psi) / h
+            dx_n[i] -= gi
+            dx_n[j] += gi
+        elif rec.pair_cases[a] == SLIP:
+            psi = eta[col]
+            col += 1
+            th, nt, fN = pdirs[a]
+            u = v1[i] - v1[j]
+            dz = z[i] - z[j]
+            dmu += -h * fN * np.dot(th, dz)
+            dPiu = -(np.dot(nrm, u) * np.eye(3) + np.outer(nrm, u)) @ Dn
+            Dt = (np.eye(3) - np.outer(th, th)) @ dPiu / nt
+            # F_i holds -h f_N (n - mu t) and F_j its negative
+            gi = h * fN * (Dn - mu * Dt).T @ dz
+            dx_n[i] += gi
+            dx_n[j] -= gi
+            # G = n.(v_i - v_j) + beta: dG/dx_i = Dn^T u + n / h = -dG/dx_j
+            gi = (Dn.T @ u + nrm / h) * psi
+            dx_n[i] -= gi
+            dx_n[j] += gi
     return dx_n, dv_n, np.array([dks, dkb, dmu]), z, eta
 
 

@@ -85,6 +85,8 @@ class Params:
     contact_margin: float = 1e-6   # detection margin delta (m)
     # compliance of the per-node contact solve: "rowsum", "diag_pinv", "diag_p" or "mass"
     contact_compliance: str = "rowsum"
+    # node-node self-collision: the distance two nodes keep (m); 0 turns it off
+    self_thickness: float = 0.0
 
 
 @dataclasses.dataclass
@@ -326,3 +328,29 @@ def serve_request(seed: int, dof_lo: float = 1e3, dof_hi: float = 3e4, steps_lo:
     prm = Params(k_stretch=ks, k_bend=kb, density=0.1, mu=mu, h=1.0 / 120.0)
     return Scene(f"request_{seed}_{n}_{n_steps}", n, pos, tris, np.zeros(0, np.int32), obst, prm,
                  pos.copy(), np.zeros_like(pos), n_steps, loss_weights(n * n, seed))
+
+
+def two_patches_scene(n: int = 4, gap: float = 0.025, approach: float = 1.0, slide: float = 0.3,
+                      thickness: float = 0.02, mu: float = 0.3, gravity: bool = False, seed: int = 0,
+                      n_steps: int = 3) -> Scene:
+    """Node-node self-collision: two n x n patches (side 0.3 m) in one mesh, the
+    upper `gap` above the lower and shifted sideways by a fifth of the thickness, moving
+    down at `approach` m/s and sideways at `slide` m/s with small seeded noise; no
+    obstacle and, by default, no gravity (so that momentum is conserved)."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5E1F]))
+    lo, tris = grid_mesh(n, side=0.3, height=0.0, x0=-0.15, z0=0.0)
+    hi = lo.copy()
+    hi[:, 1] = gap
+    hi[:, 0] += 0.2 * thickness
+    pos = np.vstack([lo, hi])
+    tris = np.vstack([tris, tris + n * n]).astype(np.int32)
+    m = 2 * n * n
+    v0 = np.zeros((m, 3))
+    v0[n * n:, 1] = -approach
+    v0[n * n:, 0] = slide
+    v0 += 0.02 * rng.standard_normal((m, 3))
+    x0 = pos + 0.002 * rng.standard_normal((m, 3))
+    prm = Params(k_stretch=200.0, k_bend=1e-3, density=0.1, mu=mu, h=1.0 / 120.0,
+                 gravity=GRAVITY if gravity else (0.0, 0.0, 0.0), self_thickness=thickness)
+    return Scene(f"two_patches_{n}_{seed}", n, pos, tris, np.zeros(0, np.int32), [], prm, x0, v0, n_steps,
+                 loss_weights(m, seed))

@@ -680,3 +680,84 @@ def test_continuity_study_analytic_vs_triangulated_sphere():
         return np.abs(np.diff(np.array(g)))
     js, jm = sweep(-1), sweep(1)
     assert jm.sum() > 10.0 * js.sum()
+
+
+# ----------------------------------------------------------------- self-collision (R13)
+
+def _pairs_sig(recs):
+    return [(tuple(r.pairs.i), tuple(r.pairs.j), tuple(r.pair_cases)) for r in recs]
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0), dict(approach=3.0)])
+def test_self_contact_conserves_momentum_and_keeps_the_thickness(kw):
+    """Two cloth patches driven into each other without gravity or obstacles:
+    the pair impulses are equal and opposite and the PD forces are internal, so
+    the total momentum is unchanged by every step; and a converged step leaves
+    every detected pair at least the thickness apart (u_N = d'(t) + (d -
+    thickness)/h >= 0 holds along the pair's normal, R13)."""
+    sc = scenes.two_patches_scene(**kw)
+    M = oc.model_from_scene(sc)
+    for tol in (None, 1e-13):
+        xs, vs, recs = oc.rollout(M, sc.x0, sc.v0, sc.n_steps, tol=tol)
+        assert sum(len(r.pairs) for r in recs) > 0
+        assert any(np.any(r.pair_cases != oc.TAKEOFF) for r in recs)
+        p0 = (M.mass[:, None] * sc.v0).sum(axis=0)
+        for v in vs[1:]:
+            p = (M.mass[:, None] * v).sum(axis=0)
+            assert np.max(np.abs(p - p0)) <= 1e-13 * np.max(np.abs(p0))
+        if tol is not None:
+            for n, r in enumerate(recs):
+                if len(r.pairs):
+                    d = np.linalg.norm(xs[n + 1][r.pairs.i] - xs[n + 1][r.pairs.j], axis=1)
+                    assert np.min(d) >= sc.params.self_thickness - 1e-12
+
+
+def test_self_contact_without_pairs_is_the_plain_step():
+    """Self-collision on, but the patches too far apart for any pair: every
+    step is bitwise the step with self-collision off."""
+    sc = scenes.two_patches_scene(gap=0.3, approach=0.5)
+    on = oc.model_from_scene(sc)
+    off = oc.model_from_scene(sc, self_thickness=0.0)
+    xa, va, ra = oc.rollout(on, sc.x0, sc.v0, sc.n_steps)
+    xb, vb, rb = oc.rollout(off, sc.x0, sc.v0, sc.n_steps)
+    assert sum(len(r.pairs) for r in ra) == 0
+    assert all(np.array_equal(a, b) for a, b in zip(xa, xb)) and all(np.array_equal(a, b) for a, b in zip(va, vb))
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0)])
+def test_self_contact_adjoint_matches_central_differences(kw):
+    """The KKT adjoint with pair rows (slip pairs; a mix of stick and slip pairs)
+    agrees with central differences of the converged forward map for x0, v0,
+    k_stretch, k_bend and mu, where the pairs and their cases are unchanged at
+    +-eps (the derivatives of the pair normal and bias with respect to both
+    nodes, and the friction term on the relative velocity, are all exercised)."""
+    sc = scenes.two_patches_scene(n_steps=2, **kw)
+    M, xs, vs, recs = _run(sc)
+    base = _pairs_sig(recs)
+    assert any(np.any(r.pair_cases == oc.SLIP) for r in recs)
+    xi = sc.loss_w
+    gx0, gv0, dth = oc.rollout_gradient(M, recs, xi)
+
+    def loss_at(**kw2):
+        x0 = kw2.pop("x0", sc.x0)
+        v0 = kw2.pop("v0", sc.v0)
+        _, xs2, _, recs2 = _run(dataclasses.replace(sc, x0=x0, v0=v0), **kw2)
+        assert _pairs_sig(recs2) == base
+        return np.sum(xi * xs2[-1])
+
+    p = sc.params
+    # relative steps of 1e-4: the tolerance-mode forward (thousands of Jacobi
+    # iterations over the pairs) leaves ~1e-14 of noise in the loss, which a
+    # 1e-6 step of the small bending stiffness would amplify past the bound
+    for idx, (name, val) in enumerate([("k_stretch", p.k_stretch), ("k_bend", p.k_bend), ("mu", p.mu)]):
+        e = 1e-4 * val
+        fd = (loss_at(**{name: val + e}) - loss_at(**{name: val - e})) / (2 * e)
+        assert abs(dth[idx] - fd) <= 2e-6 * max(abs(fd), 1e-3 * np.abs(dth).max()), (name, dth[idx], fd)
+    rng = np.random.default_rng(7)
+    for which in ("x0", "v0"):
+        d = rng.standard_normal(sc.x0.shape)
+        e = 1e-7
+        b = getattr(sc, which)
+        fd = (loss_at(**{which: b + e * d}) - loss_at(**{which: b - e * d})) / (2 * e)
+        adj = np.sum((gx0 if which == "x0" else gv0) * d)
+        assert abs(adj - fd) <= 1e-6 * abs(fd), (which, adj, fd)
