@@ -106,7 +106,7 @@ def parse_args(argv=None):
                     help="Poisson arrival rates (per s) of the served run (side run: 4,16,64; --workload served: "
                          "0.5, 1 and 2 times the capacity measured by a first run with every request at once)")
     ap.add_argument("--served-max-batch", type=int, default=None,
-                    help="requests packed into one batch context (side run 16, --workload served 64)")
+                    help="requests packed into one batch context (default 64)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--cpu-all-cores", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
@@ -741,7 +741,7 @@ def run_ours(args):
         out["single_61x61"] = single_side_run(args, dev)
         out["served"] = served_side_run(dev, n_req=args.served_requests or 64,
                                         rates=tuple(float(r) for r in (args.served_rates or "4,16,64").split(",")),
-                                        max_batch=args.served_max_batch or 16)
+                                        max_batch=args.served_max_batch or 64)
         out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline_subprocess(args.workload)
