@@ -724,13 +724,15 @@ def test_self_contact_without_pairs_is_the_plain_step():
     assert all(np.array_equal(a, b) for a, b in zip(xa, xb)) and all(np.array_equal(a, b) for a, b in zip(va, vb))
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0)])
+@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0), dict(pinned=True, gravity=True)])
 def test_self_contact_adjoint_matches_central_differences(kw):
     """The KKT adjoint with pair rows (slip pairs; a mix of stick and slip pairs)
     agrees with central differences of the converged forward map for x0, v0,
     k_stretch, k_bend and mu, where the pairs and their cases are unchanged at
     +-eps (the derivatives of the pair normal and bias with respect to both
-    nodes, and the friction term on the relative velocity, are all exercised)."""
+    nodes, and the friction term on the relative velocity, are all exercised);
+    also with gravity and pinned nodes among the pairs (a pinned node has no
+    row in the adjoint system)."""
     sc = scenes.two_patches_scene(n_steps=2, **kw)
     M, xs, vs, recs = _run(sc)
     base = _pairs_sig(recs)
@@ -756,6 +758,7 @@ def test_self_contact_adjoint_matches_central_differences(kw):
     rng = np.random.default_rng(7)
     for which in ("x0", "v0"):
         d = rng.standard_normal(sc.x0.shape)
+        d[sc.pins] = 0.0
         e = 1e-7
         b = getattr(sc, which)
         fd = (loss_at(**{which: b + e * d}) - loss_at(**{which: b - e * d})) / (2 * e)
