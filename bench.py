@@ -55,6 +55,14 @@ BATCH_WORKLOAD = ("batched: 256 cloths in one context, grids 16x16..64x64 (unifo
                   "k_bend, mu of every cloth")
 SINGLE_STEPS = 125
 SINGLE_CK = 25
+CAPS_CLOTHS = 32
+CAPS_STEPS = 100
+CAPS_CK = 10
+CAPS_WORKLOAD = ("large: 32 cloths of 200x200 nodes (40000 nodes, 79202 triangles each) in one context, each dropped "
+                 "onto the same 8 seeded capsules (radius 0.02-0.1 m) and the ground, mu 0.4, seed-varied stretch and "
+                 "bending stiffness (k_stretch 1e3 and k_bend 1e-3 times e^U(-0.7, 0.7)), 100 steps at h=1/240 s, "
+                 "20 PD iterations/step, checkpoints every 10 steps (recomputed in the backward), forward + adjoint, "
+                 "gradient w.r.t. x0, v0, k_stretch, k_bend, mu of every cloth")
 SINGLE_WORKLOAD = ("draped cloth 61x61 (3721 nodes, 7200 triangles), sphere r=0.3 m + ground plane, "
                    "125 steps at h=1/120 s, 20 PD iterations/step, forward + checkpointed adjoint (every 25 steps), "
                    "gradient w.r.t. x0, v0, k_stretch, k_bend, mu")
@@ -93,7 +101,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["batch", "single", "served"], default="batch")
+    ap.add_argument("--workload", choices=["batch", "single", "served", "capsules"], default="batch")
     ap.add_argument("--roofline-kernel", default=None, help="kernel class timed for the roofline")
     ap.add_argument("--rollout-steps", type=int, default=None,
                     help="cloth steps per rollout (default: the workload's; ncu launch lists use a shorter one)")
@@ -328,6 +336,25 @@ class Workload:
                 cat = lambda k: torch.tensor(np.concatenate([getattr(s, k) for s in self.scs]), device=dev)
                 self.x0, self.v0, self.xi = cat("x0"), cat("v0"), cat("loss_w")
                 self.cloths = len(self.scs)
+            elif kind == "capsules":
+                self.n_cloth = args.rollout_steps or CAPS_STEPS
+                base = scenes.capsule_field(n_steps=CAPS_STEPS)
+                self.scs = [base] * CAPS_CLOTHS
+                self.ctx = dc.ClothBatch([(base.rest_pos, base.tris, base.pins)] * CAPS_CLOTHS, device=dev)
+                kws = []
+                for seed in range(CAPS_CLOTHS):
+                    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xCA95, 1]))
+                    f_s, f_b = np.exp(rng.uniform(-0.7, 0.7, 2))
+                    kws.append(scene_kw(base, k_stretch=base.params.k_stretch * f_s, k_bend=base.params.k_bend * f_b,
+                                        checkpoint_every=CAPS_CK, global_solver=1, factor_on_gpu=1))
+                self.ctx.set_params(kws)
+                self.ctx.autotune()
+                self.ctx.set_graphs(True)
+                self.x0 = torch.tensor(np.concatenate([base.x0] * CAPS_CLOTHS), device=dev)
+                self.v0 = torch.tensor(np.concatenate([base.v0] * CAPS_CLOTHS), device=dev)
+                self.xi = torch.tensor(np.concatenate([scenes.loss_weights(base.m, seed) for seed in range(CAPS_CLOTHS)]),
+                                       device=dev)
+                self.cloths = CAPS_CLOTHS
             else:
                 self.n_cloth = args.rollout_steps or SINGLE_STEPS
                 sc = scenes.draped_cloth()
@@ -349,7 +376,7 @@ class Workload:
 
         import paper_2106_05306_gb300 as dc
         with torch.cuda.stream(self.stream):
-            if self.kind == "batch":
+            if self.kind in ("batch", "capsules"):
                 self.ctx.rollout(self.x0, self.v0, self.n_cloth)
                 return self.ctx.backward(self.xi, allow_nonconverged=True)
             a = self.x0.detach().requires_grad_(True)
@@ -566,13 +593,13 @@ def kernel_model(cls, st, contacts_per_launch):
     return None, None, None
 
 
-def kernel_table(wl, peaks, steps_per_pass=1):
+def kernel_table(wl, peaks, steps_per_pass=1, classes=None):
     """One extra (untimed-for-value) bench step per kernel class with that class's
     CUDA-event timer on: time per bench step, launches, mean launch time, and for
     the classes with an algorithmic count, achieved GB/s and TFLOP/s against the
     measured HBM and FMA peaks."""
     rows = {}
-    for cls in KERNEL_CLASSES:
+    for cls in (classes or KERNEL_CLASSES):
         st0 = wl.ctx.stats()
         wl.ctx.set_kernel_timer(cls)
         for _ in range(steps_per_pass):
@@ -604,7 +631,7 @@ def kernel_table(wl, peaks, steps_per_pass=1):
     return rows
 
 
-def roofline(table, peaks):
+def roofline(table, peaks, workload="batch"):
     """Roofline object of the dominant kernel: the class with an algorithmic count
     that takes the most time per bench step."""
     counted = {k: r for k, r in table.items() if "achieved_tflops" in r}
@@ -621,7 +648,7 @@ def roofline(table, peaks):
             "hbm_frac": r["hbm_frac"], "traffic": None, "mean_launch_us": r["mean_launch_us"],
             "algorithmic_flops_per_launch": r["algorithmic_flops_per_launch"],
             "algorithmic_bytes_per_launch": r["algorithmic_bytes_per_launch"]}
-    tr = TRAFFIC.get(cls)
+    tr = TRAFFIC.get(cls) if workload == "batch" else None   # captured on the 256-cloth batch
     if tr and tr.get("source_sha") == kernel_sha(os.path.join(ROOT, "paper_2106_05306_gb300", "csrc",
                                                               tr["source"])):
         roof["traffic"] = tr["bytes_per_launch"]
@@ -696,24 +723,31 @@ def run_ours(args):
     max_ms = aggregate(total_ms, world)
     value = world * args.steps * wl.steps_per_bench_step / (max_ms / 1e3)
 
-    # end to end through the public API with pinned host buffers (copies inside the timed region)
-    x0h, v0h, xih = (t.cpu().pin_memory() for t in (wl.x0, wl.v0, wl.xi))
-    e2e_s = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        wl.step_host(x0h, v0h, xih)
-        e2e_s += time.perf_counter() - t0
-    e2e_max = aggregate(e2e_s * 1e3, world) / 1e3
     m = wl.ctx.m
-    e2e = {"value": world * args.steps * wl.steps_per_bench_step / e2e_max, "unit": UNIT,
-           "h2d_bytes_per_step": 3 * m * 3 * 8,
-           "d2h_bytes_per_step": 4 * m * 3 * 8 + 3 * 8 * wl.cloths}
+    if wl.kind == "capsules":
+        # half a minute per bench step: no end-to-end repeat, and the kernel table
+        # for the two largest counted classes only
+        e2e = {"value": None, "unit": UNIT, "note": "not measured for this workload (about half a minute a step)"}
+        classes = ("front", "sweeps")
+    else:
+        # end to end through the public API with pinned host buffers (copies inside the timed region)
+        x0h, v0h, xih = (t.cpu().pin_memory() for t in (wl.x0, wl.v0, wl.xi))
+        e2e_s = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            wl.step_host(x0h, v0h, xih)
+            e2e_s += time.perf_counter() - t0
+        e2e_max = aggregate(e2e_s * 1e3, world) / 1e3
+        e2e = {"value": world * args.steps * wl.steps_per_bench_step / e2e_max, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * m * 3 * 8,
+               "d2h_bytes_per_step": 4 * m * 3 * 8 + 3 * 8 * wl.cloths}
+        classes = None
 
     peaks = measured_peaks()
-    table = kernel_table(wl, peaks)
-    roof = roofline(table, peaks)
+    table = kernel_table(wl, peaks, classes=classes)
+    roof = roofline(table, peaks, wl.kind)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True,
@@ -743,7 +777,7 @@ def run_ours(args):
                                         rates=tuple(float(r) for r in (args.served_rates or "4,16,64").split(",")),
                                         max_batch=args.served_max_batch or 64)
         out["served_vs_plain"] = out["served"]["value"] / out["served"]["plain_sequential"]["value"]
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and not args.no_cpu_baseline and args.workload != "capsules":
         out["cpu_baseline"] = cpu_baseline_subprocess(args.workload)
         out["cpu_baseline_all_cores"] = cpu_baseline_subprocess(args.workload, all_cores=True)
     if rank == 0:
@@ -754,6 +788,14 @@ def run_ours(args):
 
 
 def workload_config(wl, world):
+    if wl.kind == "capsules":
+        return {"workload": CAPS_WORKLOAD if wl.n_cloth == CAPS_STEPS else
+                CAPS_WORKLOAD.replace("100 steps", f"{wl.n_cloth} steps"),
+                "cloths": wl.cloths, "nodes": int(wl.ctx.m), "cloth_steps_per_bench_step": wl.steps_per_bench_step,
+                "pd_iters": 20, "checkpoint_every": CAPS_CK, "global_solver": "supernodal substitution (1)",
+                "factor": "P factorised on the GPU", "graphs": "rollout replayed as a captured CUDA graph",
+                "parallelism": f"replicas x{world}", "l2": "flushed (512 MB write) before every timed step; inputs "
+                                                           "also larger than L2"}
     if wl.kind == "batch":
         sizes = [s.n for s in wl.scs]
         return {"workload": BATCH_WORKLOAD if wl.n_cloth == BATCH_STEPS else
