@@ -82,7 +82,7 @@ HBM_FALLBACK_GBS = 6800.0
 # (profiles/kernel_traffic_batched_256cloths.md), valid while the kernel's source
 # file is the one measured (its hash).
 TRAFFIC = {
-    "front": {"source": "dc_frontal.cu", "source_sha": "89a6c5a5ab4cb2f3", "bytes_per_launch": 945.14e6,
+    "front": {"source": "dc_frontal.cu", "source_sha": "d56e13ad7997eba6", "bytes_per_launch": 945.14e6,
               "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum, mean of the 9 levels of one "
                       "factorisation, 256 cloths (profiles/kernel_traffic_batched_256cloths.md)"},
     "sweeps": {"source": "dc_kernels.cu", "source_sha": "232ea24582784521", "bytes_per_launch": 747.46e6,

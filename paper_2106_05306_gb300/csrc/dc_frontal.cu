@@ -10,7 +10,9 @@
 // +-tau (the preconditioner stays usable, GMRES corrects).
 //
 // Fronts are dense column-major f x f blocks (DOF granularity, 3 per node) in
-// one pool; only their lower triangles are used.  One CTA handles one front.
+// one pool; only their lower triangles are used.  One CTA handles one front; on
+// levels of larger fronts the rank-32 trailing updates run on the tensor cores
+// (tcgen05, TF32 split in three passes, see tc_trailing_update).
 #include <mutex>
 
 #include "dc_adjoint.h"
