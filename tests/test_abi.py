@@ -106,3 +106,30 @@ def test_batch_hbm_bytes_runs_on_the_host(lib):
     for bad in ([(a.rest_pos, np.array([[0, 1, 10 ** 6]]), [])], [mesh(a), mesh(b)]):
         with pytest.raises(dc.DCError):
             dc.batch_hbm_bytes(bad, [dict(kw), dict(kw, h=2e-2)] if len(bad) == 2 else kw, 10)
+
+
+def test_every_mirrored_struct_matches_the_header_field_by_field(lib):
+    """Every struct the binding mirrors (parameters, obstacles, statistics, batch
+    instances, server configuration, requests, results, server statistics): its
+    size and the offset of each of its fields, from the C compiler against the
+    header, equal the ctypes mirror's."""
+    from paper_2106_05306_gb300 import _lib
+    structs = [_lib.dc_obstacle, _lib.dc_params, _lib.dc_stats, _lib.dc_instance, _lib.dc_server_config,
+               _lib.dc_request, _lib.dc_result, _lib.dc_server_stats]
+    lines, want = [], []
+    for S in structs:
+        name = S.__name__
+        lines.append(f'  printf("%zu\\n", sizeof({name}));')
+        want.append(ctypes.sizeof(S))
+        for field in S._fields_:
+            lines.append(f'  printf("%zu\\n", offsetof({name}, {field[0]}));')
+            want.append(getattr(S, field[0]).offset)
+    prog = "#include <stdio.h>\n#include <stddef.h>\n#include \"dc.h\"\nint main(void) {\n" + "\n".join(lines) + \
+        "\n  return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "off.c")
+        exe = os.path.join(d, "off")
+        open(c, "w").write(prog)
+        subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe])
+        got = [int(v) for v in subprocess.check_output([exe]).split()]
+    assert got == want
