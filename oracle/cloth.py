@@ -63,7 +63,9 @@ Readings of passages the paper leaves open (the CUDA path implements the same on
      compliance is the Gershgorin bound of the pairs' coupling,
      c_k = sum_l |h (e_i - e_j)^T P^-1 (e_p - e_q)| over the step's pairs
      l = (p, q) (pinned nodes contribute nothing), which keeps the Jacobi
-     iteration over pairs that share nodes from overshooting.  Within an
+     iteration over pairs that share nodes from overshooting; when obstacle
+     contacts are present as well, each side's bound also counts its coupling
+     with the other kind.  Within an
      iteration the pairs are solved from the global step's v_half, Jacobi-style
      beside the obstacle contacts; node i moves by w_i (r_new - r_old) and node
      j by -w_j (r_new - r_old), w_i and w_j proportional to h (P^-1_ii - P^-1_ij)
@@ -332,6 +334,31 @@ class Model:
             wi[a] = c[a] * ai / (ai + aj)
             wj[a] = c[a] * aj / (ai + aj)
         return wi, wj
+
+    def couple_compliances(self, contacts, c, pairs):
+        """With both obstacle contacts and self-contact pairs (R13), each side's
+        Gershgorin bound also counts its coupling with the other kind:
+        c_j += sum_k |h e_j^T P^-1 (e_p - e_q)| for an obstacle contact j and
+        c_k += sum_j |h (e_p - e_q)^T P^-1 e_j| for a pair k (whose write-back
+        weights are rescaled to the new c_k).  Returns the obstacle contacts' c."""
+        nf = len(self.free)
+        pos = -np.ones(self.m, dtype=np.int64)
+        pos[self.free] = np.arange(nf)
+        E = np.zeros((nf, len(contacts.nodes)))
+        E[pos[contacts.nodes], np.arange(len(contacts.nodes))] = 1.0
+        D = np.zeros((nf, len(pairs)))
+        for a, (i, j) in enumerate(zip(pairs.i, pairs.j)):
+            if pos[i] >= 0:
+                D[pos[i], a] = 1.0
+            if pos[j] >= 0:
+                D[pos[j], a] = -1.0
+        X = np.abs(self.h * (E.T @ self.solve_P(D)))   # |h e_j^T P^-1 (e_p - e_q)|
+        c_new = pairs.c + X.sum(axis=0)
+        scale = c_new / pairs.c
+        pairs.wi = pairs.wi * scale
+        pairs.wj = pairs.wj * scale
+        pairs.c = c_new
+        return c + X.sum(axis=1)
 
     def compliance(self, contacts):
         """c_j = h (P^-1 1_I)_j for the current contact set (R5), or the
@@ -723,6 +750,8 @@ def step(model: Model, x_n, v_n, n_iters=None, tol=None, max_iters=100000, trace
     cases = np.zeros(nc, dtype=np.int64)
     pairs = model.detect_self(x_n, v_n) if model.self_thickness > 0.0 else None   # R13
     npr = len(pairs) if pairs is not None else 0
+    if npr and nc:
+        c = model.couple_compliances(contacts, c, pairs)
     fp = np.zeros((npr, 3))
     pcases = np.zeros(npr, dtype=np.int64)
     v = v_n.copy()

@@ -332,12 +332,15 @@ def serve_request(seed: int, dof_lo: float = 1e3, dof_hi: float = 3e4, steps_lo:
 
 def two_patches_scene(n: int = 4, gap: float = 0.025, approach: float = 1.0, slide: float = 0.3,
                       thickness: float = 0.02, mu: float = 0.3, gravity: bool = False, seed: int = 0,
-                      n_steps: int = 3, pinned: bool = False) -> Scene:
+                      n_steps: int = 3, pinned: bool = False, ground: bool = False) -> Scene:
     """Node-node self-collision: two n x n patches (side 0.3 m) in one mesh, the
     upper `gap` above the lower and shifted sideways by a fifth of the thickness, moving
     down at `approach` m/s and sideways at `slide` m/s with small seeded noise; no
     obstacle and, by default, no gravity (so that momentum is conserved).  With
-    `pinned`, the lower patch's four corners are pinned at their rest positions."""
+    `pinned`, the lower patch's four corners are pinned at their rest positions.
+    With `ground`, gravity is on and the lower patch falls at 0.1 m/s from half a
+    millimetre above a ground plane, so that nodes meet the ground and the other
+    patch at once."""
     rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5E1F]))
     lo, tris = grid_mesh(n, side=0.3, height=0.0, x0=-0.15, z0=0.0)
     hi = lo.copy()
@@ -351,6 +354,12 @@ def two_patches_scene(n: int = 4, gap: float = 0.025, approach: float = 1.0, sli
     v0[n * n:, 0] = slide
     v0 += 0.02 * rng.standard_normal((m, 3))
     x0 = pos + 0.002 * rng.standard_normal((m, 3))
+    obst: List[Obstacle] = []
+    if ground:
+        gravity = True
+        x0[:, 1] += 0.0005
+        v0[:n * n, 1] = -0.1
+        obst = [Obstacle("plane", normal=(0.0, 1.0, 0.0), offset=0.0)]
     pins = np.zeros(0, np.int32)
     if pinned:
         pins = np.array([0, n - 1, n * n - n, n * n - 1], dtype=np.int32)
@@ -358,4 +367,4 @@ def two_patches_scene(n: int = 4, gap: float = 0.025, approach: float = 1.0, sli
         v0[pins] = 0.0
     prm = Params(k_stretch=200.0, k_bend=1e-3, density=0.1, mu=mu, h=1.0 / 120.0,
                  gravity=GRAVITY if gravity else (0.0, 0.0, 0.0), self_thickness=thickness)
-    return Scene(f"two_patches_{n}_{seed}", n, pos, tris, pins, [], prm, x0, v0, n_steps, loss_weights(m, seed))
+    return Scene(f"two_patches_{n}_{seed}", n, pos, tris, pins, obst, prm, x0, v0, n_steps, loss_weights(m, seed))

@@ -685,7 +685,7 @@ def test_continuity_study_analytic_vs_triangulated_sphere():
 # ----------------------------------------------------------------- self-collision (R13)
 
 def _pairs_sig(recs):
-    return [(tuple(r.pairs.i), tuple(r.pairs.j), tuple(r.pair_cases)) for r in recs]
+    return [(tuple(r.pairs.i), tuple(r.pairs.j), tuple(r.pair_cases)) for r in recs] + _sig(recs)
 
 
 @pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0), dict(approach=3.0)])
@@ -724,7 +724,7 @@ def test_self_contact_without_pairs_is_the_plain_step():
     assert all(np.array_equal(a, b) for a, b in zip(xa, xb)) and all(np.array_equal(a, b) for a, b in zip(va, vb))
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0), dict(pinned=True, gravity=True)])
+@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0), dict(pinned=True, gravity=True), dict(ground=True)])
 def test_self_contact_adjoint_matches_central_differences(kw):
     """The KKT adjoint with pair rows (slip pairs; a mix of stick and slip pairs)
     agrees with central differences of the converged forward map for x0, v0,
@@ -732,7 +732,8 @@ def test_self_contact_adjoint_matches_central_differences(kw):
     +-eps (the derivatives of the pair normal and bias with respect to both
     nodes, and the friction term on the relative velocity, are all exercised);
     also with gravity and pinned nodes among the pairs (a pinned node has no
-    row in the adjoint system)."""
+    row in the adjoint system), and with nodes in contact with the ground and
+    with the other patch at once (the two kinds of rows in one KKT system)."""
     sc = scenes.two_patches_scene(n_steps=2, **kw)
     M, xs, vs, recs = _run(sc)
     base = _pairs_sig(recs)
