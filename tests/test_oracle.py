@@ -724,7 +724,8 @@ def test_self_contact_without_pairs_is_the_plain_step():
     assert all(np.array_equal(a, b) for a, b in zip(xa, xb)) and all(np.array_equal(a, b) for a, b in zip(va, vb))
 
 
-@pytest.mark.parametrize("kw", [dict(), dict(slide=0.0, mu=2.0), dict(pinned=True, gravity=True), dict(ground=True)])
+@pytest.mark.parametrize("kw", [dict(n_steps=2), dict(slide=0.0, mu=2.0, n_steps=2),
+                                dict(pinned=True, gravity=True, n_steps=1), dict(ground=True, n_steps=1)])
 def test_self_contact_adjoint_matches_central_differences(kw):
     """The KKT adjoint with pair rows (slip pairs; a mix of stick and slip pairs)
     agrees with central differences of the converged forward map for x0, v0,
@@ -734,7 +735,7 @@ def test_self_contact_adjoint_matches_central_differences(kw):
     also with gravity and pinned nodes among the pairs (a pinned node has no
     row in the adjoint system), and with nodes in contact with the ground and
     with the other patch at once (the two kinds of rows in one KKT system)."""
-    sc = scenes.two_patches_scene(n_steps=2, **kw)
+    sc = scenes.two_patches_scene(**kw)
     M, xs, vs, recs = _run(sc)
     base = _pairs_sig(recs)
     assert any(np.any(r.pair_cases == oc.SLIP) for r in recs)
