@@ -297,7 +297,8 @@ class Model:
             i, j = (a, b) if a < b else (b, a)
             if (i, j) in self._adjacent or (self.is_pin[i] and self.is_pin[j]):
                 continue
-            if np.linalg.norm(xp[i] - xp[j]) <= d_s + self.delta:
+            # (nodes that coincide at x_n have no pair normal and are left out)
+            if np.linalg.norm(xp[i] - xp[j]) <= d_s + self.delta and np.linalg.norm(x_n[i] - x_n[j]) > 0.0:
                 ii.append(i)
                 jj.append(j)
         ii = np.array(ii, dtype=np.int64)
