@@ -167,9 +167,11 @@ void prep_loop(dc_server* s) {
         std::vector<Request*> group;
         {
             std::unique_lock<std::mutex> lk(s->mu);
+            // while stopping, a thread leaves only once nothing is queued and no
+            // job runs (a failed batch puts its requests back in the queue)
             s->cv.wait(lk, [&] {
-                return s->stop ||
-                       (!s->to_prep.empty() && (int)s->ready.size() + s->preparing < s->cfg.max_prepared);
+                const bool can = !s->to_prep.empty() && (int)s->ready.size() + s->preparing < s->cfg.max_prepared;
+                return can || (s->stop && s->to_prep.empty() && s->in_flight == 0);
             });
             if (s->to_prep.empty()) return;   // stop with nothing left
             group = take_group(s);
@@ -293,7 +295,7 @@ void slot_loop(dc_server* s, int slot) {
                     Job* h = s->ready.begin()->second;
                     if (s->reserved + h->bytes <= (size_t)s->cfg.hbm_budget_bytes) return true;
                 }
-                return s->stop && s->ready.empty() && s->to_prep.empty() && s->preparing == 0;
+                return s->stop && s->ready.empty() && s->to_prep.empty() && s->preparing == 0 && s->in_flight == 0;
             });
             if (s->ready.empty()) return;
             j = s->ready.begin()->second;
