@@ -766,3 +766,30 @@ def test_self_contact_adjoint_matches_central_differences(kw):
         fd = (loss_at(**{which: b + e * d}) - loss_at(**{which: b - e * d})) / (2 * e)
         adj = np.sum((gx0 if which == "x0" else gv0) * d)
         assert abs(adj - fd) <= 1e-6 * abs(fd), (which, adj, fd)
+
+
+def test_self_contact_detection_rules():
+    """R13's detection on the two patches with a thickness above the
+    node spacing: every returned pair has i < j, at least one free node, nodes
+    that share no triangle, predicted distance within thickness + delta, a unit
+    normal from j to i and the bias (|x_i - x_j| - thickness)/h; and no pair of
+    triangle neighbours is returned although all of them are within range."""
+    sc = scenes.two_patches_scene(thickness=0.15, gap=0.3, approach=0.0, slide=0.0, pinned=True)
+    M = oc.model_from_scene(sc)
+    pr = M.detect_self(sc.x0, sc.v0)
+    assert len(pr) > 0
+    adjacent = {(min(a, b), max(a, b)) for t in sc.tris for a in t for b in t if a != b}
+    xp = sc.x0 + M.h * sc.v0
+    for a in range(len(pr)):
+        i, j = int(pr.i[a]), int(pr.j[a])
+        assert i < j and (i, j) not in adjacent and not (M.is_pin[i] and M.is_pin[j])
+        assert np.linalg.norm(xp[i] - xp[j]) <= 0.15 + M.delta
+        d = sc.x0[i] - sc.x0[j]
+        np.testing.assert_allclose(pr.normals[a], d / np.linalg.norm(d), rtol=0, atol=1e-15)
+        assert abs(pr.betas[a] - (np.linalg.norm(d) - 0.15) / M.h) <= 1e-12
+    # every non-adjacent pair within range is found
+    want = {(i, j) for i in range(sc.m) for j in range(i + 1, sc.m)
+            if (i, j) not in adjacent and not (M.is_pin[i] and M.is_pin[j])
+            and np.linalg.norm(xp[i] - xp[j]) <= 0.15 + M.delta}
+    assert want == set(zip(pr.i.tolist(), pr.j.tolist()))
+    assert any(np.linalg.norm(xp[i] - xp[j]) <= 0.15 for i, j in adjacent)
